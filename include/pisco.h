@@ -1,0 +1,156 @@
+/*
+ * pisco.h -- C ABI of a GB300 (sm_103a) implementation of the nullspace / ESPIRiT-equivalent
+ * coil-sensitivity estimator with the PISCO accelerations (Lobos, Chan & Haldar,
+ * arXiv 2302.13431).
+ *
+ * One call to pisco_estimate runs, on one GPU and on the plan's CUDA stream:
+ *   (a) the Gram C^H C of the calibration matrix C (Eq. C) by zero-padded DFTs without
+ *       forming C (Sec. V-A; the masking is neglected, so the Gram is C_full^H C_full);
+ *   (b) its approximate nullspace, thresholded at sigma_n < thr * sigma_1 (footnote of
+ *       Sec. III-B), with the split decided on FP64 Rayleigh quotients;
+ *   (c) G(x) = H(x)^H H(x) on the reduced grid straight from the collapsed filter kernel
+ *       (Sec. V-C, Eq. 24), never forming H(x);
+ *   (d) simultaneous power iteration for the eigenvector of G(x) with the smallest
+ *       eigenvalue, on B(x) = I - G(x)/|Lambda| (Sec. V-E, Eq. esp_null);
+ *   (e) the smooth phase alpha(x) from an apodised low-resolution coil combination, periodic-
+ *       sinc interpolation to the full grid (Sec. V-D) and per-pixel unit-norm output.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are C-ordered with x fastest.  Multichannel arrays put the coil index first:
+ *     calibration data is complex64 [Q][Nc_z][Nc_y][Nc_x] with its DC sample at index
+ *     floor(Nc/2) on every axis; maps are complex64 [Q][N_z][N_y][N_x].  complex64 means two
+ *     consecutive IEEE floats (re, im).  In 2D N_z = Nc_z = 1.
+ *   - Image-grid point j of an axis of length N sits at x_j = (j - N/2)/N (the FOV is the
+ *     unit cube, Sec. III-A).  The reduced grid has N/f points per axis and its points
+ *     coincide with every f-th full-grid point.
+ *   - Functions never print, never abort and never throw; they return a pisco_status.
+ *   - Device pointers are owned by the caller.  The plan owns its own workspace, which it
+ *     allocates in pisco_plan; pisco_estimate allocates nothing.
+ */
+#ifndef PISCO_H_
+#define PISCO_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PISCO_OK = 0,
+  PISCO_ERR_ARG = 1,            /* invalid parameter or pointer; nothing was launched        */
+  PISCO_ERR_CUDA = 2,           /* a CUDA runtime call failed (launch, copy, sync)            */
+  PISCO_ERR_OOM = 3,            /* workspace allocation failed in pisco_plan                  */
+  PISCO_ERR_RANK = 4,           /* R < Q-1: the necessary condition of Sec. III-B fails.  The
+                                   outputs are still written (they are not identifiable).    */
+  PISCO_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired                         */
+  PISCO_ERR_NOT_CONVERGED = 6,  /* block eigensolver saturated even at the largest block     */
+  PISCO_ERR_UNSUPPORTED = 7     /* valid request outside what this build implements          */
+} pisco_status;
+
+typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_shape;
+
+/* flags */
+#define PISCO_FLAG_HOST_IO 0x1u  /* allocate pinned/device staging for pisco_estimate_host   */
+
+typedef struct {
+  int ndim;               /* 2 or 3                                                          */
+  int grid[3];            /* full image grid N_x, N_y, N_z (N_z = 1 in 2D)                    */
+  int calib[3];           /* calibration box Nc_x, Nc_y, Nc_z (Nc_z = 1 in 2D), centred       */
+  int num_coils;          /* Q, 2 <= Q <= 64                                                  */
+  int kernel_shape;       /* PISCO_KERNEL_RECT: ||n||_inf <= tau;  PISCO_KERNEL_ELLIPSOID:
+                             sum_d (n_d/tau_d)^2 <= 1 (equal radii: ||n||_2 <= tau, Sec. V-B) */
+  int kernel_radius[3];   /* tau_x, tau_y, tau_z (tau_z = 0 in 2D)                            */
+  double null_threshold;  /* thr in (0,1): sigma_n < thr*sigma_1 is null (paper: 0.05)        */
+  int grid_reduction;     /* f >= 1; every grid[d] must be divisible by f                     */
+  int power_iters;        /* number of power iterations, >= 1 (paper: 10)                     */
+  unsigned long long seed;/* start vector: v0[j][q] = u(2q) + i u(2q+1), u(t) from
+                             SplitMix64(seed*2^40 + j*2^8 + t), a 24-bit uniform in [-1,1)   */
+  unsigned flags;         /* PISCO_FLAG_*                                                     */
+  int eig_block;          /* block size of the nullspace eigensolver (0: automatic)           */
+  int eig_iters;          /* subspace iterations of the eigensolver (0: automatic)            */
+} pisco_params;
+
+typedef struct pisco_plan_s* pisco_plan_t;
+
+/* Validate `p`, build the index tables, allocate the device workspace and bind the plan to
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  Rejected with
+ * PISCO_ERR_ARG: ndim not 2/3, Q outside [2,64], Nc <= 2*tau on some axis, Nc > N, N not
+ * divisible by f, N/f < 2*tau+1, thr outside (0,1), power_iters < 1.  On success *out owns
+ * the workspace until pisco_destroy. */
+pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* out);
+
+/* Run the whole path on the plan's stream.
+ *   d_calib: device, complex64 [Q][Nc_z][Nc_y][Nc_x], read only.
+ *   d_maps:  device, complex64 [Q][N_z][N_y][N_x], written: unit 2-norm per pixel (all zero
+ *            where the interpolated vector vanishes), phase fixed by alpha(x) of Sec. V-D.
+ *   d_eig:   device, float [N_z/f][N_y/f][N_x/f] or NULL: lambda_min(G(x))/|Lambda| in [0,1]
+ *            on the reduced grid (Rayleigh quotient after the last power iteration).
+ * Synchronises the stream once at the end to read the device status word.  Pointers must
+ * be 8-byte aligned.  Not thread-safe for one plan; distinct plans may run concurrently. */
+pisco_status pisco_estimate(pisco_plan_t plan, const void* d_calib, void* d_maps, float* d_eig);
+
+/* Same as pisco_estimate with HOST buffers of the same layouts: copies the calibration block
+ * to the device, runs the path, copies maps (and eig if non-NULL) back, all on the plan's
+ * stream.  Needs PISCO_FLAG_HOST_IO at plan time (PISCO_ERR_ARG otherwise).  Host buffers
+ * may be pageable; pinned buffers give overlap-free full-bandwidth copies. */
+pisco_status pisco_estimate_host(pisco_plan_t plan, const void* h_calib, void* h_maps, float* h_eig);
+
+/* Free the plan and its workspace.  NULL-safe. */
+void pisco_destroy(pisco_plan_t plan);
+
+/* Static English description of a status code. */
+const char* pisco_status_string(pisco_status s);
+
+/* Sizes chosen by the plan and results of the last estimate: R (nullspace dimension) and
+ * k (signal dimension, R + k = Q|Lambda|) are valid after a successful estimate (-1 before),
+ * workspace_bytes is the device memory the plan holds.  Any output pointer may be NULL. */
+pisco_status pisco_plan_info(pisco_plan_t plan, int* R, int* k, size_t* workspace_bytes);
+
+/* Intermediate results of the last estimate, for stage-by-stage verification.  Returns a
+ * device pointer into the plan's workspace (valid until the next call on the plan) and its
+ * size in bytes.  Layouts:
+ *   PISCO_BUF_LAGS   complex128 [Q][Q][B_z][B_y][B_x], the correlation
+ *                    R_pq[d] = sum_k conj(s_p[k]) s_q[k+d] on the box |d| <= 2 tau (Sec. V-A);
+ *                    only p <= q is written.  B = 4 tau + 1.
+ *   PISCO_BUF_GRAM   complex128 [Q|Lambda|][Q|Lambda|] C^H C, index q*|Lambda| + i.
+ *   PISCO_BUF_SIGNAL complex64 [Q|Lambda|][m] signal-subspace basis (column j is used when
+ *                    PISCO_BUF_WEIGHTS[j] = 1), Lambda in lexicographic order, x fastest.
+ *   PISCO_BUF_WEIGHTS float [m] 1 for signal columns, 0 otherwise.
+ *   PISCO_BUF_RITZ   double [m] Ritz values of C^H C (FP64 Rayleigh quotients where decided).
+ *   PISCO_BUF_G      complex64 [Q][Q][Nr], G_pq(x) on the reduced grid (Nr pixels).
+ *   PISCO_BUF_V      complex64 [Q][Nr] phase-aligned power-iteration vectors.
+ *   PISCO_BUF_Y      complex64 [Q][Nr] apodised low-resolution coil images (Sec. V-D). */
+enum {
+  PISCO_BUF_LAGS = 0, PISCO_BUF_GRAM = 1, PISCO_BUF_SIGNAL = 2, PISCO_BUF_WEIGHTS = 3,
+  PISCO_BUF_RITZ = 4, PISCO_BUF_G = 5, PISCO_BUF_V = 6, PISCO_BUF_Y = 7
+};
+pisco_status pisco_debug_buffer(pisco_plan_t plan, int which, void** dptr, size_t* bytes);
+
+/* Counters of the last estimate. */
+typedef struct {
+  int launches;       /* CUDA kernels enqueued by the last pisco_estimate (all retries)   */
+  int eig_block;      /* block size m of the nullspace eigensolver actually used          */
+  int eig_iters;      /* subspace iterations per solve                                   */
+  int jacobi_sweeps;  /* sweeps of the last small Rayleigh-Ritz eigensolve                */
+  int nband;          /* Ritz values decided on FP64 Rayleigh quotients                   */
+  double lambda_max;  /* largest eigenvalue of C^H C (sigma_1^2), FP64                     */
+  int signal_dim;     /* k = Q|Lambda| - R                                                 */
+  int filter_len;     /* |Lambda|                                                          */
+} pisco_stats;
+pisco_status pisco_get_stats(pisco_plan_t plan, pisco_stats* out);
+
+/* Operation timing with CUDA events on the plan's stream.  When enabled, every operation of
+ * pisco_estimate (a kernel, or a GEMM with its split-K reduction) is bracketed by two events
+ * and, after the estimate's final synchronisation, its elapsed time is added to a per-name
+ * total.  pisco_profile_entry enumerates the totals (idx = 0, 1, ... until PISCO_ERR_ARG);
+ * `name` points to a static string.  Timing adds two event records per operation. */
+pisco_status pisco_set_profiling(pisco_plan_t plan, int enable);
+pisco_status pisco_profile_reset(pisco_plan_t plan);
+pisco_status pisco_profile_entry(pisco_plan_t plan, int idx, const char** name, double* total_ms,
+                                 int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PISCO_H_ */

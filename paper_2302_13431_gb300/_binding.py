@@ -1,0 +1,184 @@
+"""ctypes binding of the C ABI declared in include/pisco.h (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts Python/torch arguments
+to the plain pointers and sizes the ABI takes.  Importing it loads `_lib/libpisco.so` and
+raises if the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpisco.so")
+
+PISCO_OK, PISCO_ERR_ARG, PISCO_ERR_CUDA, PISCO_ERR_OOM, PISCO_ERR_RANK, PISCO_ERR_TIMEOUT, \
+    PISCO_ERR_NOT_CONVERGED, PISCO_ERR_UNSUPPORTED = range(8)
+PISCO_KERNEL_RECT, PISCO_KERNEL_ELLIPSOID = 0, 1
+PISCO_FLAG_HOST_IO = 0x1
+(PISCO_BUF_LAGS, PISCO_BUF_GRAM, PISCO_BUF_SIGNAL, PISCO_BUF_WEIGHTS, PISCO_BUF_RITZ, PISCO_BUF_G,
+ PISCO_BUF_V, PISCO_BUF_Y) = range(8)
+
+
+class pisco_params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("grid", ctypes.c_int * 3),
+        ("calib", ctypes.c_int * 3),
+        ("num_coils", ctypes.c_int),
+        ("kernel_shape", ctypes.c_int),
+        ("kernel_radius", ctypes.c_int * 3),
+        ("null_threshold", ctypes.c_double),
+        ("grid_reduction", ctypes.c_int),
+        ("power_iters", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+        ("flags", ctypes.c_uint),
+        ("eig_block", ctypes.c_int),
+        ("eig_iters", ctypes.c_int),
+    ]
+
+
+class pisco_stats(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int),
+        ("eig_block", ctypes.c_int),
+        ("eig_iters", ctypes.c_int),
+        ("jacobi_sweeps", ctypes.c_int),
+        ("nband", ctypes.c_int),
+        ("lambda_max", ctypes.c_double),
+        ("signal_dim", ctypes.c_int),
+        ("filter_len", ctypes.c_int),
+    ]
+
+
+class PiscoError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {pisco_status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def load():
+    """Load libpisco.so (built by build_ext.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"PISCO CUDA library not found at {LIB_PATH}; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.pisco_plan.argtypes = [P(pisco_params), vp, P(vp)]
+    lib.pisco_plan.restype = ctypes.c_int
+    lib.pisco_estimate.argtypes = [vp, vp, vp, vp]
+    lib.pisco_estimate.restype = ctypes.c_int
+    lib.pisco_estimate_host.argtypes = [vp, vp, vp, vp]
+    lib.pisco_estimate_host.restype = ctypes.c_int
+    lib.pisco_destroy.argtypes = [vp]
+    lib.pisco_destroy.restype = None
+    lib.pisco_status_string.argtypes = [ctypes.c_int]
+    lib.pisco_status_string.restype = ctypes.c_char_p
+    lib.pisco_plan_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
+    lib.pisco_plan_info.restype = ctypes.c_int
+    lib.pisco_debug_buffer.argtypes = [vp, ctypes.c_int, P(vp), P(ctypes.c_size_t)]
+    lib.pisco_debug_buffer.restype = ctypes.c_int
+    lib.pisco_get_stats.argtypes = [vp, P(pisco_stats)]
+    lib.pisco_get_stats.restype = ctypes.c_int
+    lib.pisco_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.pisco_set_profiling.restype = ctypes.c_int
+    lib.pisco_profile_reset.argtypes = [vp]
+    lib.pisco_profile_reset.restype = ctypes.c_int
+    lib.pisco_profile_entry.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), P(ctypes.c_double),
+                                        P(ctypes.c_int)]
+    lib.pisco_profile_entry.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def pisco_status_string(status: int) -> str:
+    return load().pisco_status_string(int(status)).decode()
+
+
+def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid", null_threshold=0.05,
+                grid_reduction=1, power_iters=30, seed=0, flags=0, eig_block=0, eig_iters=0):
+    """pisco_params from (z,)y,x-ordered Python tuples (the array order); the struct is x,y,z."""
+    nd = len(grid)
+    pr = pisco_params()
+    pr.ndim = nd
+    g = list(grid)[::-1] + [1] * (3 - nd)
+    c = list(calib)[::-1] + [1] * (3 - nd)
+    tau = list(kernel_radius if not isinstance(kernel_radius, int) else [kernel_radius] * nd)[::-1] + [0] * (3 - nd)
+    for d in range(3):
+        pr.grid[d], pr.calib[d], pr.kernel_radius[d] = g[d], c[d], tau[d]
+    pr.num_coils = num_coils
+    pr.kernel_shape = {"rect": PISCO_KERNEL_RECT, "ellipsoid": PISCO_KERNEL_ELLIPSOID}[kernel_shape]
+    pr.null_threshold = null_threshold
+    pr.grid_reduction = grid_reduction
+    pr.power_iters = power_iters
+    pr.seed = seed
+    pr.flags = flags
+    pr.eig_block = eig_block
+    pr.eig_iters = eig_iters
+    return pr
+
+
+def pisco_plan(params: pisco_params, stream: int = 0):
+    """Returns (status, plan handle)."""
+    h = ctypes.c_void_p()
+    st = load().pisco_plan(ctypes.byref(params), ctypes.c_void_p(stream), ctypes.byref(h))
+    return st, h
+
+
+def pisco_estimate(plan, d_calib: int, d_maps: int, d_eig: int | None):
+    return load().pisco_estimate(plan, ctypes.c_void_p(d_calib), ctypes.c_void_p(d_maps),
+                                 ctypes.c_void_p(d_eig or 0))
+
+
+def pisco_estimate_host(plan, h_calib: int, h_maps: int, h_eig: int | None):
+    return load().pisco_estimate_host(plan, ctypes.c_void_p(h_calib), ctypes.c_void_p(h_maps),
+                                      ctypes.c_void_p(h_eig or 0))
+
+
+def pisco_destroy(plan):
+    load().pisco_destroy(plan)
+
+
+def pisco_plan_info(plan):
+    R, k, ws = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    st = load().pisco_plan_info(plan, ctypes.byref(R), ctypes.byref(k), ctypes.byref(ws))
+    return st, R.value, k.value, ws.value
+
+
+def pisco_debug_buffer(plan, which: int):
+    p, nb = ctypes.c_void_p(), ctypes.c_size_t()
+    st = load().pisco_debug_buffer(plan, int(which), ctypes.byref(p), ctypes.byref(nb))
+    return st, p.value, nb.value
+
+
+def pisco_get_stats(plan):
+    st = pisco_stats()
+    rc = load().pisco_get_stats(plan, ctypes.byref(st))
+    return rc, {f: getattr(st, f) for f, _ in pisco_stats._fields_}
+
+
+def pisco_set_profiling(plan, enable: bool):
+    return load().pisco_set_profiling(plan, 1 if enable else 0)
+
+
+def pisco_profile_reset(plan):
+    return load().pisco_profile_reset(plan)
+
+
+def pisco_profile(plan):
+    """{name: (total_ms, count)} accumulated since profiling was enabled or reset."""
+    out = {}
+    i = 0
+    name, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int()
+    while load().pisco_profile_entry(plan, i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt)) == PISCO_OK:
+        out[name.value.decode()] = (ms.value, cnt.value)
+        i += 1
+    return out

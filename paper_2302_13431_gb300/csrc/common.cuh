@@ -1,0 +1,133 @@
+// Shared device helpers and internal launcher declarations of the PISCO GB300 path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pisco.h"
+
+namespace pisco {
+
+// kernels enqueued by the calling thread (read by the host orchestration per estimate)
+inline thread_local int g_launches = 0;
+
+// ---------------------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cpx = typename cplx<T>::type;
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float2 to_c(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_z(float2 a) { return make_double2(a.x, a.y); }
+
+// ---------------------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): one output for a 64-bit counter.
+// ---------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// 24-bit uniform in [-1, 1) for counter (seed, index, t); exact in FP32.
+__host__ __device__ __forceinline__ float counter_uniform(uint64_t seed, uint64_t index, uint64_t t) {
+  uint64_t r = splitmix64((seed << 40) + (index << 8) + t) >> 40;
+  return (float)((int64_t)r - (1ll << 23)) * (1.0f / 8388608.0f);
+}
+
+// ---------------------------------------------------------------------------------------
+// device status word (written by kernels, read once per estimate)
+// ---------------------------------------------------------------------------------------
+enum : int {
+  ST_RANK = 1,          // R < Q-1
+  ST_SATURATED = 2,     // signal dimension reached the eigensolver block
+  ST_CHOL = 4,          // non-positive pivot clamped in a Cholesky factorisation
+  ST_ZERO = 8,          // calibration data identically zero
+};
+struct DevStatus {
+  int flags;
+  int k;                // signal dimension decided by the eigensolver
+  int nband;            // Ritz values refined in FP64
+  int jacobi_sweeps;    // sweeps used by the last small eigensolve
+  double lambda_max;    // largest eigenvalue of C^H C (FP64 Rayleigh quotient)
+};
+
+// ---------------------------------------------------------------------------------------
+// launchers (all asynchronous on `st`; return cudaGetLastError())
+// ---------------------------------------------------------------------------------------
+// Generic "apply a matrix along one axis": out[b][a2][o][a0] = sum_i M[o][i] in[b][a2][i][a0]
+// for a 5-level view (batch, outer, axis, inner); element types given by the template.
+struct AxisView {
+  long long batch;   // number of independent batches
+  long long outer;   // product of the axis lengths before the transformed axis
+  int n_in;          // transformed axis length on input
+  int n_out;         // transformed axis length on output
+  long long inner;   // product of the axis lengths after the transformed axis
+};
+cudaError_t apply_axis_c2z(const float2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
+cudaError_t apply_axis_z(const double2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
+cudaError_t apply_axis_c(const float2* in, const float2* M, float2* out, AxisView v, cudaStream_t st);
+
+// a1: pair products and Gram expansion
+cudaError_t gram_pair_products(const double2* S, int Q, long long nfreq, double2* P, cudaStream_t st);
+cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* lags, cudaStream_t st);
+cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L, int nbox,
+                        double2* A, float2* A32, cudaStream_t st);
+
+// dense complex GEMM: C = alpha*op(A)*op(B) + beta*C, row-major, op in {'N','C'}
+template <typename T>
+cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
+                  const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* splitk_ws,
+                  size_t ws_elems, cudaStream_t st);
+
+// a2: block eigensolver pieces
+cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, cudaStream_t st);
+cudaError_t eig_chol(const float2* Gm, int m, float2* L, DevStatus* status, cudaStream_t st);
+cudaError_t eig_trsm_rows(const float2* Y, const float2* L, int n, int m, float2* X, cudaStream_t st);
+cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
+                       DevStatus* status, cudaStream_t st);
+cudaError_t eig_scale_cols(float2* Y, int n, int m, const float* mu, float floor_rel, cudaStream_t st);
+cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
+                            cudaStream_t st);
+cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, int nb_max,
+                            double2* Xb, cudaStream_t st);
+cudaError_t eig_decide(const float* mu, int m, const int* band_idx, int nb_max, const double2* Xb,
+                       const double2* Zb, int n, double thr2, int Q, float* weights, double* ritz,
+                       DevStatus* status, cudaStream_t st);
+
+// a3: collapsed kernel and G field
+cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int m,
+                             const int* lag_ptr, const int* lag_ent, int nbox, float2* K,
+                             cudaStream_t st);
+cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_size, cudaStream_t st);
+
+// a4+a5: power iteration with the phase step
+cudaError_t power_iteration(const float2* G, const float2* Y, int Q, long long npix, int iters,
+                            float lam_size, unsigned long long seed, float2* V, float* eig,
+                            cudaStream_t st);
+
+// a6: final interpolation pass along the slowest axis fused with unit-norm normalisation
+cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long long outer_dummy,
+                                   int n_in, int n_out, long long inner, float2* maps,
+                                   cudaStream_t st);
+
+}  // namespace pisco

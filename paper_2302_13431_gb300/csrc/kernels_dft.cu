@@ -1,0 +1,55 @@
+// Separable small DFTs as "apply a dense matrix along one axis", in FP64 (Gram, Sec. V-A)
+// and FP32 (G(x) on the reduced grid, Sec. V-C; apodised low-res images and periodic-sinc
+// interpolation, Sec. V-D).  The transforms here are short (tens of points) and not powers
+// of two, so each axis is a small dense matrix product; every output element is one thread,
+// with the inner (fastest) index mapped to consecutive threads so loads are coalesced and
+// the matrix row is a warp-wide broadcast.
+#include "common.cuh"
+
+namespace pisco {
+
+template <typename Tin, typename C>
+__global__ void __launch_bounds__(256) apply_axis_kernel(const Tin* __restrict__ in,
+                                                         const C* __restrict__ M,
+                                                         C* __restrict__ out, AxisView v) {
+  const long long total = v.batch * v.outer * (long long)v.n_out * v.inner;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long t = idx;
+    const long long ii = t % v.inner; t /= v.inner;
+    const int o = (int)(t % v.n_out); t /= v.n_out;
+    const long long bo = t;  // batch*outer flattened
+    const Tin* src = in + (bo * v.n_in) * v.inner + ii;
+    const C* row = M + (long long)o * v.n_in;
+    C acc = mk(decltype(acc.x)(0), decltype(acc.x)(0));
+    for (int i = 0; i < v.n_in; ++i) {
+      const Tin s = src[(long long)i * v.inner];
+      C sv = mk(decltype(acc.x)(s.x), decltype(acc.x)(s.y));
+      cfma(acc, row[i], sv);
+    }
+    out[(bo * v.n_out + o) * v.inner + ii] = acc;
+  }
+}
+
+template <typename Tin, typename C>
+static cudaError_t launch_apply(const Tin* in, const C* M, C* out, AxisView v, cudaStream_t st) {
+  const long long total = v.batch * v.outer * (long long)v.n_out * v.inner;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  apply_axis_kernel<Tin, C><<<(unsigned)blocks, 256, 0, st>>>(in, M, out, v);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t apply_axis_c2z(const float2* in, const double2* M, double2* out, AxisView v, cudaStream_t st) {
+  return launch_apply<float2, double2>(in, M, out, v, st);
+}
+cudaError_t apply_axis_z(const double2* in, const double2* M, double2* out, AxisView v, cudaStream_t st) {
+  return launch_apply<double2, double2>(in, M, out, v, st);
+}
+cudaError_t apply_axis_c(const float2* in, const float2* M, float2* out, AxisView v, cudaStream_t st) {
+  return launch_apply<float2, float2>(in, M, out, v, st);
+}
+
+}  // namespace pisco

@@ -1,0 +1,107 @@
+// Stage (c): G(x) on the reduced grid without forming H(x) (Sec. V-C).
+//
+// With the nullspace projector W = sum_r h_r h_r^H = I - U U^H (U: orthonormal signal
+// basis), Eq. 24 collapses to a per-pair lag kernel
+//     G_pq(x) = |Lambda| delta_pq - sum_{d in Lambda-Lambda} K_pq[d] exp(+i 2 pi d^T x),
+//     K_pq[d] = sum_{b - a = d} sum_j w_j U[(q,b),j] conj(U[(p,a),j]),
+// i.e. the ESPIRiT form B(x) = I - G(x)/|Lambda| = H_s(x)^H H_s(x)/|Lambda| (Eq. esp_null).
+// This file builds K (the dense complex contraction U_q diag(w) U_p^H folded onto lags); the
+// host then evaluates the lag sums on the reduced grid with separable DFT passes.
+#include "common.cuh"
+
+namespace pisco {
+
+namespace {
+constexpr int JC = 32;  // signal columns staged per pass
+}
+
+// One CTA per (p,q).  U is [n][m] row-major (row = q*L + b).  K is [Q][Q][nbox].
+// P[b][a] = sum_j w_j Uq[b][j] conj(Up[a][j]) is accumulated in shared memory over column
+// chunks, then every lag sums its (b,a) entries in a fixed order (CSR lists lag_ptr/lag_ent),
+// so the result is bitwise reproducible.
+__global__ void __launch_bounds__(256) gkernel_kernel(const float2* __restrict__ U,
+                                                      const float* __restrict__ w, int Q, int L,
+                                                      int m, const int* __restrict__ lag_ptr,
+                                                      const int* __restrict__ lag_ent, int nbox,
+                                                      float2* __restrict__ K) {
+  extern __shared__ float2 sm[];
+  float2* Up = sm;              // L * JC
+  float2* Uq = Up + L * JC;     // L * JC
+  float2* P = Uq + L * JC;      // L * L
+  const int p = blockIdx.x / Q, q = blockIdx.x % Q;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < L * L; e += nt) P[e] = make_float2(0.f, 0.f);
+  for (int j0 = 0; j0 < m; j0 += JC) {
+    const int jc = min(JC, m - j0);
+    __syncthreads();
+    for (int e = tid; e < L * JC; e += nt) {
+      const int a = e / JC, j = e % JC;
+      float2 up = make_float2(0.f, 0.f), uq = up;
+      if (j < jc) {
+        const float wj = w[j0 + j];
+        up = U[(long long)(p * L + a) * m + j0 + j];
+        const float2 t = U[(long long)(q * L + a) * m + j0 + j];
+        uq = make_float2(t.x * wj, t.y * wj);
+      }
+      Up[e] = up;
+      Uq[e] = uq;
+    }
+    __syncthreads();
+    for (int e = tid; e < L * L; e += nt) {
+      const int b = e / L, a = e % L;
+      float2 acc = P[e];
+      const float2* ub = Uq + b * JC;
+      const float2* ua = Up + a * JC;
+#pragma unroll 8
+      for (int j = 0; j < JC; ++j) cfmac(acc, ua[j], ub[j]);
+      P[e] = acc;
+    }
+  }
+  __syncthreads();
+  float2* out = K + (long long)(p * Q + q) * nbox;
+  for (int t = tid; t < nbox; t += nt) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int e = lag_ptr[t]; e < lag_ptr[t + 1]; ++e) {
+      const float2 v = P[lag_ent[e]];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    out[t] = acc;
+  }
+}
+
+cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int m,
+                             const int* lag_ptr, const int* lag_ent, int nbox, float2* K,
+                             cudaStream_t st) {
+  const size_t smem = (2 * (size_t)L * JC + (size_t)L * L) * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(gkernel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  gkernel_kernel<<<Q * Q, 256, smem, st>>>(U, w, Q, L, m, lag_ptr, lag_ent, nbox, K);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// G <- |Lambda| I - G  (G holds sum_d K_pq[d] e^{i 2 pi d x} on entry), layout [Q][Q][npix].
+__global__ void add_identity_kernel(float2* G, int Q, long long npix, float lam_size) {
+  const long long total = (long long)Q * Q * npix;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long pq = idx / npix;
+    const int p = (int)(pq / Q), q = (int)(pq % Q);
+    float2 v = G[idx];
+    G[idx] = make_float2((p == q ? lam_size : 0.f) - v.x, -v.y);
+  }
+}
+
+cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_size, cudaStream_t st) {
+  long long blocks = ((long long)Q * Q * npix + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  add_identity_kernel<<<(unsigned)blocks, 256, 0, st>>>(G, Q, npix, lam_size);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pisco

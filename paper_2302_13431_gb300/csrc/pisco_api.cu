@@ -1,0 +1,703 @@
+// C ABI and host orchestration of the PISCO GB300 path (see include/pisco.h).
+//
+// pisco_plan validates the request, builds the index tables (Lambda, lag indices) and the
+// small DFT / interpolation matrices on the host in FP64, uploads them and allocates every
+// device buffer the path needs.  pisco_estimate then only enqueues kernels on the plan's
+// stream: Gram (a), nullspace (b), G(x) (c), power iteration + phase (d), interpolation and
+// normalisation (e).  It reads one device status word at the end.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace pisco;
+
+namespace {
+
+constexpr int kNbMax = 16;   // Ritz vectors refined in FP64 per decision
+constexpr int kMmax = 128;   // largest eigensolver block
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pisco_plan_s {
+  pisco_params prm;
+  cudaStream_t st = nullptr;
+  int D = 2;
+  // internal axis order: [0] = z, [1] = y, [2] = x
+  int N[3], Nc[3], tau[3], Nr[3], Lp[3], B[3];
+  int Q = 0, L = 0, n = 0, nbox = 0, npairs = 0;
+  int m = 0, m_max = 0, eig_iters = 10;
+  long long npix = 0, npix_red = 0, nfreq = 0;
+  std::vector<int> lam;        // L x 3 (z,y,x)
+  std::vector<int> lag_of_ij;  // L x L
+  std::vector<int> lag_ptr, lag_ent;  // CSR: entries (b*L + a) with m_b - m_a = lag
+  // device tables
+  double2* fwd[3] = {nullptr, nullptr, nullptr};
+  double2* inv[3] = {nullptr, nullptr, nullptr};
+  float2* gdft[3] = {nullptr, nullptr, nullptr};
+  float2* ydft[3] = {nullptr, nullptr, nullptr};
+  float2* interp[3] = {nullptr, nullptr, nullptr};
+  int* d_lag_of_ij = nullptr;
+  int *d_lag_ptr = nullptr, *d_lag_ent = nullptr;
+  // device buffers
+  double2 *gA = nullptr, *gB = nullptr, *S = nullptr, *P = nullptr, *Rp = nullptr, *lags = nullptr;
+  double2* A = nullptr;
+  float2* A32 = nullptr;
+  float2 *X = nullptr, *Y = nullptr, *Z = nullptr, *U = nullptr;
+  float2 *Gm = nullptr, *Rinv = nullptr, *Bm = nullptr, *Vj = nullptr;
+  float* mu = nullptr;
+  float* w = nullptr;
+  double* ritz = nullptr;
+  int* band = nullptr;
+  double2 *Xb = nullptr, *Zb = nullptr;
+  float2* ws32 = nullptr;
+  size_t ws32_elems = 0;
+  double2* ws64 = nullptr;
+  size_t ws64_elems = 0;
+  float2 *K = nullptr, *T1 = nullptr, *T2 = nullptr, *G = nullptr;
+  float2 *Ya = nullptr, *Yb = nullptr, *Yf = nullptr;
+  float2* V = nullptr;
+  float* eig_tmp = nullptr;
+  float2 *I1 = nullptr, *I2 = nullptr;
+  DevStatus* dstatus = nullptr;
+  DevStatus* hstatus = nullptr;  // pinned
+  // host IO staging
+  float2 *io_calib = nullptr, *io_maps = nullptr;
+  float* io_eig = nullptr;
+  std::vector<void*> allocs;
+  size_t ws_bytes = 0;
+  int last_R = -1, last_k = -1;
+  int last_launches = 0;
+  DevStatus last_status{};
+  // profiling: CUDA events around every operation, accumulated per tag
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;        // pairs (start, end)
+  std::vector<const char*> ev_tag;    // tag per pair
+  int ev_used = 0;
+  std::vector<const char*> prof_name;
+  std::vector<double> prof_ms;
+  std::vector<int> prof_cnt;
+};
+
+namespace {
+
+template <typename T>
+bool dalloc(pisco_plan_s* pl, T** p, size_t count) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return false;
+  pl->allocs.push_back(q);
+  pl->ws_bytes += count * sizeof(T);
+  *p = reinterpret_cast<T*>(q);
+  return true;
+}
+
+template <typename T>
+bool upload(pisco_plan_s* pl, T** p, const std::vector<T>& h) {
+  if (!dalloc(pl, p, h.size())) return false;
+  return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+const double kPi = 3.14159265358979323846;
+
+// zero-padded forward DFT along one axis: F[f][n] = exp(-i 2 pi f n / Lp), n = array index
+std::vector<double2> fwd_matrix(int Lp, int Nc) {
+  std::vector<double2> M((size_t)Lp * Nc);
+  for (int f = 0; f < Lp; ++f)
+    for (int n = 0; n < Nc; ++n) {
+      const double a = -2.0 * kPi * (double)((long long)f * n % Lp) / Lp;
+      M[(size_t)f * Nc + n] = make_double2(cos(a), sin(a));
+    }
+  return M;
+}
+// inverse DFT at lags d = -2tau..2tau: M[d][f] = exp(+i 2 pi f d / Lp) / Lp
+std::vector<double2> inv_matrix(int Lp, int tau) {
+  const int Bn = 4 * tau + 1;
+  std::vector<double2> M((size_t)Bn * Lp);
+  for (int t = 0; t < Bn; ++t) {
+    const int d = t - 2 * tau;
+    for (int f = 0; f < Lp; ++f) {
+      long long ph = ((long long)f * d) % Lp;
+      if (ph < 0) ph += Lp;
+      const double a = 2.0 * kPi * (double)ph / Lp;
+      M[(size_t)t * Lp + f] = make_double2(cos(a) / Lp, sin(a) / Lp);
+    }
+  }
+  return M;
+}
+// lag sum onto the reduced grid: M[j][d] = exp(+i 2 pi d x_j), x_j = (j - Nr/2)/Nr
+std::vector<float2> gdft_matrix(int Nr, int tau) {
+  const int Bn = 4 * tau + 1;
+  std::vector<float2> M((size_t)Nr * Bn);
+  for (int j = 0; j < Nr; ++j)
+    for (int t = 0; t < Bn; ++t) {
+      const long long d = t - 2 * tau;
+      long long num = d * (long long)(j - Nr / 2);
+      num %= Nr;
+      if (num < 0) num += Nr;
+      const double a = 2.0 * kPi * (double)num / Nr;
+      M[(size_t)j * Bn + t] = make_float2((float)cos(a), (float)sin(a));
+    }
+  return M;
+}
+// apodised low-resolution image: M[j][n] = a[n] exp(+i 2 pi n x_j), n centred index,
+// a[n] = exp(-(n/(Nc/4))^2 / 2)
+std::vector<float2> ydft_matrix(int Nr, int Nc) {
+  std::vector<float2> M((size_t)Nr * Nc);
+  const double width = Nc / 4.0;
+  for (int j = 0; j < Nr; ++j)
+    for (int idx = 0; idx < Nc; ++idx) {
+      const long long nn = idx - Nc / 2;
+      const double apo = exp(-0.5 * (nn / width) * (nn / width));
+      long long num = nn * (long long)(j - Nr / 2);
+      num %= Nr;
+      if (num < 0) num += Nr;
+      const double a = 2.0 * kPi * (double)num / Nr;
+      M[(size_t)j * Nc + idx] = make_float2((float)(apo * cos(a)), (float)(apo * sin(a)));
+    }
+  return M;
+}
+// periodic-sinc interpolation n_in -> n_out (Sec. V-D): DFT of the coarse samples, band
+// k in [-n_in/2, n_in - n_in/2), Nyquist coefficient split between +-n_in/2 for even n_in,
+// evaluated at the fine points.  Computed in FP64 as an explicit matrix.
+std::vector<float2> interp_matrix(int n_in, int n_out) {
+  std::vector<float2> M((size_t)n_out * n_in);
+  const int k0 = -(n_in / 2), k1 = n_in - n_in / 2;
+  for (int i = 0; i < n_out; ++i) {
+    const double xi = (double)(i - n_out / 2) / n_out;
+    for (int j = 0; j < n_in; ++j) {
+      const double xj = (double)(j - n_in / 2) / n_in;
+      double re = 0.0, im = 0.0;
+      for (int k = k0; k < k1; ++k) {
+        const double a = -2.0 * kPi * k * xj;  // forward coefficient
+        double er, ei;
+        if (n_in % 2 == 0 && k == k0 && n_out != n_in) {
+          // split Nyquist: (e^{-i pi n_in x} + e^{+i pi n_in x})/2 = cos(pi n_in x)
+          er = cos(kPi * n_in * xi);
+          ei = 0.0;
+        } else {
+          const double b = 2.0 * kPi * k * xi;
+          er = cos(b);
+          ei = sin(b);
+        }
+        const double fr = cos(a) / n_in, fi = sin(a) / n_in;
+        re += er * fr - ei * fi;
+        im += er * fi + ei * fr;
+      }
+      M[(size_t)i * n_in + j] = make_float2((float)re, (float)im);
+    }
+  }
+  return M;
+}
+
+void build_support(pisco_plan_s* pl) {
+  pl->lam.clear();
+  const int* t = pl->tau;
+  const bool ell = pl->prm.kernel_shape == PISCO_KERNEL_ELLIPSOID;
+  for (int z = -t[0]; z <= t[0]; ++z)
+    for (int y = -t[1]; y <= t[1]; ++y)
+      for (int x = -t[2]; x <= t[2]; ++x) {
+        if (ell) {
+          // sum (n_d/tau_d)^2 <= 1 evaluated exactly in integers:
+          // sum n_d^2 * prod_{e != d} tau_e^2 <= prod tau_e^2 over the axes with tau > 0
+          long long lhs = 0, prod = 1;
+          const int v[3] = {z, y, x};
+          for (int d = 0; d < 3; ++d)
+            if (t[d] > 0) prod *= (long long)t[d] * t[d];
+          for (int d = 0; d < 3; ++d) {
+            if (t[d] == 0) continue;
+            lhs += (long long)v[d] * v[d] * (prod / ((long long)t[d] * t[d]));
+          }
+          if (lhs > prod) continue;
+        }
+        pl->lam.push_back(z);
+        pl->lam.push_back(y);
+        pl->lam.push_back(x);
+      }
+  pl->L = (int)pl->lam.size() / 3;
+  pl->lag_of_ij.assign((size_t)pl->L * pl->L, 0);
+  for (int i = 0; i < pl->L; ++i)
+    for (int j = 0; j < pl->L; ++j) {
+      const int dz = pl->lam[3 * i] - pl->lam[3 * j] + 2 * t[0];
+      const int dy = pl->lam[3 * i + 1] - pl->lam[3 * j + 1] + 2 * t[1];
+      const int dx = pl->lam[3 * i + 2] - pl->lam[3 * j + 2] + 2 * t[2];
+      pl->lag_of_ij[(size_t)i * pl->L + j] = (dz * pl->B[1] + dy) * pl->B[2] + dx;
+    }
+  // CSR lists of the (b, a) pairs per lag box entry, in increasing b*L + a
+  const int nbox = pl->B[0] * pl->B[1] * pl->B[2];
+  pl->lag_ptr.assign(nbox + 1, 0);
+  for (int e = 0; e < pl->L * pl->L; ++e) pl->lag_ptr[pl->lag_of_ij[e] + 1]++;
+  for (int t = 0; t < nbox; ++t) pl->lag_ptr[t + 1] += pl->lag_ptr[t];
+  pl->lag_ent.assign((size_t)pl->L * pl->L, 0);
+  std::vector<int> fill(pl->lag_ptr.begin(), pl->lag_ptr.end() - 1);
+  for (int e = 0; e < pl->L * pl->L; ++e) pl->lag_ent[fill[pl->lag_of_ij[e]]++] = e;
+}
+
+pisco_status validate(const pisco_params* p) {
+  if (!p) return PISCO_ERR_ARG;
+  if (p->ndim != 2 && p->ndim != 3) return PISCO_ERR_ARG;
+  if (p->num_coils < 2 || p->num_coils > 64) return PISCO_ERR_ARG;
+  if (p->kernel_shape != PISCO_KERNEL_RECT && p->kernel_shape != PISCO_KERNEL_ELLIPSOID) return PISCO_ERR_ARG;
+  if (!(p->null_threshold > 0.0 && p->null_threshold < 1.0)) return PISCO_ERR_ARG;
+  if (p->grid_reduction < 1 || p->power_iters < 1) return PISCO_ERR_ARG;
+  const int nd = p->ndim;
+  for (int d = 0; d < 3; ++d) {
+    const bool used = d < nd;
+    if (!used) {
+      if (p->grid[d] != 1 || p->calib[d] != 1 || p->kernel_radius[d] != 0) return PISCO_ERR_ARG;
+      continue;
+    }
+    const int N = p->grid[d], Nc = p->calib[d], t = p->kernel_radius[d];
+    if (N < 1 || Nc < 1 || t < 0 || t > 16) return PISCO_ERR_ARG;
+    if (Nc <= 2 * t) return PISCO_ERR_ARG;
+    if (Nc > N) return PISCO_ERR_ARG;
+    if (N % p->grid_reduction != 0) return PISCO_ERR_ARG;
+    if (N / p->grid_reduction < 2 * t + 1) return PISCO_ERR_ARG;
+  }
+  if (p->eig_block < 0 || p->eig_block > kMmax || (p->eig_block % 2) != 0) return PISCO_ERR_ARG;
+  if (p->eig_iters < 0 || p->eig_iters > 100) return PISCO_ERR_ARG;
+  return PISCO_OK;
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e__ = (x);                      \
+    if (e__ != cudaSuccess) return PISCO_ERR_CUDA; \
+  } while (0)
+
+int prof_begin(pisco_plan_s* pl, const char* tag) {
+  if (!pl->prof) return -1;
+  if (pl->ev_used * 2 + 2 > (int)pl->ev.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+    pl->ev.push_back(a);
+    pl->ev.push_back(b);
+    pl->ev_tag.push_back(nullptr);
+  }
+  const int i = pl->ev_used++;
+  pl->ev_tag[i] = tag;
+  cudaEventRecord(pl->ev[2 * i], pl->st);
+  return i;
+}
+void prof_end(pisco_plan_s* pl, int i) {
+  if (i >= 0) cudaEventRecord(pl->ev[2 * i + 1], pl->st);
+}
+// after the stream has been synchronised: fold the recorded pairs into the per-tag totals
+void prof_collect(pisco_plan_s* pl) {
+  for (int i = 0; i < pl->ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pl->ev[2 * i], pl->ev[2 * i + 1]) != cudaSuccess) continue;
+    size_t k = 0;
+    while (k < pl->prof_name.size() && strcmp(pl->prof_name[k], pl->ev_tag[i]) != 0) ++k;
+    if (k == pl->prof_name.size()) {
+      pl->prof_name.push_back(pl->ev_tag[i]);
+      pl->prof_ms.push_back(0.0);
+      pl->prof_cnt.push_back(0);
+    }
+    pl->prof_ms[k] += ms;
+    pl->prof_cnt[k] += 1;
+  }
+  pl->ev_used = 0;
+}
+
+#define OP(tag, x)                                   \
+  do {                                               \
+    const int i__ = prof_begin(pl, tag);             \
+    cudaError_t e__ = (x);                           \
+    if (e__ != cudaSuccess) return PISCO_ERR_CUDA;   \
+    prof_end(pl, i__);                               \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// the path
+// ---------------------------------------------------------------------------------------
+pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
+  cudaStream_t st = pl->st;
+  const int Q = pl->Q;
+  const int* Nc = pl->Nc;
+  const int* Lp = pl->Lp;
+  const int* B = pl->B;
+  // forward zero-padded DFT of every channel: x, y, z
+  OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwd[2], pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1}, st));
+  OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->fwd[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
+  const double2* S = pl->gB;
+  if (pl->D == 3) {
+    OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->fwd[0], pl->S, AxisView{Q, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
+    S = pl->S;
+  }
+  OP("gram_pair_products", gram_pair_products(S, Q, pl->nfreq, pl->P, st));
+  const int np = pl->npairs;
+  OP("gram_dft_fp64", apply_axis_z(pl->P, pl->inv[2], pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1}, st));
+  if (pl->D == 3) {
+    OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->gB, AxisView{np, Lp[0], Lp[1], B[1], B[2]}, st));
+    OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->inv[0], pl->Rp, AxisView{np, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
+  } else {
+    OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->Rp, AxisView{np, 1, Lp[1], B[1], B[2]}, st));
+  }
+  OP("gram_scatter", gram_scatter_pairs(pl->Rp, Q, pl->nbox, pl->lags, st));
+  OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->A, pl->A32, st));
+  return PISCO_OK;
+}
+
+pisco_status cholqr(pisco_plan_s* pl, float2* Yin, float2* Xout, int m) {
+  cudaStream_t st = pl->st;
+  const int n = pl->n;
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, st));
+  OP("eig_chol", eig_chol(pl->Gm, m, pl->Rinv, pl->dstatus, st));
+  OP("eig_trsm", eig_trsm_rows(Yin, pl->Rinv, n, m, Xout, st));
+  return PISCO_OK;
+}
+
+pisco_status run_eig(pisco_plan_s* pl) {
+  cudaStream_t st = pl->st;
+  const int n = pl->n, m = pl->m;
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  const double thr2 = pl->prm.null_threshold * pl->prm.null_threshold;
+  OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
+  pisco_status s = cholqr(pl, pl->Y, pl->X, m);
+  if (s != PISCO_OK) return s;
+  for (int t = 0; t < pl->eig_iters; ++t) {
+    OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->X, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, st));
+    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, st));
+    OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, pl->dstatus, st));
+    if (t == pl->eig_iters - 1) {
+      OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, st));
+      break;
+    }
+    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->Z, m, pl->Vj, m, zero, pl->Y, m, pl->ws32, pl->ws32_elems, st));
+    OP("eig_misc", eig_scale_cols(pl->Y, n, m, pl->mu, 1e-6f, st));
+    if ((s = cholqr(pl, pl->Y, pl->X, m)) != PISCO_OK) return s;
+    if ((s = cholqr(pl, pl->X, pl->Y, m)) != PISCO_OK) return s;
+    std::swap(pl->X, pl->Y);
+  }
+  // FP64 Rayleigh quotients of the Ritz vectors that decide the split
+  OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st));
+  OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
+  const double2 zone = make_double2(1.0, 0.0), zzero = make_double2(0.0, 0.0);
+  OP("eig_rayleigh_fp64", cgemm<double>('N', 'N', n, kNbMax, n, zone, pl->A, n, pl->Xb, kNbMax, zzero, pl->Zb, kNbMax,
+                   pl->ws64, pl->ws64_elems, st));
+  OP("eig_decide_fp64", eig_decide(pl->mu, m, pl->band, kNbMax, pl->Xb, pl->Zb, n, thr2, pl->Q, pl->w, pl->ritz,
+                pl->dstatus, st));
+  return PISCO_OK;
+}
+
+pisco_status run_gfield(pisco_plan_s* pl) {
+  cudaStream_t st = pl->st;
+  const int Q = pl->Q;
+  const int* B = pl->B;
+  const int* Nr = pl->Nr;
+  const long long QQ = (long long)Q * Q;
+  OP("g_kernel", gassembly_kernel(pl->U, pl->w, Q, pl->L, pl->m, pl->d_lag_ptr, pl->d_lag_ent, pl->nbox, pl->K, st));
+  OP("g_dft", apply_axis_c(pl->K, pl->gdft[2], pl->T1, AxisView{QQ, (long long)B[0] * B[1], B[2], Nr[2], 1}, st));
+  if (pl->D == 3) {
+    OP("g_dft", apply_axis_c(pl->T1, pl->gdft[1], pl->T2, AxisView{QQ, B[0], B[1], Nr[1], Nr[2]}, st));
+    OP("g_dft", apply_axis_c(pl->T2, pl->gdft[0], pl->G, AxisView{QQ, 1, B[0], Nr[0], (long long)Nr[1] * Nr[2]}, st));
+  } else {
+    OP("g_dft", apply_axis_c(pl->T1, pl->gdft[1], pl->G, AxisView{QQ, 1, B[1], Nr[1], Nr[2]}, st));
+  }
+  OP("g_identity", gassembly_add_identity(pl->G, Q, pl->npix_red, (float)pl->L, st));
+  return PISCO_OK;
+}
+
+pisco_status run_lowres(pisco_plan_s* pl, const float2* calib) {
+  cudaStream_t st = pl->st;
+  const int Q = pl->Q;
+  const int* Nc = pl->Nc;
+  const int* Nr = pl->Nr;
+  OP("lowres_dft", apply_axis_c(calib, pl->ydft[2], pl->Ya, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Nr[2], 1}, st));
+  if (pl->D == 3) {
+    OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yb, AxisView{Q, Nc[0], Nc[1], Nr[1], Nr[2]}, st));
+    OP("lowres_dft", apply_axis_c(pl->Yb, pl->ydft[0], pl->Yf, AxisView{Q, 1, Nc[0], Nr[0], (long long)Nr[1] * Nr[2]}, st));
+  } else {
+    OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yf, AxisView{Q, 1, Nc[1], Nr[1], Nr[2]}, st));
+  }
+  return PISCO_OK;
+}
+
+pisco_status run_interp(pisco_plan_s* pl, float2* maps) {
+  cudaStream_t st = pl->st;
+  const int Q = pl->Q;
+  const int* N = pl->N;
+  const int* Nr = pl->Nr;
+  if (pl->prm.grid_reduction == 1) {
+    OP("interp_final_norm", interp_final_normalize(pl->V, nullptr, Q, 0, 1, 1, pl->npix, maps, st));
+    return PISCO_OK;
+  }
+  OP("interp_axis", apply_axis_c(pl->V, pl->interp[2], pl->I1, AxisView{Q, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1}, st));
+  if (pl->D == 3) {
+    OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{Q, Nr[0], Nr[1], N[1], N[2]}, st));
+    OP("interp_final_norm", interp_final_normalize(pl->I2, pl->interp[0], Q, 0, Nr[0], N[0], (long long)N[1] * N[2], maps, st));
+  } else {
+    OP("interp_final_norm", interp_final_normalize(pl->I1, pl->interp[1], Q, 0, Nr[1], N[1], N[2], maps, st));
+  }
+  return PISCO_OK;
+}
+
+pisco_status run_all(pisco_plan_s* pl, const float2* calib, float2* maps, float* eig) {
+  cudaStream_t st = pl->st;
+  g_launches = 0;
+  CK(cudaMemsetAsync(pl->dstatus, 0, sizeof(DevStatus), st));
+  pisco_status s;
+  if ((s = run_gram(pl, calib)) != PISCO_OK) return s;
+  if ((s = run_eig(pl)) != PISCO_OK) return s;
+  if ((s = run_gfield(pl)) != PISCO_OK) return s;
+  if ((s = run_lowres(pl, calib)) != PISCO_OK) return s;
+  OP("power_iteration", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->prm.power_iters, (float)pl->L,
+                     pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st));
+  if ((s = run_interp(pl, maps)) != PISCO_OK) return s;
+  CK(cudaMemcpyAsync(pl->hstatus, pl->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  return PISCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pisco_status_string(pisco_status s) {
+  switch (s) {
+    case PISCO_OK: return "ok";
+    case PISCO_ERR_ARG: return "invalid argument";
+    case PISCO_ERR_CUDA: return "CUDA runtime error";
+    case PISCO_ERR_OOM: return "device allocation failed";
+    case PISCO_ERR_RANK: return "nullspace dimension R < Q-1 (maps not identifiable)";
+    case PISCO_ERR_TIMEOUT: return "bounded device wait expired";
+    case PISCO_ERR_NOT_CONVERGED: return "eigensolver block saturated at its largest size";
+    case PISCO_ERR_UNSUPPORTED: return "request outside this build";
+  }
+  return "unknown status";
+}
+
+void pisco_destroy(pisco_plan_t pl) {
+  if (!pl) return;
+  if (pl->st) cudaStreamSynchronize(pl->st);
+  for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
+  for (void* p : pl->allocs) cudaFree(p);
+  if (pl->hstatus) cudaFreeHost(pl->hstatus);
+  delete pl;
+}
+
+pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* out) {
+  if (!out) return PISCO_ERR_ARG;
+  *out = nullptr;
+  pisco_status s = validate(p);
+  if (s != PISCO_OK) return s;
+  pisco_plan_s* pl = new (std::nothrow) pisco_plan_s();
+  if (!pl) return PISCO_ERR_OOM;
+  pl->prm = *p;
+  pl->st = (cudaStream_t)cuda_stream;
+  pl->D = p->ndim;
+  for (int d = 0; d < 3; ++d) {  // params are x,y,z; internal z,y,x
+    pl->N[2 - d] = p->grid[d];
+    pl->Nc[2 - d] = p->calib[d];
+    pl->tau[2 - d] = p->kernel_radius[d];
+  }
+  const int f = p->grid_reduction;
+  pl->Q = p->num_coils;
+  for (int d = 0; d < 3; ++d) {
+    pl->Nr[d] = pl->N[d] / f;
+    if (pl->N[d] == 1) pl->Nr[d] = 1;
+    pl->Lp[d] = pl->Nc[d] + 2 * pl->tau[d];
+    pl->B[d] = 4 * pl->tau[d] + 1;
+  }
+  build_support(pl);
+  pl->n = pl->Q * pl->L;
+  pl->nbox = pl->B[0] * pl->B[1] * pl->B[2];
+  pl->npairs = pl->Q * (pl->Q + 1) / 2;
+  pl->npix = (long long)pl->N[0] * pl->N[1] * pl->N[2];
+  pl->npix_red = (long long)pl->Nr[0] * pl->Nr[1] * pl->Nr[2];
+  pl->nfreq = (long long)pl->Lp[0] * pl->Lp[1] * pl->Lp[2];
+  // shared-memory budget of the G-kernel build (two staged column chunks + the L x L block)
+  if ((2 * (size_t)pl->L * 32 + (size_t)pl->L * pl->L) * sizeof(float2) > 220 * 1024) {
+    delete pl;
+    return PISCO_ERR_UNSUPPORTED;
+  }
+  int mmax = std::min(kMmax, pl->n - (pl->n % 2));
+  pl->m_max = mmax;
+  pl->m = p->eig_block > 0 ? std::min(p->eig_block, mmax) : std::min(64, mmax);
+  if (pl->m < 2) { delete pl; return PISCO_ERR_ARG; }
+  pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 8;
+
+  const int Q = pl->Q, n = pl->n, np = pl->npairs;
+  const int* Nc = pl->Nc;
+  const int* Lp = pl->Lp;
+  const int* B = pl->B;
+  const int* Nr = pl->Nr;
+  const int* N = pl->N;
+  bool ok = true;
+  // tables
+  for (int d = 0; d < 3; ++d) {
+    ok = ok && upload(pl, &pl->fwd[d], fwd_matrix(Lp[d], Nc[d]));
+    ok = ok && upload(pl, &pl->inv[d], inv_matrix(Lp[d], pl->tau[d]));
+    ok = ok && upload(pl, &pl->gdft[d], gdft_matrix(Nr[d], pl->tau[d]));
+    ok = ok && upload(pl, &pl->ydft[d], ydft_matrix(Nr[d], Nc[d]));
+    ok = ok && upload(pl, &pl->interp[d], interp_matrix(Nr[d], N[d]));
+  }
+  ok = ok && upload(pl, &pl->d_lag_of_ij, pl->lag_of_ij);
+  ok = ok && upload(pl, &pl->d_lag_ptr, pl->lag_ptr) && upload(pl, &pl->d_lag_ent, pl->lag_ent);
+  // Gram
+  const long long gA = std::max((long long)Q * Nc[0] * Nc[1] * Lp[2], (long long)np * Lp[0] * Lp[1] * B[2]);
+  const long long gB = std::max((long long)Q * Nc[0] * Lp[1] * Lp[2], (long long)np * Lp[0] * B[1] * B[2]);
+  ok = ok && dalloc(pl, &pl->gA, gA) && dalloc(pl, &pl->gB, gB);
+  ok = ok && dalloc(pl, &pl->S, (size_t)Q * pl->nfreq) && dalloc(pl, &pl->P, (size_t)np * pl->nfreq);
+  ok = ok && dalloc(pl, &pl->Rp, (size_t)np * pl->nbox) && dalloc(pl, &pl->lags, (size_t)Q * Q * pl->nbox);
+  ok = ok && dalloc(pl, &pl->A, (size_t)n * n) && dalloc(pl, &pl->A32, (size_t)n * n);
+  // eigensolver (sized for the largest block)
+  const int M = pl->m_max;
+  ok = ok && dalloc(pl, &pl->X, (size_t)n * M) && dalloc(pl, &pl->Y, (size_t)n * M);
+  ok = ok && dalloc(pl, &pl->Z, (size_t)n * M) && dalloc(pl, &pl->U, (size_t)n * M);
+  ok = ok && dalloc(pl, &pl->Gm, (size_t)M * M) && dalloc(pl, &pl->Rinv, (size_t)M * M);
+  ok = ok && dalloc(pl, &pl->Bm, (size_t)M * M) && dalloc(pl, &pl->Vj, (size_t)2 * M * M);
+  ok = ok && dalloc(pl, &pl->mu, (size_t)M) && dalloc(pl, &pl->w, (size_t)M) && dalloc(pl, &pl->ritz, (size_t)M);
+  ok = ok && dalloc(pl, &pl->band, (size_t)kNbMax);
+  ok = ok && dalloc(pl, &pl->Xb, (size_t)n * kNbMax) && dalloc(pl, &pl->Zb, (size_t)n * kNbMax);
+  pl->ws32_elems = (size_t)16 * n * M;
+  pl->ws64_elems = (size_t)64 * n * kNbMax;
+  ok = ok && dalloc(pl, &pl->ws32, pl->ws32_elems) && dalloc(pl, &pl->ws64, pl->ws64_elems);
+  // G field
+  const long long QQ = (long long)Q * Q;
+  ok = ok && dalloc(pl, &pl->K, (size_t)(QQ * pl->nbox));
+  ok = ok && dalloc(pl, &pl->T1, (size_t)(QQ * B[0] * B[1] * Nr[2]));
+  ok = ok && dalloc(pl, &pl->T2, (size_t)(QQ * B[0] * Nr[1] * Nr[2]));
+  ok = ok && dalloc(pl, &pl->G, (size_t)(QQ * pl->npix_red));
+  // low-res images, PI output, interpolation intermediates
+  ok = ok && dalloc(pl, &pl->Ya, (size_t)Q * Nc[0] * Nc[1] * Nr[2]);
+  ok = ok && dalloc(pl, &pl->Yb, (size_t)Q * Nc[0] * Nr[1] * Nr[2]);
+  ok = ok && dalloc(pl, &pl->Yf, (size_t)(Q * pl->npix_red));
+  ok = ok && dalloc(pl, &pl->V, (size_t)(Q * pl->npix_red));
+  ok = ok && dalloc(pl, &pl->eig_tmp, (size_t)pl->npix_red);
+  ok = ok && dalloc(pl, &pl->I1, (size_t)Q * Nr[0] * Nr[1] * N[2]);
+  ok = ok && dalloc(pl, &pl->I2, (size_t)Q * Nr[0] * N[1] * N[2]);
+  ok = ok && dalloc(pl, &pl->dstatus, 1);
+  if (ok && (p->flags & PISCO_FLAG_HOST_IO)) {
+    ok = dalloc(pl, &pl->io_calib, (size_t)Q * Nc[0] * Nc[1] * Nc[2]) &&
+         dalloc(pl, &pl->io_maps, (size_t)(Q * pl->npix)) && dalloc(pl, &pl->io_eig, (size_t)pl->npix_red);
+  }
+  if (ok) ok = cudaMallocHost((void**)&pl->hstatus, sizeof(DevStatus)) == cudaSuccess;
+  if (ok) ok = cudaMemset(pl->lags, 0, sizeof(double2) * (size_t)Q * Q * pl->nbox) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pisco_destroy(pl);
+    return PISCO_ERR_OOM;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    pisco_destroy(pl);
+    return PISCO_ERR_CUDA;
+  }
+  *out = pl;
+  return PISCO_OK;
+}
+
+pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, float* d_eig) {
+  if (!pl || !d_calib || !d_maps) return PISCO_ERR_ARG;
+  if (((uintptr_t)d_calib | (uintptr_t)d_maps | (uintptr_t)d_eig) & 7) return PISCO_ERR_ARG;
+  for (;;) {
+    pisco_status s = run_all(pl, (const float2*)d_calib, (float2*)d_maps, d_eig);
+    if (s != PISCO_OK) return s;
+    if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+    pl->last_launches = g_launches;
+    if (pl->prof) prof_collect(pl);
+    const DevStatus h = *pl->hstatus;
+    pl->last_status = h;
+    if ((h.flags & ST_SATURATED) && pl->m < pl->m_max) {
+      pl->m = std::min(pl->m * 2, pl->m_max);
+      continue;
+    }
+    pl->last_k = h.k;
+    pl->last_R = pl->n - h.k;
+    if (h.flags & ST_SATURATED) return PISCO_ERR_NOT_CONVERGED;
+    if (h.flags & ST_RANK) return PISCO_ERR_RANK;
+    return PISCO_OK;
+  }
+}
+
+pisco_status pisco_estimate_host(pisco_plan_t pl, const void* h_calib, void* h_maps, float* h_eig) {
+  if (!pl || !h_calib || !h_maps) return PISCO_ERR_ARG;
+  if (!pl->io_calib) return PISCO_ERR_ARG;
+  const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
+  const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
+  if (cudaMemcpyAsync(pl->io_calib, h_calib, cb, cudaMemcpyHostToDevice, pl->st) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  pisco_status s = pisco_estimate(pl, pl->io_calib, pl->io_maps, h_eig ? pl->io_eig : nullptr);
+  if (s != PISCO_OK && s != PISCO_ERR_RANK) return s;
+  if (cudaMemcpyAsync(h_maps, pl->io_maps, mb, cudaMemcpyDeviceToHost, pl->st) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  if (h_eig && cudaMemcpyAsync(h_eig, pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost,
+                               pl->st) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+  return s;
+}
+
+pisco_status pisco_plan_info(pisco_plan_t pl, int* R, int* k, size_t* workspace_bytes) {
+  if (!pl) return PISCO_ERR_ARG;
+  if (R) *R = pl->last_R;
+  if (k) *k = pl->last_k;
+  if (workspace_bytes) *workspace_bytes = pl->ws_bytes;
+  return PISCO_OK;
+}
+
+pisco_status pisco_debug_buffer(pisco_plan_t pl, int which, void** dptr, size_t* bytes) {
+  if (!pl || !dptr || !bytes) return PISCO_ERR_ARG;
+  const size_t n = pl->n;
+  switch (which) {
+    case PISCO_BUF_LAGS: *dptr = pl->lags; *bytes = sizeof(double2) * (size_t)pl->Q * pl->Q * pl->nbox; break;
+    case PISCO_BUF_GRAM: *dptr = pl->A; *bytes = sizeof(double2) * n * n; break;
+    case PISCO_BUF_SIGNAL: *dptr = pl->U; *bytes = sizeof(float2) * n * pl->m; break;
+    case PISCO_BUF_WEIGHTS: *dptr = pl->w; *bytes = sizeof(float) * pl->m; break;
+    case PISCO_BUF_RITZ: *dptr = pl->ritz; *bytes = sizeof(double) * pl->m; break;
+    case PISCO_BUF_G: *dptr = pl->G; *bytes = sizeof(float2) * (size_t)pl->Q * pl->Q * pl->npix_red; break;
+    case PISCO_BUF_V: *dptr = pl->V; *bytes = sizeof(float2) * (size_t)pl->Q * pl->npix_red; break;
+    case PISCO_BUF_Y: *dptr = pl->Yf; *bytes = sizeof(float2) * (size_t)pl->Q * pl->npix_red; break;
+    default: return PISCO_ERR_ARG;
+  }
+  return PISCO_OK;
+}
+
+pisco_status pisco_get_stats(pisco_plan_t pl, pisco_stats* out) {
+  if (!pl || !out) return PISCO_ERR_ARG;
+  out->launches = pl->last_launches;
+  out->eig_block = pl->m;
+  out->eig_iters = pl->eig_iters;
+  out->jacobi_sweeps = pl->last_status.jacobi_sweeps;
+  out->nband = pl->last_status.nband;
+  out->lambda_max = pl->last_status.lambda_max;
+  out->signal_dim = pl->last_k;
+  out->filter_len = pl->L;
+  return PISCO_OK;
+}
+
+pisco_status pisco_set_profiling(pisco_plan_t pl, int enable) {
+  if (!pl) return PISCO_ERR_ARG;
+  pl->prof = enable != 0;
+  pl->ev_used = 0;
+  return PISCO_OK;
+}
+
+pisco_status pisco_profile_reset(pisco_plan_t pl) {
+  if (!pl) return PISCO_ERR_ARG;
+  pl->prof_name.clear();
+  pl->prof_ms.clear();
+  pl->prof_cnt.clear();
+  return PISCO_OK;
+}
+
+pisco_status pisco_profile_entry(pisco_plan_t pl, int idx, const char** name, double* total_ms, int* count) {
+  if (!pl || idx < 0 || idx >= (int)pl->prof_name.size()) return PISCO_ERR_ARG;
+  if (name) *name = pl->prof_name[idx];
+  if (total_ms) *total_ms = pl->prof_ms[idx];
+  if (count) *count = pl->prof_cnt[idx];
+  return PISCO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+"""torch-facing wrapper of the PISCO C ABI.
+
+torch provides device memory and the CUDA stream; every step of the estimator runs in the
+CUDA library (see include/pisco.h).  There is no CPU fallback: constructing an estimator
+without the library or without a GPU raises.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+class _DevView:
+    """Exposes a raw device pointer through __cuda_array_interface__ for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2}
+
+
+class PiscoEstimator:
+    """One plan of the estimator for a fixed problem shape.
+
+    grid, calib_shape: (z,)y,x sizes of the image grid and the centred calibration box.
+    tau: radius (int or per-axis tuple); kernel_shape: "ellipsoid" (Sec. V-B) or "rect".
+    reduction: grid-reduction factor f (Sec. V-D); iters: power iterations (Sec. V-E).
+    """
+
+    def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
+                 reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
+                 stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
+        self.grid = tuple(int(g) for g in grid)
+        self.calib_shape = tuple(int(c) for c in calib_shape)
+        self.Q = int(num_coils)
+        self.reduction = int(reduction)
+        self.reduced = tuple(g // reduction for g in self.grid)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
+                                    reduction, iters, seed, B.PISCO_FLAG_HOST_IO if host_io else 0,
+                                    eig_block, eig_iters)
+        st, h = B.pisco_plan(self.params, self.stream.cuda_stream)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_plan")
+        self._plan = h
+        self.last_status = None
+
+    # ------------------------------------------------------------------------------------
+    def estimate_into(self, calib: torch.Tensor, maps: torch.Tensor, eig: torch.Tensor | None):
+        """Run on device tensors (complex64 calib [Q,*calib], maps [Q,*grid], float32 eig)."""
+        for t, name in ((calib, "calib"), (maps, "maps")):
+            if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor")
+        if tuple(calib.shape) != (self.Q,) + self.calib_shape:
+            raise ValueError(f"calib shape {tuple(calib.shape)} != {(self.Q,) + self.calib_shape}")
+        if tuple(maps.shape) != (self.Q,) + self.grid:
+            raise ValueError(f"maps shape {tuple(maps.shape)} != {(self.Q,) + self.grid}")
+        if eig is not None and (eig.dtype != torch.float32 or not eig.is_cuda or eig.numel() != int(np.prod(self.reduced))):
+            raise ValueError("eig must be a float32 CUDA tensor with one entry per reduced pixel")
+        st = B.pisco_estimate(self._plan, calib.data_ptr(), maps.data_ptr(),
+                              eig.data_ptr() if eig is not None else None)
+        self.last_status = st
+        if st not in (B.PISCO_OK, B.PISCO_ERR_RANK):
+            raise B.PiscoError(st, "pisco_estimate")
+        return st
+
+    def __call__(self, calib: torch.Tensor):
+        maps = torch.empty((self.Q,) + self.grid, dtype=torch.complex64, device=calib.device)
+        eig = torch.empty(self.reduced, dtype=torch.float32, device=calib.device)
+        self.estimate_into(calib.contiguous(), maps, eig)
+        return maps, eig
+
+    def estimate_host(self, calib: np.ndarray, maps: np.ndarray, eig: np.ndarray | None):
+        """Host-buffer call (pisco_estimate_host): numpy complex64 in, numpy out."""
+        if calib.dtype != np.complex64 or maps.dtype != np.complex64:
+            raise ValueError("host buffers must be complex64")
+        if not (calib.flags.c_contiguous and maps.flags.c_contiguous):
+            raise ValueError("host buffers must be C-contiguous")
+        st = B.pisco_estimate_host(self._plan, calib.ctypes.data, maps.ctypes.data,
+                                   eig.ctypes.data if eig is not None else None)
+        self.last_status = st
+        if st not in (B.PISCO_OK, B.PISCO_ERR_RANK):
+            raise B.PiscoError(st, "pisco_estimate_host")
+        return st
+
+    # ------------------------------------------------------------------------------------
+    def info(self):
+        st, R, k, ws = B.pisco_plan_info(self._plan)
+        return dict(R=R, k=k, workspace_bytes=ws)
+
+    def stats(self):
+        st, d = B.pisco_get_stats(self._plan)
+        return d
+
+    def set_profiling(self, enable=True):
+        B.pisco_set_profiling(self._plan, enable)
+
+    def profile_reset(self):
+        B.pisco_profile_reset(self._plan)
+
+    def profile(self):
+        return B.pisco_profile(self._plan)
+
+    _BUF_TYPES = {B.PISCO_BUF_LAGS: "<c16", B.PISCO_BUF_GRAM: "<c16", B.PISCO_BUF_SIGNAL: "<c8",
+                  B.PISCO_BUF_WEIGHTS: "<f4", B.PISCO_BUF_RITZ: "<f8", B.PISCO_BUF_G: "<c8",
+                  B.PISCO_BUF_V: "<c8", B.PISCO_BUF_Y: "<c8"}
+
+    def debug_buffer(self, which: int) -> torch.Tensor:
+        """A copy of one intermediate buffer of the last estimate (flat tensor)."""
+        st, ptr, nbytes = B.pisco_debug_buffer(self._plan, which)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_debug_buffer")
+        ts = self._BUF_TYPES[which]
+        item = int(ts[2:])
+        view = _DevView(ptr, (nbytes // item,), ts)
+        self.stream.synchronize()
+        return torch.as_tensor(view, device="cuda").clone()
+
+    def close(self):
+        if getattr(self, "_plan", None):
+            B.pisco_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,210 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, stage by stage and
+end to end, on seeded synthetic data.
+
+Tolerances (derived from the arithmetic; the design doc lists them):
+  * Gram (FP64 on both sides): max |A_gpu - A_oracle| <= 1e-11 * max|A|.
+  * signal dimension k: exact (integer decision taken on FP64 Rayleigh quotients).
+  * signal projector U U^H (FP32 subspace iteration): max abs entry error <= 2e-5.
+  * G(x) (FP32 assembly): max |G_gpu - G_oracle| <= 2e-5 * |Lambda|.
+  * maps: relative L2 error after per-pixel channel-1 phase alignment <= 1e-4 inside the
+    phantom support eroded by 2 pixels, at pixels whose eigen-gap (lambda_2 - lambda_1)/|Lambda|
+    exceeds 1e-3; eigenvalue map |lambda_gpu - lambda_oracle| <= 1e-5 on the [0,1] scale.
+"""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from oracle import pisco_oracle as O
+from paper_2302_13431_gb300.phantoms import make_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU collection
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2302_13431_gb300 import _binding as B  # noqa: E402
+from paper_2302_13431_gb300.estimator import PiscoEstimator  # noqa: E402
+
+CASES = {
+    # name: grid, Q, calib, tau, shape, reduction, iters, phase
+    "2d_small_rect": ((64, 64), 8, (24, 24), 2, "rect", 1, 30, "linear"),
+    "2d_ragged": ((40, 48), 5, (18, 20), (2, 3), "ellipsoid", 2, 30, "poly4"),
+    "2d_q33": ((48, 48), 33, (20, 20), 2, "ellipsoid", 2, 20, "poly4"),
+    "3d_small": ((16, 24, 20), 4, (10, 12, 10), 2, "ellipsoid", 2, 30, "poly4"),
+    "2d_256_q32": ((256, 256), 32, (32, 32), 3, "ellipsoid", 4, 30, "poly4"),
+}
+_cache = {}
+
+
+def _run(name, seed=0):
+    key = (name, seed)
+    if key in _cache:
+        return _cache[key]
+    grid, Q, cs, tau, shape, red, iters, phase = CASES[name]
+    case = make_case(grid, Q, cs, seed=seed, phase=phase)
+    ref = O.estimate(case.calib, grid, tau, shape=shape, reduction=red, iters=iters, seed=seed,
+                     return_all=True, exact=False)
+    est = PiscoEstimator(grid, cs, Q, tau, kernel_shape=shape, reduction=red, iters=iters, seed=seed)
+    maps, eig = est(torch.from_numpy(case.calib).cuda())
+    torch.cuda.synchronize()
+    out = dict(case=case, ref=ref, est=est, maps=maps.cpu().numpy(), eig=eig.cpu().numpy(),
+               grid=grid, Q=Q, red=red, tau=tau, shape=shape)
+    out["A"] = est.debug_buffer(B.PISCO_BUF_GRAM).cpu().numpy()
+    out["U"] = est.debug_buffer(B.PISCO_BUF_SIGNAL).cpu().numpy()
+    out["w"] = est.debug_buffer(B.PISCO_BUF_WEIGHTS).cpu().numpy()
+    out["ritz"] = est.debug_buffer(B.PISCO_BUF_RITZ).cpu().numpy()
+    out["G"] = est.debug_buffer(B.PISCO_BUF_G).cpu().numpy()
+    out["V"] = est.debug_buffer(B.PISCO_BUF_V).cpu().numpy()
+    out["Y"] = est.debug_buffer(B.PISCO_BUF_Y).cpu().numpy()
+    out["info"] = est.info()
+    _cache[key] = out
+    return out
+
+
+def _align(v):
+    """Per-pixel phase alignment to channel 1 (v: [npix, Q])."""
+    ph = np.exp(-1j * np.angle(v[:, :1]))
+    return v * ph
+
+
+def _gated_mask(r, reduced=False):
+    case, ref = r["case"], r["ref"]
+    supp = np.abs(case.rho) > 0
+    inner = ndimage.binary_erosion(supp, iterations=2)
+    red = r["red"]
+    if reduced:
+        sl = tuple(slice(None, None, red) for _ in r["grid"])
+        inner = inner[sl]
+    # gap from LAPACK eigenvalues of the oracle's G (library route, reduced grid)
+    w = np.linalg.eigvalsh(ref["G"]) / ref["lam"].shape[0]
+    gap = (w[:, 1] - w[:, 0]).reshape(tuple(g // red for g in r["grid"]))
+    if reduced:
+        return inner & (gap > 1e-3)
+    # full grid: a pixel counts when its nearest reduced pixel is gapped
+    up = gap
+    for ax in range(gap.ndim):
+        up = np.repeat(up, red, axis=ax)
+    return inner & (up > 1e-3)
+
+
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33"])
+def test_gram_matches_explicit_CtC(name):
+    r = _run(name)
+    C = r["ref"]["C"]
+    A_ref = C.conj().T @ C
+    n = A_ref.shape[0]
+    A = r["A"].reshape(n, n)
+    err = np.abs(A - A_ref).max() / np.abs(A_ref).max()
+    assert err <= 1e-11, err
+
+
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_nullspace_split_and_projector(name):
+    r = _run(name)
+    ref = r["ref"]
+    k_ref = ref["U_sig"].shape[1]
+    assert r["info"]["k"] == k_ref
+    assert r["info"]["R"] == ref["V_null"].shape[1]
+    n = ref["U_sig"].shape[0]
+    m = r["w"].shape[0]
+    U = r["U"].reshape(n, m)[:, r["w"] > 0].astype(np.complex128)
+    P = U @ U.conj().T
+    P_ref = ref["U_sig"] @ ref["U_sig"].conj().T
+    err = np.abs(P - P_ref).max()
+    assert err <= 2e-5, err
+    # FP64 Rayleigh quotients of the decided Ritz values against LAPACK
+    lam = np.sort(ref["sigma"] ** 2)[::-1]
+    ritz = r["ritz"]
+    assert abs(ritz[0] - lam[0]) <= 1e-9 * lam[0]
+
+
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_G_field(name):
+    r = _run(name)
+    ref = r["ref"]
+    Q = r["Q"]
+    L = ref["lam"].shape[0]
+    npix = ref["G"].shape[0]
+    G = r["G"].reshape(Q, Q, npix).transpose(2, 0, 1)
+    err = np.abs(G - ref["G"]).max() / L
+    assert err <= 2e-5, err
+
+
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_lowres_images(name):
+    r = _run(name)
+    Q = r["Q"]
+    Y = r["Y"].reshape(Q, -1).T
+    ref = r["ref"]["y"]
+    err = np.abs(Y - ref).max() / np.abs(ref).max()
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_power_iteration_phase_and_eig(name):
+    r = _run(name)
+    Q = r["Q"]
+    m = _gated_mask(r, reduced=True).reshape(-1)
+    v = r["V"].reshape(Q, -1).T
+    vr = r["ref"]["v_aligned"]
+    err = np.linalg.norm((_align(v) - _align(vr))[m]) / np.linalg.norm(vr[m])
+    assert err <= 1e-4, err
+    eerr = np.abs(r["eig"].reshape(-1) - r["ref"]["eig"].reshape(-1))[m].max()
+    assert eerr <= 1e-5, eerr
+
+
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_end_to_end_maps(name):
+    r = _run(name)
+    Q = r["Q"]
+    a = r["maps"].reshape(Q, -1).T
+    b = r["ref"]["maps"].reshape(Q, -1).T
+    m = _gated_mask(r).reshape(-1)
+    err = np.linalg.norm((_align(a) - _align(b))[m]) / np.linalg.norm(b[m])
+    assert err <= 1e-4, err
+    nrm = np.linalg.norm(a, axis=1)
+    assert np.all((np.abs(nrm - 1) < 1e-5) | (nrm == 0))
+
+
+def test_host_entry_point_matches_device_entry_point():
+    grid, Q, cs, tau, shape, red, iters, phase = CASES["2d_ragged"]
+    case = make_case(grid, Q, cs, seed=4, phase=phase)
+    est = PiscoEstimator(grid, cs, Q, tau, kernel_shape=shape, reduction=red, iters=iters, host_io=True)
+    maps_d, eig_d = est(torch.from_numpy(case.calib).cuda())
+    maps_h = np.empty((Q,) + grid, np.complex64)
+    eig_h = np.empty(tuple(g // red for g in grid), np.float32)
+    est.estimate_host(case.calib, maps_h, eig_h)
+    np.testing.assert_array_equal(maps_h, maps_d.cpu().numpy())
+    np.testing.assert_array_equal(eig_h, eig_d.cpu().numpy())
+    est.close()
+
+
+def test_repeated_calls_are_deterministic():
+    r = _run("2d_ragged")
+    est = r["est"]
+    calib = torch.from_numpy(r["case"].calib).cuda()
+    m1, e1 = est(calib)
+    m2, e2 = est(calib)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(e1, e2)
+
+
+def test_zero_calibration_reports_rank_failure():
+    grid, Q, cs, tau = (32, 32), 4, (12, 12), 2
+    est = PiscoEstimator(grid, cs, Q, tau, kernel_shape="rect")
+    calib = torch.zeros((Q,) + cs, dtype=torch.complex64, device="cuda")
+    maps = torch.empty((Q,) + grid, dtype=torch.complex64, device="cuda")
+    st = est.estimate_into(calib, maps, None)
+    assert st == B.PISCO_ERR_RANK
+    assert bool(torch.isfinite(torch.view_as_real(maps)).all())
+    est.close()
+
+
+def test_invalid_arguments_are_rejected_without_launch():
+    grid, Q, cs = (32, 32), 4, (12, 12)
+    est = PiscoEstimator(grid, cs, Q, 2, kernel_shape="rect")
+    calib = torch.zeros((Q,) + cs, dtype=torch.complex64, device="cuda")
+    assert B.pisco_estimate(est._plan, calib.data_ptr(), 0, None) == B.PISCO_ERR_ARG
+    assert B.pisco_estimate(est._plan, calib.data_ptr() + 4, calib.data_ptr(), None) == B.PISCO_ERR_ARG
+    est.close()
