@@ -87,7 +87,11 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
  *   d_eig:   device, float [N_z/f][N_y/f][N_x/f] or NULL: lambda_min(G(x))/|Lambda| in [0,1]
  *            on the reduced grid (Rayleigh quotient after the last power iteration).
  * Synchronises the stream once at the end to read the device status word.  Pointers must
- * be 8-byte aligned.  Not thread-safe for one plan; distinct plans may run concurrently. */
+ * be 8-byte aligned.  Not thread-safe for one plan; distinct plans may run concurrently.
+ * After one call with a given (d_calib, d_maps, d_eig), the next call with the same pointers
+ * captures the whole path into a CUDA graph on the plan's stream and later calls with those
+ * pointers replay it (one graph launch instead of ~80 kernel launches); other pointers run
+ * eagerly.  The stream must not be under capture by the caller. */
 pisco_status pisco_estimate(pisco_plan_t plan, const void* d_calib, void* d_maps, float* d_eig);
 
 /* Same as pisco_estimate with HOST buffers of the same layouts: copies the calibration block
@@ -118,12 +122,16 @@ pisco_status pisco_plan_info(pisco_plan_t plan, int* R, int* k, size_t* workspac
  *                    PISCO_BUF_WEIGHTS[j] = 1), Lambda in lexicographic order, x fastest.
  *   PISCO_BUF_WEIGHTS float [m] 1 for signal columns, 0 otherwise.
  *   PISCO_BUF_RITZ   double [m] Ritz values of C^H C (FP64 Rayleigh quotients where decided).
- *   PISCO_BUF_G      complex64 [Q][Q][Nr], G_pq(x) on the reduced grid (Nr pixels).
+ *   PISCO_BUF_G      complex64 [Nr][Q][Q], G_pq(x) on the reduced grid (Nr pixels).
  *   PISCO_BUF_V      complex64 [Q][Nr] phase-aligned power-iteration vectors.
- *   PISCO_BUF_Y      complex64 [Q][Nr] apodised low-resolution coil images (Sec. V-D). */
+ *   PISCO_BUF_Y      complex64 [Q][Nr] apodised low-resolution coil images (Sec. V-D).
+ *   PISCO_BUF_BLOCK  complex64 [Q|Lambda|][m] orthonormal block before the Rayleigh-Ritz step.
+ *   PISCO_BUF_RITZ32 float [m] FP32 Ritz values of C^H C / scale, descending.
+ *   PISCO_BUF_SCALE  double: scale = max diagonal entry of C^H C. */
 enum {
   PISCO_BUF_LAGS = 0, PISCO_BUF_GRAM = 1, PISCO_BUF_SIGNAL = 2, PISCO_BUF_WEIGHTS = 3,
-  PISCO_BUF_RITZ = 4, PISCO_BUF_G = 5, PISCO_BUF_V = 6, PISCO_BUF_Y = 7
+  PISCO_BUF_RITZ = 4, PISCO_BUF_G = 5, PISCO_BUF_V = 6, PISCO_BUF_Y = 7, PISCO_BUF_BLOCK = 8,
+  PISCO_BUF_RITZ32 = 9, PISCO_BUF_SCALE = 10
 };
 pisco_status pisco_debug_buffer(pisco_plan_t plan, int which, void** dptr, size_t* bytes);
 

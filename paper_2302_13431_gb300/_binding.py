@@ -17,7 +17,7 @@ PISCO_OK, PISCO_ERR_ARG, PISCO_ERR_CUDA, PISCO_ERR_OOM, PISCO_ERR_RANK, PISCO_ER
 PISCO_KERNEL_RECT, PISCO_KERNEL_ELLIPSOID = 0, 1
 PISCO_FLAG_HOST_IO = 0x1
 (PISCO_BUF_LAGS, PISCO_BUF_GRAM, PISCO_BUF_SIGNAL, PISCO_BUF_WEIGHTS, PISCO_BUF_RITZ, PISCO_BUF_G,
- PISCO_BUF_V, PISCO_BUF_Y) = range(8)
+ PISCO_BUF_V, PISCO_BUF_Y, PISCO_BUF_BLOCK, PISCO_BUF_RITZ32, PISCO_BUF_SCALE) = range(11)
 
 
 class pisco_params(ctypes.Structure):

@@ -82,6 +82,7 @@ struct AxisView {
   int n_in;          // transformed axis length on input
   int n_out;         // transformed axis length on output
   long long inner;   // product of the axis lengths after the transformed axis
+  int pixel_major;   // 1 (needs outer == 1): write out[(o*inner + ii)*batch + b] instead
 };
 cudaError_t apply_axis_c2z(const float2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
 cudaError_t apply_axis_z(const double2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
@@ -90,29 +91,43 @@ cudaError_t apply_axis_c(const float2* in, const float2* M, float2* out, AxisVie
 // a1: pair products and Gram expansion
 cudaError_t gram_pair_products(const double2* S, int Q, long long nfreq, double2* P, cudaStream_t st);
 cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* lags, cudaStream_t st);
+cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* scale, cudaStream_t st);
 cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L, int nbox,
-                        double2* A, float2* A32, cudaStream_t st);
+                        const double* scale, double2* A, float2* A32, cudaStream_t st);
 
 // dense complex GEMM: C = alpha*op(A)*op(B) + beta*C, row-major, op in {'N','C'}
+// Split-K partials go to splitk_ws (ws_elems entries); tile_count must hold 4096 zeroed ints
+// (the kernel returns them to zero).  With splitk_ws == nullptr there is no split.
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* splitk_ws,
-                  size_t ws_elems, cudaStream_t st);
+                  size_t ws_elems, int* tile_count, cudaStream_t st);
 
 // a2: block eigensolver pieces
 cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, cudaStream_t st);
-cudaError_t eig_chol(const float2* Gm, int m, float2* L, DevStatus* status, cudaStream_t st);
-cudaError_t eig_trsm_rows(const float2* Y, const float2* L, int n, int m, float2* X, cudaStream_t st);
+cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_rel,
+                     const float* acc_in, float2* L, float* dout, float* diagR, DevStatus* status,
+                     cudaStream_t st);
+cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, int m, float2* X,
+                     cudaStream_t st);
+cudaError_t eig_chol_inv_warp(const float2* Gm, int m, const float* dscale, float shift_rel,
+                              const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
+                              cudaStream_t st);
+cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, float shift_rel,
+                                 const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
+                                 cudaStream_t st);
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
-                       DevStatus* status, cudaStream_t st);
-cudaError_t eig_scale_cols(float2* Y, int n, int m, const float* mu, float floor_rel, cudaStream_t st);
+                       float skip_rel, DevStatus* status, cudaStream_t st);
+cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, double2* Zb,
+                            cudaStream_t st);
+cudaError_t eig_pow(float* d, int m, float e, cudaStream_t st);
 cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
                             cudaStream_t st);
 cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, int nb_max,
                             double2* Xb, cudaStream_t st);
 cudaError_t eig_decide(const float* mu, int m, const int* band_idx, int nb_max, const double2* Xb,
-                       const double2* Zb, int n, double thr2, int Q, float* weights, double* ritz,
-                       DevStatus* status, cudaStream_t st);
+                       const double2* Zb, int n, double thr2, int Q, const double* scale,
+                       float* weights, double* ritz, DevStatus* status, cudaStream_t st);
 
 // a3: collapsed kernel and G field
 cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int m,

@@ -27,7 +27,10 @@ __global__ void __launch_bounds__(256) apply_axis_kernel(const Tin* __restrict__
       C sv = mk(decltype(acc.x)(s.x), decltype(acc.x)(s.y));
       cfma(acc, row[i], sv);
     }
-    out[(bo * v.n_out + o) * v.inner + ii] = acc;
+    if (v.pixel_major)
+      out[((long long)o * v.inner + ii) * v.batch + bo] = acc;
+    else
+      out[(bo * v.n_out + o) * v.inner + ii] = acc;
   }
 }
 

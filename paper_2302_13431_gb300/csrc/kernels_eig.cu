@@ -38,78 +38,496 @@ cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, c
 }
 
 // ---------------------------------------------------------------------------------------
-// Cholesky-QR pieces.  chol_kernel (1 CTA): Gm = L L^H for a small Hermitian positive
-// definite m x m matrix, right-looking in shared memory, two barriers per column; pivots
-// below 1e-12 * max diag are clamped (status ST_CHOL).  trsm_rows_kernel (many CTAs):
-// X = Y L^{-H} row by row (x L^H = y, forward substitution), one warp per row with L staged
-// in shared memory, so no explicit inverse is formed.
+// Cholesky-QR pieces.
+// chol_kernel (1 CTA, m <= 128): factor the Gram G = Y^H Y of an n x m block,
+//   - optional column scaling D = diag(dscale) (floored at 1e-6 * max, clamped to
+//     [1e-18, 1e18]): G <- D^-1 G D^-1, i.e. the block Y D^-1 is factored (the rescaling of
+//     orthogonal iteration by the previous diag(R), which keeps Cholesky-QR well conditioned);
+//   - optional diagonal shift s*trace(G) (shifted Cholesky-QR for an ill-conditioned block,
+//     Fukaya et al. 2020);
+//   - right-looking Cholesky G = L L^H in shared memory, 2D thread map, pivots below
+//     1e-12 * max diag clamped (status ST_CHOL);
+//   - writes Lout (lower, with the column scaling folded in: Lout = D L so that
+//     Y = X (D L)^H... see trsm) and diagR[j] = L_jj * d_j * (acc ? acc[j] : 1).
+// trsm_rows_kernel: X = (Y D^-1) L^-H row by row, one thread per row (x L^H = y D^-1 by
+// forward substitution, the row in registers, L broadcast from shared memory).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) chol_kernel(const float2* __restrict__ Gm, int m,
-                                                    float2* __restrict__ Lout, DevStatus* status) {
-  // left-looking: column j needs the finished columns k < j only.  Every warp recomputes the
-  // pivot of column j itself (no extra barrier), then fills its rows of column j.
+__global__ void __launch_bounds__(256) chol_kernel(const float2* __restrict__ Gm, int m,
+                                                   const float* __restrict__ dscale,
+                                                   float shift_rel,
+                                                   const float* __restrict__ acc_in,
+                                                   float2* __restrict__ Lout,
+                                                   float* __restrict__ dout,
+                                                   float* __restrict__ diagR,
+                                                   DevStatus* status) {
   extern __shared__ float2 sm[];
-  float2* Lm = sm;  // m*m, row-major, lower triangle
-  __shared__ float s_floor;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int i = tid; i < m * m; i += blockDim.x) Lm[i] = Gm[i];
-  __syncthreads();
-  if (tid == 0) {
-    float md = 0.f;
-    for (int i = 0; i < m; ++i) md = fmaxf(md, Lm[i * m + i].x);
-    s_floor = fmaxf(md, 1e-30f) * 1e-12f;
+  float2* Lm = sm;                                   // m*m
+  float* ds = reinterpret_cast<float*>(Lm + m * m);  // m (scaling)
+  float* dg = ds + m;                                // m (pivots)
+  __shared__ float s_floor, s_shift;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int tx = tid & 15, ty = tid >> 4;            // 16 x 16 map
+  if (warp == 0) {
+    float mx = 0.f;
+    if (dscale)
+      for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(dscale[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_floor = mx;
   }
   __syncthreads();
-  const float floor_piv = s_floor;
-  for (int j = 0; j < m; ++j) {
-    // pivot: G_jj - sum_{k<j} |L_jk|^2
-    float sq = 0.f;
-    for (int k = lane; k < j; k += 32) {
-      const float2 l = Lm[j * m + k];
-      sq += l.x * l.x + l.y * l.y;
-    }
+  for (int i = tid; i < m; i += nt) {
+    float d = 1.f;
+    if (dscale) d = fminf(fmaxf(fmaxf(fabsf(dscale[i]), 1e-6f * s_floor), 1e-18f), 1e18f);
+    if (!(d > 0.f) || !(d < 1e30f)) d = 1.f;
+    ds[i] = d;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, j = e % m;
+    const float2 g = Gm[e];
+    const float sc = 1.f / (ds[i] * ds[j]);
+    Lm[e] = make_float2(g.x * sc, g.y * sc);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float md = 0.f, tr = 0.f;
+    for (int i = lane; i < m; i += 32) { md = fmaxf(md, Lm[i * m + i].x); tr += Lm[i * m + i].x; }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    const float d = Lm[j * m + j].x - sq;
+    for (int o = 16; o > 0; o >>= 1) {
+      md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    }
+    if (lane == 0) {
+      s_shift = shift_rel * tr;
+      s_floor = (md + s_shift > 1e-30f) ? (md + s_shift) * 1e-12f : 1.0f;  // zero Gram: factor as I
+    }
+  }
+  __syncthreads();
+  const float floor_piv = s_floor, shift = s_shift;
+  for (int j = 0; j < m; ++j) {
+    const float d = Lm[j * m + j].x + shift;
     const float piv = sqrtf(d > floor_piv ? d : floor_piv);
     const float inv = 1.0f / piv;
-    for (int i = j + 1 + warp; i < m; i += nw) {
-      float ar = 0.f, ai = 0.f;
-      for (int k = lane; k < j; k += 32) {
-        const float2 a = Lm[i * m + k], b = Lm[j * m + k];  // a * conj(b)
-        ar += a.x * b.x + a.y * b.y;
-        ai += a.y * b.x - a.x * b.y;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ar += __shfl_xor_sync(0xffffffffu, ar, o);
-        ai += __shfl_xor_sync(0xffffffffu, ai, o);
-      }
-      if (lane == 0) {
-        const float2 g = Lm[i * m + j];
-        Lm[i * m + j] = make_float2((g.x - ar) * inv, (g.y - ai) * inv);
+    for (int i = j + 1 + tid; i < m; i += nt) {
+      const float2 v = Lm[i * m + j];
+      Lm[i * m + j] = make_float2(v.x * inv, v.y * inv);
+    }
+    if (tid == 0) {
+      dg[j] = piv;
+      if (!(d > floor_piv) && status) atomicOr(&status->flags, (int)ST_CHOL);
+    }
+    __syncthreads();
+    for (int i = j + 1 + ty; i < m; i += 16) {
+      const float2 a = Lm[i * m + j];
+      for (int k = j + 1 + tx; k <= i; k += 16) {
+        const float2 b = Lm[k * m + j];
+        float2 g = Lm[i * m + k];
+        g.x -= a.x * b.x + a.y * b.y;
+        g.y -= a.y * b.x - a.x * b.y;
+        Lm[i * m + k] = g;
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      Lm[j * m + j] = make_float2(piv, 0.f);
-      if (!(d > floor_piv) && status) atomicOr(&status->flags, (int)ST_CHOL);
-    }
-    // the diagonal entry is not read again by later columns' off-diagonal sums (k < j' only
-    // touches columns < j'), and the next pivot reads row j' only, so no barrier is needed here
   }
-  __syncthreads();
-  for (int e = tid; e < m * m; e += blockDim.x) {
+  for (int i = tid; i < m; i += nt) {
+    diagR[i] = dg[i] * ds[i] * (acc_in ? acc_in[i] : 1.f);
+    dout[i] = ds[i];
+  }
+  for (int e = tid; e < m * m; e += nt) {
     const int i = e / m, k = e % m;
-    Lout[e] = (k <= i) ? Lm[e] : make_float2(0.f, 0.f);
+    Lout[e] = (k < i) ? Lm[e] : (k == i ? make_float2(dg[i], 0.f) : make_float2(0.f, 0.f));
   }
 }
 
-__global__ void __launch_bounds__(256) trsm_rows_kernel(const float2* __restrict__ Y,
-                                                        const float2* __restrict__ Lg, int n, int m,
+// Blocked Cholesky-QR factor for m <= 96 (1 CTA, 256 threads, 16 x 16 blocks): the same
+// inputs and scaling/shift/floor rules as chol_kernel, but the result is the explicit
+// Rinv = D^-1 L^-H (upper triangular, m x m) so that X = Y * Rinv is a plain GEMM.
+//   - each diagonal block is factored and inverted by warp 0 in registers (row per lane);
+//   - panels L_IJ = A_IJ Linv_JJ^H and trailing updates A_IK -= L_IJ L_KJ^H are 16x16x16
+//     block products over all threads;
+//   - off-diagonal blocks of L^-1 follow by block diagonals:
+//     Linv_IJ = -Linv_II * sum_{K=J}^{I-1} L_IK Linv_KJ.
+// About 3 barriers per block column instead of 2 per column.
+constexpr int CB = 16;
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+__global__ void __launch_bounds__(256) chol_inv_blocked_kernel(const float2* __restrict__ Gm, int m,
+                                                               const float* __restrict__ dscale,
+                                                               float shift_rel,
+                                                               const float* __restrict__ acc_in,
+                                                               float2* __restrict__ Rinv,
+                                                               float* __restrict__ diagR,
+                                                               DevStatus* status) {
+  extern __shared__ float2 sm[];
+  const int NB = (m + CB - 1) / CB, M = NB * CB;
+  float2* A = sm;                                    // M*M, L in the lower triangle
+  float2* Li = A + M * M;                            // M*M, L^-1 (lower)
+  float* ds = reinterpret_cast<float*>(Li + M * M);  // M scaling
+  float* piv_s = ds + M;                             // M pivots
+  __shared__ float s_mx, s_shift, s_floor;
+  __shared__ int s_clamp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ei = tid >> 4, ej = tid & 15;            // element of a 16x16 block owned by this thread
+  const int pr = tid >> 2, pc = (tid & 3) * 4;       // panel: row pr (0..63), columns pc..pc+3
+  if (warp == 0) {
+    float mx = 0.f;
+    if (dscale)
+      for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(dscale[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) { s_mx = mx; s_clamp = 0; }
+  }
+  __syncthreads();
+  for (int i = tid; i < M; i += 256) {
+    float d = 1.f;
+    if (dscale && i < m) d = fminf(fmaxf(fmaxf(fabsf(dscale[i]), 1e-6f * s_mx), 1e-18f), 1e18f);
+    if (!(d > 0.f) || !(d < 1e30f)) d = 1.f;
+    ds[i] = d;
+  }
+  __syncthreads();
+  for (int r = tid >> 4; r < M; r += 16) {
+    for (int c = tid & 15; c < M; c += 16) {
+      float2 v = make_float2(0.f, 0.f);
+      if (r < m && c < m) {
+        const float2 g = Gm[r * m + c];
+        const float sc = 1.f / (ds[r] * ds[c]);
+        v = make_float2(g.x * sc, g.y * sc);
+      } else if (r == c) {
+        v = make_float2(1.f, 0.f);
+      }
+      A[r * M + c] = v;
+      Li[r * M + c] = make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float md = 0.f, tr = 0.f;
+    for (int i = lane; i < m; i += 32) { md = fmaxf(md, A[i * M + i].x); tr += A[i * M + i].x; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    }
+    if (lane == 0) {
+      s_shift = shift_rel * tr;
+      s_floor = (md + s_shift > 1e-30f) ? (md + s_shift) * 1e-12f : 1.0f;  // zero Gram: factor as I
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += 256) A[i * M + i].x += s_shift;
+  __syncthreads();
+  const float floor_piv = s_floor;
+  for (int J = 0; J < NB; ++J) {
+    const int j0 = J * CB;
+    // (a) panel factorisation of rows j0..M-1, columns j0..j0+15: thread (pr, pc) keeps 4
+    //     entries in registers; one barrier per pivot (the pivot row publishes its column)
+    const int row = j0 + pr;
+    const bool own = row < M;
+    float2 a[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t] = own ? A[row * M + j0 + pc + t] : make_float2(0.f, 0.f);
+    for (int j = 0; j < CB; ++j) {
+      // publish the current column j of the panel, then every thread reads the pivot and the
+      // entries of column j it needs from shared memory (one barrier per pivot)
+      const bool owns_j = own && ((j >> 2) == (pc >> 2));
+      if (owns_j) A[row * M + j0 + j] = a[j & 3];
+      __syncthreads();
+      const float dj = A[(j0 + j) * M + j0 + j].x;
+      const bool clamp = !(dj > floor_piv);
+      const float piv = sqrtf(clamp ? floor_piv : dj);
+      const float inv = 1.f / piv;
+      if (tid == 0) { piv_s[j0 + j] = piv; if (clamp) s_clamp = 1; }
+      if (own && pr >= j) {
+        const float2 ar = A[row * M + j0 + j];
+        const float2 lrj = make_float2(ar.x * inv, ar.y * inv);  // L[row][j0+j]
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int c = pc + t;
+          if (c > j && c <= pr) {
+            const float2 ac = A[(j0 + c) * M + j0 + j];
+            const float2 lcj = make_float2(ac.x * inv, ac.y * inv);  // L[j0+c][j0+j]
+            const float2 pp = cmulc(lrj, lcj);
+            a[t].x -= pp.x; a[t].y -= pp.y;
+          }
+        }
+        if (owns_j) a[j & 3] = (pr > j) ? lrj : make_float2(piv, 0.f);
+      }
+    }
+    __syncthreads();
+    if (own) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (pc + t <= pr) A[row * M + j0 + pc + t] = a[t];
+    }
+    __syncthreads();
+    // (b) trailing update A_IK -= L_IJ L_KJ^H for J < K <= I
+    for (int I = J + 1; I < NB; ++I)
+      for (int K = J + 1; K <= I; ++K) {
+        const int i = I * CB + ei, k = K * CB + ej;
+        if (K == I && ej > ei) continue;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < CB; ++t) {
+          const float2 p = cmulc(A[i * M + j0 + t], A[k * M + j0 + t]);
+          acc.x += p.x; acc.y += p.y;
+        }
+        const float2 g = A[i * M + k];
+        A[i * M + k] = make_float2(g.x - acc.x, g.y - acc.y);
+      }
+    __syncthreads();
+  }
+  // (c) inverses of all diagonal blocks at once: warp J inverts block J (lane c < 16: column c)
+  if (warp < NB && lane < CB) {
+    const int j0 = warp * CB, c = lane;
+    float2 x[CB];
+#pragma unroll
+    for (int r = 0; r < CB; ++r) {
+      float2 acc = make_float2(r == c ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < r; ++k) {
+        const float2 l = A[(j0 + r) * M + j0 + k];
+        acc.x -= l.x * x[k].x - l.y * x[k].y;
+        acc.y -= l.x * x[k].y + l.y * x[k].x;
+      }
+      const float di = 1.f / A[(j0 + r) * M + j0 + r].x;
+      x[r] = (r >= c) ? make_float2(acc.x * di, acc.y * di) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < CB; ++r) Li[(j0 + r) * M + j0 + c] = x[r];
+  }
+  __syncthreads();
+  // (d) off-diagonal blocks of L^-1 by block diagonals:
+  //   T_IJ = sum_{K=J}^{I-1} L_IK Linv_KJ (staged in Li's (I,J) block), Linv_IJ = -Linv_II T_IJ
+  for (int d = 1; d < NB; ++d) {
+    float2 res[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const int I = d + u;
+      if (I >= NB) break;
+      const int J = I - d;
+      const int i = I * CB + ei, j = J * CB + ej;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int K = J; K < I; ++K) {
+#pragma unroll
+        for (int t = 0; t < CB; ++t) {
+          const float2 l = A[i * M + K * CB + t];
+          const float2 xx = Li[(K * CB + t) * M + j];
+          acc.x += l.x * xx.x - l.y * xx.y;
+          acc.y += l.x * xx.y + l.y * xx.x;
+        }
+      }
+      res[u] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const int I = d + u;
+      if (I >= NB) break;
+      Li[(I * CB + ei) * M + (I - d) * CB + ej] = res[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const int I = d + u;
+      if (I >= NB) break;
+      const int J = I - d;
+      const int i = I * CB + ei, j = J * CB + ej;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < CB; ++t) {
+        const float2 l = Li[i * M + I * CB + t];
+        const float2 xx = Li[(I * CB + t) * M + j];
+        acc.x -= l.x * xx.x - l.y * xx.y;
+        acc.y -= l.x * xx.y + l.y * xx.x;
+      }
+      res[u] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const int I = d + u;
+      if (I >= NB) break;
+      Li[(I * CB + ei) * M + (I - d) * CB + ej] = res[u];
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += 256) diagR[i] = piv_s[i] * ds[i] * (acc_in ? acc_in[i] : 1.f);
+  for (int r = tid >> 4; r < m; r += 16)
+    for (int c = tid & 15; c < m; c += 16) {
+      const float2 v = Li[c * M + r];
+      const float id = 1.f / ds[r];
+      Rinv[r * m + c] = make_float2(v.x * id, -v.y * id);
+    }
+  if (tid == 0 && s_clamp && status) atomicOr(&status->flags, (int)ST_CHOL);
+}
+
+// Single-warp Cholesky-QR factor (m <= 96): same inputs, scaling, shift and floor rules as
+// chol_inv_blocked_kernel and the same outputs (Rinv = D^-1 L^-H, diag(R)).  One warp owns the
+// whole factorisation, so its m pivot steps are ordered by __syncwarp only (no block
+// barriers): the right-looking update touches the lower triangle with lanes striding the
+// rows, and L^-1 is formed row by row with lanes striding the columns.
+__global__ void __launch_bounds__(32) chol_inv_warp_kernel(const float2* __restrict__ Gm, int m,
+                                                           const float* __restrict__ dscale,
+                                                           float shift_rel,
+                                                           const float* __restrict__ acc_in,
+                                                           float2* __restrict__ Rinv,
+                                                           float* __restrict__ diagR,
+                                                           DevStatus* status) {
+  extern __shared__ float2 sm[];
+  float2* A = sm;                                    // m*m (lower triangle: L)
+  float2* Li = A + m * m;                            // m*m (lower triangle: L^-1)
+  float* ds = reinterpret_cast<float*>(Li + m * m);  // m
+  float* pv = ds + m;                                // m
+  const int lane = threadIdx.x;
+  float mx = 0.f;
+  if (dscale)
+    for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(dscale[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int i = lane; i < m; i += 32) {
+    float d = 1.f;
+    if (dscale) d = fminf(fmaxf(fmaxf(fabsf(dscale[i]), 1e-6f * mx), 1e-18f), 1e18f);
+    if (!(d > 0.f) || !(d < 1e30f)) d = 1.f;
+    ds[i] = d;
+  }
+  __syncwarp();
+  float md = 0.f, tr = 0.f;
+  for (int r = 0; r < m; ++r) {
+    const float dr = ds[r];
+    for (int c = lane; c <= r; c += 32) {
+      const float2 g = Gm[r * m + c];
+      const float sc = 1.f / (dr * ds[c]);
+      A[r * m + c] = make_float2(g.x * sc, g.y * sc);
+      if (c == r) { md = fmaxf(md, g.x * sc); tr += g.x * sc; }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  }
+  const float shift = shift_rel * tr;
+  const float floor_piv = (md + shift > 1e-30f) ? (md + shift) * 1e-12f : 1.0f;
+  __syncwarp();
+  int clamped = 0;
+  for (int j = 0; j < m; ++j) {
+    const float d = A[j * m + j].x + shift;
+    const bool clamp = !(d > floor_piv);
+    clamped |= clamp;
+    const float piv = sqrtf(clamp ? floor_piv : d);
+    const float inv = 1.f / piv;
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const float2 v = A[i * m + j];
+      A[i * m + j] = make_float2(v.x * inv, v.y * inv);
+    }
+    if (lane == 0) pv[j] = piv;
+    __syncwarp();
+    // trailing lower triangle: rows i > j (lanes stride i), columns j < k <= i
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const float2 a = A[i * m + j];
+      for (int k = j + 1; k <= i; ++k) {
+        const float2 b = A[k * m + j];
+        float2 g = A[i * m + k];
+        const float2 p = cmulc(a, b);
+        g.x -= p.x; g.y -= p.y;
+        A[i * m + k] = g;
+      }
+    }
+    __syncwarp();
+  }
+  // L^-1 row by row: Li[r][c] = (delta_rc - sum_{c<=k<r} L[r][k] Li[k][c]) / L[r][r]
+  for (int r = 0; r < m; ++r) {
+    const float di = 1.f / pv[r];
+    for (int c = lane; c <= r; c += 32) {
+      float2 acc = make_float2(r == c ? 1.f : 0.f, 0.f);
+      for (int k = c; k < r; ++k) {
+        const float2 l = A[r * m + k];
+        const float2 x = Li[k * m + c];
+        acc.x -= l.x * x.x - l.y * x.y;
+        acc.y -= l.x * x.y + l.y * x.x;
+      }
+      Li[r * m + c] = make_float2(acc.x * di, acc.y * di);
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) diagR[i] = pv[i] * ds[i] * (acc_in ? acc_in[i] : 1.f);
+  // Rinv[r][c] = conj(Li[c][r]) / d_r (upper triangular)
+  for (int r = 0; r < m; ++r) {
+    const float id = 1.f / ds[r];
+    for (int c = lane; c < m; c += 32) {
+      float2 v = make_float2(0.f, 0.f);
+      if (c >= r) { const float2 x = Li[c * m + r]; v = make_float2(x.x * id, -x.y * id); }
+      Rinv[r * m + c] = v;
+    }
+  }
+  if (clamped && status) atomicOr(&status->flags, (int)ST_CHOL);
+}
+
+cudaError_t eig_chol_inv_warp(const float2* Gm, int m, const float* dscale, float shift_rel,
+                              const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
+                              cudaStream_t st) {
+  if (m > 96) return cudaErrorInvalidValue;
+  const size_t smem = 2 * (size_t)m * m * sizeof(float2) + 2 * m * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(chol_inv_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  chol_inv_warp_kernel<<<1, 32, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, Rinv, diagR, status);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// One thread per row r: x L^H = y with y = Y[r] D^-1, i.e. for c = 0..m-1
+//   x_c = (y_c - sum_{k<c} x_k conj(L[c][k])) / L[c][c].
+template <int MP>
+__global__ void __launch_bounds__(128) trsm_rows_kernel(const float2* __restrict__ Y,
+                                                        const float2* __restrict__ Lg,
+                                                        const float* __restrict__ ds, int n, int m,
                                                         float2* __restrict__ X) {
   extern __shared__ float2 sm[];
-  float2* Ls = sm;  // m*m
+  float2* Ls = sm;                                       // m*m
+  float* dinv = reinterpret_cast<float*>(Ls + m * m);    // m
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ls[e] = Lg[e];
+  for (int e = threadIdx.x; e < m; e += blockDim.x) dinv[e] = 1.0f / ds[e];
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const float2* y = Y + (long long)r * m;
+  float2 x[MP];
+#pragma unroll
+  for (int c = 0; c < MP; ++c) {
+    if (c < m) {
+      const float2 yc = y[c];
+      float ar = yc.x * dinv[c], ai = yc.y * dinv[c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) {
+        const float2 l = Ls[c * m + k];  // x_k conj(l)
+        ar -= x[k].x * l.x + x[k].y * l.y;
+        ai -= x[k].y * l.x - x[k].x * l.y;
+      }
+      const float di = 1.0f / Ls[c * m + c].x;
+      x[c] = make_float2(ar * di, ai * di);
+    } else {
+      x[c] = make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < MP; ++c)
+    if (c < m) X[(long long)r * m + c] = x[c];
+}
+
+// warp-per-row fallback for m > 64: lanes split the k sum, the row lives in registers
+__global__ void __launch_bounds__(256) trsm_rows_warp_kernel(const float2* __restrict__ Y,
+                                                             const float2* __restrict__ Lg,
+                                                             const float* __restrict__ ds, int n,
+                                                             int m, float2* __restrict__ X) {
+  extern __shared__ float2 sm[];
+  float2* Ls = sm;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ls[e] = Lg[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -121,10 +539,9 @@ __global__ void __launch_bounds__(256) trsm_rows_kernel(const float2* __restrict
     for (int s = 0; s < 4; ++s) {
       xs[s] = make_float2(0.f, 0.f);
       const int k = s * 32 + lane;
-      ys[s] = (k < m) ? y[k] : make_float2(0.f, 0.f);
+      ys[s] = (k < m) ? make_float2(y[k].x / ds[k], y[k].y / ds[k]) : make_float2(0.f, 0.f);
     }
     for (int c = 0; c < m; ++c) {
-      // sum_{k<c} x_k conj(L[c][k]), lanes split k
       float ar = 0.f, ai = 0.f;
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
@@ -161,29 +578,57 @@ __global__ void __launch_bounds__(256) trsm_rows_kernel(const float2* __restrict
   }
 }
 
-cudaError_t eig_chol(const float2* Gm, int m, float2* L, DevStatus* status, cudaStream_t st) {
-  const size_t smem = (size_t)m * m * sizeof(float2);
+cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_rel,
+                     const float* acc_in, float2* L, float* dout, float* diagR, DevStatus* status,
+                     cudaStream_t st) {
+  if (m > 128) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)m * m * sizeof(float2) + 2 * m * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  chol_kernel<<<1, 1024, smem, st>>>(Gm, m, L, status);
+  chol_kernel<<<1, 256, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, L, dout, diagR, status);
   ++g_launches;
   return cudaGetLastError();
 }
 
-cudaError_t eig_trsm_rows(const float2* Y, const float2* L, int n, int m, float2* X, cudaStream_t st) {
-  if (m > 128) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)m * m * sizeof(float2);
+cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, float shift_rel,
+                                 const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
+                                 cudaStream_t st) {
+  if (m > 96) return cudaErrorInvalidValue;
+  const int M = ((m + CB - 1) / CB) * CB;
+  const size_t smem = 2 * (size_t)M * M * sizeof(float2) + 2 * M * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(chol_inv_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  int blocks = (n + 7) / 8;
-  if (blocks > 152) blocks = 152;
-  trsm_rows_kernel<<<blocks, 256, smem, st>>>(Y, L, n, m, X);
+  chol_inv_blocked_kernel<<<1, 256, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, Rinv, diagR, status);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, int m, float2* X,
+                     cudaStream_t st) {
+  if (m > 128) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)m * m * sizeof(float2) + m * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(trsm_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(trsm_rows_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(trsm_rows_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (m <= 32) {
+    trsm_rows_kernel<32><<<(n + 127) / 128, 128, smem, st>>>(Y, L, ds, n, m, X);
+  } else if (m <= 64) {
+    trsm_rows_kernel<64><<<(n + 127) / 128, 128, smem, st>>>(Y, L, ds, n, m, X);
+  } else {
+    int blocks = (n + 7) / 8;
+    if (blocks > 152) blocks = 152;
+    trsm_rows_warp_kernel<<<blocks, 256, smem, st>>>(Y, L, ds, n, m, X);
+  }
   ++g_launches;
   return cudaGetLastError();
 }
@@ -204,7 +649,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
                                                      float* __restrict__ mu,
                                                      float2* __restrict__ Vout,
                                                      float2* __restrict__ Vg, int max_sweeps,
-                                                     DevStatus* status) {
+                                                     float skip_rel, DevStatus* status) {
   extern __shared__ float2 sm[];
   float2* Bs = sm;                                         // m*m
   float2* Vw = VSMEM ? (Bs + m * m) : Vg;                  // m*m
@@ -223,14 +668,23 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
     Vw[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < 32) {
     float bn = 0.f;
-    for (int i = 0; i < m; ++i) bn = fmaxf(bn, fabsf(Bs[i * m + i].x));
-    s_bnorm = bn;
-    s_rot = 0;
+    for (int i = tid; i < m; i += 32) bn = fmaxf(bn, fabsf(Bs[i * m + i].x));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+    if (tid == 0) { s_bnorm = bn; s_rot = 0; }
   }
   __syncthreads();
   const float abs_tol = 3e-9f * s_bnorm;
+  // Ritz values below 1e-4 * max are far below any threshold split (thr^2 >= 1e-3 for the
+  // supported thresholds is not assumed; the split is re-decided in FP64): rotations among
+  // such vectors only reorder noise, so their relative test uses this floor.
+  const float noise = 1e-4f * s_bnorm;
+  // pairs whose diagonals both lie below skip_rel * max are left alone: such Ritz vectors are
+  // far below the threshold split and mixing among them cannot change the signal subspace
+  const float skip_below = skip_rel * s_bnorm;
+  const int tx = tid & 31, ty = tid >> 5, nty = nt >> 5;  // 32 x (nt/32) map
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     for (int r = 0; r < m - 1; ++r) {
@@ -244,7 +698,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
         const float app = Bs[p * m + p].x, aqq = Bs[q * m + q].x;
         float c = 1.f, ser = 0.f, sei = 0.f;
         int on = 0;
-        if (mag > 3e-7f * sqrtf(fabsf(app * aqq)) + abs_tol) {
+        const bool both_low = fabsf(app) < skip_below && fabsf(aqq) < skip_below;
+        if (!both_low && mag > 3e-7f * sqrtf(fmaxf(fabsf(app), noise) * fmaxf(fabsf(aqq), noise)) + abs_tol) {
           const float z = (app - aqq) / (2.f * mag);
           const float t = (z >= 0.f ? 1.f : -1.f) / (fabsf(z) + sqrtf(1.f + z * z));
           c = rsqrtf(1.f + t * t);
@@ -258,8 +713,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
       }
       __syncthreads();
       // 2x2 blocks: rows of pair i, columns of pair j
-      for (int e = tid; e < half * half; e += nt) {
-        const int i = e / half, j = e % half;
+      for (int i = ty; i < half; i += nty)
+      for (int j = tx; j < half; j += 32) {
         const int ai = act[i], aj = act[j];
         if (!ai && !aj) continue;
         const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
@@ -285,8 +740,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
         Bs[pi * m + pj] = x00; Bs[pi * m + qj] = x01; Bs[qi * m + pj] = x10; Bs[qi * m + qj] = x11;
       }
       // V <- V J: row k, pair j
-      for (int e = tid; e < m * half; e += nt) {
-        const int k = e / half, j = e % half;
+      for (int k = ty; k < m; k += nty)
+      for (int j = tx; j < half; j += 32) {
         if (!act[j]) continue;
         const int pj = pp[j], qj = qq[j];
         const float c = rc[4 * j];
@@ -325,7 +780,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
 }
 
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
-                       DevStatus* status, cudaStream_t st) {
+                       float skip_rel, DevStatus* status, cudaStream_t st) {
   // V must have room for 2*m*m entries: [0, m*m) output, [m*m, 2*m*m) scratch
   const bool vsmem = m <= 96;
   const size_t smem = (size_t)(vsmem ? 2 : 1) * m * m * sizeof(float2) + 4 * (m / 2) * sizeof(float) +
@@ -338,30 +793,21 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
   }
   const int threads = 512;
   if (vsmem)
-    jacobi_kernel<true><<<1, threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps, status);
+    jacobi_kernel<true><<<1, threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps, skip_rel, status);
   else
-    jacobi_kernel<false><<<1, threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps, status);
+    jacobi_kernel<false><<<1, threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps, skip_rel, status);
   ++g_launches;
   return cudaGetLastError();
 }
 
-// Y[:, j] /= max(mu_j, floor_rel*mu_0): keeps the block well conditioned for Cholesky-QR.
-__global__ void scale_cols_kernel(float2* Y, int n, int m, const float* __restrict__ mu, float floor_rel) {
-  const long long total = (long long)n * m;
-  const float top = fmaxf(mu[0], 1e-30f);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % m);
-    const float d = fmaxf(mu[c], floor_rel * top);
-    float2 v = Y[idx];
-    Y[idx] = make_float2(v.x / d, v.y / d);
-  }
+// d <- |d|^e (rescales diag(R) of `cur` Gram products to the next group's product count)
+__global__ void pow_kernel(float* d, int m, float e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) d[i] = powf(fabsf(d[i]), e);
 }
 
-cudaError_t eig_scale_cols(float2* Y, int n, int m, const float* mu, float floor_rel, cudaStream_t st) {
-  long long blocks = ((long long)n * m + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  scale_cols_kernel<<<(unsigned)blocks, 256, 0, st>>>(Y, n, m, mu, floor_rel);
+cudaError_t eig_pow(float* d, int m, float e, cudaStream_t st) {
+  pow_kernel<<<(m + 127) / 128, 128, 0, st>>>(d, m, e);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -422,13 +868,65 @@ cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, 
   return cudaGetLastError();
 }
 
+// Zb = A * Xb for the FP64 Gram A (n x n) and the nb <= 16 band columns: one warp per row of
+// A (lanes stride the row, so loads are coalesced), Xb staged in shared memory in chunks,
+// FP64 accumulation, warp reduction.  FP64-FMA bound: n^2 * nb complex MACs.
+template <int NBV>
+__global__ void __launch_bounds__(256) band_matvec_kernel(const double2* __restrict__ A,
+                                                          const double2* __restrict__ Xb, int n,
+                                                          double2* __restrict__ Zb) {
+  constexpr int KC = 256;  // rows of Xb per chunk (32 KiB of shared memory for 8 columns)
+  __shared__ double2 xs[KC * NBV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * 8 + warp;
+  double2 acc[NBV];
+#pragma unroll
+  for (int c = 0; c < NBV; ++c) acc[c] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    const int kc = min(KC, n - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kc * NBV; e += blockDim.x) xs[e] = Xb[(long long)k0 * NBV + e];
+    __syncthreads();
+    if (r < n) {
+      const double2* arow = A + (long long)r * n + k0;
+      for (int k = lane; k < kc; k += 32) {
+        const double2 a = arow[k];
+#pragma unroll
+        for (int c = 0; c < NBV; ++c) cfma(acc[c], a, xs[k * NBV + c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NBV; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+    }
+  }
+  if (r < n && lane == 0) {
+#pragma unroll
+    for (int c = 0; c < NBV; ++c) Zb[(long long)r * NBV + c] = acc[c];
+  }
+}
+
+cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, double2* Zb,
+                            cudaStream_t st) {
+  if (nb != 8) return cudaErrorInvalidValue;
+  band_matvec_kernel<8><<<(n + 7) / 8, 256, 0, st>>>(A, Xb, n, Zb);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 // FP64 Rayleigh quotients mu~_c = Re(x_c^H A x_c) / (x_c^H x_c) of the band vectors, then the
 // threshold split on the FP64 values (band) and the FP32 values (far from the threshold).
 __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ mu, int m,
                                                      const int* __restrict__ band_idx, int nb_max,
                                                      const double2* __restrict__ Xb,
                                                      const double2* __restrict__ Zb, int n,
-                                                     double thr2, int Q, float* __restrict__ w,
+                                                     double thr2, int Q,
+                                                     const double* __restrict__ scale,
+                                                     float* __restrict__ w,
                                                      double* __restrict__ ritz, DevStatus* status) {
   __shared__ double num[32], den[32];
   __shared__ double s_lmax;
@@ -453,8 +951,9 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
   __syncthreads();
   const double lmax = s_lmax;
   const double theta = thr2 * lmax;
+  const double sc = *scale;  // FP32 Ritz values are of the Gram divided by `scale`
   for (int j = tid; j < m; j += blockDim.x) {
-    double v = (double)mu[j];
+    double v = (double)mu[j] * sc;
     for (int c = 0; c < nb_max; ++c)
       if (band_idx[c] == j && den[c] > 0.0) v = num[c] / den[c];
     ritz[j] = v;
@@ -483,9 +982,9 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
 }
 
 cudaError_t eig_decide(const float* mu, int m, const int* band_idx, int nb_max, const double2* Xb,
-                       const double2* Zb, int n, double thr2, int Q, float* weights, double* ritz,
-                       DevStatus* status, cudaStream_t st) {
-  decide_kernel<<<1, 256, 0, st>>>(mu, m, band_idx, nb_max, Xb, Zb, n, thr2, Q, weights, ritz, status);
+                       const double2* Zb, int n, double thr2, int Q, const double* scale,
+                       float* weights, double* ritz, DevStatus* status, cudaStream_t st) {
+  decide_kernel<<<1, 256, 0, st>>>(mu, m, band_idx, nb_max, Xb, Zb, n, thr2, Q, scale, weights, ritz, status);
   ++g_launches;
   return cudaGetLastError();
 }

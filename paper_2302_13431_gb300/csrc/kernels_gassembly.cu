@@ -84,13 +84,14 @@ cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int 
   return cudaGetLastError();
 }
 
-// G <- |Lambda| I - G  (G holds sum_d K_pq[d] e^{i 2 pi d x} on entry), layout [Q][Q][npix].
+// G <- |Lambda| I - G  (G holds sum_d K_pq[d] e^{i 2 pi d x} on entry), layout [npix][Q][Q].
 __global__ void add_identity_kernel(float2* G, int Q, long long npix, float lam_size) {
   const long long total = (long long)Q * Q * npix;
+  const int QQ = Q * Q;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long pq = idx / npix;
-    const int p = (int)(pq / Q), q = (int)(pq % Q);
+    const int pq = (int)(idx % QQ);
+    const int p = pq / Q, q = pq % Q;
     float2 v = G[idx];
     G[idx] = make_float2((p == q ? lam_size : 0.f) - v.x, -v.y);
   }

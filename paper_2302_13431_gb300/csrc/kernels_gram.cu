@@ -57,11 +57,32 @@ cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* 
   return cudaGetLastError();
 }
 
-// A[(p,i),(q,j)] = R_pq[m_i - m_j] for p <= q, and the Hermitian mirror for p > q.
+// scale = max_p R_pp[0] (the largest diagonal entry of C^H C); 1 if the data are all zero.
+// The FP32 copy of the Gram is divided by it so that products of the iterated block stay in
+// FP32 range whatever the data scale.
+__global__ void gram_scale_kernel(const double2* __restrict__ lags, int Q, int nbox, int lag0,
+                                  double* __restrict__ scale) {
+  double mx = 0.0;
+  for (int p = threadIdx.x; p < Q; p += 32) mx = fmax(mx, lags[((long long)p * Q + p) * nbox + lag0].x);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (threadIdx.x == 0) *scale = mx > 0.0 ? mx : 1.0;
+}
+
+cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* scale, cudaStream_t st) {
+  gram_scale_kernel<<<1, 32, 0, st>>>(lags, Q, nbox, lag0, scale);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// A[(p,i),(q,j)] = R_pq[m_i - m_j] for p <= q, and the Hermitian mirror for p > q;
+// A32 = A / scale in FP32.
 __global__ void gram_expand_kernel(const double2* __restrict__ lags,
                                    const int* __restrict__ lag_of_ij, int Q, int L, int nbox,
+                                   const double* __restrict__ scale,
                                    double2* __restrict__ A, float2* __restrict__ A32) {
   const long long n = (long long)Q * L;
+  const double inv = 1.0 / *scale;
   const long long total = n * n;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -76,16 +97,16 @@ __global__ void gram_expand_kernel(const double2* __restrict__ lags,
       v = cconj(lags[((long long)q * Q + p) * nbox + lag_of_ij[j * L + i]]);
     }
     A[idx] = v;
-    A32[idx] = to_c(v);
+    A32[idx] = make_float2((float)(v.x * inv), (float)(v.y * inv));
   }
 }
 
 cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L, int nbox,
-                        double2* A, float2* A32, cudaStream_t st) {
+                        const double* scale, double2* A, float2* A32, cudaStream_t st) {
   const long long n = (long long)Q * L;
   long long blocks = (n * n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  gram_expand_kernel<<<(unsigned)blocks, 256, 0, st>>>(lags, lag_of_ij, Q, L, nbox, A, A32);
+  gram_expand_kernel<<<(unsigned)blocks, 256, 0, st>>>(lags, lag_of_ij, Q, L, nbox, scale, A, A32);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -63,9 +63,85 @@ __global__ void __launch_bounds__(128) interp_final_kernel(const float2* __restr
   }
 }
 
+// Tiled form for M != nullptr: a CTA computes a TO x TI tile of (output index along the axis,
+// inner index) for every coil.  The TO rows of M are staged once; the coils are processed in
+// chunks of QC whose T rows [n_in][TI] are staged in shared memory, so T is read from L2 once
+// per tile column instead of once per output pixel.  Each thread keeps all its coils in
+// registers (QB <= 64), normalises and writes the maps once.
+template <int QB>
+__global__ void __launch_bounds__(256) interp_tiled_kernel(const float2* __restrict__ T,
+                                                           const float2* __restrict__ M, int Q,
+                                                           int n_in, int n_out, long long inner,
+                                                           float2* __restrict__ maps) {
+  constexpr int TO = 16, TI = 16, QC = 4;
+  extern __shared__ float2 sm[];
+  float2* Ms = sm;                      // TO * n_in
+  float2* Ts = Ms + TO * n_in;          // QC * n_in * TI
+  const int tid = threadIdx.x;
+  const int to = tid / TI, ti = tid % TI;
+  const int o0 = blockIdx.y * TO;
+  const long long i0 = (long long)blockIdx.x * TI;
+  const int o = o0 + to;
+  const long long ii = i0 + ti;
+  const long long plane_in = (long long)n_in * inner, plane_out = (long long)n_out * inner;
+  for (int e = tid; e < TO * n_in; e += 256) {
+    const int r = e / n_in, c = e % n_in;
+    Ms[e] = (o0 + r < n_out) ? M[(long long)(o0 + r) * n_in + c] : make_float2(0.f, 0.f);
+  }
+  float2 acc[QB];
+#pragma unroll
+  for (int c = 0; c < QB; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q0 = 0; q0 < QB; q0 += QC) {
+    if (q0 >= Q) break;
+    __syncthreads();
+    for (int e = tid; e < QC * n_in * TI; e += 256) {
+      const int c = e / (n_in * TI);
+      const int rem = e % (n_in * TI);
+      const int i = rem / TI, t = rem % TI;
+      float2 v = make_float2(0.f, 0.f);
+      if (q0 + c < Q && i0 + t < inner) v = T[(long long)(q0 + c) * plane_in + (long long)i * inner + i0 + t];
+      Ts[e] = v;
+    }
+    __syncthreads();
+    const float2* mrow = Ms + to * n_in;
+    for (int i = 0; i < n_in; ++i) {
+      const float2 mo = mrow[i];
+#pragma unroll
+      for (int c = 0; c < QC; ++c) cfma(acc[q0 + c], mo, Ts[(c * n_in + i) * TI + ti]);
+    }
+  }
+  if (o >= n_out || ii >= inner) return;
+  float n2 = 0.f;
+#pragma unroll
+  for (int c = 0; c < QB; ++c)
+    if (c < Q) n2 += acc[c].x * acc[c].x + acc[c].y * acc[c].y;
+  const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
+  const long long out0 = (long long)o * inner + ii;
+#pragma unroll
+  for (int c = 0; c < QB; ++c)
+    if (c < Q) maps[(long long)c * plane_out + out0] = make_float2(acc[c].x * s, acc[c].y * s);
+}
+
 cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long long /*unused*/,
                                    int n_in, int n_out, long long inner, float2* maps,
                                    cudaStream_t st) {
+  if (M != nullptr && n_in <= 128 && Q <= 64) {
+    const size_t smem = (size_t)(16 * n_in + 4 * n_in * 16) * sizeof(float2);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(interp_tiled_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(interp_tiled_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    dim3 grid((unsigned)((inner + 15) / 16), (unsigned)((n_out + 15) / 16));
+    if (Q <= 32)
+      interp_tiled_kernel<32><<<grid, 256, smem, st>>>(T, M, Q, n_in, n_out, inner, maps);
+    else
+      interp_tiled_kernel<64><<<grid, 256, smem, st>>>(T, M, Q, n_in, n_out, inner, maps);
+    ++g_launches;
+    return cudaGetLastError();
+  }
   const long long total = (long long)n_out * inner;
   long long blocks = (total + 127) / 128;
   if (blocks > 152 * 32) blocks = 152 * 32;

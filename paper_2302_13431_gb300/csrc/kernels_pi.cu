@@ -3,11 +3,10 @@
 // of Sec. V-D: v <- v * rho/|rho| with rho = v^H y(x), y the apodised low-resolution coil
 // images, so that the coil-combined reconstruction becomes real and non-negative.
 //
-// A CTA holds PIX pixels; the Q x Q matrix of every pixel is staged once in shared memory
-// (pixel-major, row p contiguous) and the Q threads of a pixel each own one coil.  Thread q
-// forms (G v)_q = sum_p conj(G_pq) v_p from row p (Hermitian), which makes the Q lanes read
-// consecutive shared-memory words; v is broadcast from shared memory.  All iterations run
-// out of shared memory, so G is read from HBM once.
+// A CTA holds PIX pixels and the Q threads of a pixel each own one coil.  G is stored
+// pixel-major ([pixel][p][q]); thread q keeps column q of its pixel's G in registers, so every
+// iteration (G v)_q = sum_p conj(G_pq) v_p (G Hermitian) reads only v from shared memory
+// (a broadcast).  G is read from HBM once, coalesced across the Q threads.
 #include "common.cuh"
 
 namespace pisco {
@@ -37,45 +36,36 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
                                                  unsigned long long seed, float2* __restrict__ V,
                                                  float* __restrict__ eig) {
   constexpr int PIX = 256 / QP;
-  extern __shared__ float2 sm[];
-  const long long QQ = (long long)Q * Q;
-  const long long GST = QQ + 1;             // padded per-pixel stride (bank spread)
-  float2* Gs = sm;                          // PIX * GST
-  float2* vs = Gs + (size_t)PIX * GST;      // PIX * QP
-  float* red = reinterpret_cast<float*>(vs + PIX * QP);  // PIX * 2
+  __shared__ float2 vs[PIX * QP];
+  __shared__ float red[PIX * 2];
   const int tid = threadIdx.x;
   const int xi = tid / QP, q = tid % QP;
-  const long long x0 = (long long)blockIdx.x * PIX;
-  const long long x = x0 + xi;
+  const long long x = (long long)blockIdx.x * PIX + xi;
   const bool live = (x < npix) && (q < Q);
-  // stage G tile: global [p][q][x] -> shared [xi][p][q]
-  for (long long e = tid; e < QQ * PIX; e += blockDim.x) {
-    const int xx = (int)(e % PIX);
-    const long long pq = e / PIX;
-    float2 g = make_float2(0.f, 0.f);
-    if (x0 + xx < npix) g = G[pq * npix + x0 + xx];
-    Gs[(long long)xx * GST + pq] = g;
+  const long long QQ = (long long)Q * Q;
+  float2 gcol[QP];
+#pragma unroll
+  for (int p = 0; p < QP; ++p) {
+    gcol[p] = make_float2(0.f, 0.f);
+    if (live && p < Q) gcol[p] = G[x * QQ + (long long)p * Q + q];
   }
   const float inv_lam = 1.0f / lam_size;
-  // start vector (normalised)
   float2 v = make_float2(0.f, 0.f);
   if (live) v = make_float2(counter_uniform(seed, (uint64_t)x, 2 * q), counter_uniform(seed, (uint64_t)x, 2 * q + 1));
   {
-    float n2 = pixel_sum<QP>(v.x * v.x + v.y * v.y, red, xi, q);
+    const float n2 = pixel_sum<QP>(v.x * v.x + v.y * v.y, red, xi, q);
     const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
     v.x *= s; v.y *= s;
   }
   vs[xi * QP + q] = v;
   __syncthreads();
-  const float2* Gx = Gs + (long long)xi * GST;
   float2 gv = make_float2(0.f, 0.f);
   for (int it = 0; it <= iters; ++it) {
     gv = make_float2(0.f, 0.f);
-    if (q < Q) {
-      for (int p = 0; p < Q; ++p) cfmac(gv, Gx[p * Q + q], vs[xi * QP + p]);
-    }
+#pragma unroll
+    for (int p = 0; p < QP; ++p) cfmac(gv, gcol[p], vs[xi * QP + p]);
     if (it == iters) break;
-    float2 nv = make_float2(v.x - gv.x * inv_lam, v.y - gv.y * inv_lam);
+    const float2 nv = make_float2(v.x - gv.x * inv_lam, v.y - gv.y * inv_lam);
     const float n2 = pixel_sum<QP>(nv.x * nv.x + nv.y * nv.y, red, xi, q);
     const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
     v = make_float2(nv.x * s, nv.y * s);
@@ -105,14 +95,8 @@ static cudaError_t launch_pi(const float2* G, const float2* Y, int Q, long long 
                              float lam_size, unsigned long long seed, float2* V, float* eig,
                              cudaStream_t st) {
   constexpr int PIX = 256 / QP;
-  const size_t smem = (size_t)PIX * ((size_t)Q * Q + 1) * sizeof(float2) + PIX * QP * sizeof(float2) + PIX * 2 * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(pi_kernel<QP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   const long long blocks = (npix + PIX - 1) / PIX;
-  pi_kernel<QP><<<(unsigned)blocks, 256, smem, st>>>(G, Y, Q, npix, iters, lam_size, seed, V, eig);
+  pi_kernel<QP><<<(unsigned)blocks, 256, 0, st>>>(G, Y, Q, npix, iters, lam_size, seed, V, eig);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -18,7 +18,7 @@ using namespace pisco;
 
 namespace {
 
-constexpr int kNbMax = 16;   // Ritz vectors refined in FP64 per decision
+constexpr int kNbMax = 8;    // Ritz vectors refined in FP64 per decision
 constexpr int kMmax = 128;   // largest eigensolver block
 
 struct DevBuf {
@@ -36,6 +36,7 @@ struct pisco_plan_s {
   int N[3], Nc[3], tau[3], Nr[3], Lp[3], B[3];
   int Q = 0, L = 0, n = 0, nbox = 0, npairs = 0;
   int m = 0, m_max = 0, eig_iters = 10;
+  int chol_variant = 1;  // 1: blocked 256-thread factor (default), 0: single-warp factor
   long long npix = 0, npix_red = 0, nfreq = 0;
   std::vector<int> lam;        // L x 3 (z,y,x)
   std::vector<int> lag_of_ij;  // L x L
@@ -55,6 +56,10 @@ struct pisco_plan_s {
   float2 *X = nullptr, *Y = nullptr, *Z = nullptr, *U = nullptr;
   float2 *Gm = nullptr, *Rinv = nullptr, *Bm = nullptr, *Vj = nullptr;
   float* mu = nullptr;
+  float *dR0 = nullptr, *dR1 = nullptr;  // diag(R) of the last orthonormalisation (ping-pong)
+  float* dsc = nullptr;                    // column scaling used by the last Cholesky
+  double* gscale = nullptr;                // max diag of C^H C (A32 = A / gscale)
+  int* tiles = nullptr;                    // split-K tile counters
   float* w = nullptr;
   double* ritz = nullptr;
   int* band = nullptr;
@@ -70,6 +75,7 @@ struct pisco_plan_s {
   float2 *I1 = nullptr, *I2 = nullptr;
   DevStatus* dstatus = nullptr;
   DevStatus* hstatus = nullptr;  // pinned
+  float2* calib_stage = nullptr;  // every estimate reads its calibration block from here
   // host IO staging
   float2 *io_calib = nullptr, *io_maps = nullptr;
   float* io_eig = nullptr;
@@ -83,6 +89,22 @@ struct pisco_plan_s {
   std::vector<cudaEvent_t> ev;        // pairs (start, end)
   std::vector<const char*> ev_tag;    // tag per pair
   int ev_used = 0;
+  // CUDA graph of the whole path (captured after one eager run with the same arguments)
+  bool use_graph = true;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_calib = nullptr;
+  void* g_maps = nullptr;
+  float* g_eig = nullptr;
+  int g_m = -1;
+  bool g_prof = false;
+  int g_launches = 0;
+  int g_events = 0;
+  const void* eager_calib = nullptr;  // arguments of the last eager run
+  void* eager_maps = nullptr;
+  float* eager_eig = nullptr;
+  int eager_m = -1;
+  bool eager_prof = false;
   std::vector<const char*> prof_name;
   std::vector<double> prof_ms;
   std::vector<int> prof_cnt;
@@ -293,8 +315,8 @@ void prof_end(pisco_plan_s* pl, int i) {
   if (i >= 0) cudaEventRecord(pl->ev[2 * i + 1], pl->st);
 }
 // after the stream has been synchronised: fold the recorded pairs into the per-tag totals
-void prof_collect(pisco_plan_s* pl) {
-  for (int i = 0; i < pl->ev_used; ++i) {
+void prof_collect(pisco_plan_s* pl, int count) {
+  for (int i = 0; i < count; ++i) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, pl->ev[2 * i], pl->ev[2 * i + 1]) != cudaSuccess) continue;
     size_t k = 0;
@@ -307,7 +329,14 @@ void prof_collect(pisco_plan_s* pl) {
     pl->prof_ms[k] += ms;
     pl->prof_cnt[k] += 1;
   }
-  pl->ev_used = 0;
+}
+
+void graph_reset(pisco_plan_s* pl) {
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  pl->gexec = nullptr;
+  pl->graph = nullptr;
+  pl->g_m = -1;
 }
 
 #define OP(tag, x)                                   \
@@ -345,50 +374,86 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
     OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->Rp, AxisView{np, 1, Lp[1], B[1], B[2]}, st));
   }
   OP("gram_scatter", gram_scatter_pairs(pl->Rp, Q, pl->nbox, pl->lags, st));
-  OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->A, pl->A32, st));
+  const int lag0 = (2 * pl->tau[0] * B[1] + 2 * pl->tau[1]) * B[2] + 2 * pl->tau[2];
+  OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st));
+  OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st));
   return PISCO_OK;
 }
 
-pisco_status cholqr(pisco_plan_s* pl, float2* Yin, float2* Xout, int m) {
+// One Cholesky-QR pass: Xout = (Yin D^-1) L^-H with orthonormal columns.  dscale: optional
+// column scaling D (previous diag(R)); shift_rel: optional shift; acc_in: diag(R) of earlier
+// passes of the same factorisation; diag(R) of the whole factorisation goes to diag_out.
+pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, const float* dscale,
+                    float shift_rel, const float* acc_in, float* diag_out) {
   cudaStream_t st = pl->st;
   const int n = pl->n;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, st));
-  OP("eig_chol", eig_chol(pl->Gm, m, pl->Rinv, pl->dstatus, st));
-  OP("eig_trsm", eig_trsm_rows(Yin, pl->Rinv, n, m, Xout, st));
+  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  if (m <= 96) {
+    if (pl->chol_variant == 1)
+      OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
+    else
+      OP("eig_chol", eig_chol_inv_warp(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
+    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, Yin, m, pl->Rinv, m, zero, Xout, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  } else {
+    OP("eig_chol", eig_chol(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, pl->dsc, diag_out, pl->dstatus, st));
+    OP("eig_trsm", eig_trsm(Yin, pl->Rinv, pl->dsc, n, m, Xout, st));
+  }
   return PISCO_OK;
 }
 
+// Nullspace of the Gram (Sec. III-A, threshold footnote of Sec. III-B): orthogonal
+// iteration on an m-column block in FP32, two Gram products per orthonormalisation with the
+// block rescaled by the square of the previous diag(R) (keeps Cholesky-QR well conditioned),
+// one Rayleigh-Ritz at the end, and the threshold split decided on FP64 Rayleigh quotients
+// against the FP64 Gram.
 pisco_status run_eig(pisco_plan_s* pl) {
   cudaStream_t st = pl->st;
   const int n = pl->n, m = pl->m;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
   const double thr2 = pl->prm.null_threshold * pl->prm.null_threshold;
+  pisco_status s;
+  // random start; the first product can be ill conditioned -> shifted Cholesky-QR + two passes
   OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
-  pisco_status s = cholqr(pl, pl->Y, pl->X, m);
-  if (s != PISCO_OK) return s;
-  for (int t = 0; t < pl->eig_iters; ++t) {
-    OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->X, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, st));
-    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, st));
-    OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, pl->dstatus, st));
-    if (t == pl->eig_iters - 1) {
-      OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, st));
-      break;
+  OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->Y, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  const float shift = 11.0f * ((float)m * n + (float)m * (m + 1)) * 5.9604645e-8f;
+  if ((s = cholqr(pl, pl->Z, pl->Y, m, nullptr, shift, nullptr, pl->dR1)) != PISCO_OK) return s;
+  if ((s = cholqr(pl, pl->Y, pl->Z, m, nullptr, 0.f, pl->dR1, pl->dR0)) != PISCO_OK) return s;
+  if ((s = cholqr(pl, pl->Z, pl->X, m, nullptr, 0.f, pl->dR0, pl->dR1)) != PISCO_OK) return s;
+  float* dprev = pl->dR1;
+  float* dnext = pl->dR0;
+  // orthogonal iteration: X <- orth(A^2 X diag(R)^-2) (the last group may be a single product)
+  // dprev approximates lambda^cur for the block columns (diag(R) of `cur` products)
+  int left = pl->eig_iters - 1, cur = 1;
+  while (left > 0) {
+    // one Gram product per orthonormalisation: with two, the squared dynamic range of the
+    // noise-level columns (~(1e-5)^2) exceeds what FP32 Cholesky-QR can resolve
+    const int g = 1;
+    OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->X, m, zero, pl->Y, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+    const float2* src = pl->Y;
+    if (g == 2) {
+      OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->Y, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+      src = pl->Z;
     }
-    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->Z, m, pl->Vj, m, zero, pl->Y, m, pl->ws32, pl->ws32_elems, st));
-    OP("eig_misc", eig_scale_cols(pl->Y, n, m, pl->mu, 1e-6f, st));
-    if ((s = cholqr(pl, pl->Y, pl->X, m)) != PISCO_OK) return s;
-    if ((s = cholqr(pl, pl->X, pl->Y, m)) != PISCO_OK) return s;
-    std::swap(pl->X, pl->Y);
+    if (g != cur) OP("eig_misc", eig_pow(dprev, m, (float)g / (float)cur, st));
+    cur = g;
+    if ((s = cholqr(pl, src, pl->X, m, dprev, 0.f, nullptr, dnext)) != PISCO_OK) return s;
+    std::swap(dprev, dnext);
+    left -= g;
   }
+  // Rayleigh-Ritz on the block
+  OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->X, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
+  OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
   // FP64 Rayleigh quotients of the Ritz vectors that decide the split
   OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st));
   OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
   const double2 zone = make_double2(1.0, 0.0), zzero = make_double2(0.0, 0.0);
-  OP("eig_rayleigh_fp64", cgemm<double>('N', 'N', n, kNbMax, n, zone, pl->A, n, pl->Xb, kNbMax, zzero, pl->Zb, kNbMax,
-                   pl->ws64, pl->ws64_elems, st));
-  OP("eig_decide_fp64", eig_decide(pl->mu, m, pl->band, kNbMax, pl->Xb, pl->Zb, n, thr2, pl->Q, pl->w, pl->ritz,
-                pl->dstatus, st));
+  OP("eig_rayleigh_fp64", eig_band_matvec(pl->A, pl->Xb, n, kNbMax, pl->Zb, st));
+  (void)zone; (void)zzero;
+  OP("eig_decide_fp64", eig_decide(pl->mu, m, pl->band, kNbMax, pl->Xb, pl->Zb, n, thr2, pl->Q, pl->gscale,
+                pl->w, pl->ritz, pl->dstatus, st));
   return PISCO_OK;
 }
 
@@ -402,9 +467,9 @@ pisco_status run_gfield(pisco_plan_s* pl) {
   OP("g_dft", apply_axis_c(pl->K, pl->gdft[2], pl->T1, AxisView{QQ, (long long)B[0] * B[1], B[2], Nr[2], 1}, st));
   if (pl->D == 3) {
     OP("g_dft", apply_axis_c(pl->T1, pl->gdft[1], pl->T2, AxisView{QQ, B[0], B[1], Nr[1], Nr[2]}, st));
-    OP("g_dft", apply_axis_c(pl->T2, pl->gdft[0], pl->G, AxisView{QQ, 1, B[0], Nr[0], (long long)Nr[1] * Nr[2]}, st));
+    OP("g_dft", apply_axis_c(pl->T2, pl->gdft[0], pl->G, AxisView{QQ, 1, B[0], Nr[0], (long long)Nr[1] * Nr[2], 1}, st));
   } else {
-    OP("g_dft", apply_axis_c(pl->T1, pl->gdft[1], pl->G, AxisView{QQ, 1, B[1], Nr[1], Nr[2]}, st));
+    OP("g_dft", apply_axis_c(pl->T1, pl->gdft[1], pl->G, AxisView{QQ, 1, B[1], Nr[1], Nr[2], 1}, st));
   }
   OP("g_identity", gassembly_add_identity(pl->G, Q, pl->npix_red, (float)pl->L, st));
   return PISCO_OK;
@@ -481,6 +546,7 @@ const char* pisco_status_string(pisco_status s) {
 void pisco_destroy(pisco_plan_t pl) {
   if (!pl) return;
   if (pl->st) cudaStreamSynchronize(pl->st);
+  graph_reset(pl);
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   for (void* p : pl->allocs) cudaFree(p);
   if (pl->hstatus) cudaFreeHost(pl->hstatus);
@@ -527,6 +593,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->m = p->eig_block > 0 ? std::min(p->eig_block, mmax) : std::min(64, mmax);
   if (pl->m < 2) { delete pl; return PISCO_ERR_ARG; }
   pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 8;
+  if (const char* cv = getenv("PISCO_CHOL")) pl->chol_variant = atoi(cv);
 
   const int Q = pl->Q, n = pl->n, np = pl->npairs;
   const int* Nc = pl->Nc;
@@ -560,6 +627,9 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->Bm, (size_t)M * M) && dalloc(pl, &pl->Vj, (size_t)2 * M * M);
   ok = ok && dalloc(pl, &pl->mu, (size_t)M) && dalloc(pl, &pl->w, (size_t)M) && dalloc(pl, &pl->ritz, (size_t)M);
   ok = ok && dalloc(pl, &pl->band, (size_t)kNbMax);
+  ok = ok && dalloc(pl, &pl->dR0, (size_t)M) && dalloc(pl, &pl->dR1, (size_t)M) && dalloc(pl, &pl->dsc, (size_t)M);
+  ok = ok && dalloc(pl, &pl->tiles, (size_t)4096);
+  ok = ok && dalloc(pl, &pl->gscale, (size_t)1);
   ok = ok && dalloc(pl, &pl->Xb, (size_t)n * kNbMax) && dalloc(pl, &pl->Zb, (size_t)n * kNbMax);
   pl->ws32_elems = (size_t)16 * n * M;
   pl->ws64_elems = (size_t)64 * n * kNbMax;
@@ -579,12 +649,20 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->I1, (size_t)Q * Nr[0] * Nr[1] * N[2]);
   ok = ok && dalloc(pl, &pl->I2, (size_t)Q * Nr[0] * N[1] * N[2]);
   ok = ok && dalloc(pl, &pl->dstatus, 1);
+  ok = ok && dalloc(pl, &pl->calib_stage, (size_t)Q * Nc[0] * Nc[1] * Nc[2]);
   if (ok && (p->flags & PISCO_FLAG_HOST_IO)) {
     ok = dalloc(pl, &pl->io_calib, (size_t)Q * Nc[0] * Nc[1] * Nc[2]) &&
          dalloc(pl, &pl->io_maps, (size_t)(Q * pl->npix)) && dalloc(pl, &pl->io_eig, (size_t)pl->npix_red);
   }
   if (ok) ok = cudaMallocHost((void**)&pl->hstatus, sizeof(DevStatus)) == cudaSuccess;
+  for (int i = 0; ok && i < 2 * 160; ++i) {  // event pool for operation timing
+    cudaEvent_t e;
+    ok = cudaEventCreate(&e) == cudaSuccess;
+    if (ok) pl->ev.push_back(e);
+    if (ok && (i & 1)) pl->ev_tag.push_back(nullptr);
+  }
   if (ok) ok = cudaMemset(pl->lags, 0, sizeof(double2) * (size_t)Q * Q * pl->nbox) == cudaSuccess;
+  if (ok) ok = cudaMemset(pl->tiles, 0, sizeof(int) * 4096) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     pisco_destroy(pl);
@@ -601,12 +679,61 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
 pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, float* d_eig) {
   if (!pl || !d_calib || !d_maps) return PISCO_ERR_ARG;
   if (((uintptr_t)d_calib | (uintptr_t)d_maps | (uintptr_t)d_eig) & 7) return PISCO_ERR_ARG;
+  // the path (and its graph) always reads the plan's staging copy of the calibration block
+  if (d_calib != pl->calib_stage &&
+      cudaMemcpyAsync(pl->calib_stage, d_calib,
+                      sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2],
+                      cudaMemcpyDeviceToDevice, pl->st) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  d_calib = pl->calib_stage;
   for (;;) {
-    pisco_status s = run_all(pl, (const float2*)d_calib, (float2*)d_maps, d_eig);
-    if (s != PISCO_OK) return s;
-    if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
-    pl->last_launches = g_launches;
-    if (pl->prof) prof_collect(pl);
+    const bool same_as_graph = pl->gexec && pl->g_calib == d_calib && pl->g_maps == d_maps &&
+                               pl->g_eig == d_eig && pl->g_m == pl->m && pl->g_prof == pl->prof;
+    const bool same_as_eager = pl->eager_calib == d_calib && pl->eager_maps == d_maps &&
+                               pl->eager_eig == d_eig && pl->eager_m == pl->m && pl->eager_prof == pl->prof;
+    if (pl->use_graph && !same_as_graph && same_as_eager) {
+      // capture the path once the same arguments have run eagerly (attributes set, sizes settled)
+      graph_reset(pl);
+      pl->ev_used = 0;
+      if (cudaStreamBeginCapture(pl->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        pisco_status s = run_all(pl, (const float2*)d_calib, (float2*)d_maps, d_eig);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(pl->st, &g);
+        if (s == PISCO_OK && ec == cudaSuccess && g &&
+            cudaGraphInstantiate(&pl->gexec, g, 0) == cudaSuccess) {
+          pl->graph = g;
+          pl->g_calib = d_calib; pl->g_maps = d_maps; pl->g_eig = d_eig;
+          pl->g_m = pl->m; pl->g_prof = pl->prof;
+          pl->g_launches = g_launches;
+          pl->g_events = pl->ev_used;
+        } else {
+          if (g) cudaGraphDestroy(g);
+          pl->gexec = nullptr;
+          pl->use_graph = false;  // fall back to eager launches for this plan
+          cudaGetLastError();
+        }
+      } else {
+        pl->use_graph = false;
+        cudaGetLastError();
+      }
+    }
+    const bool replay = pl->use_graph && pl->gexec && pl->g_calib == d_calib && pl->g_maps == d_maps &&
+                        pl->g_eig == d_eig && pl->g_m == pl->m && pl->g_prof == pl->prof;
+    if (replay) {
+      if (cudaGraphLaunch(pl->gexec, pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+      if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+      pl->last_launches = pl->g_launches;
+      if (pl->prof) prof_collect(pl, pl->g_events);
+    } else {
+      pl->ev_used = 0;
+      pisco_status s = run_all(pl, (const float2*)d_calib, (float2*)d_maps, d_eig);
+      if (s != PISCO_OK) return s;
+      if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+      pl->last_launches = g_launches;
+      if (pl->prof) prof_collect(pl, pl->ev_used);
+      pl->eager_calib = d_calib; pl->eager_maps = d_maps; pl->eager_eig = d_eig;
+      pl->eager_m = pl->m; pl->eager_prof = pl->prof;
+    }
     const DevStatus h = *pl->hstatus;
     pl->last_status = h;
     if ((h.flags & ST_SATURATED) && pl->m < pl->m_max) {
@@ -626,9 +753,9 @@ pisco_status pisco_estimate_host(pisco_plan_t pl, const void* h_calib, void* h_m
   if (!pl->io_calib) return PISCO_ERR_ARG;
   const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
   const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
-  if (cudaMemcpyAsync(pl->io_calib, h_calib, cb, cudaMemcpyHostToDevice, pl->st) != cudaSuccess)
+  if (cudaMemcpyAsync(pl->calib_stage, h_calib, cb, cudaMemcpyHostToDevice, pl->st) != cudaSuccess)
     return PISCO_ERR_CUDA;
-  pisco_status s = pisco_estimate(pl, pl->io_calib, pl->io_maps, h_eig ? pl->io_eig : nullptr);
+  pisco_status s = pisco_estimate(pl, pl->calib_stage, pl->io_maps, h_eig ? pl->io_eig : nullptr);
   if (s != PISCO_OK && s != PISCO_ERR_RANK) return s;
   if (cudaMemcpyAsync(h_maps, pl->io_maps, mb, cudaMemcpyDeviceToHost, pl->st) != cudaSuccess)
     return PISCO_ERR_CUDA;
@@ -659,6 +786,9 @@ pisco_status pisco_debug_buffer(pisco_plan_t pl, int which, void** dptr, size_t*
     case PISCO_BUF_G: *dptr = pl->G; *bytes = sizeof(float2) * (size_t)pl->Q * pl->Q * pl->npix_red; break;
     case PISCO_BUF_V: *dptr = pl->V; *bytes = sizeof(float2) * (size_t)pl->Q * pl->npix_red; break;
     case PISCO_BUF_Y: *dptr = pl->Yf; *bytes = sizeof(float2) * (size_t)pl->Q * pl->npix_red; break;
+    case PISCO_BUF_BLOCK: *dptr = pl->X; *bytes = sizeof(float2) * n * pl->m; break;
+    case PISCO_BUF_RITZ32: *dptr = pl->mu; *bytes = sizeof(float) * pl->m; break;
+    case PISCO_BUF_SCALE: *dptr = pl->gscale; *bytes = sizeof(double); break;
     default: return PISCO_ERR_ARG;
   }
   return PISCO_OK;
@@ -680,7 +810,6 @@ pisco_status pisco_get_stats(pisco_plan_t pl, pisco_stats* out) {
 pisco_status pisco_set_profiling(pisco_plan_t pl, int enable) {
   if (!pl) return PISCO_ERR_ARG;
   pl->prof = enable != 0;
-  pl->ev_used = 0;
   return PISCO_OK;
 }
 

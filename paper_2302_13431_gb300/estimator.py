@@ -106,7 +106,8 @@ class PiscoEstimator:
 
     _BUF_TYPES = {B.PISCO_BUF_LAGS: "<c16", B.PISCO_BUF_GRAM: "<c16", B.PISCO_BUF_SIGNAL: "<c8",
                   B.PISCO_BUF_WEIGHTS: "<f4", B.PISCO_BUF_RITZ: "<f8", B.PISCO_BUF_G: "<c8",
-                  B.PISCO_BUF_V: "<c8", B.PISCO_BUF_Y: "<c8"}
+                  B.PISCO_BUF_V: "<c8", B.PISCO_BUF_Y: "<c8", B.PISCO_BUF_BLOCK: "<c8",
+                  B.PISCO_BUF_RITZ32: "<f4", B.PISCO_BUF_SCALE: "<f8"}
 
     def debug_buffer(self, which: int) -> torch.Tensor:
         """A copy of one intermediate buffer of the last estimate (flat tensor)."""

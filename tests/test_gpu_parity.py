@@ -126,7 +126,7 @@ def test_G_field(name):
     Q = r["Q"]
     L = ref["lam"].shape[0]
     npix = ref["G"].shape[0]
-    G = r["G"].reshape(Q, Q, npix).transpose(2, 0, 1)
+    G = r["G"].reshape(npix, Q, Q)
     err = np.abs(G - ref["G"]).max() / L
     assert err <= 2e-5, err
 
