@@ -45,7 +45,9 @@ typedef enum {
                                    outputs are still written (they are not identifiable).    */
   PISCO_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired                         */
   PISCO_ERR_NOT_CONVERGED = 6,  /* block eigensolver saturated even at the largest block     */
-  PISCO_ERR_UNSUPPORTED = 7     /* valid request outside what this build implements          */
+  PISCO_ERR_UNSUPPORTED = 7,    /* valid request outside what this build implements          */
+  PISCO_ERR_TOO_LARGE = 8       /* request needs more than the fixed scratch of
+                                   pisco_gram_lags_noalloc (nothing was launched)            */
 } pisco_status;
 
 typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_shape;
@@ -157,6 +159,27 @@ pisco_status pisco_set_profiling(pisco_plan_t plan, int enable);
 pisco_status pisco_profile_reset(pisco_plan_t plan);
 pisco_status pisco_profile_entry(pisco_plan_t plan, int idx, const char** name, double* total_ms,
                                  int* count);
+
+/* Allocation-free variant of stage (a).  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the result -- code
+ * under a fixed-budget or custom allocator that forbids cudaMalloc/cudaFree on its hot path,
+ * pipelines that must not synchronise the device (cudaFree does), or embedded hosts that hand
+ * in pre-sized buffers.  It computes the same lag table as pisco_estimate (PISCO_BUF_LAGS):
+ *   d_calib: device, complex64 [Q][Nc_z][Nc_y][Nc_x] (8-byte aligned), read only;
+ *   d_lags:  device, complex128 [Q][Q][B_z][B_y][B_x] with B = 4 tau + 1 (16-byte aligned),
+ *            written in full: R_pq[d] for p <= q, zero for p > q.
+ * Only p->ndim, calib, num_coils and kernel_radius are read.  Every intermediate lives in one
+ * 32 MiB scratch array compiled into the library, which each GPU that loads the library
+ * holds until the process exits; requests that need more return PISCO_ERR_TOO_LARGE (the 2D
+ * 32x32 Q=32 radius-3 case needs about 20 MiB).  No cudaMalloc, cudaFree or allocating
+ * library call is made.  The first call on a device resolves the scratch array's device
+ * address for that device (cudaGetSymbolAddress, with that device current), so make that
+ * first call before any stream capture.  All calls share the scratch and it keeps the last
+ * call's contents; calls that overlap on the GPU (two streams, two threads) race.
+ * Work is enqueued on `cuda_stream` (NULL: legacy default stream); returns without
+ * synchronising. */
+pisco_status pisco_gram_lags_noalloc(const pisco_params* p, const void* d_calib, void* d_lags,
+                                     void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpisco.so")
 
 PISCO_OK, PISCO_ERR_ARG, PISCO_ERR_CUDA, PISCO_ERR_OOM, PISCO_ERR_RANK, PISCO_ERR_TIMEOUT, \
-    PISCO_ERR_NOT_CONVERGED, PISCO_ERR_UNSUPPORTED = range(8)
+    PISCO_ERR_NOT_CONVERGED, PISCO_ERR_UNSUPPORTED, PISCO_ERR_TOO_LARGE = range(9)
 PISCO_KERNEL_RECT, PISCO_KERNEL_ELLIPSOID = 0, 1
 PISCO_FLAG_HOST_IO = 0x1
 (PISCO_BUF_LAGS, PISCO_BUF_GRAM, PISCO_BUF_SIGNAL, PISCO_BUF_WEIGHTS, PISCO_BUF_RITZ, PISCO_BUF_G,
@@ -95,6 +95,8 @@ def load():
     lib.pisco_profile_entry.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), P(ctypes.c_double),
                                         P(ctypes.c_int)]
     lib.pisco_profile_entry.restype = ctypes.c_int
+    lib.pisco_gram_lags_noalloc.argtypes = [P(pisco_params), vp, vp, vp]
+    lib.pisco_gram_lags_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -182,3 +184,9 @@ def pisco_profile(plan):
         out[name.value.decode()] = (ms.value, cnt.value)
         i += 1
     return out
+
+
+def pisco_gram_lags_noalloc(params: pisco_params, d_calib: int, d_lags: int, stream: int = 0):
+    """Allocation-free lag-table entry point (see include/pisco.h)."""
+    return load().pisco_gram_lags_noalloc(ctypes.byref(params), ctypes.c_void_p(d_calib),
+                                          ctypes.c_void_p(d_lags), ctypes.c_void_p(stream))

@@ -539,6 +539,7 @@ const char* pisco_status_string(pisco_status s) {
     case PISCO_ERR_TIMEOUT: return "bounded device wait expired";
     case PISCO_ERR_NOT_CONVERGED: return "eigensolver block saturated at its largest size";
     case PISCO_ERR_UNSUPPORTED: return "request outside this build";
+    case PISCO_ERR_TOO_LARGE: return "request exceeds the fixed scratch of the no-allocation entry point";
   }
   return "unknown status";
 }
