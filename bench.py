@@ -2,7 +2,8 @@
 """Throughput of the PISCO sensitivity-map estimator on GB300.
 
 One step = one full pass of the hot path (Gram, nullspace, G(x), power iteration + phase,
-interpolation + normalisation) over one multichannel calibration block of the 2D workload
+interpolation + normalisation) over one batch (default 64) of multichannel calibration blocks
+of the 2D workload
 256x256 grid, Q=32 coils, 32x32 calibration, ellipsoidal kernel of radius 3, G(x) on the
 64x64 reduced grid, 30 power iterations, complex64 synthetic input (seeded phantoms x
 smooth coil maps).  The metric is maps/s (and reduced-grid pixel eigensolves/s).
@@ -222,6 +223,23 @@ def roofline_for(op, prof, w, stats, peaks):
     return dict(bound="latency", achieved=None, peak=None, unit=None, note=f"no roofline formula for {op}")
 
 
+def _time_steps(run_step, steps, flush, stream, nvtx_name):
+    """CUDA-event time of `steps` calls of run_step(i), L2 flushed (outside the events) before
+    each; returns the per-step milliseconds.  Each step sits in an NVTX range `nvtx_name`
+    (profilers can filter on it; it costs nothing when no profiler is attached)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        torch.cuda.nvtx.range_push(nvtx_name)
+        run_step(i)
+        torch.cuda.nvtx.range_pop()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def run_gpu(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -232,74 +250,83 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2302_13431_gb300.estimator import PiscoEstimator
+    from paper_2302_13431_gb300.estimator import PiscoBatch, PiscoEstimator
     w = WORKLOAD
     calibs_h = make_inputs(rank)
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
-    est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
-                         thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0,
-                         host_io=True)
-    maps = torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64, device="cuda")
     red = tuple(g // w["reduction"] for g in w["grid"])
-    eig = torch.empty(red, dtype=torch.float32, device="cuda")
+    nr = red[0] * red[1]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    spec = dict(grid=w["grid"], calib_shape=w["calib"], num_coils=w["Q"], tau=w["tau"],
+                kernel_shape=w["shape"], thr=w["thr"], reduction=w["reduction"], iters=w["iters"])
 
-    for i in range(args.warmup):
-        est.estimate_into(calibs[i % N_CASES], maps, eig)
+    # ---- plain single-map estimates (one plan, one map per call): context + op profile ----
+    est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
+                         thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0)
+    maps1 = torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64, device="cuda")
+    eig1 = torch.empty(red, dtype=torch.float32, device="cuda")
+    for i in range(max(args.warmup, 3)):
+        est.estimate_into(calibs[i % N_CASES], maps1, eig1)
     torch.cuda.synchronize()
+    plain_ms = _time_steps(lambda i: est.estimate_into(calibs[i % N_CASES], maps1, eig1),
+                           min(args.steps, 20), flush, stream, "pisco_single_step")
+    plain_value = len(plain_ms) / (sum(plain_ms) / 1e3)
+    stats = est.stats()
+    est.set_profiling(True)
+    est.estimate_into(calibs[0], maps1, eig1)
+    est.estimate_into(calibs[0], maps1, eig1)
+    est.profile_reset()
+    for i in range(min(args.steps, 20)):
+        flush.zero_()
+        est.estimate_into(calibs[i % N_CASES], maps1, eig1)
+    torch.cuda.synchronize()
+    prof = est.profile()
+    nprof = min(args.steps, 20)
+    est.set_profiling(False)
+    est.close()
 
-    # ---- device-resident timed region (no profiling events inside) ----
+    # ---- batched form: one step = one CUDA-graph launch over `batch` maps ----
+    nb = args.batch
+    batch = PiscoBatch([spec] * nb)
+    bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
+    bmaps, beigs = batch.alloc_outputs()
+    for i in range(args.warmup):
+        batch.estimate_into(bcal, bmaps, beigs)
+    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()                       # evict L2 between steps (256 MiB write)
-        evs[i][0].record(stream)
-        est.estimate_into(calibs[i % N_CASES], maps, eig)
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = _time_steps(lambda i: batch.estimate_into(bcal, bmaps, beigs), args.steps, flush, stream,
+                          "pisco_batch_step")
     if dist:
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(step_ms)
-    stats = est.stats()
-    # ---- per-operation breakdown: the same steps again with CUDA events around every op ----
-    est.set_profiling(True)
-    est.estimate_into(calibs[0], maps, eig)   # graph with event nodes is captured on the next call
-    est.estimate_into(calibs[0], maps, eig)
-    est.profile_reset()
-    for i in range(args.steps):
-        flush.zero_()
-        est.estimate_into(calibs[i % N_CASES], maps, eig)
-    torch.cuda.synchronize()
-    prof = est.profile()
-    est.set_profiling(False)
     if dist:
         t = torch.tensor([tot_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    value = world * nb * args.steps / (tot_ms / 1e3)
+    binfo = batch.info()
 
-    # ---- end to end through the host-buffer entry point ----
-    pin_c = [torch.from_numpy(c).pin_memory().numpy() for c in calibs_h]
-    hmaps = torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64).pin_memory().numpy()
-    heig = torch.empty(red, dtype=torch.float32).pin_memory().numpy()
+    # ---- end to end: host buffers in and out, copies inside the timed region ----
+    pin_c = [torch.from_numpy(calibs_h[i % N_CASES]).pin_memory().numpy() for i in range(nb)]
+    hmaps = [torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64).pin_memory().numpy() for _ in range(nb)]
+    heig = [torch.empty(red, dtype=torch.float32).pin_memory().numpy() for _ in range(nb)]
     for i in range(min(args.warmup, 3)):
-        est.estimate_host(pin_c[i % N_CASES], hmaps, heig)
+        batch.estimate_host(pin_c, hmaps, heig)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        est.estimate_host(pin_c[i % N_CASES], hmaps, heig)
+        batch.estimate_host(pin_c, hmaps, heig)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -307,7 +334,8 @@ def run_gpu(args):
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_value = world * args.steps / (e2e_ms / 1e3)
+    e2e_value = world * nb * args.steps / (e2e_ms / 1e3)
+    batch.close()
 
     peaks = _peaks()
     dom = max(prof, key=lambda k: prof[k][0]) if prof else None
@@ -316,7 +344,7 @@ def run_gpu(args):
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
     roof["traffic"] = None
-    nr = red[0] * red[1]
+    roof["measured"] = "CUDA events around each launch of the op in the profiled single-map pass"
 
     line = {
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
@@ -324,20 +352,25 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": "FP64 Gram and FP64 threshold split of the nullspace; FP32 elsewhere",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "l2": "flushed between timed steps (256 MiB write)",
-                   "inputs": f"{N_CASES} seeded calibration blocks resident in HBM, cycled",
-                   "parallelism": f"{world} independent replicas (one map per rank per step)"},
+        "config": {"workload": WORKLOAD_DESC, "batch": nb,
+                   "step": f"one CUDA-graph launch estimating {nb} independent map sets",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "inputs": f"{nb} calibration blocks ({N_CASES} distinct seeded contents) resident in HBM",
+                   "parallelism": f"{world} independent replicas"},
         "pixel_eigensolves_per_s": value * nr,
+        "plain_single_map": {"value": plain_value, "unit": "maps/s",
+                             "note": "one plan, one map per call (per-slice launches)"},
         "wall_s": t_wall,
-        "gpu_launches": int(stats["launches"]) * args.steps,
+        "gpu_launches": int(binfo["launches"]) * args.steps,
         "e2e": {"value": e2e_value, "unit": "maps/s",
-                "h2d_bytes_per_step": int(calibs_h[0].nbytes),
-                "d2h_bytes_per_step": int(hmaps.nbytes + heig.nbytes)},
+                "h2d_bytes_per_step": int(sum(c.nbytes for c in pin_c)),
+                "d2h_bytes_per_step": int(sum(m.nbytes for m in hmaps) + sum(e.nbytes for e in heig))},
         "roofline": roof,
         "clocks": clocks,
         "eig": {"k": stats["signal_dim"], "block": stats["eig_block"], "iters": stats["eig_iters"],
                 "jacobi_sweeps": stats["jacobi_sweeps"], "fp64_band": stats["nband"]},
-        "ops_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "ops_ms_per_map": {k: v[0] / nprof for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "workspace_bytes_batch": binfo["workspace_bytes"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_s = 3
@@ -349,7 +382,6 @@ def run_gpu(args):
                                 "kind": "oracle", "sample": oracle_sample_desc() + f"; {n_s} maps"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    est.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -362,6 +394,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["pisco", "reference"], default="pisco")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=64, help="map sets per step (one graph launch)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "pisco":
         args.warmup = 3

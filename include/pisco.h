@@ -160,6 +160,30 @@ pisco_status pisco_profile_reset(pisco_plan_t plan);
 pisco_status pisco_profile_entry(pisco_plan_t plan, int idx, const char** name, double* total_ms,
                                  int* count);
 
+/* Batches of independent estimates (many slices or volumes, sizes and coil counts may
+ * differ).  pisco_batch_plan builds one plan per item (params[i], with its own workspace and
+ * stream).  pisco_batch_estimate captures every item's path into ONE CUDA graph whose
+ * per-item branches run concurrently on the GPU (the small latency-bound kernels of different
+ * items then occupy different SMs), launches it on `cuda_stream`, synchronises once and
+ * reports each item's status in item_status[i] (may be NULL).  The graph is replayed while
+ * the pointer arrays stay the same.  Pointer arrays hold `count` device pointers with the
+ * layouts of pisco_estimate (d_eig may be NULL, or hold NULL entries).  An item whose signal
+ * dimension saturates its eigensolver block is re-run alone with a larger block.  Returns the
+ * most severe item status.  The _host variant takes host pointers (pinned memory for full
+ * copy bandwidth) and copies inside the graph.  pisco_batch_item exposes item i's plan for
+ * pisco_plan_info / pisco_debug_buffer / pisco_get_stats (owned by the batch). */
+typedef struct pisco_batch_s* pisco_batch_t;
+pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_stream,
+                              pisco_batch_t* out);
+pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,
+                                  float* const* d_eig, pisco_status* item_status);
+pisco_status pisco_batch_estimate_host(pisco_batch_t b, const void* const* h_calib,
+                                       void* const* h_maps, float* const* h_eig,
+                                       pisco_status* item_status);
+pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t* workspace_bytes);
+pisco_status pisco_batch_item(pisco_batch_t b, int i, pisco_plan_t* plan);
+void pisco_batch_destroy(pisco_batch_t b);
+
 /* Allocation-free variant of stage (a).  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the result -- code
  * under a fixed-budget or custom allocator that forbids cudaMalloc/cudaFree on its hot path,

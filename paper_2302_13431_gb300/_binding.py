@@ -95,6 +95,19 @@ def load():
     lib.pisco_profile_entry.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), P(ctypes.c_double),
                                         P(ctypes.c_int)]
     lib.pisco_profile_entry.restype = ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.pisco_batch_plan.argtypes = [P(pisco_params), ctypes.c_int, vp, P(vp)]
+    lib.pisco_batch_plan.restype = ctypes.c_int
+    lib.pisco_batch_estimate.argtypes = [vp, PP, PP, PP, P(ctypes.c_int)]
+    lib.pisco_batch_estimate.restype = ctypes.c_int
+    lib.pisco_batch_estimate_host.argtypes = [vp, PP, PP, PP, P(ctypes.c_int)]
+    lib.pisco_batch_estimate_host.restype = ctypes.c_int
+    lib.pisco_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
+    lib.pisco_batch_info.restype = ctypes.c_int
+    lib.pisco_batch_item.argtypes = [vp, ctypes.c_int, P(vp)]
+    lib.pisco_batch_item.restype = ctypes.c_int
+    lib.pisco_batch_destroy.argtypes = [vp]
+    lib.pisco_batch_destroy.restype = None
     lib.pisco_gram_lags_noalloc.argtypes = [P(pisco_params), vp, vp, vp]
     lib.pisco_gram_lags_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -190,3 +203,41 @@ def pisco_gram_lags_noalloc(params: pisco_params, d_calib: int, d_lags: int, str
     """Allocation-free lag-table entry point (see include/pisco.h)."""
     return load().pisco_gram_lags_noalloc(ctypes.byref(params), ctypes.c_void_p(d_calib),
                                           ctypes.c_void_p(d_lags), ctypes.c_void_p(stream))
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p if p else None
+    return arr
+
+
+def pisco_batch_plan(params_list, stream: int = 0):
+    arr = (pisco_params * len(params_list))(*params_list)
+    h = ctypes.c_void_p()
+    st = load().pisco_batch_plan(arr, len(params_list), ctypes.c_void_p(stream), ctypes.byref(h))
+    return st, h
+
+
+def pisco_batch_estimate(batch, calibs, maps, eigs, host=False):
+    n = len(calibs)
+    stat = (ctypes.c_int * n)()
+    fn = load().pisco_batch_estimate_host if host else load().pisco_batch_estimate
+    st = fn(batch, _ptr_array(calibs), _ptr_array(maps), _ptr_array(eigs) if eigs is not None else None, stat)
+    return st, list(stat)
+
+
+def pisco_batch_info(batch):
+    c, l, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    st = load().pisco_batch_info(batch, ctypes.byref(c), ctypes.byref(l), ctypes.byref(w))
+    return st, c.value, l.value, w.value
+
+
+def pisco_batch_item(batch, i):
+    h = ctypes.c_void_p()
+    st = load().pisco_batch_item(batch, i, ctypes.byref(h))
+    return st, h
+
+
+def pisco_batch_destroy(batch):
+    load().pisco_batch_destroy(batch)

@@ -89,7 +89,10 @@ struct pisco_plan_s {
   std::vector<cudaEvent_t> ev;        // pairs (start, end)
   std::vector<const char*> ev_tag;    // tag per pair
   int ev_used = 0;
-  // CUDA graph of the whole path (captured after one eager run with the same arguments)
+  // CUDA graph of the whole path (captured after one eager run with the same arguments) on a
+  // private non-blocking stream (the caller's stream may be the uncapturable legacy stream)
+  cudaStream_t cap_st = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   bool use_graph = true;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -318,7 +321,10 @@ void prof_end(pisco_plan_s* pl, int i) {
 void prof_collect(pisco_plan_s* pl, int count) {
   for (int i = 0; i < count; ++i) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, pl->ev[2 * i], pl->ev[2 * i + 1]) != cudaSuccess) continue;
+    if (cudaEventElapsedTime(&ms, pl->ev[2 * i], pl->ev[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
     size_t k = 0;
     while (k < pl->prof_name.size() && strcmp(pl->prof_name[k], pl->ev_tag[i]) != 0) ++k;
     if (k == pl->prof_name.size()) {
@@ -548,6 +554,9 @@ void pisco_destroy(pisco_plan_t pl) {
   if (!pl) return;
   if (pl->st) cudaStreamSynchronize(pl->st);
   graph_reset(pl);
+  if (pl->cap_st) { cudaStreamSynchronize(pl->cap_st); cudaStreamDestroy(pl->cap_st); }
+  if (pl->ev_in) cudaEventDestroy(pl->ev_in);
+  if (pl->ev_out) cudaEventDestroy(pl->ev_out);
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
   for (void* p : pl->allocs) cudaFree(p);
   if (pl->hstatus) cudaFreeHost(pl->hstatus);
@@ -633,7 +642,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->gscale, (size_t)1);
   ok = ok && dalloc(pl, &pl->Xb, (size_t)n * kNbMax) && dalloc(pl, &pl->Zb, (size_t)n * kNbMax);
   pl->ws32_elems = (size_t)16 * n * M;
-  pl->ws64_elems = (size_t)64 * n * kNbMax;
+  pl->ws64_elems = (size_t)16 * kNbMax;  // FP64 split-K scratch (the band product has its own kernel)
   ok = ok && dalloc(pl, &pl->ws32, pl->ws32_elems) && dalloc(pl, &pl->ws64, pl->ws64_elems);
   // G field
   const long long QQ = (long long)Q * Q;
@@ -656,6 +665,9 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
          dalloc(pl, &pl->io_maps, (size_t)(Q * pl->npix)) && dalloc(pl, &pl->io_eig, (size_t)pl->npix_red);
   }
   if (ok) ok = cudaMallocHost((void**)&pl->hstatus, sizeof(DevStatus)) == cudaSuccess;
+  if (ok) ok = cudaStreamCreateWithFlags(&pl->cap_st, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; ok && i < 2 * 160; ++i) {  // event pool for operation timing
     cudaEvent_t e;
     ok = cudaEventCreate(&e) == cudaSuccess;
@@ -692,14 +704,18 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
                                pl->g_eig == d_eig && pl->g_m == pl->m && pl->g_prof == pl->prof;
     const bool same_as_eager = pl->eager_calib == d_calib && pl->eager_maps == d_maps &&
                                pl->eager_eig == d_eig && pl->eager_m == pl->m && pl->eager_prof == pl->prof;
-    if (pl->use_graph && !same_as_graph && same_as_eager) {
+    // profiled calls always run eagerly: their per-operation events time individual launches
+    if (pl->use_graph && !pl->prof && !same_as_graph && same_as_eager) {
       // capture the path once the same arguments have run eagerly (attributes set, sizes settled)
       graph_reset(pl);
       pl->ev_used = 0;
-      if (cudaStreamBeginCapture(pl->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      if (cudaStreamBeginCapture(pl->cap_st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cudaStream_t user = pl->st;
+        pl->st = pl->cap_st;
         pisco_status s = run_all(pl, (const float2*)d_calib, (float2*)d_maps, d_eig);
+        pl->st = user;
         cudaGraph_t g = nullptr;
-        const cudaError_t ec = cudaStreamEndCapture(pl->st, &g);
+        const cudaError_t ec = cudaStreamEndCapture(pl->cap_st, &g);
         if (s == PISCO_OK && ec == cudaSuccess && g &&
             cudaGraphInstantiate(&pl->gexec, g, 0) == cudaSuccess) {
           pl->graph = g;
@@ -718,10 +734,16 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
         cudaGetLastError();
       }
     }
-    const bool replay = pl->use_graph && pl->gexec && pl->g_calib == d_calib && pl->g_maps == d_maps &&
+    const bool replay = pl->use_graph && !pl->prof && pl->gexec && pl->g_calib == d_calib && pl->g_maps == d_maps &&
                         pl->g_eig == d_eig && pl->g_m == pl->m && pl->g_prof == pl->prof;
     if (replay) {
-      if (cudaGraphLaunch(pl->gexec, pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+      // order the graph after earlier work on the caller's stream, and the caller after it
+      if (cudaEventRecord(pl->ev_in, pl->st) != cudaSuccess ||
+          cudaStreamWaitEvent(pl->cap_st, pl->ev_in, 0) != cudaSuccess ||
+          cudaGraphLaunch(pl->gexec, pl->cap_st) != cudaSuccess ||
+          cudaEventRecord(pl->ev_out, pl->cap_st) != cudaSuccess ||
+          cudaStreamWaitEvent(pl->st, pl->ev_out, 0) != cudaSuccess)
+        return PISCO_ERR_CUDA;
       if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
       pl->last_launches = pl->g_launches;
       if (pl->prof) prof_collect(pl, pl->g_events);
@@ -827,6 +849,245 @@ pisco_status pisco_profile_entry(pisco_plan_t pl, int idx, const char** name, do
   if (name) *name = pl->prof_name[idx];
   if (total_ms) *total_ms = pl->prof_ms[idx];
   if (count) *count = pl->prof_cnt[idx];
+  return PISCO_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batches: one sub-plan (own workspace and stream) per item, all items captured into one
+// CUDA graph whose branches run concurrently; replayed while the pointer sets stay the same.
+// ---------------------------------------------------------------------------------------
+struct pisco_batch_s {
+  std::vector<pisco_plan_s*> items;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t main = nullptr;   // private non-blocking stream: capture and graph launch
+  cudaStream_t user = nullptr;   // the caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> g_in;
+  std::vector<void*> g_out;
+  std::vector<float*> g_eig;
+  bool g_host = false;
+  int launches = 0;
+  bool warmed = false;  // one eager run first: kernel attributes are set outside any capture
+};
+
+static void batch_graph_reset(pisco_batch_s* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->g_in.clear();
+  b->g_out.clear();
+  b->g_eig.clear();
+}
+
+void pisco_batch_destroy(pisco_batch_t b) {
+  if (!b) return;
+  if (b->main) cudaStreamSynchronize(b->main);
+  batch_graph_reset(b);
+  if (b->main) cudaStreamDestroy(b->main);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (auto* pl : b->items) pisco_destroy(pl);
+  for (auto s : b->streams) if (s) cudaStreamDestroy(s);
+  for (auto e : b->join) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_stream,
+                              pisco_batch_t* out) {
+  if (!out || !params || count < 1 || count > 4096) return PISCO_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    pisco_status s = validate(&params[i]);
+    if (s != PISCO_OK) return s;
+  }
+  pisco_batch_s* b = new (std::nothrow) pisco_batch_s();
+  if (!b) return PISCO_ERR_OOM;
+  b->user = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    pisco_batch_destroy(b);
+    return PISCO_ERR_CUDA;
+  }
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
+      pisco_batch_destroy(b);
+      return PISCO_ERR_CUDA;
+    }
+    b->streams.push_back(st);
+    b->join.push_back(ev);
+    pisco_params pi = params[i];
+    pi.flags |= PISCO_FLAG_HOST_IO;
+    pisco_plan_t pl = nullptr;
+    pisco_status s = pisco_plan(&pi, st, &pl);
+    if (s != PISCO_OK) {
+      pisco_batch_destroy(b);
+      return s;
+    }
+    pl->use_graph = false;
+    b->items.push_back(pl);
+  }
+  *out = b;
+  return PISCO_OK;
+}
+
+// capture (if the pointer set changed) and launch the whole batch; host_io: in/out are host
+// pointers (copied through each item's staging buffers inside the graph)
+static pisco_status batch_run(pisco_batch_s* b, const void* const* in, void* const* outp,
+                              float* const* eig, bool host_io, pisco_status* item_status) {
+  const int n = (int)b->items.size();
+  for (int i = 0; i < n; ++i)
+    if (!in[i] || !outp[i]) return PISCO_ERR_ARG;
+  if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess ||
+      cudaStreamWaitEvent(b->main, b->ev_in, 0) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  bool same = b->gexec && b->g_host == host_io && (int)b->g_in.size() == n;
+  for (int i = 0; same && i < n; ++i)
+    same = b->g_in[i] == in[i] && b->g_out[i] == outp[i] && b->g_eig[i] == (eig ? eig[i] : nullptr);
+  if (!same && !b->warmed) {
+    // first call: run every item eagerly on its own stream (same work as the graph)
+    pisco_status s = PISCO_OK;
+    if (cudaEventRecord(b->fork, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+    for (int i = 0; i < n && s == PISCO_OK; ++i) {
+      pisco_plan_s* pl = b->items[i];
+      cudaStream_t st = pl->st;
+      if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) return PISCO_ERR_CUDA;
+      const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
+      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          st) != cudaSuccess) return PISCO_ERR_CUDA;
+      float2* maps_dst = host_io ? pl->io_maps : (float2*)outp[i];
+      float* eig_dst = eig && eig[i] ? (host_io ? pl->io_eig : eig[i]) : nullptr;
+      pl->ev_used = 0;
+      s = run_all(pl, pl->calib_stage, maps_dst, eig_dst);
+      if (s != PISCO_OK) return s;
+      if (host_io) {
+        const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
+        if (cudaMemcpyAsync(outp[i], pl->io_maps, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PISCO_ERR_CUDA;
+        if (eig_dst && cudaMemcpyAsync(eig[i], pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PISCO_ERR_CUDA;
+      }
+      if (cudaEventRecord(b->join[i], st) != cudaSuccess ||
+          cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess) return PISCO_ERR_CUDA;
+    }
+    b->warmed = true;
+  } else if (!same) {
+    batch_graph_reset(b);
+    if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PISCO_ERR_CUDA;
+    int total_launches = 0;
+    pisco_status s = PISCO_OK;
+    if (cudaEventRecord(b->fork, b->main) != cudaSuccess) s = PISCO_ERR_CUDA;
+    for (int i = 0; i < n && s == PISCO_OK; ++i) {
+      pisco_plan_s* pl = b->items[i];
+      cudaStream_t st = pl->st;
+      if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
+      const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
+      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
+      float2* maps_dst = host_io ? pl->io_maps : (float2*)outp[i];
+      float* eig_dst = eig && eig[i] ? (host_io ? pl->io_eig : eig[i]) : nullptr;
+      pl->ev_used = 0;
+      s = run_all(pl, pl->calib_stage, maps_dst, eig_dst);  // counts its launches from zero
+      if (s != PISCO_OK) break;
+      total_launches += g_launches;
+      if (host_io) {
+        const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
+        if (cudaMemcpyAsync(outp[i], pl->io_maps, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
+        if (eig_dst && cudaMemcpyAsync(eig[i], pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost, st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
+      }
+      if (cudaEventRecord(b->join[i], st) != cudaSuccess ||
+          cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->main, &g);
+    if (s != PISCO_OK || ec != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return s != PISCO_OK ? s : PISCO_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      b->gexec = nullptr;
+      return PISCO_ERR_CUDA;
+    }
+    b->graph = g;
+    b->launches = total_launches;
+    b->g_host = host_io;
+    for (int i = 0; i < n; ++i) {
+      b->g_in.push_back(in[i]);
+      b->g_out.push_back(outp[i]);
+      b->g_eig.push_back(eig ? eig[i] : nullptr);
+    }
+  }
+  if (b->gexec && cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+  if (cudaEventRecord(b->ev_out, b->main) != cudaSuccess ||
+      cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  if (cudaStreamSynchronize(b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+  pisco_status worst = PISCO_OK;
+  for (int i = 0; i < n; ++i) {
+    pisco_plan_s* pl = b->items[i];
+    const DevStatus h = *pl->hstatus;
+    pl->last_status = h;
+    pl->last_launches = 0;
+    pisco_status si = PISCO_OK;
+    if (h.flags & ST_SATURATED) {
+      // the signal dimension reached the block: redo this item alone with a larger block
+      if (pl->m < pl->m_max) {
+        pl->m = std::min(pl->m * 2, pl->m_max);
+        batch_graph_reset(b);
+        si = host_io ? pisco_estimate_host(pl, in[i], outp[i], eig ? eig[i] : nullptr)
+                     : pisco_estimate(pl, in[i], outp[i], eig ? eig[i] : nullptr);
+      } else {
+        si = PISCO_ERR_NOT_CONVERGED;
+      }
+    } else {
+      pl->last_k = h.k;
+      pl->last_R = pl->n - h.k;
+      if (h.flags & ST_RANK) si = PISCO_ERR_RANK;
+    }
+    if (item_status) item_status[i] = si;
+    if (si != PISCO_OK && (worst == PISCO_OK || worst == PISCO_ERR_RANK)) worst = si;
+  }
+  return worst;
+}
+
+pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,
+                                  float* const* d_eig, pisco_status* item_status) {
+  if (!b || !d_calib || !d_maps) return PISCO_ERR_ARG;
+  return batch_run(b, d_calib, d_maps, d_eig, false, item_status);
+}
+
+pisco_status pisco_batch_estimate_host(pisco_batch_t b, const void* const* h_calib, void* const* h_maps,
+                                       float* const* h_eig, pisco_status* item_status) {
+  if (!b || !h_calib || !h_maps) return PISCO_ERR_ARG;
+  return batch_run(b, h_calib, h_maps, h_eig, true, item_status);
+}
+
+pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t* workspace_bytes) {
+  if (!b) return PISCO_ERR_ARG;
+  if (count) *count = (int)b->items.size();
+  if (launches) *launches = b->launches;
+  if (workspace_bytes) {
+    size_t t = 0;
+    for (auto* pl : b->items) t += pl->ws_bytes;
+    *workspace_bytes = t;
+  }
+  return PISCO_OK;
+}
+
+pisco_status pisco_batch_item(pisco_batch_t b, int i, pisco_plan_t* plan) {
+  if (!b || !plan || i < 0 || i >= (int)b->items.size()) return PISCO_ERR_ARG;
+  *plan = b->items[i];
   return PISCO_OK;
 }
 

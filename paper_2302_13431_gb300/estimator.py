@@ -130,3 +130,79 @@ class PiscoEstimator:
             self.close()
         except Exception:
             pass
+
+
+class PiscoBatch:
+    """A batch of independent estimates (shapes may differ), run as one CUDA graph.
+
+    specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
+    kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters.
+    """
+
+    def __init__(self, specs, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("PiscoBatch needs a CUDA GPU (no CPU fallback)")
+        self.specs = [dict(s) for s in specs]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        params = []
+        for sp in self.specs:
+            params.append(B.make_params(tuple(sp["grid"]), tuple(sp["calib_shape"]), sp["num_coils"],
+                                        sp["tau"], sp.get("kernel_shape", "ellipsoid"),
+                                        sp.get("thr", 0.05), sp.get("reduction", 1),
+                                        sp.get("iters", 30), sp.get("seed", 0), 0,
+                                        sp.get("eig_block", 0), sp.get("eig_iters", 0)))
+        st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_batch_plan")
+        self._b = h
+        self.last_item_status = None
+
+    def __len__(self):
+        return len(self.specs)
+
+    def estimate_into(self, calibs, maps, eigs=None):
+        st, items = B.pisco_batch_estimate(self._b, [c.data_ptr() for c in calibs],
+                                           [m.data_ptr() for m in maps],
+                                           [e.data_ptr() if e is not None else 0 for e in eigs] if eigs is not None else None)
+        self.last_item_status = items
+        if st not in (B.PISCO_OK, B.PISCO_ERR_RANK):
+            raise B.PiscoError(st, "pisco_batch_estimate")
+        return st
+
+    def estimate_host(self, calibs, maps, eigs=None):
+        st, items = B.pisco_batch_estimate(self._b, [c.ctypes.data for c in calibs],
+                                           [m.ctypes.data for m in maps],
+                                           [e.ctypes.data for e in eigs] if eigs is not None else None,
+                                           host=True)
+        self.last_item_status = items
+        if st not in (B.PISCO_OK, B.PISCO_ERR_RANK):
+            raise B.PiscoError(st, "pisco_batch_estimate_host")
+        return st
+
+    def alloc_outputs(self, device="cuda"):
+        maps, eigs = [], []
+        for sp in self.specs:
+            g = tuple(sp["grid"])
+            r = tuple(x // sp.get("reduction", 1) for x in g)
+            maps.append(torch.empty((sp["num_coils"],) + g, dtype=torch.complex64, device=device))
+            eigs.append(torch.empty(r, dtype=torch.float32, device=device))
+        return maps, eigs
+
+    def info(self):
+        st, c, l, w = B.pisco_batch_info(self._b)
+        return dict(count=c, launches=l, workspace_bytes=w)
+
+    def item_stats(self, i):
+        st, h = B.pisco_batch_item(self._b, i)
+        return B.pisco_get_stats(h)[1]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            B.pisco_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -208,3 +208,27 @@ def test_invalid_arguments_are_rejected_without_launch():
     assert B.pisco_estimate(est._plan, calib.data_ptr(), 0, None) == B.PISCO_ERR_ARG
     assert B.pisco_estimate(est._plan, calib.data_ptr() + 4, calib.data_ptr(), None) == B.PISCO_ERR_ARG
     est.close()
+
+
+def test_graph_replay_reads_new_calibration_data():
+    """Same buffers on every call: the first call runs eagerly, the second captures a CUDA graph,
+    the third replays it.  The replay must pick up the new contents of the calibration buffer."""
+    grid, Q, cs, tau, shape, red, iters, phase = CASES["2d_ragged"]
+    a = make_case(grid, Q, cs, seed=11, phase=phase).calib
+    b = make_case(grid, Q, cs, seed=12, phase=phase).calib
+    est = PiscoEstimator(grid, cs, Q, tau, kernel_shape=shape, reduction=red, iters=iters)
+    calib = torch.from_numpy(a).cuda()
+    maps = torch.empty((Q,) + grid, dtype=torch.complex64, device="cuda")
+    eig = torch.empty(tuple(g // red for g in grid), dtype=torch.float32, device="cuda")
+    est.estimate_into(calib, maps, eig)
+    first = maps.clone()
+    est.estimate_into(calib, maps, eig)
+    assert torch.equal(first, maps)
+    calib.copy_(torch.from_numpy(b))
+    est.estimate_into(calib, maps, eig)
+    fresh = PiscoEstimator(grid, cs, Q, tau, kernel_shape=shape, reduction=red, iters=iters)
+    maps_b, eig_b = fresh(torch.from_numpy(b).cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(maps, maps_b) and torch.equal(eig, eig_b)
+    est.close()
+    fresh.close()
