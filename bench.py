@@ -44,6 +44,7 @@ ORACLE_PIX_STRIDE = 8   # the CPU sample runs the per-pixel stages on every 8th 
 SMS, SM_MAX_MHZ = 152, 2070.0
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 128 FP32 lanes/SM, FMA = 2 flops
 FP64_PEAK_TFLOPS = 1.25                                      # GB300 FP64 (nominal)
+TF32_PER_BF16 = 1.1 / 2.25                                   # nominal dense tf32 : bf16 ratio
 
 
 def _peaks():
@@ -190,8 +191,16 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
-def roofline_for(op, prof, w, stats, peaks):
-    """Algorithmic work per launch of the dominant operation and its roofline."""
+def n_lags(w):
+    """|Lambda - Lambda| of the workload's kernel support (2D ellipse / rectangle)."""
+    t = w["tau"]
+    pts = [(y, x) for y in range(-t, t + 1) for x in range(-t, t + 1)
+           if w["shape"] == "rect" or y * y + x * x <= t * t]
+    return len({(a[0] - b[0], a[1] - b[1]) for a in pts for b in pts})
+
+
+def roofline_for(op, prof, w, stats, peaks, precision):
+    """Algorithmic work per launch of one operation and its roofline."""
     Q, L = w["Q"], stats["filter_len"]
     n = Q * L
     m = stats["eig_block"]
@@ -199,10 +208,27 @@ def roofline_for(op, prof, w, stats, peaks):
     npix = w["grid"][0] * w["grid"][1]
     total_ms, count = prof[op]
     avg_s = total_ms / count / 1e3
-    if op == "eig_gemm_AX_fp32":
+    terms = 1 if "1pass" in precision else 3
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
+    tc_note = (f"tcgen05 kind::tf32, {terms} TF32 pass(es) per product (the tensor pipe executes "
+               f"{terms}x the algorithmic flops); peak = measured dense bf16 x {TF32_PER_BF16:.3f} "
+               "(nominal tf32/bf16 ratio 1.1/2.25)")
+    if op == "eig_gemm_AX":
         work = 8.0 * n * n * m                       # complex MAC = 8 real flops
+        if "eig" in precision:
+            return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                        note="complex GEMM A(n x n) X(n x m); " + tc_note)
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="FP32 CUDA-core complex GEMM A(n x n) X(n x m); peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
+    if op == "g_field_tc":
+        work = 8.0 * nr * Q * Q * n_lags(w)
+        return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                    note="G[x][pq] = sum_l E[x][l] K[l][pq]: complex GEMM (N_r x |Lambda-Lambda|) by "
+                         "(|Lambda-Lambda| x Q^2); " + tc_note)
+    if op == "g_herk_tc":
+        work = 8.0 * n * n * m
+        return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                    note="P = U diag(w) U^H: complex GEMM (n x m) by (m x n); " + tc_note)
     if op == "eig_rayleigh_fp64":
         work = 8.0 * n * n * 16
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
@@ -261,17 +287,26 @@ def run_gpu(args):
     spec = dict(grid=w["grid"], calib_shape=w["calib"], num_coils=w["Q"], tau=w["tau"],
                 kernel_shape=w["shape"], thr=w["thr"], reduction=w["reduction"], iters=w["iters"])
 
-    # ---- plain single-map estimates (one plan, one map per call): context + op profile ----
-    est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
-                         thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0)
+    # ---- plain FP32 PISCO, one plan, one map per call (per-slice launches): comparison point ----
     maps1 = torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64, device="cuda")
     eig1 = torch.empty(red, dtype=torch.float32, device="cuda")
-    for i in range(max(args.warmup, 3)):
-        est.estimate_into(calibs[i % N_CASES], maps1, eig1)
-    torch.cuda.synchronize()
-    plain_ms = _time_steps(lambda i: est.estimate_into(calibs[i % N_CASES], maps1, eig1),
-                           min(args.steps, 20), flush, stream, "pisco_single_step")
-    plain_value = len(plain_ms) / (sum(plain_ms) / 1e3)
+    single = {}
+    for prec in dict.fromkeys(["fp32", args.precision]):
+        e1 = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"], thr=w["thr"],
+                            reduction=w["reduction"], iters=w["iters"], seed=0, precision=prec)
+        for i in range(max(args.warmup, 3)):
+            e1.estimate_into(calibs[i % N_CASES], maps1, eig1)
+        torch.cuda.synchronize()
+        ms = _time_steps(lambda i: e1.estimate_into(calibs[i % N_CASES], maps1, eig1),
+                         min(args.steps, 20), flush, stream, "pisco_single_step")
+        single[prec] = len(ms) / (sum(ms) / 1e3)
+        e1.close()
+    plain_value = single["fp32"]
+    # ---- op profile of one map (eager launches, CUDA events around each operation) ----
+    est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
+                         thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0,
+                         precision=args.precision)
+    est.estimate_into(calibs[0], maps1, eig1)
     stats = est.stats()
     est.set_profiling(True)
     est.estimate_into(calibs[0], maps1, eig1)
@@ -288,7 +323,7 @@ def run_gpu(args):
 
     # ---- batched form: one step = one CUDA-graph launch over `batch` maps ----
     nb = args.batch
-    batch = PiscoBatch([spec] * nb)
+    batch = PiscoBatch([dict(spec, precision=args.precision)] * nb)
     bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
     bmaps, beigs = batch.alloc_outputs()
     for i in range(args.warmup):
@@ -338,10 +373,16 @@ def run_gpu(args):
     batch.close()
 
     peaks = _peaks()
+    stages = {}
+    for op in prof:
+        r = roofline_for(op, prof, w, stats, peaks, args.precision)
+        if r.get("achieved") is not None and r.get("peak"):
+            r["frac"] = r["achieved"] / r["peak"]
+        r["ms_per_map"] = prof[op][0] / nprof
+        stages[op] = r
     dom = max(prof, key=lambda k: prof[k][0]) if prof else None
-    roof = roofline_for(dom, prof, w, stats, peaks) if dom else {}
-    if roof.get("achieved") is not None and roof.get("peak"):
-        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof = dict(stages[dom]) if dom else {}
+    roof.pop("ms_per_map", None)
     roof["kernel"] = dom
     roof["traffic"] = None
     roof["measured"] = "CUDA events around each launch of the op in the profiled single-map pass"
@@ -350,7 +391,11 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": "FP64 Gram and FP64 threshold split of the nullspace; FP32 elsewhere",
+        "precision": ("FP64 Gram and FP64 threshold split of the nullspace; " +
+                      {"fp32": "FP32 CUDA-core products elsewhere"}.get(
+                          args.precision, "split-precision TF32 tensor-core products (FP32 accumulate) for "
+                          + ("G(x) assembly and the eigensolver block products" if "eig" in args.precision
+                             else "G(x) assembly") + ", FP32 elsewhere")),
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "batch": nb,
                    "step": f"one CUDA-graph launch estimating {nb} independent map sets",
@@ -358,8 +403,11 @@ def run_gpu(args):
                    "inputs": f"{nb} calibration blocks ({N_CASES} distinct seeded contents) resident in HBM",
                    "parallelism": f"{world} independent replicas"},
         "pixel_eigensolves_per_s": value * nr,
-        "plain_single_map": {"value": plain_value, "unit": "maps/s",
-                             "note": "one plan, one map per call (per-slice launches)"},
+        "plain_fp32_single_map": {"value": plain_value, "unit": "maps/s",
+                                  "note": "plain FP32 PISCO: one plan, one map per call (per-slice "
+                                          "launches), CUDA-core FP32 products, same iterations"},
+        "single_map_same_precision": {"value": single[args.precision], "unit": "maps/s"},
+        "precision_mode": args.precision,
         "wall_s": t_wall,
         "gpu_launches": int(binfo["launches"]) * args.steps,
         "e2e": {"value": e2e_value, "unit": "maps/s",
@@ -369,7 +417,7 @@ def run_gpu(args):
         "clocks": clocks,
         "eig": {"k": stats["signal_dim"], "block": stats["eig_block"], "iters": stats["eig_iters"],
                 "jacobi_sweeps": stats["jacobi_sweeps"], "fp64_band": stats["nband"]},
-        "ops_ms_per_map": {k: v[0] / nprof for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "stages": {k: stages[k] for k in sorted(stages, key=lambda k: -stages[k]["ms_per_map"])},
         "workspace_bytes_batch": binfo["workspace_bytes"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -395,6 +443,8 @@ def main():
     ap.add_argument("--impl", choices=["pisco", "reference"], default="pisco")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=64, help="map sets per step (one graph launch)")
+    ap.add_argument("--precision", default="tc_g_eig",
+                    help="fp32 | tc_g | tc_g_eig | tc_g_1pass | tc_g_eig_1pass (see estimator.PRECISIONS)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "pisco":
         args.warmup = 3

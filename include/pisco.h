@@ -54,6 +54,17 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
 
 /* flags */
 #define PISCO_FLAG_HOST_IO 0x1u  /* allocate pinned/device staging for pisco_estimate_host   */
+#define PISCO_FLAG_TC_GFIELD 0x2u /* build G(x) (Sec. V-C, Eq. 24 in its lag form) with two
+                                     tensor-core GEMMs: P = U diag(w) U^H, folded onto the lags of
+                                     Lambda-Lambda, then G = |Lambda| I - E K with E the lag-to-
+                                     pixel exponentials.  Products in split-precision TF32
+                                     (three TF32 passes per product: head*head + head*tail +
+                                     tail*head), FP32 accumulate.  Default: CUDA-core FP32.     */
+#define PISCO_FLAG_TC_EIG 0x4u    /* the n x n by n x m block products of the nullspace
+                                     eigensolver on the tensor cores, same split precision.
+                                     The threshold split itself stays FP64 (Sec. III-B).       */
+#define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
+                                     11 significant bits) instead of three; for error studies */
 
 typedef struct {
   int ndim;               /* 2 or 3                                                          */
@@ -204,6 +215,24 @@ void pisco_batch_destroy(pisco_batch_t b);
  * synchronising. */
 pisco_status pisco_gram_lags_noalloc(const pisco_params* p, const void* d_calib, void* d_lags,
                                      void* cuda_stream);
+
+/* The dense complex contraction behind PISCO_FLAG_TC_GFIELD / PISCO_FLAG_TC_EIG, exposed for
+ * testing and reuse: C = alpha * A * op(B) + beta * C on the tensor cores (tcgen05, TF32
+ * operands, FP32 accumulation in tensor memory).
+ *   nterms: 3 = each FP32 operand split into a TF32 head and tail, three products per entry
+ *           (close to FP32 accuracy); 1 = one TF32 product (about 11 significant bits);
+ *   A: device complex64 M x K, row-major, leading dimension lda >= K;
+ *   opB 0: B is device complex64 K x N row-major, ldb >= N;
+ *   opB 1: op(B) = conj(Bs^T) with Bs device complex64 N x K row-major, ldb >= K;
+ *   C: device complex64 M x N row-major, ldc >= N, read when beta != 0, written;
+ *   alpha, beta: host float[2] (real, imaginary);
+ *   d_status: optional device int; bit 16 is OR-ed in if a bounded device wait expired.
+ * All device pointers 8-byte aligned (PISCO_ERR_ARG otherwise, nothing launched).  Enqueued on
+ * `cuda_stream`; returns without synchronising.  The first call sets kernel attributes, so
+ * make it outside stream capture. */
+pisco_status pisco_tc_cgemm(int nterms, int M, int N, int K, const float* alpha, const void* d_A,
+                            int lda, const void* d_B, int ldb, int opB, const float* beta, void* d_C,
+                            int ldc, int* d_status, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,9 @@ PISCO_OK, PISCO_ERR_ARG, PISCO_ERR_CUDA, PISCO_ERR_OOM, PISCO_ERR_RANK, PISCO_ER
     PISCO_ERR_NOT_CONVERGED, PISCO_ERR_UNSUPPORTED, PISCO_ERR_TOO_LARGE = range(9)
 PISCO_KERNEL_RECT, PISCO_KERNEL_ELLIPSOID = 0, 1
 PISCO_FLAG_HOST_IO = 0x1
+PISCO_FLAG_TC_GFIELD = 0x2
+PISCO_FLAG_TC_EIG = 0x4
+PISCO_FLAG_TC_1PASS = 0x8
 (PISCO_BUF_LAGS, PISCO_BUF_GRAM, PISCO_BUF_SIGNAL, PISCO_BUF_WEIGHTS, PISCO_BUF_RITZ, PISCO_BUF_G,
  PISCO_BUF_V, PISCO_BUF_Y, PISCO_BUF_BLOCK, PISCO_BUF_RITZ32, PISCO_BUF_SCALE) = range(11)
 
@@ -110,6 +113,10 @@ def load():
     lib.pisco_batch_destroy.restype = None
     lib.pisco_gram_lags_noalloc.argtypes = [P(pisco_params), vp, vp, vp]
     lib.pisco_gram_lags_noalloc.restype = ctypes.c_int
+    lib.pisco_tc_cgemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_float), vp,
+                                   ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_float), vp,
+                                   ctypes.c_int, vp, vp]
+    lib.pisco_tc_cgemm.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -241,3 +248,12 @@ def pisco_batch_item(batch, i):
 
 def pisco_batch_destroy(batch):
     load().pisco_batch_destroy(batch)
+
+
+def pisco_tc_cgemm(nterms, M, N, K, alpha, d_A, lda, d_B, ldb, opB, beta, d_C, ldc, d_status=0, stream=0):
+    """C = alpha*A*op(B) + beta*C on the tensor cores (see include/pisco.h); alpha, beta complex."""
+    a = (ctypes.c_float * 2)(float(complex(alpha).real), float(complex(alpha).imag))
+    b = (ctypes.c_float * 2)(float(complex(beta).real), float(complex(beta).imag))
+    return load().pisco_tc_cgemm(nterms, M, N, K, a, ctypes.c_void_p(d_A), lda, ctypes.c_void_p(d_B), ldb, opB,
+                                 b, ctypes.c_void_p(d_C), ldc, ctypes.c_void_p(d_status or 0),
+                                 ctypes.c_void_p(stream))

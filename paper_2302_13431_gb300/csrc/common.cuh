@@ -62,9 +62,10 @@ enum : int {
   ST_SATURATED = 2,     // signal dimension reached the eigensolver block
   ST_CHOL = 4,          // non-positive pivot clamped in a Cholesky factorisation
   ST_ZERO = 8,          // calibration data identically zero
+  ST_TIMEOUT = 16,      // a bounded wait of a tensor-core kernel expired
 };
 struct DevStatus {
-  int flags;
+  int flags;            // ST_* bits
   int k;                // signal dimension decided by the eigensolver
   int nband;            // Ritz values refined in FP64
   int jacobi_sweeps;    // sweeps used by the last small eigensolve
@@ -134,6 +135,17 @@ cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int 
                              const int* lag_ptr, const int* lag_ent, int nbox, float2* K,
                              cudaStream_t st);
 cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_size, cudaStream_t st);
+cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
+                               const int* lag_ent, int nlag, float2* KT, cudaStream_t st);
+
+// tensor-core complex GEMM (kernels_tc.cu): C = alpha*A*op(B) + beta*C (+ diag_val on columns
+// c % diag_stride == 0, c < diag_limit); A M x K row-major with optional per-k real scale;
+// opB 0: B K x N row-major, 1: conj of an N x K row-major array; nterms 3 (head/tail split TF32)
+// or 1 (TF32); err gets bit 16 on a bounded-wait expiry
+cudaError_t tc_gemm_prepare();
+cudaError_t tc_cgemm(int nterms, int M, int N, int K, float2 alpha, const float2* A, int lda,
+                     const float* kscale, const float2* B, int ldb, int opB, float2 beta, float2* C,
+                     int ldc, float diag_val, int diag_stride, int diag_limit, int* err, cudaStream_t st);
 
 // a4+a5: power iteration with the phase step
 cudaError_t power_iteration(const float2* G, const float2* Y, int Q, long long npix, int iters,

@@ -106,3 +106,44 @@ cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_s
 }
 
 }  // namespace pisco
+
+namespace pisco {
+
+// Tensor-core route of stage (c): with P = U diag(w) U^H (n x n, row (q,b), column (p,a)) formed
+// by a tensor-core GEMM, fold P onto the lags of Lambda - Lambda:
+//     KT[l][p*Q + q] = sum_{(b,a): b - a = d_l} P[(q,b)][(p,a)],
+// the entries of each lag summed in the fixed CSR order (bitwise reproducible).  KT is the
+// K x N operand of the second GEMM, G[x][pq] = |Lambda| delta_pq - sum_l E[x][l] KT[l][pq].
+__global__ void collapse_lags_kernel(const float2* __restrict__ P, int n, int Q, int L,
+                                     const int* __restrict__ lagc_ptr, const int* __restrict__ lag_ent,
+                                     int nlag, float2* __restrict__ KT) {
+  const int QQ = Q * Q;
+  const long long total = (long long)nlag * QQ;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / QQ), pq = (int)(idx % QQ);
+    const int p = pq / Q, q = pq % Q;
+    const float2* rowq = P + (long long)q * L * n + (long long)p * L;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int e = lagc_ptr[l]; e < lagc_ptr[l + 1]; ++e) {
+      const int ent = lag_ent[e];
+      const int b = ent / L, a = ent % L;
+      const float2 v = rowq[(long long)b * n + a];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    KT[idx] = acc;
+  }
+}
+
+cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
+                               const int* lag_ent, int nlag, float2* KT, cudaStream_t st) {
+  const long long total = (long long)nlag * Q * Q;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  collapse_lags_kernel<<<(unsigned)blocks, 256, 0, st>>>(P, n, Q, L, lagc_ptr, lag_ent, nlag, KT);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pisco

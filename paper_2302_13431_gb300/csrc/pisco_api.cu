@@ -49,6 +49,15 @@ struct pisco_plan_s {
   float2* interp[3] = {nullptr, nullptr, nullptr};
   int* d_lag_of_ij = nullptr;
   int *d_lag_ptr = nullptr, *d_lag_ent = nullptr;
+  // tensor-core routes (PISCO_FLAG_TC_*): lags of Lambda-Lambda only (compressed CSR), the
+  // lag-to-pixel exponentials E [npix_red][nlag] and the folded lag table KT [nlag][Q*Q]
+  bool tc_g = false, tc_eig = false;
+  int tc_terms = 3;
+  int nlag = 0;
+  std::vector<int> lagc_ptr, lag_ids;
+  int* d_lagc_ptr = nullptr;
+  float2* E = nullptr;
+  float2* KT = nullptr;
   // device buffers
   double2 *gA = nullptr, *gB = nullptr, *S = nullptr, *P = nullptr, *Rp = nullptr, *lags = nullptr;
   double2* A = nullptr;
@@ -194,6 +203,33 @@ std::vector<float2> ydft_matrix(int Nr, int Nc) {
 // periodic-sinc interpolation n_in -> n_out (Sec. V-D): DFT of the coarse samples, band
 // k in [-n_in/2, n_in - n_in/2), Nyquist coefficient split between +-n_in/2 for even n_in,
 // evaluated at the fine points.  Computed in FP64 as an explicit matrix.
+// lag-to-pixel exponentials of the tensor-core G route: E[j][l] = exp(+i 2 pi d_l . x_j) with
+// x_j = (j - Nr/2)/Nr per axis (the points of the separable lag sums), phases reduced exactly
+// in integers before the FP64 sine and cosine
+std::vector<float2> lag_pixel_matrix(const int* Nr, const int* B, const int* tau,
+                                     const std::vector<int>& lag_ids) {
+  const long long np = (long long)Nr[0] * Nr[1] * Nr[2];
+  const int nl = (int)lag_ids.size();
+  std::vector<float2> E((size_t)np * nl);
+  for (long long x = 0; x < np; ++x) {
+    const long long j[3] = {x / ((long long)Nr[1] * Nr[2]), (x / Nr[2]) % Nr[1], x % Nr[2]};
+    for (int l = 0; l < nl; ++l) {
+      const int t = lag_ids[l];
+      const long long d[3] = {t / (B[1] * B[2]) - 2 * tau[0], (t / B[2]) % B[1] - 2 * tau[1],
+                              t % B[2] - 2 * tau[2]};
+      double frac = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        long long num = (d[a] * (j[a] - Nr[a] / 2)) % Nr[a];
+        if (num < 0) num += Nr[a];
+        frac += (double)num / Nr[a];
+      }
+      const double ang = 2.0 * kPi * frac;
+      E[(size_t)x * nl + l] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+  }
+  return E;
+}
+
 std::vector<float2> interp_matrix(int n_in, int n_out) {
   std::vector<float2> M((size_t)n_out * n_in);
   const int k0 = -(n_in / 2), k1 = n_in - n_in / 2;
@@ -265,6 +301,15 @@ void build_support(pisco_plan_s* pl) {
   pl->lag_ent.assign((size_t)pl->L * pl->L, 0);
   std::vector<int> fill(pl->lag_ptr.begin(), pl->lag_ptr.end() - 1);
   for (int e = 0; e < pl->L * pl->L; ++e) pl->lag_ent[fill[pl->lag_of_ij[e]]++] = e;
+  // the same lists restricted to the lags that occur (Lambda - Lambda), same entry order
+  pl->lagc_ptr.assign(1, 0);
+  pl->lag_ids.clear();
+  for (int t = 0; t < nbox; ++t)
+    if (pl->lag_ptr[t + 1] > pl->lag_ptr[t]) {
+      pl->lag_ids.push_back(t);
+      pl->lagc_ptr.push_back(pl->lag_ptr[t + 1]);
+    }
+  pl->nlag = (int)pl->lag_ids.size();
 }
 
 pisco_status validate(const pisco_params* p) {
@@ -408,6 +453,17 @@ pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, co
   return PISCO_OK;
 }
 
+// Y = A32 X (n x n by n x m): tensor cores (split TF32) or CUDA cores (FP32)
+cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y) {
+  const int n = pl->n, m = pl->m;
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  if (pl->tc_eig)
+    return tc_cgemm(pl->tc_terms, n, m, n, one, pl->A32, n, nullptr, X, m, 0, zero, Y, m, 0.f, 0, 0,
+                    &pl->dstatus->flags, pl->st);
+  return cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, X, m, zero, Y, m, pl->ws32, pl->ws32_elems,
+                      pl->tiles, pl->st);
+}
+
 // Nullspace of the Gram (Sec. III-A, threshold footnote of Sec. III-B): orthogonal
 // iteration on an m-column block in FP32, two Gram products per orthonormalisation with the
 // block rescaled by the square of the previous diag(R) (keeps Cholesky-QR well conditioned),
@@ -421,7 +477,7 @@ pisco_status run_eig(pisco_plan_s* pl) {
   pisco_status s;
   // random start; the first product can be ill conditioned -> shifted Cholesky-QR + two passes
   OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
-  OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->Y, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  OP("eig_gemm_AX", ax_product(pl, pl->Y, pl->Z));
   const float shift = 11.0f * ((float)m * n + (float)m * (m + 1)) * 5.9604645e-8f;
   if ((s = cholqr(pl, pl->Z, pl->Y, m, nullptr, shift, nullptr, pl->dR1)) != PISCO_OK) return s;
   if ((s = cholqr(pl, pl->Y, pl->Z, m, nullptr, 0.f, pl->dR1, pl->dR0)) != PISCO_OK) return s;
@@ -435,10 +491,10 @@ pisco_status run_eig(pisco_plan_s* pl) {
     // one Gram product per orthonormalisation: with two, the squared dynamic range of the
     // noise-level columns (~(1e-5)^2) exceeds what FP32 Cholesky-QR can resolve
     const int g = 1;
-    OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->X, m, zero, pl->Y, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+    OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Y));
     const float2* src = pl->Y;
     if (g == 2) {
-      OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->Y, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+      OP("eig_gemm_AX", ax_product(pl, pl->Y, pl->Z));
       src = pl->Z;
     }
     if (g != cur) OP("eig_misc", eig_pow(dprev, m, (float)g / (float)cur, st));
@@ -448,7 +504,7 @@ pisco_status run_eig(pisco_plan_s* pl) {
     left -= g;
   }
   // Rayleigh-Ritz on the block
-  OP("eig_gemm_AX_fp32", cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, pl->X, m, zero, pl->Z, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
+  OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
   OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
   OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
   OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st));
@@ -469,6 +525,19 @@ pisco_status run_gfield(pisco_plan_s* pl) {
   const int* B = pl->B;
   const int* Nr = pl->Nr;
   const long long QQ = (long long)Q * Q;
+  if (pl->tc_g) {
+    // P = U diag(w) U^H into the (now free) FP32 Gram buffer, fold onto the lags, then
+    // G = |Lambda| I - E KT, all products on the tensor cores
+    const int n = pl->n;
+    int* err = &pl->dstatus->flags;
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f), mone = make_float2(-1.f, 0.f);
+    OP("g_herk_tc", tc_cgemm(pl->tc_terms, n, n, pl->m, one, pl->U, pl->m, pl->w, pl->U, pl->m, 1, zero,
+                             pl->A32, n, 0.f, 0, 0, err, st));
+    OP("g_collapse", gassembly_collapse(pl->A32, n, Q, pl->L, pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->KT, st));
+    OP("g_field_tc", tc_cgemm(pl->tc_terms, (int)pl->npix_red, (int)QQ, pl->nlag, mone, pl->E, pl->nlag, nullptr,
+                              pl->KT, (int)QQ, 0, zero, pl->G, (int)QQ, (float)pl->L, Q + 1, (int)QQ, err, st));
+    return PISCO_OK;
+  }
   OP("g_kernel", gassembly_kernel(pl->U, pl->w, Q, pl->L, pl->m, pl->d_lag_ptr, pl->d_lag_ent, pl->nbox, pl->K, st));
   OP("g_dft", apply_axis_c(pl->K, pl->gdft[2], pl->T1, AxisView{QQ, (long long)B[0] * B[1], B[2], Nr[2], 1}, st));
   if (pl->D == 3) {
@@ -603,6 +672,14 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->m = p->eig_block > 0 ? std::min(p->eig_block, mmax) : std::min(64, mmax);
   if (pl->m < 2) { delete pl; return PISCO_ERR_ARG; }
   pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 8;
+  pl->tc_g = (p->flags & PISCO_FLAG_TC_GFIELD) != 0;
+  pl->tc_eig = (p->flags & PISCO_FLAG_TC_EIG) != 0;
+  pl->tc_terms = (p->flags & PISCO_FLAG_TC_1PASS) ? 1 : 3;
+  if ((pl->tc_g || pl->tc_eig) && tc_gemm_prepare() != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return PISCO_ERR_CUDA;
+  }
   if (const char* cv = getenv("PISCO_CHOL")) pl->chol_variant = atoi(cv);
 
   const int Q = pl->Q, n = pl->n, np = pl->npairs;
@@ -650,6 +727,11 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->T1, (size_t)(QQ * B[0] * B[1] * Nr[2]));
   ok = ok && dalloc(pl, &pl->T2, (size_t)(QQ * B[0] * Nr[1] * Nr[2]));
   ok = ok && dalloc(pl, &pl->G, (size_t)(QQ * pl->npix_red));
+  if (ok && pl->tc_g) {
+    ok = upload(pl, &pl->d_lagc_ptr, pl->lagc_ptr) &&
+         upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
+         dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ);
+  }
   // low-res images, PI output, interpolation intermediates
   ok = ok && dalloc(pl, &pl->Ya, (size_t)Q * Nc[0] * Nc[1] * Nr[2]);
   ok = ok && dalloc(pl, &pl->Yb, (size_t)Q * Nc[0] * Nr[1] * Nr[2]);
@@ -759,6 +841,7 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
     }
     const DevStatus h = *pl->hstatus;
     pl->last_status = h;
+    if (h.flags & ST_TIMEOUT) return PISCO_ERR_TIMEOUT;
     if ((h.flags & ST_SATURATED) && pl->m < pl->m_max) {
       pl->m = std::min(pl->m * 2, pl->m_max);
       continue;
@@ -1040,7 +1123,9 @@ static pisco_status batch_run(pisco_batch_s* b, const void* const* in, void* con
     pl->last_status = h;
     pl->last_launches = 0;
     pisco_status si = PISCO_OK;
-    if (h.flags & ST_SATURATED) {
+    if (h.flags & ST_TIMEOUT) {
+      si = PISCO_ERR_TIMEOUT;
+    } else if (h.flags & ST_SATURATED) {
       // the signal dimension reached the block: redo this item alone with a larger block
       if (pl->m < pl->m_max) {
         pl->m = std::min(pl->m * 2, pl->m_max);
@@ -1059,6 +1144,24 @@ static pisco_status batch_run(pisco_batch_s* b, const void* const* in, void* con
     if (si != PISCO_OK && (worst == PISCO_OK || worst == PISCO_ERR_RANK)) worst = si;
   }
   return worst;
+}
+
+pisco_status pisco_tc_cgemm(int nterms, int M, int N, int K, const float* alpha, const void* d_A, int lda,
+                            const void* d_B, int ldb, int opB, const float* beta, void* d_C, int ldc,
+                            int* d_status, void* cuda_stream) {
+  if (M < 0 || N < 0 || K < 0 || (nterms != 1 && nterms != 3) || (opB != 0 && opB != 1)) return PISCO_ERR_ARG;
+  if (M == 0 || N == 0) return PISCO_OK;
+  if (!d_C || !alpha || !beta || (K > 0 && (!d_A || !d_B))) return PISCO_ERR_ARG;  // K = 0: A, B unread
+  if (lda < K || ldc < N || ldb < (opB == 0 ? N : K)) return PISCO_ERR_ARG;
+  if (((uintptr_t)d_A | (uintptr_t)d_B | (uintptr_t)d_C) & 7) return PISCO_ERR_ARG;
+  if (tc_gemm_prepare() != cudaSuccess) {
+    cudaGetLastError();
+    return PISCO_ERR_CUDA;
+  }
+  const cudaError_t e = tc_cgemm(nterms, M, N, K, make_float2(alpha[0], alpha[1]), (const float2*)d_A, lda,
+                                 nullptr, (const float2*)d_B, ldb, opB, make_float2(beta[0], beta[1]),
+                                 (float2*)d_C, ldc, 0.f, 0, 0, d_status, (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? PISCO_OK : PISCO_ERR_CUDA;
 }
 
 pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,

@@ -20,6 +20,24 @@ class _DevView:
                                          "data": (int(ptr), False), "version": 2}
 
 
+PRECISIONS = {
+    # name: (flags, meaning)
+    "fp32": (0, "CUDA-core FP32 products everywhere (the plain path)"),
+    "tc_g": (B.PISCO_FLAG_TC_GFIELD, "G(x) assembly on tensor cores, 3-pass split TF32"),
+    "tc_g_eig": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_EIG,
+                 "G(x) assembly and eigensolver block products on tensor cores, 3-pass split TF32"),
+    "tc_g_1pass": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_1PASS, "G(x) assembly, single TF32 pass"),
+    "tc_g_eig_1pass": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_EIG | B.PISCO_FLAG_TC_1PASS,
+                       "G(x) and eigensolver products, single TF32 pass"),
+}
+
+
+def precision_flags(precision: str) -> int:
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    return PRECISIONS[precision][0]
+
+
 class PiscoEstimator:
     """One plan of the estimator for a fixed problem shape.
 
@@ -30,7 +48,7 @@ class PiscoEstimator:
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
-                 stream=None):
+                 stream=None, precision="fp32"):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -39,9 +57,9 @@ class PiscoEstimator:
         self.reduction = int(reduction)
         self.reduced = tuple(g // reduction for g in self.grid)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        flags = (B.PISCO_FLAG_HOST_IO if host_io else 0) | precision_flags(precision)
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
-                                    reduction, iters, seed, B.PISCO_FLAG_HOST_IO if host_io else 0,
-                                    eig_block, eig_iters)
+                                    reduction, iters, seed, flags, eig_block, eig_iters)
         st, h = B.pisco_plan(self.params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
             raise B.PiscoError(st, "pisco_plan")
@@ -136,7 +154,7 @@ class PiscoBatch:
     """A batch of independent estimates (shapes may differ), run as one CUDA graph.
 
     specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
-    kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters.
+    kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision.
     """
 
     def __init__(self, specs, stream=None):
@@ -149,7 +167,8 @@ class PiscoBatch:
             params.append(B.make_params(tuple(sp["grid"]), tuple(sp["calib_shape"]), sp["num_coils"],
                                         sp["tau"], sp.get("kernel_shape", "ellipsoid"),
                                         sp.get("thr", 0.05), sp.get("reduction", 1),
-                                        sp.get("iters", 30), sp.get("seed", 0), 0,
+                                        sp.get("iters", 30), sp.get("seed", 0),
+                                        precision_flags(sp.get("precision", "fp32")),
                                         sp.get("eig_block", 0), sp.get("eig_iters", 0)))
         st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
