@@ -211,6 +211,19 @@ class PiscoBatch:
         st, c, l, w = B.pisco_batch_info(self._b)
         return dict(count=c, launches=l, workspace_bytes=w)
 
+    def debug_buffer(self, i, which: int) -> torch.Tensor:
+        """A copy of one intermediate buffer of item i's last estimate (flat tensor)."""
+        st, h = B.pisco_batch_item(self._b, i)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_batch_item")
+        st, ptr, nbytes = B.pisco_debug_buffer(h, which)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_debug_buffer")
+        ts = PiscoEstimator._BUF_TYPES[which]
+        view = _DevView(ptr, (nbytes // int(ts[2:]),), ts)
+        torch.cuda.synchronize()
+        return torch.as_tensor(view, device="cuda").clone()
+
     def item_stats(self, i):
         st, h = B.pisco_batch_item(self._b, i)
         return B.pisco_get_stats(h)[1]

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "grid_coords", "ellipse_phantom", "coil_maps", "centered_dft", "add_noise",
-    "crop_center", "SyntheticCase", "make_case", "PAPER_WORKLOADS",
+    "crop_center", "SyntheticCase", "make_case", "PAPER_WORKLOADS", "uneven_slice_specs",
 ]
 
 
@@ -157,3 +157,20 @@ PAPER_WORKLOADS = {
     "3d_128x128x96": dict(grid=(96, 128, 128), Q=32, calib=(24, 24, 24), kernel="ellipsoid",
                           tau=3, reduction=4, iters=30, phase="poly4"),
 }
+
+
+def uneven_slice_specs(count=96, seed=0):
+    """Seeded shapes of the batched uneven-slice workload: square grids drawn uniformly from
+    {192, 224, 256, 288, 320}, Q from {16, 32, 48, 64}, square calibration 24..40 (inclusive),
+    ellipsoidal kernel of radius 3, grid reduction 4, 30 power iterations.  Each spec carries
+    the seed of its own synthetic case (data seed = 5000 + index)."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(rng.choice([192, 224, 256, 288, 320]))
+        q = int(rng.choice([16, 32, 48, 64]))
+        c = int(rng.integers(24, 41))
+        specs.append(dict(grid=(n, n), calib_shape=(c, c), num_coils=q, tau=3, kernel_shape="ellipsoid",
+                          reduction=4, iters=30, data_seed=5000 + i))
+    return specs
+
