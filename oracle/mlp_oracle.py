@@ -6,10 +6,11 @@ the product path never does.
 The warm start proposes each pixel's power-iteration start vector (Sec. V-E) from the pixel's
 normalised low-resolution coil vector y(x)/||y(x)|| (Sec. V-D) with a small per-pixel MLP:
 
-    h1 = relu(W1 x + b1),  h2 = relu(W2 h1 + b2),  out = W3 h2 + b3
+    h1 = relu(W1 x + b1),  h2 = relu(W2 h1 + b2),  out = x + W3 h2 + b3
 
 x and out are 2Q reals (real and imaginary parts interleaved per coil), the hidden layers have
-H units.  Weights are stored in FP16 (biases FP32); the oracle evaluates the FP16-rounded
+H units.  The skip term x (present whenever the input and output widths agree) makes the
+network a learned correction of the heuristic start y(x)/||y(x)||.  Weights are stored in FP16 (biases FP32); the oracle evaluates the FP16-rounded
 weights in FP64.  Loss: mean over the batch of the squared error to the target vector,
 L = (1/B) sum_b ||out_b - t_b||^2.  Optimiser: Adam with bias correction (Kingma & Ba, 2015)
 on FP32 master weights.
@@ -29,13 +30,14 @@ def shapes(n_in, n_hidden, n_out):
             "W3": (n_out, n_hidden), "b3": (n_out,)}
 
 
-def init_params(n_in, n_hidden, n_out, seed=0):
-    """He-normal weights (std sqrt(2/fan_in)), zero biases, FP32 master copies."""
+def init_params(n_in, n_hidden, n_out, seed=0, last_scale=1.0):
+    """He-normal weights (std sqrt(2/fan_in); W3 scaled by last_scale), zero biases, FP32."""
     rng = np.random.default_rng(seed)
     p = {}
     for name, shp in shapes(n_in, n_hidden, n_out).items():
         if name.startswith("W"):
-            p[name] = (rng.standard_normal(shp) * np.sqrt(2.0 / shp[1])).astype(np.float32)
+            sc = last_scale if name == "W3" else 1.0
+            p[name] = (rng.standard_normal(shp) * np.sqrt(2.0 / shp[1]) * sc).astype(np.float32)
         else:
             p[name] = np.zeros(shp, np.float32)
     return p
@@ -72,6 +74,8 @@ def forward(p, x, round16=True):
     z2 = h1 @ e["W2"].T + e["b2"]
     h2 = np.maximum(z2, 0.0)
     out = h2 @ e["W3"].T + e["b3"]
+    if x.shape[1] == out.shape[1]:
+        out = out + x
     return out, dict(x=x, z1=z1, h1=h1, z2=z2, h2=h2)
 
 

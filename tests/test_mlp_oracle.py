@@ -10,9 +10,10 @@ def _rand_params(rng, n_in, H, n_out, scale=0.7):
     return {k: rng.standard_normal(s) * scale for k, s in M.shapes(n_in, H, n_out).items()}
 
 
-def test_gradient_matches_central_differences():
+@pytest.mark.parametrize("n_out", [3, 4])
+def test_gradient_matches_central_differences(n_out):
     rng = np.random.default_rng(0)
-    n_in, H, n_out, B = 4, 5, 3, 7
+    n_in, H, B = 4, 5, 7
     p = _rand_params(rng, n_in, H, n_out)
     x = rng.standard_normal((B, n_in))
     t = rng.standard_normal((B, n_out))
@@ -32,11 +33,13 @@ def test_gradient_matches_central_differences():
             assert abs(g[k].reshape(-1)[idx] - fd) <= 1e-6 * max(1.0, abs(fd)), (k, idx)
 
 
-def test_zero_weights_closed_form():
-    """W1 = W2 = W3 = 0: the hidden units are the constants relu(b1), relu(b2), the output is b3
-    for every sample; only W3 and b3 receive gradient: g_b3 = 2(b3 - mean t), g_W3 = g_b3 relu(b2)^T."""
+@pytest.mark.parametrize("n_out", [6, 5])
+def test_zero_weights_closed_form(n_out):
+    """W1 = W2 = W3 = 0: the hidden units are the constants relu(b1), relu(b2), the output is
+    b3 (+ x when the widths agree: the skip term); only W3 and b3 receive gradient:
+    g_b3 = 2 mean(out - t), g_W3 = g_b3 relu(b2)^T."""
     rng = np.random.default_rng(1)
-    n_in, H, n_out, B = 6, 8, 6, 11
+    n_in, H, B = 6, 8, 11
     p = {k: np.zeros(s) for k, s in M.shapes(n_in, H, n_out).items()}
     p["b1"] = rng.standard_normal(H)
     p["b2"] = rng.standard_normal(H)
@@ -44,8 +47,9 @@ def test_zero_weights_closed_form():
     x = rng.standard_normal((B, n_in))
     t = rng.standard_normal((B, n_out))
     L, g = M.backward(p, x, t)
-    assert np.isclose(L, np.mean(np.sum((p["b3"][None] - t) ** 2, axis=1)))
-    gb3 = 2 * (p["b3"] - t.mean(axis=0))
+    out = p["b3"][None] + (x if n_out == n_in else 0.0)
+    assert np.isclose(L, np.mean(np.sum((out - t) ** 2, axis=1)))
+    gb3 = 2 * (out - t).mean(axis=0)
     np.testing.assert_allclose(g["b3"], gb3, atol=1e-12)
     np.testing.assert_allclose(g["W3"], np.outer(gb3, np.maximum(p["b2"], 0)), atol=1e-12)
     for k in ("W1", "b1", "W2", "b2"):
@@ -88,3 +92,11 @@ def test_pack_unpack_and_features():
     np.testing.assert_allclose(np.linalg.norm(x, axis=1)[[0, 1, 2, 4]], 1.0)
     assert np.all(x[3] == 0)
     np.testing.assert_allclose(M.to_complex(x)[0] * np.linalg.norm(y[0]), y[0])
+
+
+def test_zero_last_layer_starts_at_the_heuristic():
+    """With W3 = 0 and b3 = 0 the network returns its input (the normalised low-res vector)."""
+    p = M.init_params(8, 16, 8, seed=8, last_scale=0.0)
+    x = np.random.default_rng(9).standard_normal((5, 8))
+    out, _ = M.forward(p, x)
+    np.testing.assert_array_equal(out, x)
