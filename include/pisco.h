@@ -158,6 +158,7 @@ typedef struct {
   double lambda_max;  /* largest eigenvalue of C^H C (sigma_1^2), FP64                     */
   int signal_dim;     /* k = Q|Lambda| - R                                                 */
   int filter_len;     /* |Lambda|                                                          */
+  int warm_fallback;  /* pixels re-solved from the plain start (warm start only)            */
 } pisco_stats;
 pisco_status pisco_get_stats(pisco_plan_t plan, pisco_stats* out);
 
@@ -215,6 +216,54 @@ void pisco_batch_destroy(pisco_batch_t b);
  * synchronising. */
 pisco_status pisco_gram_lags_noalloc(const pisco_params* p, const void* d_calib, void* d_lags,
                                      void* cuda_stream);
+
+/* ---- Learned warm start of the power iteration (an addition of this library; the paper
+ * starts every pixel from an arbitrary vector, Sec. V-E) ------------------------------------
+ * A per-pixel MLP maps the pixel's normalised low-resolution coil vector y(x)/||y(x)||
+ * (Sec. V-D; 2Q reals, real and imaginary parts interleaved per coil) through two ReLU hidden
+ * layers to a proposed start vector (2Q reals):
+ *     h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), out = x + W3 h2 + b3,
+ * the skip term x present when n_in == n_out (the network corrects the heuristic start
+ * y(x)/||y(x)||; with W3 = 0, b3 = 0 it returns that start).
+ * Parameters travel as one FP32 blob [W1 | b1 | W2 | b2 | W3 | b3], weights row-major
+ * (W1: n_hidden x n_in, W2: n_hidden x n_hidden, W3: n_out x n_hidden).  The network
+ * evaluates FP16-rounded weights with FP32 accumulation; Adam updates FP32 master weights.
+ * All widths are in [1, 128].  Calls are enqueued on the stream given at creation. */
+typedef struct pisco_mlp_s* pisco_mlp_t;
+
+/* Create a network with the given parameters (host blob, copied) and device workspace for
+ * batches of up to max_batch samples (<= 2^26). */
+pisco_status pisco_mlp_create(int n_in, int n_hidden, int n_out, const float* h_params,
+                              long long max_batch, void* cuda_stream, pisco_mlp_t* out);
+/* Replace the parameters (host blob) and reset the Adam moments and step count. */
+pisco_status pisco_mlp_write(pisco_mlp_t mlp, const float* h_params);
+/* d_out[b][:] = network(d_x[b][:]); device FP32 arrays [batch][n_in] and [batch][n_out]. */
+pisco_status pisco_mlp_forward(pisco_mlp_t mlp, const float* d_x, long long batch, float* d_out);
+/* Forward and backward pass of L = (1/batch) sum_b ||out_b - t_b||^2 for device FP32 inputs
+ * d_x [batch][n_in] and targets d_target [batch][n_out]; the gradient of every parameter is
+ * kept in the network (pisco_mlp_read which = 1).  h_loss (optional): L, after a
+ * synchronisation. */
+pisco_status pisco_mlp_backward(pisco_mlp_t mlp, const float* d_x, const float* d_target,
+                                long long batch, double* h_loss);
+/* One Adam step (bias-corrected) with the last gradient. */
+pisco_status pisco_mlp_adam(pisco_mlp_t mlp, float lr, float beta1, float beta2, float eps);
+/* Copy the FP32 parameters (which = 0) or the last gradient (which = 1) into a host blob;
+ * synchronises. */
+pisco_status pisco_mlp_read(pisco_mlp_t mlp, int which, float* h_out);
+void pisco_mlp_destroy(pisco_mlp_t mlp); /* NULL-safe */
+/* The network's input features, as the estimate computes them: from low-resolution coil images
+ * d_y (device complex64 [Q][npix], the layout of PISCO_BUF_Y) to d_x (device FP32 [npix][2Q]),
+ * x_j = y_j/||y_j|| with real and imaginary parts interleaved; zero vectors stay zero. */
+pisco_status pisco_warm_start_features(const void* d_y, int Q, long long npix, float* d_x,
+                                       void* cuda_stream);
+
+/* Use `mlp` (n_in = n_out = 2Q, copied into the plan; NULL switches the warm start off) to
+ * start the power iteration of every reduced-grid pixel, run `iters` iterations, and
+ * re-solve from the plain start vector with `fallback_iters` iterations every pixel whose
+ * residual ||G v - lambda |Lambda| v|| / |Lambda| exceeds `gate` (gate <= 0: no fallback).
+ * The number of re-solved pixels of the last estimate is in pisco_stats.warm_fallback. */
+pisco_status pisco_set_warm_start(pisco_plan_t plan, pisco_mlp_t mlp, int iters, float gate,
+                                  int fallback_iters);
 
 /* The dense complex contraction behind PISCO_FLAG_TC_GFIELD / PISCO_FLAG_TC_EIG, exposed for
  * testing and reuse: C = alpha * A * op(B) + beta * C on the tensor cores (tcgen05, TF32

@@ -51,6 +51,7 @@ class pisco_stats(ctypes.Structure):
         ("lambda_max", ctypes.c_double),
         ("signal_dim", ctypes.c_int),
         ("filter_len", ctypes.c_int),
+        ("warm_fallback", ctypes.c_int),
     ]
 
 
@@ -117,6 +118,25 @@ def load():
                                    ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_float), vp,
                                    ctypes.c_int, vp, vp]
     lib.pisco_tc_cgemm.restype = ctypes.c_int
+    fp = P(ctypes.c_float)
+    lib.pisco_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, ctypes.c_longlong, vp, P(vp)]
+    lib.pisco_mlp_create.restype = ctypes.c_int
+    lib.pisco_mlp_write.argtypes = [vp, fp]
+    lib.pisco_mlp_write.restype = ctypes.c_int
+    lib.pisco_mlp_forward.argtypes = [vp, vp, ctypes.c_longlong, vp]
+    lib.pisco_mlp_forward.restype = ctypes.c_int
+    lib.pisco_mlp_backward.argtypes = [vp, vp, vp, ctypes.c_longlong, P(ctypes.c_double)]
+    lib.pisco_mlp_backward.restype = ctypes.c_int
+    lib.pisco_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    lib.pisco_mlp_adam.restype = ctypes.c_int
+    lib.pisco_mlp_read.argtypes = [vp, ctypes.c_int, fp]
+    lib.pisco_mlp_read.restype = ctypes.c_int
+    lib.pisco_mlp_destroy.argtypes = [vp]
+    lib.pisco_mlp_destroy.restype = None
+    lib.pisco_set_warm_start.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float, ctypes.c_int]
+    lib.pisco_set_warm_start.restype = ctypes.c_int
+    lib.pisco_warm_start_features.argtypes = [vp, ctypes.c_int, ctypes.c_longlong, vp, vp]
+    lib.pisco_warm_start_features.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -257,3 +277,60 @@ def pisco_tc_cgemm(nterms, M, N, K, alpha, d_A, lda, d_B, ldb, opB, beta, d_C, l
     return load().pisco_tc_cgemm(nterms, M, N, K, a, ctypes.c_void_p(d_A), lda, ctypes.c_void_p(d_B), ldb, opB,
                                  b, ctypes.c_void_p(d_C), ldc, ctypes.c_void_p(d_status or 0),
                                  ctypes.c_void_p(stream))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def pisco_mlp_create(n_in, n_hidden, n_out, params, max_batch, stream=0):
+    """params: float32 numpy blob [W1|b1|W2|b2|W3|b3].  Returns (status, handle)."""
+    import numpy as np
+    blob = np.ascontiguousarray(params, dtype=np.float32)
+    h = ctypes.c_void_p()
+    st = load().pisco_mlp_create(n_in, n_hidden, n_out, _fptr(blob), max_batch, ctypes.c_void_p(stream),
+                                 ctypes.byref(h))
+    return st, h
+
+
+def pisco_mlp_write(mlp, params):
+    import numpy as np
+    blob = np.ascontiguousarray(params, dtype=np.float32)
+    return load().pisco_mlp_write(mlp, _fptr(blob))
+
+
+def pisco_mlp_forward(mlp, d_x, batch, d_out):
+    return load().pisco_mlp_forward(mlp, ctypes.c_void_p(d_x), batch, ctypes.c_void_p(d_out))
+
+
+def pisco_mlp_backward(mlp, d_x, d_t, batch, want_loss=True):
+    """Returns (status, loss or None)."""
+    loss = ctypes.c_double()
+    st = load().pisco_mlp_backward(mlp, ctypes.c_void_p(d_x), ctypes.c_void_p(d_t), batch,
+                                   ctypes.byref(loss) if want_loss else None)
+    return st, (loss.value if want_loss else None)
+
+
+def pisco_mlp_adam(mlp, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    return load().pisco_mlp_adam(mlp, lr, beta1, beta2, eps)
+
+
+def pisco_mlp_read(mlp, which, nparam):
+    import numpy as np
+    out = np.empty(nparam, np.float32)
+    st = load().pisco_mlp_read(mlp, which, _fptr(out))
+    return st, out
+
+
+def pisco_mlp_destroy(mlp):
+    load().pisco_mlp_destroy(mlp)
+
+
+def pisco_set_warm_start(plan, mlp, iters, gate, fallback_iters):
+    return load().pisco_set_warm_start(plan, mlp, iters, gate, fallback_iters)
+
+
+def pisco_warm_start_features(d_y, Q, npix, d_x, stream=0):
+    return load().pisco_warm_start_features(ctypes.c_void_p(d_y), Q, npix, ctypes.c_void_p(d_x),
+                                            ctypes.c_void_p(stream))
+

@@ -1,5 +1,6 @@
 // Shared device helpers and internal launcher declarations of the PISCO GB300 path.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,6 +71,7 @@ struct DevStatus {
   int nband;            // Ritz values refined in FP64
   int jacobi_sweeps;    // sweeps used by the last small eigensolve
   double lambda_max;    // largest eigenvalue of C^H C (FP64 Rayleigh quotient)
+  int ws_fallback;      // pixels re-solved after the warm start's residual gate
 };
 
 // ---------------------------------------------------------------------------------------
@@ -138,6 +140,29 @@ cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_s
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
                                const int* lag_ent, int nlag, float2* KT, cudaStream_t st);
 
+// warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out, widths <= 128; w32 is the FP32
+// parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its FP16 copy (the
+// matrices are read from w16, the biases from w32)
+struct MlpView {
+  int n_in, H, n_out;
+  const float* w32;
+  const __half* w16;
+};
+MlpView mlp_view(const pisco_mlp_s* m);
+void mlp_dims(const pisco_mlp_s* m, int* n_in, int* H, int* n_out, size_t* nparam);
+cudaError_t mlp_prepare();
+size_t mlp_param_count(int n_in, int H, int n_out);
+size_t mlp_part_floats(long long max_batch, int n_in, int H, int n_out);
+cudaError_t mlp_forward(const MlpView& m, const float* X, long long B, float* H1, float* H2, float* out,
+                        cudaStream_t st);
+cudaError_t mlp_backward(const MlpView& m, const float* X, const float* T, long long B, float* H1, float* H2,
+                         float* out, float* dO, float* dH2, float* dH1, float* part, float* grad,
+                         float* loss_part, int loss_blocks, cudaStream_t st);
+cudaError_t mlp_adam(float* w32, __half* w16, const float* g, float* m1, float* m2, long long n, float lr,
+                     float b1, float b2, float eps, int step, cudaStream_t st);
+cudaError_t mlp_to_half(const float* w32, __half* w16, long long n, cudaStream_t st);
+cudaError_t mlp_features(const float2* Y, int Q, long long npix, float* X, cudaStream_t st);
+
 // tensor-core complex GEMM (kernels_tc.cu): C = alpha*A*op(B) + beta*C (+ diag_val on columns
 // c % diag_stride == 0, c < diag_limit); A M x K row-major with optional per-k real scale;
 // opB 0: B K x N row-major, 1: conj of an N x K row-major array; nterms 3 (head/tail split TF32)
@@ -148,9 +173,19 @@ cudaError_t tc_cgemm(int nterms, int M, int N, int K, float2 alpha, const float2
                      int ldc, float diag_val, int diag_stride, int diag_limit, int* err, cudaStream_t st);
 
 // a4+a5: power iteration with the phase step
+// warm-start options of the power iteration: v0 [npix][2Q] start proposals (null: counter
+// start); gate > 0 flags pixels with residual above it (flags [npix], count += flagged);
+// only != null re-solves only the pixels with only[x] != 0
+struct PiOpts {
+  const float* v0 = nullptr;
+  float gate = 0.f;
+  int* flags = nullptr;
+  int* count = nullptr;
+  const int* only = nullptr;
+};
 cudaError_t power_iteration(const float2* G, const float2* Y, int Q, long long npix, int iters,
                             float lam_size, unsigned long long seed, float2* V, float* eig,
-                            cudaStream_t st);
+                            cudaStream_t st, const PiOpts& opt = PiOpts{});
 
 // a6: final interpolation pass along the slowest axis fused with unit-norm normalisation
 cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long long outer_dummy,

@@ -29,19 +29,34 @@ __device__ __forceinline__ float pixel_sum(float v, float* red, int xi, int q) {
   }
 }
 
+// Optional warm start (PiOpts): v0 from a proposal [npix][2Q] (interleaved re/im) instead of
+// the counter-based start; a residual gate that flags pixels whose final residual
+// ||G v - lambda |Lambda| v|| / |Lambda| exceeds `gate`; and a fallback pass that re-solves
+// only the flagged pixels (CTAs without one exit at once; the others write flagged pixels only).
 template <int QP>
 __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
                                                  const float2* __restrict__ Y, int Q,
                                                  long long npix, int iters, float lam_size,
                                                  unsigned long long seed, float2* __restrict__ V,
-                                                 float* __restrict__ eig) {
+                                                 float* __restrict__ eig, PiOpts opt) {
   constexpr int PIX = 256 / QP;
   __shared__ float2 vs[PIX * QP];
   __shared__ float red[PIX * 2];
+  __shared__ int any_flag;
   const int tid = threadIdx.x;
   const int xi = tid / QP, q = tid % QP;
   const long long x = (long long)blockIdx.x * PIX + xi;
   const bool live = (x < npix) && (q < Q);
+  bool write = true;
+  if (opt.only != nullptr) {  // fallback pass: uniform early exit for CTAs without a flagged pixel
+    if (tid == 0) any_flag = 0;
+    __syncthreads();
+    const bool mine = (x < npix) && opt.only[x] != 0;
+    if (mine && q == 0) any_flag = 1;
+    __syncthreads();
+    if (any_flag == 0) return;
+    write = mine;
+  }
   const long long QQ = (long long)Q * Q;
   float2 gcol[QP];
 #pragma unroll
@@ -51,7 +66,12 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
   }
   const float inv_lam = 1.0f / lam_size;
   float2 v = make_float2(0.f, 0.f);
-  if (live) v = make_float2(counter_uniform(seed, (uint64_t)x, 2 * q), counter_uniform(seed, (uint64_t)x, 2 * q + 1));
+  if (live) {
+    if (opt.v0 != nullptr)
+      v = make_float2(opt.v0[x * 2 * Q + 2 * q], opt.v0[x * 2 * Q + 2 * q + 1]);
+    else
+      v = make_float2(counter_uniform(seed, (uint64_t)x, 2 * q), counter_uniform(seed, (uint64_t)x, 2 * q + 1));
+  }
   {
     const float n2 = pixel_sum<QP>(v.x * v.x + v.y * v.y, red, xi, q);
     const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
@@ -74,7 +94,17 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
     __syncthreads();
   }
   // Rayleigh quotient and phase of the coil-combined low-resolution image
-  const float lam = pixel_sum<QP>(v.x * gv.x + v.y * gv.y, red, xi, q) * inv_lam;
+  const float lraw = pixel_sum<QP>(v.x * gv.x + v.y * gv.y, red, xi, q);
+  const float lam = lraw * inv_lam;
+  if (opt.gate > 0.f) {
+    const float rx = gv.x - lraw * v.x, ry = gv.y - lraw * v.y;
+    const float r2 = pixel_sum<QP>(live ? rx * rx + ry * ry : 0.f, red, xi, q);
+    const bool bad = sqrtf(r2) * inv_lam > opt.gate;
+    if (x < npix && q == 0) {
+      opt.flags[x] = bad ? 1 : 0;
+      if (bad) atomicAdd(opt.count, 1);
+    }
+  }
   float2 y = make_float2(0.f, 0.f);
   if (live) y = Y[(long long)q * npix + x];
   const float rr = pixel_sum<QP>(v.x * y.x + v.y * y.y, red, xi, q);
@@ -84,7 +114,7 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
     const float cr = rr / mag, ci = ri / mag;
     v = make_float2(v.x * cr - v.y * ci, v.x * ci + v.y * cr);
   }
-  if (live) {
+  if (live && write) {
     V[(long long)q * npix + x] = v;
     if (q == 0 && eig != nullptr) eig[x] = lam;
   }
@@ -93,23 +123,24 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
 template <int QP>
 static cudaError_t launch_pi(const float2* G, const float2* Y, int Q, long long npix, int iters,
                              float lam_size, unsigned long long seed, float2* V, float* eig,
-                             cudaStream_t st) {
+                             const PiOpts& opt, cudaStream_t st) {
   constexpr int PIX = 256 / QP;
   const long long blocks = (npix + PIX - 1) / PIX;
-  pi_kernel<QP><<<(unsigned)blocks, 256, 0, st>>>(G, Y, Q, npix, iters, lam_size, seed, V, eig);
+  pi_kernel<QP><<<(unsigned)blocks, 256, 0, st>>>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt);
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t power_iteration(const float2* G, const float2* Y, int Q, long long npix, int iters,
                             float lam_size, unsigned long long seed, float2* V, float* eig,
-                            cudaStream_t st) {
-  if (Q <= 2) return launch_pi<2>(G, Y, Q, npix, iters, lam_size, seed, V, eig, st);
-  if (Q <= 4) return launch_pi<4>(G, Y, Q, npix, iters, lam_size, seed, V, eig, st);
-  if (Q <= 8) return launch_pi<8>(G, Y, Q, npix, iters, lam_size, seed, V, eig, st);
-  if (Q <= 16) return launch_pi<16>(G, Y, Q, npix, iters, lam_size, seed, V, eig, st);
-  if (Q <= 32) return launch_pi<32>(G, Y, Q, npix, iters, lam_size, seed, V, eig, st);
-  if (Q <= 64) return launch_pi<64>(G, Y, Q, npix, iters, lam_size, seed, V, eig, st);
+                            cudaStream_t st, const PiOpts& opt) {
+  if (opt.gate > 0.f && (opt.flags == nullptr || opt.count == nullptr)) return cudaErrorInvalidValue;
+  if (Q <= 2) return launch_pi<2>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt, st);
+  if (Q <= 4) return launch_pi<4>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt, st);
+  if (Q <= 8) return launch_pi<8>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt, st);
+  if (Q <= 16) return launch_pi<16>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt, st);
+  if (Q <= 32) return launch_pi<32>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt, st);
+  if (Q <= 64) return launch_pi<64>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt, st);
   return cudaErrorInvalidValue;
 }
 

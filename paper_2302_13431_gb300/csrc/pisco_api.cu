@@ -58,6 +58,14 @@ struct pisco_plan_s {
   int* d_lagc_ptr = nullptr;
   float2* E = nullptr;
   float2* KT = nullptr;
+  // learned warm start of the power iteration (pisco_set_warm_start)
+  bool ws_on = false;
+  int ws_iters = 0, ws_fb_iters = 0, ws_H = 0;
+  float ws_gate = 0.f;
+  float* ws_w32 = nullptr;
+  __half* ws_w16 = nullptr;
+  float *ws_X = nullptr, *ws_H1 = nullptr, *ws_H2 = nullptr, *ws_out = nullptr;
+  int* fb_flags = nullptr;
   // device buffers
   double2 *gA = nullptr, *gB = nullptr, *S = nullptr, *P = nullptr, *Rp = nullptr, *lags = nullptr;
   double2* A = nullptr;
@@ -593,8 +601,29 @@ pisco_status run_all(pisco_plan_s* pl, const float2* calib, float2* maps, float*
   if ((s = run_eig(pl)) != PISCO_OK) return s;
   if ((s = run_gfield(pl)) != PISCO_OK) return s;
   if ((s = run_lowres(pl, calib)) != PISCO_OK) return s;
-  OP("power_iteration", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->prm.power_iters, (float)pl->L,
-                     pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st));
+  if (pl->ws_on) {
+    // learned start vectors, fewer iterations, residual-gated re-solve from the plain start
+    const MlpView mv{2 * pl->Q, pl->ws_H, 2 * pl->Q, pl->ws_w32, pl->ws_w16};
+    OP("warm_start_mlp", mlp_features(pl->Yf, pl->Q, pl->npix_red, pl->ws_X, st));
+    OP("warm_start_mlp", mlp_forward(mv, pl->ws_X, pl->npix_red, pl->ws_H1, pl->ws_H2, pl->ws_out, st));
+    PiOpts o1;
+    o1.v0 = pl->ws_out;
+    o1.gate = pl->ws_gate;
+    o1.flags = pl->fb_flags;
+    o1.count = &pl->dstatus->ws_fallback;
+    if (o1.gate <= 0.f) o1.flags = nullptr, o1.count = nullptr;
+    OP("power_iteration", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->ws_iters, (float)pl->L,
+                                          pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st, o1));
+    if (o1.gate > 0.f) {
+      PiOpts o2;
+      o2.only = pl->fb_flags;
+      OP("pi_fallback", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->ws_fb_iters, (float)pl->L,
+                                        pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st, o2));
+    }
+  } else {
+    OP("power_iteration", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->prm.power_iters, (float)pl->L,
+                                          pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st));
+  }
   if ((s = run_interp(pl, maps)) != PISCO_OK) return s;
   CK(cudaMemcpyAsync(pl->hstatus, pl->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   return PISCO_OK;
@@ -910,6 +939,46 @@ pisco_status pisco_get_stats(pisco_plan_t pl, pisco_stats* out) {
   out->lambda_max = pl->last_status.lambda_max;
   out->signal_dim = pl->last_k;
   out->filter_len = pl->L;
+  out->warm_fallback = pl->ws_on ? pl->last_status.ws_fallback : 0;
+  return PISCO_OK;
+}
+
+pisco_status pisco_set_warm_start(pisco_plan_t pl, pisco_mlp_t mlp, int iters, float gate, int fallback_iters) {
+  if (!pl) return PISCO_ERR_ARG;
+  if (!mlp) {
+    pl->ws_on = false;
+    graph_reset(pl);
+    pl->eager_calib = nullptr;
+    return PISCO_OK;
+  }
+  int n_in, H, n_out;
+  size_t np;
+  mlp_dims(mlp, &n_in, &H, &n_out, &np);
+  if (n_in != 2 * pl->Q || n_out != 2 * pl->Q || iters < 0 || fallback_iters < 1 || !(gate == gate)) return PISCO_ERR_ARG;
+  if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
+  const size_t npmax = mlp_param_count(2 * pl->Q, 128, 2 * pl->Q);
+  if (!pl->ws_w32) {
+    const size_t nr = (size_t)pl->npix_red;
+    const bool ok = dalloc(pl, &pl->ws_w32, npmax) && dalloc(pl, &pl->ws_w16, npmax) &&
+                    dalloc(pl, &pl->ws_X, nr * 2 * pl->Q) && dalloc(pl, &pl->ws_H1, nr * 128) &&
+                    dalloc(pl, &pl->ws_H2, nr * 128) && dalloc(pl, &pl->ws_out, nr * 2 * pl->Q) &&
+                    dalloc(pl, &pl->fb_flags, nr);
+    if (!ok || mlp_prepare() != cudaSuccess) {
+      cudaGetLastError();
+      return PISCO_ERR_OOM;
+    }
+  }
+  const MlpView src = mlp_view(mlp);
+  if (cudaMemcpy(pl->ws_w32, src.w32, sizeof(float) * np, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+      cudaMemcpy(pl->ws_w16, src.w16, sizeof(__half) * np, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  pl->ws_H = H;
+  pl->ws_iters = iters;
+  pl->ws_gate = gate;
+  pl->ws_fb_iters = fallback_iters;
+  pl->ws_on = true;
+  graph_reset(pl);
+  pl->eager_calib = nullptr;  // the next call runs eagerly, the one after captures the new sequence
   return PISCO_OK;
 }
 
