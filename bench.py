@@ -58,11 +58,30 @@ def _peaks():
 # ------------------------------------------------------------------------------------------
 # synthetic inputs
 # ------------------------------------------------------------------------------------------
+def rank_seeds(rank):
+    """Seeds of the calibration blocks a rank estimates: ranks work on disjoint data."""
+    return [1000 * rank + i for i in range(N_CASES)]
+
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The maximum of a per-rank float over all ranks (the job's time is the slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, total_ms):
+    """Units all ranks processed divided by the (max-over-ranks) time."""
+    return world * units_per_rank / (total_ms / 1e3)
+
+
 def make_inputs(rank):
     from paper_2302_13431_gb300.phantoms import make_case
     w = WORKLOAD
-    return [make_case(w["grid"], w["Q"], w["calib"], seed=1000 * rank + i, phase="poly4").calib
-            for i in range(N_CASES)]
+    return [make_case(w["grid"], w["Q"], w["calib"], seed=sd, phase="poly4").calib for sd in rank_seeds(rank)]
 
 
 # ------------------------------------------------------------------------------------------
@@ -341,12 +360,8 @@ def run_gpu(args):
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * nb * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = whole_job_rate(nb * args.steps, world, tot_ms)
     binfo = batch.info()
 
     # ---- end to end: host buffers in and out, copies inside the timed region ----
@@ -364,12 +379,8 @@ def run_gpu(args):
         batch.estimate_host(pin_c, hmaps, heig)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * nb * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    e2e_value = whole_job_rate(nb * args.steps, world, e2e_ms)
     batch.close()
 
     peaks = _peaks()
