@@ -82,6 +82,7 @@ typedef struct {
   unsigned flags;         /* PISCO_FLAG_*                                                     */
   int eig_block;          /* block size of the nullspace eigensolver (0: automatic)           */
   int eig_iters;          /* subspace iterations of the eigensolver (0: automatic)            */
+  int tc_splits;          /* K splits of the tensor-core GEMMs (PISCO_FLAG_TC_*; 0: automatic) */
 } pisco_params;
 
 typedef struct pisco_plan_s* pisco_plan_t;
@@ -282,6 +283,19 @@ pisco_status pisco_set_warm_start(pisco_plan_t plan, pisco_mlp_t mlp, int iters,
 pisco_status pisco_tc_cgemm(int nterms, int M, int N, int K, const float* alpha, const void* d_A,
                             int lda, const void* d_B, int ldb, int opB, const float* beta, void* d_C,
                             int ldc, int* d_status, void* cuda_stream);
+
+/* The same product through the pipelined kernel the estimator uses: the operands are first split
+ * into TF32 head/tail arrays in the caller's workspace (the tensor core's K-major layout), then
+ * TMA loads feed a 4-stage shared-memory ring consumed by tcgen05.mma.  K may be split over
+ * `splits` CTAs per tile (partials summed in a fixed order, deterministic).  d_workspace: device,
+ * 16-byte aligned, at least pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, splits) bytes
+ * (PISCO_ERR_ARG otherwise).  Other arguments as pisco_tc_cgemm. */
+size_t pisco_tc_cgemm_pipelined_workspace(int nterms, int M, int N, int K, int splits);
+pisco_status pisco_tc_cgemm_pipelined(int nterms, int M, int N, int K, const float* alpha,
+                                      const void* d_A, int lda, const void* d_B, int ldb, int opB,
+                                      const float* beta, void* d_C, int ldc, int splits,
+                                      void* d_workspace, size_t workspace_bytes, int* d_status,
+                                      void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,7 @@ class pisco_params(ctypes.Structure):
         ("flags", ctypes.c_uint),
         ("eig_block", ctypes.c_int),
         ("eig_iters", ctypes.c_int),
+        ("tc_splits", ctypes.c_int),
     ]
 
 
@@ -118,6 +119,13 @@ def load():
                                    ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_float), vp,
                                    ctypes.c_int, vp, vp]
     lib.pisco_tc_cgemm.restype = ctypes.c_int
+    lib.pisco_tc_cgemm_pipelined_workspace.argtypes = [ctypes.c_int] * 5
+    lib.pisco_tc_cgemm_pipelined_workspace.restype = ctypes.c_size_t
+    lib.pisco_tc_cgemm_pipelined.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             P(ctypes.c_float), vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                                             P(ctypes.c_float), vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
+                                             vp, vp]
+    lib.pisco_tc_cgemm_pipelined.restype = ctypes.c_int
     fp = P(ctypes.c_float)
     lib.pisco_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, ctypes.c_longlong, vp, P(vp)]
     lib.pisco_mlp_create.restype = ctypes.c_int
@@ -146,7 +154,7 @@ def pisco_status_string(status: int) -> str:
 
 
 def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid", null_threshold=0.05,
-                grid_reduction=1, power_iters=30, seed=0, flags=0, eig_block=0, eig_iters=0):
+                grid_reduction=1, power_iters=30, seed=0, flags=0, eig_block=0, eig_iters=0, tc_splits=0):
     """pisco_params from (z,)y,x-ordered Python tuples (the array order); the struct is x,y,z."""
     nd = len(grid)
     pr = pisco_params()
@@ -165,6 +173,7 @@ def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid",
     pr.flags = flags
     pr.eig_block = eig_block
     pr.eig_iters = eig_iters
+    pr.tc_splits = tc_splits
     return pr
 
 
@@ -333,4 +342,17 @@ def pisco_set_warm_start(plan, mlp, iters, gate, fallback_iters):
 def pisco_warm_start_features(d_y, Q, npix, d_x, stream=0):
     return load().pisco_warm_start_features(ctypes.c_void_p(d_y), Q, npix, ctypes.c_void_p(d_x),
                                             ctypes.c_void_p(stream))
+
+
+def pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, splits):
+    return load().pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, splits)
+
+
+def pisco_tc_cgemm_pipelined(nterms, M, N, K, alpha, d_A, lda, d_B, ldb, opB, beta, d_C, ldc, splits, d_ws,
+                             ws_bytes, d_status=0, stream=0):
+    a = (ctypes.c_float * 2)(float(complex(alpha).real), float(complex(alpha).imag))
+    b = (ctypes.c_float * 2)(float(complex(beta).real), float(complex(beta).imag))
+    return load().pisco_tc_cgemm_pipelined(nterms, M, N, K, a, ctypes.c_void_p(d_A), lda, ctypes.c_void_p(d_B), ldb,
+                                           opB, b, ctypes.c_void_p(d_C), ldc, splits, ctypes.c_void_p(d_ws),
+                                           ws_bytes, ctypes.c_void_p(d_status or 0), ctypes.c_void_p(stream))
 

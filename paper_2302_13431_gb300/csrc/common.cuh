@@ -86,6 +86,8 @@ struct AxisView {
   int n_out;         // transformed axis length on output
   long long inner;   // product of the axis lengths after the transformed axis
   int pixel_major;   // 1 (needs outer == 1): write out[(o*inner + ii)*batch + b] instead
+  int mt = 0;        // 1: the matrix is stored transposed, M[i][o] ([n_in][n_out]); for
+                     // inner == 1 passes this makes a warp's matrix reads contiguous
 };
 cudaError_t apply_axis_c2z(const float2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
 cudaError_t apply_axis_z(const double2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
@@ -162,6 +164,19 @@ cudaError_t mlp_adam(float* w32, __half* w16, const float* g, float* m1, float* 
                      float b1, float b2, float eps, int step, cudaStream_t st);
 cudaError_t mlp_to_half(const float* w32, __half* w16, long long n, cudaStream_t st);
 cudaError_t mlp_features(const float2* Y, int Q, long long npix, float* X, cudaStream_t st);
+
+// TMA-fed tensor-core complex GEMM over operands split once in global memory (kernels_tc2.cu).
+// A' head/tail: [M][tc2_k2p(K)] floats; B' head/tail: [2 tc2_np(N)][tc2_k2p(K)] floats
+// (lo pointers may be null for one pass).  splits > 1 needs ws of splits*M*N complex.
+int tc2_k2p(int K);
+int tc2_np(int N);
+cudaError_t tc2_prepare();
+cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
+                        cudaStream_t st);
+cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st);
+cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
+                     const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
+                     int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st);
 
 // tensor-core complex GEMM (kernels_tc.cu): C = alpha*A*op(B) + beta*C (+ diag_val on columns
 // c % diag_stride == 0, c < diag_limit); A M x K row-major with optional per-k real scale;

@@ -3,7 +3,9 @@
 // interpolation, Sec. V-D).  The transforms here are short (tens of points) and not powers
 // of two, so each axis is a small dense matrix product; every output element is one thread,
 // with the inner (fastest) index mapped to consecutive threads so loads are coalesced and
-// the matrix row is a warp-wide broadcast.
+// the matrix row is a warp-wide broadcast.  Along the contiguous axis (inner == 1) consecutive
+// threads are consecutive outputs instead; those passes read a transposed matrix (AxisView::mt)
+// so that a warp's matrix loads stay contiguous while the input element is the broadcast.
 #include "common.cuh"
 
 namespace pisco {
@@ -20,12 +22,13 @@ __global__ void __launch_bounds__(256) apply_axis_kernel(const Tin* __restrict__
     const int o = (int)(t % v.n_out); t /= v.n_out;
     const long long bo = t;  // batch*outer flattened
     const Tin* src = in + (bo * v.n_in) * v.inner + ii;
-    const C* row = M + (long long)o * v.n_in;
+    const C* row = v.mt ? M + o : M + (long long)o * v.n_in;
+    const long long mstep = v.mt ? v.n_out : 1;
     C acc = mk(decltype(acc.x)(0), decltype(acc.x)(0));
     for (int i = 0; i < v.n_in; ++i) {
       const Tin s = src[(long long)i * v.inner];
       C sv = mk(decltype(acc.x)(s.x), decltype(acc.x)(s.y));
-      cfma(acc, row[i], sv);
+      cfma(acc, row[(long long)i * mstep], sv);
     }
     if (v.pixel_major)
       out[((long long)o * v.inner + ii) * v.batch + bo] = acc;

@@ -1,0 +1,421 @@
+// Dense complex GEMM on the tensor cores, fed by TMA: the pipelined form of the split-precision
+// contraction of kernels_tc.cu.
+//
+//   C = alpha * A * op(B) + beta * C  (+ diag_val on columns c % diag_stride == 0, c < diag_limit)
+//
+// The operands are split once, in global memory, into the real K-major layout the tensor core
+// reads (tc2_split_a / tc2_split_b): A' [M][K2p] with the complex row interleaved (Re, Im),
+// B' [2 Np][K2p] with, per 32-column tile t, rows 64t..64t+31 = [Re b, -Im b] (real part of
+// C) and rows 64t+32..64t+63 = [Im b, Re b] (imaginary part); each as a TF32 head array and a
+// TF32 tail array.  A GEMM then moves no data through registers: per K step of 32 real columns
+// one thread issues the TMA loads of the step's four tiles (head/tail of A and B, 128-byte
+// swizzled) into a 2- or 4-stage ring, another thread issues the tcgen05.mma instructions (TF32,
+// FP32 accumulator 128 x 64 in TMEM) and releases each stage through tcgen05.commit, and the
+// 4 warps read the accumulator back for the epilogue.  K may be split across gridDim.z; the
+// partial tiles are then summed in a fixed order by a second kernel (deterministic).
+//
+// Every mbarrier wait is bounded; on expiry the kernel sets bit 16 of *err, stops issuing and
+// still frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace pisco {
+
+namespace {
+
+constexpr int BM = 128;           // rows of C per CTA (TMEM lanes)
+constexpr int BNC = 32;           // complex columns of C per CTA (64 accumulator columns)
+constexpr int BK = 32;            // real K per stage (128 bytes of FP32: one swizzle row)
+constexpr uint32_t A_TILE = BM * BK * 4;        // 16384
+constexpr uint32_t B_TILE = 2 * BNC * BK * 4;   // 8192
+constexpr uint32_t TMEM_COLS = 64;
+constexpr long long kWait = 4000000000ll;       // ~2 s at 2 GHz
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, 128-byte swizzle: start >> 4, LBO field 1 (unused for this layout), SBO 1024 B
+// (next 8-row group), descriptor version 1, layout type 2 (SWIZZLE_128B)
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint32_t b, uint32_t par) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(b), "r"(par)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t par) {
+  const long long t0 = clock64();
+  while (!bar_try(b, par))
+    if (clock64() - t0 > kWait) return false;
+  return true;
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint32_t b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float head(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+
+struct Args {
+  int M, N, K2;   // K2 = 2K (real columns of A' and B')
+  int kpb;        // K steps per split (gridDim.z splits)
+  float2* C;
+  int ldc;
+  float2 alpha, beta;
+  float diag_val;
+  int diag_stride, diag_limit;
+  float2* ws;     // [splits][M][N] partial products when gridDim.z > 1
+  int* err;
+};
+
+template <int NT, int STAGES>
+__global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUtensorMap tAh,
+                                                     const __grid_constant__ CUtensorMap tAl,
+                                                     const __grid_constant__ CUtensorMap tBh,
+                                                     const __grid_constant__ CUtensorMap tBl, Args g) {
+  constexpr uint32_t STAGE = (NT == 3 ? 2u : 1u) * (A_TILE + B_TILE);
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = su32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE);  // full[4], empty[4], accum
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE + 9 * 8);
+  const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[STAGES]), accum = su32(&bars[2 * STAGES]);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNC;
+  const int total = (g.K2 + BK - 1) / BK;
+  const int kb0 = blockIdx.z * g.kpb;
+  const int nk = min(g.kpb, total - kb0);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      bar_init(full0 + 8 * s, 1);
+      bar_init(empty0 + 8 * s, 1);
+    }
+    bar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0 && nk > 0) {
+    // producer: TMA loads of the four tiles of every K step into the stage ring
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % STAGES, c = i / STAGES;
+      if (i >= STAGES) ok = bar_wait(empty0 + 8 * s, (uint32_t)((c - 1) & 1));
+      if (!ok) break;
+      const uint32_t st = base + s * STAGE;
+      const uint32_t fb = full0 + 8 * s;
+      bar_expect_tx(fb, STAGE);
+      const int kx = (kb0 + i) * BK;
+      tma_2d(st, &tAh, kx, m0, fb);
+      if (NT == 3) tma_2d(st + A_TILE, &tAl, kx, m0, fb);
+      const uint32_t sb = st + (NT == 3 ? 2 * A_TILE : A_TILE);
+      tma_2d(sb, &tBh, kx, 2 * n0, fb);
+      if (NT == 3) tma_2d(sb + B_TILE, &tBl, kx, 2 * n0, fb);
+    }
+  } else if (warp == 1 && lane == 0 && nk > 0) {
+    // MMA issuer: 4 MMAs of K = 8 per stage (x3 for the head/tail split)
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % STAGES, c = i / STAGES;
+      ok = bar_wait(full0 + 8 * s, (uint32_t)(c & 1));
+      if (!ok) break;
+      fence_after();
+      const uint32_t st = base + s * STAGE;
+      const uint32_t sb = st + (NT == 3 ? 2 * A_TILE : A_TILE);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t ah = desc_sw128(st + 32 * j), bh = desc_sw128(sb + 32 * j);
+        mma(tmem, ah, bh, (i > 0 || j > 0) ? 1u : 0u);
+        if (NT == 3) {
+          mma(tmem, ah, desc_sw128(sb + B_TILE + 32 * j), 1u);
+          mma(tmem, desc_sw128(st + A_TILE + 32 * j), bh, 1u);
+        }
+      }
+      commit(empty0 + 8 * s);
+    }
+    commit(accum);
+  }
+  __syncwarp();
+  if (nk > 0) {
+    if (!bar_wait(accum, 0)) ok = false;
+  }
+  if (!ok && g.err) atomicOr(g.err, 16);
+  fence_after();
+  // accumulator -> registers -> shared tile [128][33] (the stage ring is free: all MMAs done)
+  float2* tile = reinterpret_cast<float2*>(gbase);
+  {
+    const int row = warp * 32 + lane;
+    uint32_t r[32];
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    if (nk > 0) tmem_ld32(tl, r);
+    else
+#pragma unroll
+      for (int c = 0; c < 32; ++c) r[c] = 0u;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) tile[row * 33 + c].x = __uint_as_float(r[c]);
+    if (nk > 0) tmem_ld32(tl + 32, r);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) tile[row * 33 + c].y = __uint_as_float(r[c]);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (gridDim.z > 1) {  // raw partial tile
+    float2* out = g.ws + (long long)blockIdx.z * g.M * g.N;
+    for (int rr = warp; rr < BM; rr += 4) {
+      const int gm = m0 + rr, gn = n0 + lane;
+      if (gm < g.M && gn < g.N) out[(long long)gm * g.N + gn] = tile[rr * 33 + lane];
+    }
+    return;
+  }
+  const bool has_beta = (g.beta.x != 0.f || g.beta.y != 0.f);
+  for (int rr = warp; rr < BM; rr += 4) {
+    const int gm = m0 + rr, gn = n0 + lane;
+    if (gm >= g.M || gn >= g.N) continue;
+    const float2 a = tile[rr * 33 + lane];
+    float2 o = make_float2(g.alpha.x * a.x - g.alpha.y * a.y, g.alpha.x * a.y + g.alpha.y * a.x);
+    float2* cp = g.C + (long long)gm * g.ldc + gn;
+    if (has_beta) {
+      const float2 c = *cp;
+      o.x += g.beta.x * c.x - g.beta.y * c.y;
+      o.y += g.beta.x * c.y + g.beta.y * c.x;
+    }
+    if (g.diag_stride > 0 && gn < g.diag_limit && gn % g.diag_stride == 0) o.x += g.diag_val;
+    *cp = o;
+  }
+}
+
+// C = alpha * sum_z ws[z] + beta * C (+ diag), partials summed in z order
+__global__ void splitk_reduce_kernel(const float2* __restrict__ ws, int splits, int M, int N, float2 alpha,
+                                     float2 beta, float2* __restrict__ C, int ldc, float diag_val, int diag_stride,
+                                     int diag_limit) {
+  const long long total = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int z = 0; z < splits; ++z) {
+      const float2 v = ws[(long long)z * total + e];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    const int m = (int)(e / N), n = (int)(e % N);
+    float2 o = make_float2(alpha.x * a.x - alpha.y * a.y, alpha.x * a.y + alpha.y * a.x);
+    float2* cp = C + (long long)m * ldc + n;
+    if (beta.x != 0.f || beta.y != 0.f) {
+      const float2 c = *cp;
+      o.x += beta.x * c.x - beta.y * c.y;
+      o.y += beta.x * c.y + beta.y * c.x;
+    }
+    if (diag_stride > 0 && n < diag_limit && n % diag_stride == 0) o.x += diag_val;
+    *cp = o;
+  }
+}
+
+// A' head/tail: A'[m][2k] = Re(A[m][k] w_k), A'[m][2k+1] = Im(...), w_k = kscale[k] (or 1)
+__global__ void split_a_kernel(const float2* __restrict__ A, int lda, const float* __restrict__ kscale, int M, int K,
+                               float* __restrict__ hi, float* __restrict__ lo, int K2p) {
+  const long long total = (long long)M * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / K), k = (int)(e % K);
+    float2 v = A[(long long)m * lda + k];
+    if (kscale) {
+      const float w = kscale[k];
+      v.x *= w;
+      v.y *= w;
+    }
+    const float hx = head(v.x), hy = head(v.y);
+    const long long o = (long long)m * K2p + 2 * k;
+    *reinterpret_cast<float2*>(hi + o) = make_float2(hx, hy);
+    if (lo) *reinterpret_cast<float2*>(lo + o) = make_float2(head(v.x - hx), head(v.y - hy));
+  }
+}
+
+// B' head/tail rows (see the file comment); columns c >= N of the last tile are zero
+__global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, int K, int N, int Np,
+                               float* __restrict__ hi, float* __restrict__ lo, int K2p) {
+  const long long total = (long long)Np * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / K), k = (int)(e % K);
+    float2 b = make_float2(0.f, 0.f);
+    if (c < N) {
+      if (opB == 0) b = B[(long long)k * ldb + c];
+      else {
+        const float2 s = B[(long long)c * ldb + k];
+        b = make_float2(s.x, -s.y);
+      }
+    }
+    const int t = c / BNC, cl = c % BNC;
+    const long long rre = (long long)(64 * t + cl) * K2p + 2 * k;
+    const long long rim = (long long)(64 * t + 32 + cl) * K2p + 2 * k;
+    const float2 vre = make_float2(b.x, -b.y), vim = make_float2(b.y, b.x);
+    const float2 hre = make_float2(head(vre.x), head(vre.y)), him = make_float2(head(vim.x), head(vim.y));
+    *reinterpret_cast<float2*>(hi + rre) = hre;
+    *reinterpret_cast<float2*>(hi + rim) = him;
+    if (lo) {
+      *reinterpret_cast<float2*>(lo + rre) = make_float2(head(vre.x - hre.x), head(vre.y - hre.y));
+      *reinterpret_cast<float2*>(lo + rim) = make_float2(head(vim.x - him.x), head(vim.y - him.y));
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
+
+bool encode_2d(CUtensorMap* map, const float* base, int cols, int rows, int ld_floats, int box_rows) {
+  if (!g_encode) {
+    std::lock_guard<std::mutex> lk(g_encode_mu);
+    if (!g_encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld_floats * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT, int STAGES>
+size_t smem_bytes() {
+  return (size_t)STAGES * (NT == 3 ? 2u : 1u) * (A_TILE + B_TILE) + 1024 + 128;
+}
+
+unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+int tc2_k2p(int K) { return ((2 * K + 3) / 4) * 4; }
+int tc2_np(int N) { return ((N + BNC - 1) / BNC) * BNC; }
+
+template <int NT, int S>
+static cudaError_t set_smem() {
+  return cudaFuncSetAttribute(tc2_kernel<NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<NT, S>());
+}
+
+cudaError_t tc2_prepare() {
+  cudaError_t e = set_smem<3, 4>();
+  if (e == cudaSuccess) e = set_smem<3, 2>();
+  if (e == cudaSuccess) e = set_smem<1, 4>();
+  if (e == cudaSuccess) e = set_smem<1, 2>();
+  return e;
+}
+
+cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
+                        cudaStream_t st) {
+  split_a_kernel<<<grid_for((long long)M * K), 256, 0, st>>>(A, lda, kscale, M, K, hi, lo, tc2_k2p(K));
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st) {
+  const int Np = tc2_np(N);
+  split_b_kernel<<<grid_for((long long)Np * K), 256, 0, st>>>(B, ldb, opB, K, N, Np, hi, lo, tc2_k2p(K));
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
+                     const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
+                     int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const int K2 = 2 * K, K2p = tc2_k2p(K), Np = tc2_np(N);
+  const int total = (K2 + BK - 1) / BK;
+  if (splits < 1 || ws == nullptr) splits = 1;
+  if (splits > total) splits = total > 0 ? total : 1;
+  const int kpb = total > 0 ? (total + splits - 1) / splits : 0;
+  if (kpb > 0) splits = (total + kpb - 1) / kpb;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  const float* al = nterms == 3 ? Alo : Ahi;
+  const float* bl = nterms == 3 ? Blo : Bhi;
+  const int kcols = K2 > 0 ? K2 : 1;
+  if (!encode_2d(&mAh, Ahi, kcols, M, K2p, BM) || !encode_2d(&mAl, al, kcols, M, K2p, BM) ||
+      !encode_2d(&mBh, Bhi, kcols, 2 * Np, K2p, 2 * BNC) || !encode_2d(&mBl, bl, kcols, 2 * Np, K2p, 2 * BNC))
+    return cudaErrorInvalidValue;
+  Args g{M, N, K2, kpb, C, ldc, alpha, beta, diag_val, diag_stride, diag_limit, ws, err};
+  dim3 grid(Np / BNC, (M + BM - 1) / BM, splits);
+  // short K loops (<= 8 steps per CTA) keep 2 stages: half the shared memory, 2 CTAs per SM, so
+  // one CTA's epilogue overlaps another's loads; long loops keep 4 stages in flight
+  const bool deep = kpb > 8;
+  if (nterms == 1) {
+    if (deep) tc2_kernel<1, 4><<<grid, 128, smem_bytes<1, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
+    else tc2_kernel<1, 2><<<grid, 128, smem_bytes<1, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
+  } else {
+    if (deep) tc2_kernel<3, 4><<<grid, 128, smem_bytes<3, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
+    else tc2_kernel<3, 2><<<grid, 128, smem_bytes<3, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
+  }
+  ++g_launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(ws, splits, M, N, alpha, beta, C, ldc, diag_val,
+                                                                   diag_stride, diag_limit);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pisco

@@ -45,6 +45,9 @@ struct pisco_plan_s {
   double2* fwd[3] = {nullptr, nullptr, nullptr};
   double2* inv[3] = {nullptr, nullptr, nullptr};
   float2* gdft[3] = {nullptr, nullptr, nullptr};
+  // transposed copies ([n_in][n_out]) of the tables of the contiguous axis (inner == 1 passes)
+  double2 *fwdT = nullptr, *invT = nullptr;
+  float2 *gdftT = nullptr, *ydftT = nullptr, *interpT = nullptr;
   float2* ydft[3] = {nullptr, nullptr, nullptr};
   float2* interp[3] = {nullptr, nullptr, nullptr};
   int* d_lag_of_ij = nullptr;
@@ -58,6 +61,13 @@ struct pisco_plan_s {
   int* d_lagc_ptr = nullptr;
   float2* E = nullptr;
   float2* KT = nullptr;
+  // split operands of the TMA-fed tensor-core GEMMs (head/tail arrays) and split-K scratch
+  int tc_splits_ax = 4, tc_splits_g = 1;
+  float *Ah = nullptr, *Al = nullptr, *Xh = nullptr, *Xl = nullptr;        // A32 and the block
+  float *Eh = nullptr, *El = nullptr, *KTh = nullptr, *KTl = nullptr;      // E and the lag table
+  float *UAh = nullptr, *UAl = nullptr, *UBh = nullptr, *UBl = nullptr;    // U diag(w), conj(U)^T
+  float2* tc_ws = nullptr;
+  size_t tc_ws_elems = 0;
   // learned warm start of the power iteration (pisco_set_warm_start)
   bool ws_on = false;
   int ws_iters = 0, ws_fb_iters = 0, ws_H = 0;
@@ -147,6 +157,14 @@ template <typename T>
 bool upload(pisco_plan_s* pl, T** p, const std::vector<T>& h) {
   if (!dalloc(pl, p, h.size())) return false;
   return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+template <typename T>
+std::vector<T> transposed(const std::vector<T>& M, int rows, int cols) {
+  std::vector<T> out((size_t)rows * cols);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) out[(size_t)c * rows + r] = M[(size_t)r * cols + c];
+  return out;
 }
 
 const double kPi = 3.14159265358979323846;
@@ -416,7 +434,7 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   const int* Lp = pl->Lp;
   const int* B = pl->B;
   // forward zero-padded DFT of every channel: x, y, z
-  OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwd[2], pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1}, st));
+  OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwdT, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
   OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->fwd[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
   const double2* S = pl->gB;
   if (pl->D == 3) {
@@ -425,7 +443,7 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   }
   OP("gram_pair_products", gram_pair_products(S, Q, pl->nfreq, pl->P, st));
   const int np = pl->npairs;
-  OP("gram_dft_fp64", apply_axis_z(pl->P, pl->inv[2], pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1}, st));
+  OP("gram_dft_fp64", apply_axis_z(pl->P, pl->invT, pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
   if (pl->D == 3) {
     OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->gB, AxisView{np, Lp[0], Lp[1], B[1], B[2]}, st));
     OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->inv[0], pl->Rp, AxisView{np, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
@@ -465,9 +483,12 @@ pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, co
 cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y) {
   const int n = pl->n, m = pl->m;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  if (pl->tc_eig)
-    return tc_cgemm(pl->tc_terms, n, m, n, one, pl->A32, n, nullptr, X, m, 0, zero, Y, m, 0.f, 0, 0,
-                    &pl->dstatus->flags, pl->st);
+  if (pl->tc_eig) {
+    cudaError_t e = tc2_split_b(X, m, 0, n, m, pl->Xh, pl->tc_terms == 3 ? pl->Xl : nullptr, pl->st);
+    if (e != cudaSuccess) return e;
+    return tc2_gemm(pl->tc_terms, n, m, n, pl->Ah, pl->Al, pl->Xh, pl->Xl, one, zero, Y, m, 0.f, 0, 0,
+                    pl->tc_splits_ax, pl->tc_ws, &pl->dstatus->flags, pl->st);
+  }
   return cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, X, m, zero, Y, m, pl->ws32, pl->ws32_elems,
                       pl->tiles, pl->st);
 }
@@ -485,6 +506,8 @@ pisco_status run_eig(pisco_plan_s* pl) {
   pisco_status s;
   // random start; the first product can be ill conditioned -> shifted Cholesky-QR + two passes
   OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
+  if (pl->tc_eig)  // the Gram's TF32 head/tail split, shared by every block product of the solve
+    OP("eig_gemm_AX", tc2_split_a(pl->A32, n, nullptr, n, n, pl->Ah, pl->tc_terms == 3 ? pl->Al : nullptr, st));
   OP("eig_gemm_AX", ax_product(pl, pl->Y, pl->Z));
   const float shift = 11.0f * ((float)m * n + (float)m * (m + 1)) * 5.9604645e-8f;
   if ((s = cholqr(pl, pl->Z, pl->Y, m, nullptr, shift, nullptr, pl->dR1)) != PISCO_OK) return s;
@@ -539,15 +562,20 @@ pisco_status run_gfield(pisco_plan_s* pl) {
     const int n = pl->n;
     int* err = &pl->dstatus->flags;
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f), mone = make_float2(-1.f, 0.f);
-    OP("g_herk_tc", tc_cgemm(pl->tc_terms, n, n, pl->m, one, pl->U, pl->m, pl->w, pl->U, pl->m, 1, zero,
-                             pl->A32, n, 0.f, 0, 0, err, st));
+    const bool tt = pl->tc_terms == 3;
+    OP("g_herk_tc", tc2_split_a(pl->U, pl->m, pl->w, n, pl->m, pl->UAh, tt ? pl->UAl : nullptr, st));
+    OP("g_herk_tc", tc2_split_b(pl->U, pl->m, 1, pl->m, n, pl->UBh, tt ? pl->UBl : nullptr, st));
+    OP("g_herk_tc", tc2_gemm(pl->tc_terms, n, n, pl->m, pl->UAh, pl->UAl, pl->UBh, pl->UBl, one, zero, pl->A32, n,
+                             0.f, 0, 0, 1, nullptr, err, st));
     OP("g_collapse", gassembly_collapse(pl->A32, n, Q, pl->L, pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->KT, st));
-    OP("g_field_tc", tc_cgemm(pl->tc_terms, (int)pl->npix_red, (int)QQ, pl->nlag, mone, pl->E, pl->nlag, nullptr,
-                              pl->KT, (int)QQ, 0, zero, pl->G, (int)QQ, (float)pl->L, Q + 1, (int)QQ, err, st));
+    OP("g_field_tc", tc2_split_b(pl->KT, (int)QQ, 0, pl->nlag, (int)QQ, pl->KTh, tt ? pl->KTl : nullptr, st));
+    OP("g_field_tc", tc2_gemm(pl->tc_terms, (int)pl->npix_red, (int)QQ, pl->nlag, pl->Eh, pl->El, pl->KTh, pl->KTl,
+                              mone, zero, pl->G, (int)QQ, (float)pl->L, Q + 1, (int)QQ, pl->tc_splits_g, pl->tc_ws,
+                              err, st));
     return PISCO_OK;
   }
   OP("g_kernel", gassembly_kernel(pl->U, pl->w, Q, pl->L, pl->m, pl->d_lag_ptr, pl->d_lag_ent, pl->nbox, pl->K, st));
-  OP("g_dft", apply_axis_c(pl->K, pl->gdft[2], pl->T1, AxisView{QQ, (long long)B[0] * B[1], B[2], Nr[2], 1}, st));
+  OP("g_dft", apply_axis_c(pl->K, pl->gdftT, pl->T1, AxisView{QQ, (long long)B[0] * B[1], B[2], Nr[2], 1, 0, 1}, st));
   if (pl->D == 3) {
     OP("g_dft", apply_axis_c(pl->T1, pl->gdft[1], pl->T2, AxisView{QQ, B[0], B[1], Nr[1], Nr[2]}, st));
     OP("g_dft", apply_axis_c(pl->T2, pl->gdft[0], pl->G, AxisView{QQ, 1, B[0], Nr[0], (long long)Nr[1] * Nr[2], 1}, st));
@@ -563,7 +591,7 @@ pisco_status run_lowres(pisco_plan_s* pl, const float2* calib) {
   const int Q = pl->Q;
   const int* Nc = pl->Nc;
   const int* Nr = pl->Nr;
-  OP("lowres_dft", apply_axis_c(calib, pl->ydft[2], pl->Ya, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Nr[2], 1}, st));
+  OP("lowres_dft", apply_axis_c(calib, pl->ydftT, pl->Ya, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Nr[2], 1, 0, 1}, st));
   if (pl->D == 3) {
     OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yb, AxisView{Q, Nc[0], Nc[1], Nr[1], Nr[2]}, st));
     OP("lowres_dft", apply_axis_c(pl->Yb, pl->ydft[0], pl->Yf, AxisView{Q, 1, Nc[0], Nr[0], (long long)Nr[1] * Nr[2]}, st));
@@ -582,7 +610,7 @@ pisco_status run_interp(pisco_plan_s* pl, float2* maps) {
     OP("interp_final_norm", interp_final_normalize(pl->V, nullptr, Q, 0, 1, 1, pl->npix, maps, st));
     return PISCO_OK;
   }
-  OP("interp_axis", apply_axis_c(pl->V, pl->interp[2], pl->I1, AxisView{Q, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1}, st));
+  OP("interp_axis", apply_axis_c(pl->V, pl->interpT, pl->I1, AxisView{Q, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1, 0, 1}, st));
   if (pl->D == 3) {
     OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{Q, Nr[0], Nr[1], N[1], N[2]}, st));
     OP("interp_final_norm", interp_final_normalize(pl->I2, pl->interp[0], Q, 0, Nr[0], N[0], (long long)N[1] * N[2], maps, st));
@@ -704,7 +732,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->tc_g = (p->flags & PISCO_FLAG_TC_GFIELD) != 0;
   pl->tc_eig = (p->flags & PISCO_FLAG_TC_EIG) != 0;
   pl->tc_terms = (p->flags & PISCO_FLAG_TC_1PASS) ? 1 : 3;
-  if ((pl->tc_g || pl->tc_eig) && tc_gemm_prepare() != cudaSuccess) {
+  if ((pl->tc_g || pl->tc_eig) && (tc_gemm_prepare() != cudaSuccess || tc2_prepare() != cudaSuccess)) {
     cudaGetLastError();
     delete pl;
     return PISCO_ERR_CUDA;
@@ -726,6 +754,11 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     ok = ok && upload(pl, &pl->ydft[d], ydft_matrix(Nr[d], Nc[d]));
     ok = ok && upload(pl, &pl->interp[d], interp_matrix(Nr[d], N[d]));
   }
+  ok = ok && upload(pl, &pl->fwdT, transposed(fwd_matrix(Lp[2], Nc[2]), Lp[2], Nc[2]));
+  ok = ok && upload(pl, &pl->invT, transposed(inv_matrix(Lp[2], pl->tau[2]), B[2], Lp[2]));
+  ok = ok && upload(pl, &pl->gdftT, transposed(gdft_matrix(Nr[2], pl->tau[2]), Nr[2], B[2]));
+  ok = ok && upload(pl, &pl->ydftT, transposed(ydft_matrix(Nr[2], Nc[2]), Nr[2], Nc[2]));
+  ok = ok && upload(pl, &pl->interpT, transposed(interp_matrix(Nr[2], N[2]), N[2], Nr[2]));
   ok = ok && upload(pl, &pl->d_lag_of_ij, pl->lag_of_ij);
   ok = ok && upload(pl, &pl->d_lag_ptr, pl->lag_ptr) && upload(pl, &pl->d_lag_ent, pl->lag_ent);
   // Gram
@@ -756,10 +789,30 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->T1, (size_t)(QQ * B[0] * B[1] * Nr[2]));
   ok = ok && dalloc(pl, &pl->T2, (size_t)(QQ * B[0] * Nr[1] * Nr[2]));
   ok = ok && dalloc(pl, &pl->G, (size_t)(QQ * pl->npix_red));
-  if (ok && pl->tc_g) {
-    ok = upload(pl, &pl->d_lagc_ptr, pl->lagc_ptr) &&
-         upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
-         dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ);
+  if (ok && (pl->tc_g || pl->tc_eig)) {
+    if (p->tc_splits > 0) pl->tc_splits_ax = std::min(p->tc_splits, 64);
+    const size_t k2n = (size_t)tc2_k2p(n), k2m = (size_t)tc2_k2p(pl->m_max);
+    const size_t lo_n = pl->tc_terms == 3 ? 1 : 0;
+    pl->tc_ws_elems = std::max<size_t>((size_t)pl->tc_splits_ax * n * pl->m_max,
+                                       pl->tc_splits_g > 1 ? (size_t)(pl->tc_splits_g * pl->npix_red * QQ) : 0);
+    ok = dalloc(pl, &pl->tc_ws, pl->tc_ws_elems);
+    if (ok && pl->tc_eig)
+      ok = dalloc(pl, &pl->Ah, (size_t)n * k2n) && dalloc(pl, &pl->Al, lo_n * n * k2n + 1) &&
+           dalloc(pl, &pl->Xh, (size_t)2 * tc2_np(pl->m_max) * k2n) &&
+           dalloc(pl, &pl->Xl, lo_n * 2 * tc2_np(pl->m_max) * k2n + 1);
+    if (ok && pl->tc_g) {
+      const size_t k2l = (size_t)tc2_k2p(pl->nlag);
+      ok = upload(pl, &pl->d_lagc_ptr, pl->lagc_ptr) &&
+           upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
+           dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->Eh, (size_t)pl->npix_red * k2l) &&
+           dalloc(pl, &pl->El, lo_n * pl->npix_red * k2l + 1) && dalloc(pl, &pl->KTh, (size_t)2 * tc2_np((int)QQ) * k2l) &&
+           dalloc(pl, &pl->KTl, lo_n * 2 * tc2_np((int)QQ) * k2l + 1) && dalloc(pl, &pl->UAh, (size_t)n * k2m) &&
+           dalloc(pl, &pl->UAl, lo_n * n * k2m + 1) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m) &&
+           dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m + 1);
+      // the lag exponentials never change: split them once here
+      ok = ok && tc2_split_a(pl->E, pl->nlag, nullptr, (int)pl->npix_red, pl->nlag, pl->Eh,
+                             pl->tc_terms == 3 ? pl->El : nullptr, nullptr) == cudaSuccess;
+    }
   }
   // low-res images, PI output, interpolation intermediates
   ok = ok && dalloc(pl, &pl->Ya, (size_t)Q * Nc[0] * Nc[1] * Nr[2]);
@@ -1231,6 +1284,57 @@ pisco_status pisco_tc_cgemm(int nterms, int M, int N, int K, const float* alpha,
                                  nullptr, (const float2*)d_B, ldb, opB, make_float2(beta[0], beta[1]),
                                  (float2*)d_C, ldc, 0.f, 0, 0, d_status, (cudaStream_t)cuda_stream);
   return e == cudaSuccess ? PISCO_OK : PISCO_ERR_CUDA;
+}
+
+// workspace layout of pisco_tc_cgemm_pipelined: A' head, A' tail, B' head, B' tail, partials
+static void tc2_ws_layout(int nterms, int M, int N, int K, int splits, size_t off[5], size_t* total) {
+  const size_t k2 = (size_t)tc2_k2p(K), np2 = 2 * (size_t)tc2_np(N);
+  const size_t a = (size_t)M * k2 * sizeof(float), b = np2 * k2 * sizeof(float);
+  off[0] = 0;
+  off[1] = off[0] + a;
+  off[2] = off[1] + (nterms == 3 ? a : 0);
+  off[3] = off[2] + b;
+  off[4] = off[3] + (nterms == 3 ? b : 0);
+  *total = off[4] + (splits > 1 ? (size_t)splits * M * N * sizeof(float2) : 0);
+}
+
+size_t pisco_tc_cgemm_pipelined_workspace(int nterms, int M, int N, int K, int splits) {
+  if (M <= 0 || N <= 0 || K < 0) return 0;
+  size_t off[5], tot;
+  tc2_ws_layout(nterms, M, N, K, splits, off, &tot);
+  return tot;
+}
+
+pisco_status pisco_tc_cgemm_pipelined(int nterms, int M, int N, int K, const float* alpha, const void* d_A, int lda,
+                                      const void* d_B, int ldb, int opB, const float* beta, void* d_C, int ldc,
+                                      int splits, void* d_workspace, size_t workspace_bytes, int* d_status,
+                                      void* cuda_stream) {
+  if (M < 0 || N < 0 || K < 0 || (nterms != 1 && nterms != 3) || (opB != 0 && opB != 1) || splits < 1) return PISCO_ERR_ARG;
+  if (M == 0 || N == 0) return PISCO_OK;
+  if (!d_C || !alpha || !beta || (K > 0 && (!d_A || !d_B)) || !d_workspace) return PISCO_ERR_ARG;
+  if (lda < K || ldc < N || ldb < (opB == 0 ? N : K)) return PISCO_ERR_ARG;
+  if ((((uintptr_t)d_A | (uintptr_t)d_B | (uintptr_t)d_C) & 7) || ((uintptr_t)d_workspace & 15)) return PISCO_ERR_ARG;
+  size_t off[5], tot;
+  tc2_ws_layout(nterms, M, N, K, splits, off, &tot);
+  if (workspace_bytes < tot) return PISCO_ERR_ARG;
+  if (tc2_prepare() != cudaSuccess) {
+    cudaGetLastError();
+    return PISCO_ERR_CUDA;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  unsigned char* w = static_cast<unsigned char*>(d_workspace);
+  float* ah = reinterpret_cast<float*>(w + off[0]);
+  float* al = nterms == 3 ? reinterpret_cast<float*>(w + off[1]) : nullptr;
+  float* bh = reinterpret_cast<float*>(w + off[2]);
+  float* bl = nterms == 3 ? reinterpret_cast<float*>(w + off[3]) : nullptr;
+  float2* part = splits > 1 ? reinterpret_cast<float2*>(w + off[4]) : nullptr;
+  if (K > 0 && (tc2_split_a((const float2*)d_A, lda, nullptr, M, K, ah, al, st) != cudaSuccess ||
+                tc2_split_b((const float2*)d_B, ldb, opB, K, N, bh, bl, st) != cudaSuccess))
+    return PISCO_ERR_CUDA;
+  if (tc2_gemm(nterms, M, N, K, ah, al, bh, bl, make_float2(alpha[0], alpha[1]), make_float2(beta[0], beta[1]),
+               (float2*)d_C, ldc, 0.f, 0, 0, splits, part, d_status, st) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  return PISCO_OK;
 }
 
 pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,
