@@ -306,13 +306,21 @@ def run_gpu(args):
     spec = dict(grid=w["grid"], calib_shape=w["calib"], num_coils=w["Q"], tau=w["tau"],
                 kernel_shape=w["shape"], thr=w["thr"], reduction=w["reduction"], iters=w["iters"])
 
+    # ---- launch configuration of the batched form, picked by the autotuner (cached) ----
+    nb = args.batch
+    bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
+    tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0}, [])
+    if args.tune:
+        from paper_2302_13431_gb300.autotune import tune
+        tuned, tune_table = tune([spec] * nb, calibs=bcal)
     # ---- plain FP32 PISCO, one plan, one map per call (per-slice launches): comparison point ----
     maps1 = torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64, device="cuda")
     eig1 = torch.empty(red, dtype=torch.float32, device="cuda")
     single = {}
-    for prec in dict.fromkeys(["fp32", args.precision]):
+    for prec in dict.fromkeys(["fp32", tuned["precision"]]):
+        kw = dict(tc_splits=tuned["tc_splits"]) if prec == tuned["precision"] else {}
         e1 = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"], thr=w["thr"],
-                            reduction=w["reduction"], iters=w["iters"], seed=0, precision=prec)
+                            reduction=w["reduction"], iters=w["iters"], seed=0, precision=prec, **kw)
         for i in range(max(args.warmup, 3)):
             e1.estimate_into(calibs[i % N_CASES], maps1, eig1)
         torch.cuda.synchronize()
@@ -324,7 +332,8 @@ def run_gpu(args):
     # ---- op profile of one map (eager launches, CUDA events around each operation) ----
     est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
                          thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0,
-                         precision=args.precision)
+                         precision=tuned["precision"], tc_splits=tuned["tc_splits"],
+                         gemm_splits=tuned["gemm_splits"])
     est.estimate_into(calibs[0], maps1, eig1)
     stats = est.stats()
     est.set_profiling(True)
@@ -341,9 +350,7 @@ def run_gpu(args):
     est.close()
 
     # ---- batched form: one step = one CUDA-graph launch over `batch` maps ----
-    nb = args.batch
-    batch = PiscoBatch([dict(spec, precision=args.precision)] * nb)
-    bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
+    batch = PiscoBatch([dict(spec, **tuned)] * nb)
     bmaps, beigs = batch.alloc_outputs()
     for i in range(args.warmup):
         batch.estimate_into(bcal, bmaps, beigs)
@@ -386,7 +393,7 @@ def run_gpu(args):
     peaks = _peaks()
     stages = {}
     for op in prof:
-        r = roofline_for(op, prof, w, stats, peaks, args.precision)
+        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"])
         if r.get("achieved") is not None and r.get("peak"):
             r["frac"] = r["achieved"] / r["peak"]
         r["ms_per_map"] = prof[op][0] / nprof
@@ -404,8 +411,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": ("FP64 Gram and FP64 threshold split of the nullspace; " +
                       {"fp32": "FP32 CUDA-core products elsewhere"}.get(
-                          args.precision, "split-precision TF32 tensor-core products (FP32 accumulate) for "
-                          + ("G(x) assembly and the eigensolver block products" if "eig" in args.precision
+                          tuned["precision"], "split-precision TF32 tensor-core products (FP32 accumulate) for "
+                          + ("G(x) assembly and the eigensolver block products" if "eig" in tuned["precision"]
                              else "G(x) assembly") + ", FP32 elsewhere")),
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "batch": nb,
@@ -417,8 +424,11 @@ def run_gpu(args):
         "plain_fp32_single_map": {"value": plain_value, "unit": "maps/s",
                                   "note": "plain FP32 PISCO: one plan, one map per call (per-slice "
                                           "launches), CUDA-core FP32 products, same iterations"},
-        "single_map_same_precision": {"value": single[args.precision], "unit": "maps/s"},
-        "precision_mode": args.precision,
+        "single_map_same_precision": {"value": single[tuned["precision"]], "unit": "maps/s"},
+        "precision_mode": tuned["precision"],
+        "launch_config": dict(tuned, autotuned=bool(args.tune),
+                              candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}":
+                                                      round(r["ms"], 3) for r in tune_table}),
         "wall_s": t_wall,
         "gpu_launches": int(binfo["launches"]) * args.steps,
         "e2e": {"value": e2e_value, "unit": "maps/s",
@@ -457,10 +467,15 @@ def run_gpu_uneven(args):
     from paper_2302_13431_gb300.estimator import PiscoBatch, PiscoEstimator
     from paper_2302_13431_gb300.phantoms import make_case, uneven_slice_specs
     torch.cuda.set_device(0)
-    specs = [dict(sp, precision=args.precision) for sp in uneven_slice_specs(96)]
+    specs = uneven_slice_specs(96)
     calibs_h = [make_case(sp["grid"], sp["num_coils"], sp["calib_shape"], seed=sp["data_seed"]).calib
                 for sp in specs]
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
+    tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0}, [])
+    if args.tune:
+        from paper_2302_13431_gb300.autotune import tune
+        tuned, tune_table = tune(specs, calibs=calibs)
+    specs = [dict(sp, **tuned) for sp in specs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     batch = PiscoBatch(specs)
@@ -496,7 +511,10 @@ def run_gpu_uneven(args):
     line = {
         "metric": UNEVEN_METRIC, "value": value, "unit": "slices/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision_mode": args.precision,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision_mode": tuned["precision"],
+        "launch_config": dict(tuned, autotuned=bool(args.tune),
+                              candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}":
+                                                      round(r["ms"], 3) for r in tune_table}),
         "data": "synthetic",
         "config": {"workload": "96 uneven 2D slices (seeded shapes, see phantoms.uneven_slice_specs)",
                    "batch": len(specs), "step": "one CUDA-graph launch estimating all 96 slices",
@@ -524,7 +542,9 @@ def main():
     ap.add_argument("--workload", choices=["2d_256_q32", "uneven96"], default="2d_256_q32",
                     help="2d_256_q32: the headline workload; uneven96: 96 uneven slices in one batch")
     ap.add_argument("--precision", default="tc_g_eig",
-                    help="fp32 | tc_g | tc_g_eig | tc_g_1pass | tc_g_eig_1pass (see estimator.PRECISIONS)")
+                    help="with --no-tune: fp32 | tc_g | tc_g_eig | tc_g_1pass | tc_g_eig_1pass")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the autotuner (which picks precision route and split factors, cached)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "pisco":
         args.warmup = 3

@@ -83,6 +83,8 @@ typedef struct {
   int eig_block;          /* block size of the nullspace eigensolver (0: automatic)           */
   int eig_iters;          /* subspace iterations of the eigensolver (0: automatic)            */
   int tc_splits;          /* K splits of the tensor-core GEMMs (PISCO_FLAG_TC_*; 0: automatic) */
+  int gemm_splits;        /* split-K cap of the CUDA-core block products (0: automatic, about
+                             two CTAs per SM; small values suit batches of concurrent plans)  */
 } pisco_params;
 
 typedef struct pisco_plan_s* pisco_plan_t;

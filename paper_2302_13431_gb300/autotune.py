@@ -1,0 +1,109 @@
+"""Autotuner of the batched estimator's launch configuration.
+
+For a batch of problem shapes it times every candidate configuration on the device, as a
+captured batch (one CUDA-graph replay per step, the way the batch runs in production), and keeps
+the fastest.  The knobs are ones whose best value depends on the shapes and on how many estimates
+share the GPU:
+
+* precision route: CUDA-core FP32 products, or split-TF32 tensor-core products for the G(x)
+  assembly only or also for the eigensolver's block products (all three meet the FP32 parity
+  gates; the one-pass TF32 routes do not and are never candidates);
+* `tc_splits`: K splits of the tensor-core block products (more splits shorten one product,
+  fewer cost less SM time and reduction traffic);
+* `gemm_splits`: split-K cap of the CUDA-core block products (same trade-off).
+
+Results are cached in a JSON file keyed by the device name, the shapes and the batch size.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import torch
+
+from .estimator import PiscoBatch
+from .phantoms import make_case
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
+
+KNOB_KEYS = ("precision", "tc_splits", "gemm_splits")
+
+
+def candidates():
+    out = []
+    for gs in (0, 2, 8):
+        out.append(dict(precision="fp32", tc_splits=0, gemm_splits=gs))
+        out.append(dict(precision="tc_g", tc_splits=0, gemm_splits=gs))
+        for ts in (1, 4):
+            out.append(dict(precision="tc_g_eig", tc_splits=ts, gemm_splits=gs))
+    return out
+
+
+def _shape_key(specs, batch_note=""):
+    shapes = [(tuple(s["grid"]), tuple(s["calib_shape"]), s["num_coils"], s["tau"] if isinstance(s["tau"], int)
+               else tuple(s["tau"]), s.get("kernel_shape", "ellipsoid"), s.get("reduction", 1), s.get("iters", 30))
+              for s in specs]
+    h = hashlib.sha1(repr(shapes).encode()).hexdigest()[:16]
+    dev = torch.cuda.get_device_name(0) if torch.cuda.is_available() else "cpu"
+    return f"{dev}|{len(specs)} items|{h}{batch_note}"
+
+
+def _time_batch(specs, calibs, steps, warmup):
+    batch = PiscoBatch(specs)
+    maps, eigs = batch.alloc_outputs()
+    try:
+        for _ in range(warmup):
+            batch.estimate_into(calibs, maps, eigs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            batch.estimate_into(calibs, maps, eigs)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    finally:
+        batch.close()
+
+
+def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None, refresh=False, verbose=False):
+    """Best configuration (dict of KNOB_KEYS) for the batch `specs` (PiscoBatch spec dicts).
+
+    calibs: device calibration tensors (synthetic ones are generated when None).  Returns
+    (config, table) where table lists every candidate with its milliseconds per batch step."""
+    key = _shape_key(specs)
+    db = {}
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                db = json.load(f)
+        except Exception:
+            db = {}
+    if not refresh and key in db:
+        return db[key]["config"], db[key]["table"]
+    if calibs is None:
+        calibs = [torch.from_numpy(make_case(s["grid"], s["num_coils"], s["calib_shape"], seed=7000 + i).calib).cuda()
+                  for i, s in enumerate(specs)]
+    table = []
+    t0 = time.time()
+    for c in (cands or candidates()):
+        sp = [dict(s, **c) for s in specs]
+        ms = _time_batch(sp, calibs, steps, warmup)
+        table.append(dict(c, ms=ms))
+        if verbose:
+            print(f"  autotune {c}: {ms:.2f} ms/step", flush=True)
+    best = min(table, key=lambda r: r["ms"])
+    config = {k: best[k] for k in KNOB_KEYS}
+    if cache:
+        db[key] = dict(config=config, table=table, seconds=time.time() - t0)
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(db, f, indent=1)
+    return config, table
+
+
+def apply(specs, config):
+    """The batch specs with the tuned knobs set."""
+    return [dict(s, **config) for s in specs]

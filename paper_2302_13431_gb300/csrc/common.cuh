@@ -103,10 +103,12 @@ cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L,
 // dense complex GEMM: C = alpha*op(A)*op(B) + beta*C, row-major, op in {'N','C'}
 // Split-K partials go to splitk_ws (ws_elems entries); tile_count must hold 4096 zeroed ints
 // (the kernel returns them to zero).  With splitk_ws == nullptr there is no split.
+// max_splits caps the split-K factor (0: automatic, about two CTAs per SM): many splits cut the
+// latency of one product, few splits its SM-time (what a batch of concurrent estimates needs)
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* splitk_ws,
-                  size_t ws_elems, int* tile_count, cudaStream_t st);
+                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits = 0);
 
 // a2: block eigensolver pieces
 cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, cudaStream_t st);
@@ -123,8 +125,8 @@ cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, f
                                  cudaStream_t st);
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
                        float skip_rel, DevStatus* status, cudaStream_t st);
-cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, double2* Zb,
-                            cudaStream_t st);
+cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, const int* band_idx,
+                            double2* Zb, cudaStream_t st);
 cudaError_t eig_pow(float* d, int m, float e, cudaStream_t st);
 cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
                             cudaStream_t st);

@@ -871,14 +871,21 @@ cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, 
 // Zb = A * Xb for the FP64 Gram A (n x n) and the nb <= 16 band columns: one warp per row of
 // A (lanes stride the row, so loads are coalesced), Xb staged in shared memory in chunks,
 // FP64 accumulation, warp reduction.  FP64-FMA bound: n^2 * nb complex MACs.
+// Only the band columns in use (band_idx >= 0; they come first) are multiplied: the unused
+// ones are zero and cost no FP64 work.
 template <int NBV>
 __global__ void __launch_bounds__(256) band_matvec_kernel(const double2* __restrict__ A,
                                                           const double2* __restrict__ Xb, int n,
+                                                          const int* __restrict__ band_idx,
                                                           double2* __restrict__ Zb) {
   constexpr int KC = 256;  // rows of Xb per chunk (32 KiB of shared memory for 8 columns)
   __shared__ double2 xs[KC * NBV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.x * 8 + warp;
+  int nbu = 0;
+#pragma unroll
+  for (int c = 0; c < NBV; ++c)
+    if (band_idx[c] >= 0) nbu = c + 1;
   double2 acc[NBV];
 #pragma unroll
   for (int c = 0; c < NBV; ++c) acc[c] = make_double2(0.0, 0.0);
@@ -892,7 +899,8 @@ __global__ void __launch_bounds__(256) band_matvec_kernel(const double2* __restr
       for (int k = lane; k < kc; k += 32) {
         const double2 a = arow[k];
 #pragma unroll
-        for (int c = 0; c < NBV; ++c) cfma(acc[c], a, xs[k * NBV + c]);
+        for (int c = 0; c < NBV; ++c)
+          if (c < nbu) cfma(acc[c], a, xs[k * NBV + c]);
       }
     }
   }
@@ -910,10 +918,10 @@ __global__ void __launch_bounds__(256) band_matvec_kernel(const double2* __restr
   }
 }
 
-cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, double2* Zb,
-                            cudaStream_t st) {
+cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, const int* band_idx,
+                            double2* Zb, cudaStream_t st) {
   if (nb != 8) return cudaErrorInvalidValue;
-  band_matvec_kernel<8><<<(n + 7) / 8, 256, 0, st>>>(A, Xb, n, Zb);
+  band_matvec_kernel<8><<<(n + 7) / 8, 256, 0, st>>>(A, Xb, n, band_idx, Zb);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) cgemm64_kernel(char opA, char opB, int M,
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* ws,
-                  size_t ws_elems, int* tile_count, cudaStream_t st) {
+                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (M >= 48 && N >= 48 && K >= 4096) {  // large-K shapes only: the 32x32 kernel wins below
     // 64 x 64 tiles; split K until ~1 CTA per SM, at most 16 slices of >= 2 k-steps each
@@ -250,6 +250,7 @@ cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const c
       sp = (152 + tiles2 - 1) / tiles2;
       sp = std::min(sp, std::max(1, kb / 2));
       sp = std::min(sp, 16);
+      if (max_splits > 0) sp = std::min(sp, max_splits);
       while (sp > 1 && (size_t)sp * M * N > ws_elems) --sp;
     }
     const int kc = ((kb + sp - 1) / sp) * BK2;
@@ -267,6 +268,7 @@ cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const c
     splits = (2 * 152 + tiles - 1) / tiles;
     if (splits > kblocks) splits = kblocks;
     if (splits > 64) splits = 64;
+    if (max_splits > 0 && splits > max_splits) splits = max_splits;
     while (splits > 1 && (size_t)splits * M * N > ws_elems) --splits;
     if (splits < 1) splits = 1;
   }
@@ -280,9 +282,9 @@ cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const c
 }
 
 template cudaError_t cgemm<float>(char, char, int, int, int, float2, const float2*, int, const float2*,
-                                  int, float2, float2*, int, float2*, size_t, int*, cudaStream_t);
+                                  int, float2, float2*, int, float2*, size_t, int*, cudaStream_t, int);
 template cudaError_t cgemm<double>(char, char, int, int, int, double2, const double2*, int,
                                    const double2*, int, double2, double2*, int, double2*, size_t, int*,
-                                   cudaStream_t);
+                                   cudaStream_t, int);
 
 }  // namespace pisco

@@ -48,7 +48,7 @@ class PiscoEstimator:
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
-                 stream=None, precision="fp32", tc_splits=0):
+                 stream=None, precision="fp32", tc_splits=0, gemm_splits=0):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -59,7 +59,8 @@ class PiscoEstimator:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = (B.PISCO_FLAG_HOST_IO if host_io else 0) | precision_flags(precision)
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
-                                    reduction, iters, seed, flags, eig_block, eig_iters, tc_splits)
+                                    reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
+                                    gemm_splits)
         st, h = B.pisco_plan(self.params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
             raise B.PiscoError(st, "pisco_plan")
@@ -154,7 +155,8 @@ class PiscoBatch:
     """A batch of independent estimates (shapes may differ), run as one CUDA graph.
 
     specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
-    kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision.
+    kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision, tc_splits,
+    gemm_splits.
     """
 
     def __init__(self, specs, stream=None):
@@ -169,7 +171,8 @@ class PiscoBatch:
                                         sp.get("thr", 0.05), sp.get("reduction", 1),
                                         sp.get("iters", 30), sp.get("seed", 0),
                                         precision_flags(sp.get("precision", "fp32")),
-                                        sp.get("eig_block", 0), sp.get("eig_iters", 0), sp.get("tc_splits", 0)))
+                                        sp.get("eig_block", 0), sp.get("eig_iters", 0), sp.get("tc_splits", 0),
+                                        sp.get("gemm_splits", 0)))
         st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
             raise B.PiscoError(st, "pisco_batch_plan")
