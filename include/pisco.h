@@ -63,6 +63,12 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
 #define PISCO_FLAG_TC_EIG 0x4u    /* the n x n by n x m block products of the nullspace
                                      eigensolver on the tensor cores, same split precision.
                                      The threshold split itself stays FP64 (Sec. III-B).       */
+#define PISCO_FLAG_MASKED_GRAM 0x10u /* exact Gram of the masked calibration matrix (only the
+                                     rows n with n - Lambda inside the calibration box: Eq. C as
+                                     written, before Sec. V-A neglects the masking), from
+                                     FP64 summed-area tables of the lagged products instead of
+                                     the FFT route.  Needs prod(Nc) <= 12288 (shared memory of
+                                     one tile); PISCO_ERR_UNSUPPORTED otherwise.              */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 

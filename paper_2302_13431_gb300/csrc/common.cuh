@@ -144,6 +144,13 @@ cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_s
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
                                const int* lag_ent, int nlag, float2* KT, cudaStream_t st);
 
+// exact Gram of the masked calibration matrix (kernels_gram.cu): A (FP64 n x n), scale, A32
+cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo, const int* hi, const int* lam,
+                        int L, const int* lag_ids, const int* lagc_ptr, const int* lag_ent, int nlag, const int* tau,
+                        const int* B, double2* A, double* scale, float2* A32, cudaStream_t st);
+cudaError_t gram_masked_prepare(int nvol);
+size_t gram_masked_smem(int nvol);
+
 // warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out, widths <= 128; w32 is the FP32
 // parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its FP16 copy (the
 // matrices are read from w16, the biases from w32)

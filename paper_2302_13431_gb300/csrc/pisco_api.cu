@@ -55,6 +55,9 @@ struct pisco_plan_s {
   // tensor-core routes (PISCO_FLAG_TC_*): lags of Lambda-Lambda only (compressed CSR), the
   // lag-to-pixel exponentials E [npix_red][nlag] and the folded lag table KT [nlag][Q*Q]
   bool tc_g = false, tc_eig = false;
+  bool masked = false;                 // PISCO_FLAG_MASKED_GRAM
+  int lam_lo[3] = {0, 0, 0}, lam_hi[3] = {0, 0, 0};
+  int *d_lam = nullptr, *d_lag_ids = nullptr;
   int tc_terms = 3;
   int nlag = 0;
   std::vector<int> lagc_ptr, lag_ids;
@@ -433,6 +436,12 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   const int Q = pl->Q;
   const int* Nc = pl->Nc;
   const int* Lp = pl->Lp;
+  if (pl->masked) {
+    OP("gram_masked_fp64", gram_masked(calib, Q, Nc, pl->lam_lo, pl->lam_hi, pl->d_lam, pl->L, pl->d_lag_ids,
+                                       pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->tau, pl->B, pl->A, pl->gscale,
+                                       pl->A32, st));
+    return PISCO_OK;
+  }
   const int* B = pl->B;
   // forward zero-padded DFT of every channel: x, y, z
   OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwdT, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
@@ -731,6 +740,27 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   if (pl->m < 2) { delete pl; return PISCO_ERR_ARG; }
   pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 8;
   pl->gemm_splits = p->gemm_splits > 0 ? std::min(p->gemm_splits, 64) : 0;
+  pl->masked = (p->flags & PISCO_FLAG_MASKED_GRAM) != 0;
+  if (pl->masked) {
+    const int nvol = pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
+    if (nvol > 12288) {
+      delete pl;
+      return PISCO_ERR_UNSUPPORTED;
+    }
+    for (int d = 0; d < 3; ++d) {
+      pl->lam_lo[d] = 1 << 20;
+      pl->lam_hi[d] = -(1 << 20);
+      for (int i = 0; i < pl->L; ++i) {
+        pl->lam_lo[d] = std::min(pl->lam_lo[d], pl->lam[3 * i + d]);
+        pl->lam_hi[d] = std::max(pl->lam_hi[d], pl->lam[3 * i + d]);
+      }
+    }
+    if (gram_masked_prepare(nvol) != cudaSuccess) {
+      cudaGetLastError();
+      delete pl;
+      return PISCO_ERR_CUDA;
+    }
+  }
   pl->tc_g = (p->flags & PISCO_FLAG_TC_GFIELD) != 0;
   pl->tc_eig = (p->flags & PISCO_FLAG_TC_EIG) != 0;
   pl->tc_terms = (p->flags & PISCO_FLAG_TC_1PASS) ? 1 : 3;
@@ -763,6 +793,8 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && upload(pl, &pl->interpT, transposed(interp_matrix(Nr[2], N[2]), N[2], Nr[2]));
   ok = ok && upload(pl, &pl->d_lag_of_ij, pl->lag_of_ij);
   ok = ok && upload(pl, &pl->d_lag_ptr, pl->lag_ptr) && upload(pl, &pl->d_lag_ent, pl->lag_ent);
+  ok = ok && upload(pl, &pl->d_lagc_ptr, pl->lagc_ptr) && upload(pl, &pl->d_lag_ids, pl->lag_ids) &&
+       upload(pl, &pl->d_lam, pl->lam);
   // Gram
   const long long gA = std::max((long long)Q * Nc[0] * Nc[1] * Lp[2], (long long)np * Lp[0] * Lp[1] * B[2]);
   const long long gB = std::max((long long)Q * Nc[0] * Lp[1] * Lp[2], (long long)np * Lp[0] * B[1] * B[2]);
@@ -804,8 +836,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
            dalloc(pl, &pl->Xl, lo_n * 2 * tc2_np(pl->m_max) * k2n + 1);
     if (ok && pl->tc_g) {
       const size_t k2l = (size_t)tc2_k2p(pl->nlag);
-      ok = upload(pl, &pl->d_lagc_ptr, pl->lagc_ptr) &&
-           upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
+      ok = upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
            dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->Eh, (size_t)pl->npix_red * k2l) &&
            dalloc(pl, &pl->El, lo_n * pl->npix_red * k2l + 1) && dalloc(pl, &pl->KTh, (size_t)2 * tc2_np((int)QQ) * k2l) &&
            dalloc(pl, &pl->KTl, lo_n * 2 * tc2_np((int)QQ) * k2l + 1) && dalloc(pl, &pl->UAh, (size_t)n * k2m) &&

@@ -44,11 +44,12 @@ class PiscoEstimator:
     grid, calib_shape: (z,)y,x sizes of the image grid and the centred calibration box.
     tau: radius (int or per-axis tuple); kernel_shape: "ellipsoid" (Sec. V-B) or "rect".
     reduction: grid-reduction factor f (Sec. V-D); iters: power iterations (Sec. V-E).
+    masked_gram: the exact Gram of the masked calibration matrix instead of Sec. V-A's FFT route.
     """
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
-                 stream=None, precision="fp32", tc_splits=0, gemm_splits=0):
+                 stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -58,6 +59,8 @@ class PiscoEstimator:
         self.reduced = tuple(g // reduction for g in self.grid)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = (B.PISCO_FLAG_HOST_IO if host_io else 0) | precision_flags(precision)
+        if masked_gram:
+            flags |= B.PISCO_FLAG_MASKED_GRAM
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
                                     reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
                                     gemm_splits)
