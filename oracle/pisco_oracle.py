@@ -260,12 +260,13 @@ def _splitmix64_vec(x):
     return z ^ (z >> np.uint64(31))
 
 
-def start_vectors(seed, npix, Q):
-    """Power-iteration start vectors: v0[j][q] = u(2q) + i u(2q+1) with
+def start_vectors(seed, npix, Q, offset=0):
+    """Power-iteration start vectors: v0[j][q] = u(offset+2q) + i u(offset+2q+1) with
     u(t) = ((splitmix64(seed*2^40 + j*2^8 + t) >> 40) - 2^23) / 2^23, a 24-bit uniform in
-    [-1, 1).  Exactly representable in FP32, so the CUDA path draws identical vectors."""
+    [-1, 1).  Exactly representable in FP32, so the CUDA path draws identical vectors.
+    offset = 2Q gives the second vector of the block iteration."""
     j = np.arange(npix, dtype=np.uint64)[:, None]
-    t = np.arange(2 * Q, dtype=np.uint64)[None, :]
+    t = np.arange(offset, offset + 2 * Q, dtype=np.uint64)[None, :]
     with np.errstate(over="ignore"):
         ctr = (np.uint64(seed) << np.uint64(40)) + (j << np.uint64(8)) + t
     r = _splitmix64_vec(ctr) >> np.uint64(40)
@@ -290,6 +291,32 @@ def power_iteration(G, v0, iters, lam_size):
     lam = np.real(np.sum(np.conj(v) * Gv, axis=1)) / lam_size
     res = np.linalg.norm(Gv - (lam * lam_size)[:, None] * v, axis=1) / lam_size
     return v, lam, res
+
+
+def block_power_iteration(G, V0, iters, lam_size):
+    """Power iteration on a two-vector block (subspace iteration) for pixels whose two smallest
+    eigenvalues of G(x) are close, then Rayleigh-Ritz on the block.  Each step applies
+    B = I - G/|Lambda| to both vectors and re-orthonormalises them by Gram-Schmidt (first
+    vector normalised, second made orthogonal to it and normalised).  At the end the 2x2 matrix
+    H = V^H G V is diagonalised and the Ritz vector of its smallest eigenvalue is returned with
+    lambda = that eigenvalue / |Lambda|.  V0: [npix, Q, 2]."""
+    V = np.array(V0, dtype=np.complex128)
+    def orth(V):
+        v1 = V[:, :, 0] / np.linalg.norm(V[:, :, 0], axis=1, keepdims=True)
+        w2 = V[:, :, 1] - np.sum(np.conj(v1) * V[:, :, 1], axis=1, keepdims=True) * v1
+        v2 = w2 / np.linalg.norm(w2, axis=1, keepdims=True)
+        return np.stack([v1, v2], axis=2)
+    V = orth(V)
+    for _ in range(iters):
+        GV = np.einsum("jpq,jqb->jpb", G, V)
+        V = orth(V - GV / lam_size)
+    GV = np.einsum("jpq,jqb->jpb", G, V)
+    H = np.einsum("jpa,jpb->jab", np.conj(V), GV)
+    H = 0.5 * (H + np.conj(np.swapaxes(H, 1, 2)))
+    w, Y = np.linalg.eigh(H)
+    v = np.einsum("jqb,jb->jq", V, Y[:, :, 0])
+    v = v / np.linalg.norm(v, axis=1, keepdims=True)
+    return v, w[:, 0] / lam_size
 
 
 # ----------------------------------------------------------------------------------------

@@ -435,3 +435,55 @@ def test_end_to_end_small_case_support_and_maps():
     me = out["maps"].reshape(4, -1).T[m]
     assert np.linalg.norm(al(mt) - al(me)) / np.linalg.norm(mt) < 0.05
     assert np.allclose(np.linalg.norm(out["maps"].reshape(4, -1), axis=0), 1.0)
+
+
+def _hermitian_with_spectrum(rng, Q, lams):
+    M = rng.standard_normal((Q, Q)) + 1j * rng.standard_normal((Q, Q))
+    U, _ = np.linalg.qr(M)
+    return (U * np.asarray(lams)) @ U.conj().T, U
+
+
+def test_block_power_iteration_spans_the_matrix_power_subspace():
+    """After t steps the block spans (I - G/L)^t V0: compared through the projectors, with the
+    power formed explicitly (matrix_power) and orthonormalised by QR."""
+    rng = np.random.default_rng(31)
+    Q, L, t = 6, 9.0, 5
+    G, _ = _hermitian_with_spectrum(rng, Q, [0.1, 0.4, 2.0, 3.0, 5.0, 8.0])
+    V0 = rng.standard_normal((1, Q, 2)) + 1j * rng.standard_normal((1, Q, 2))
+    Bt = np.linalg.matrix_power(np.eye(Q) - G / L, t)
+    Qm, _ = np.linalg.qr(Bt @ V0[0])
+    P_ref = Qm @ Qm.conj().T
+    # the oracle's block before Rayleigh-Ritz is recovered from its Ritz vector's subspace:
+    # run with t steps and check the Ritz vector lies in span(Bt V0)
+    v, lam = O.block_power_iteration(G[None], V0, t, L)
+    assert np.linalg.norm(P_ref @ v[0] - v[0]) < 1e-12
+    # and it is the Ritz vector of the projected matrix
+    H = Qm.conj().T @ G @ Qm
+    w, Y = np.linalg.eigh(H)
+    assert abs(lam[0] - w[0] / L) < 1e-12
+    y = Qm @ Y[:, 0]
+    assert abs(abs(np.vdot(y, v[0])) - 1.0) < 1e-12
+
+
+def test_block_iteration_converges_where_single_vector_iteration_lags():
+    """Two nearly equal smallest eigenvalues (gap 1e-3 |Lambda|) and a large third one: after 30
+    steps the single-vector iteration is still far from the null vector (its rate is set by
+    lambda_2), the block iteration with Rayleigh-Ritz has converged at the rate set by lambda_3:
+    1 - |<v, v*>| ~ ((1 - lambda_3/L) / (1 - lambda_1/L))^(2t) = 0.7^60 = 5e-10."""
+    rng = np.random.default_rng(32)
+    Q, L = 8, 20.0
+    G, U = _hermitian_with_spectrum(rng, Q, [0.0, 0.02, 6.0, 7.0, 9.0, 11.0, 14.0, 19.0])
+    v0 = O.start_vectors(3, 1, Q)
+    V0 = np.stack([v0, O.start_vectors(3, 1, Q, offset=2 * Q)], axis=2)
+    vp, _, _ = O.power_iteration(G[None], v0, 30, L)
+    vb, lb = O.block_power_iteration(G[None], V0, 30, L)
+    err_p = 1 - abs(np.vdot(U[:, 0], vp[0]))
+    err_b = 1 - abs(np.vdot(U[:, 0], vb[0]))
+    assert err_p > 1e-2
+    assert err_b < 10 * 0.7 ** 60 and abs(lb[0]) < 10 * 0.7 ** 60
+
+
+def test_start_vector_offset_draws_the_next_counters():
+    a = O.start_vectors(7, 3, 4, offset=8)
+    b = O.start_vectors(7, 3, 8)
+    np.testing.assert_array_equal(a, b[:, 4:])
