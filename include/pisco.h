@@ -69,6 +69,11 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
                                      FP64 summed-area tables of the lagged products instead of
                                      the FFT route.  Needs prod(Nc) <= 12288 (shared memory of
                                      one tile); PISCO_ERR_UNSUPPORTED otherwise.              */
+#define PISCO_FLAG_BLOCK_PI 0x20u  /* power iteration on a two-vector block (Gram-Schmidt every
+                                     step, 2x2 Rayleigh-Ritz at the end) for pixels whose two
+                                     smallest eigenvalues of G(x) are close: convergence set by
+                                     the third eigenvalue (Sec. V-E's iteration on a block);
+                                     twice the work of the plain iteration                    */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 
@@ -225,6 +230,14 @@ void pisco_batch_destroy(pisco_batch_t b);
  * synchronising. */
 pisco_status pisco_gram_lags_noalloc(const pisco_params* p, const void* d_calib, void* d_lags,
                                      void* cuda_stream);
+
+/* Reduced-grid support mask from an eigenvalue map (as pisco_estimate writes it):
+ * d_mask[i] = 1 where d_eig[i] < threshold, else 0.  lambda_min(G)/|Lambda| is ~0 inside the
+ * object, where the maps are identifiable (Sec. II), and grows outside; 0.05 mirrors the
+ * nullspace threshold.  d_eig: device float[n]; d_mask: device uint8[n]; enqueued on
+ * cuda_stream, no synchronisation. */
+pisco_status pisco_support_mask(const float* d_eig, long long n, float threshold, unsigned char* d_mask,
+                                void* cuda_stream);
 
 /* ---- Learned warm start of the power iteration (an addition of this library; the paper
  * starts every pixel from an arbitrary vector, Sec. V-E) ------------------------------------

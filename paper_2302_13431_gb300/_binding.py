@@ -20,6 +20,7 @@ PISCO_FLAG_TC_GFIELD = 0x2
 PISCO_FLAG_TC_EIG = 0x4
 PISCO_FLAG_TC_1PASS = 0x8
 PISCO_FLAG_MASKED_GRAM = 0x10
+PISCO_FLAG_BLOCK_PI = 0x20
 (PISCO_BUF_LAGS, PISCO_BUF_GRAM, PISCO_BUF_SIGNAL, PISCO_BUF_WEIGHTS, PISCO_BUF_RITZ, PISCO_BUF_G,
  PISCO_BUF_V, PISCO_BUF_Y, PISCO_BUF_BLOCK, PISCO_BUF_RITZ32, PISCO_BUF_SCALE) = range(11)
 
@@ -143,6 +144,8 @@ def load():
     lib.pisco_mlp_read.restype = ctypes.c_int
     lib.pisco_mlp_destroy.argtypes = [vp]
     lib.pisco_mlp_destroy.restype = None
+    lib.pisco_support_mask.argtypes = [vp, ctypes.c_longlong, ctypes.c_float, vp, vp]
+    lib.pisco_support_mask.restype = ctypes.c_int
     lib.pisco_set_warm_start.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float, ctypes.c_int]
     lib.pisco_set_warm_start.restype = ctypes.c_int
     lib.pisco_warm_start_features.argtypes = [vp, ctypes.c_int, ctypes.c_longlong, vp, vp]
@@ -359,4 +362,9 @@ def pisco_tc_cgemm_pipelined(nterms, M, N, K, alpha, d_A, lda, d_B, ldb, opB, be
     return load().pisco_tc_cgemm_pipelined(nterms, M, N, K, a, ctypes.c_void_p(d_A), lda, ctypes.c_void_p(d_B), ldb,
                                            opB, b, ctypes.c_void_p(d_C), ldc, splits, ctypes.c_void_p(d_ws),
                                            ws_bytes, ctypes.c_void_p(d_status or 0), ctypes.c_void_p(stream))
+
+
+def pisco_support_mask(d_eig, n, threshold, d_mask, stream=0):
+    return load().pisco_support_mask(ctypes.c_void_p(d_eig), n, threshold, ctypes.c_void_p(d_mask),
+                                     ctypes.c_void_p(stream))
 

@@ -197,6 +197,9 @@ cudaError_t tc_cgemm(int nterms, int M, int N, int K, float2 alpha, const float2
                      int ldc, float diag_val, int diag_stride, int diag_limit, int* err, cudaStream_t st);
 
 // a4+a5: power iteration with the phase step
+cudaError_t power_iteration_block2(const float2* G, const float2* Y, int Q, long long npix, int iters,
+                                   float lam_size, unsigned long long seed, float2* V, float* eig, cudaStream_t st);
+cudaError_t support_mask(const float* eig, long long n, float thr, unsigned char* mask, cudaStream_t st);
 // warm-start options of the power iteration: v0 [npix][2Q] start proposals (null: counter
 // start); gate > 0 flags pixels with residual above it (flags [npix], count += flagged);
 // only != null re-solves only the pixels with only[x] != 0

@@ -56,6 +56,7 @@ struct pisco_plan_s {
   // lag-to-pixel exponentials E [npix_red][nlag] and the folded lag table KT [nlag][Q*Q]
   bool tc_g = false, tc_eig = false;
   bool masked = false;                 // PISCO_FLAG_MASKED_GRAM
+  bool block_pi = false;               // PISCO_FLAG_BLOCK_PI
   int lam_lo[3] = {0, 0, 0}, lam_hi[3] = {0, 0, 0};
   int *d_lam = nullptr, *d_lag_ids = nullptr;
   int tc_terms = 3;
@@ -658,6 +659,9 @@ pisco_status run_all(pisco_plan_s* pl, const float2* calib, float2* maps, float*
       OP("pi_fallback", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->ws_fb_iters, (float)pl->L,
                                         pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st, o2));
     }
+  } else if (pl->block_pi) {
+    OP("power_iteration", power_iteration_block2(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->prm.power_iters,
+                                                 (float)pl->L, pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st));
   } else {
     OP("power_iteration", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->prm.power_iters, (float)pl->L,
                                           pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st));
@@ -741,6 +745,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 8;
   pl->gemm_splits = p->gemm_splits > 0 ? std::min(p->gemm_splits, 64) : 0;
   pl->masked = (p->flags & PISCO_FLAG_MASKED_GRAM) != 0;
+  pl->block_pi = (p->flags & PISCO_FLAG_BLOCK_PI) != 0;
   if (pl->masked) {
     const int nvol = pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
     if (nvol > 12288) {
@@ -1041,6 +1046,7 @@ pisco_status pisco_set_warm_start(pisco_plan_t pl, pisco_mlp_t mlp, int iters, f
   size_t np;
   mlp_dims(mlp, &n_in, &H, &n_out, &np);
   if (n_in != 2 * pl->Q || n_out != 2 * pl->Q || iters < 0 || fallback_iters < 1 || !(gate == gate)) return PISCO_ERR_ARG;
+  if (pl->block_pi) return PISCO_ERR_UNSUPPORTED;  // the block iteration draws its own two starts
   if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
   const size_t npmax = mlp_param_count(2 * pl->Q, 128, 2 * pl->Q);
   if (!pl->ws_w32) {
@@ -1368,6 +1374,15 @@ pisco_status pisco_tc_cgemm_pipelined(int nterms, int M, int N, int K, const flo
                (float2*)d_C, ldc, 0.f, 0, 0, splits, part, d_status, st) != cudaSuccess)
     return PISCO_ERR_CUDA;
   return PISCO_OK;
+}
+
+pisco_status pisco_support_mask(const float* d_eig, long long n, float threshold, unsigned char* d_mask,
+                                void* cuda_stream) {
+  if (n < 0 || !(threshold == threshold)) return PISCO_ERR_ARG;
+  if (n == 0) return PISCO_OK;
+  if (!d_eig || !d_mask) return PISCO_ERR_ARG;
+  return support_mask(d_eig, n, threshold, d_mask, (cudaStream_t)cuda_stream) == cudaSuccess ? PISCO_OK
+                                                                                           : PISCO_ERR_CUDA;
 }
 
 pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,

@@ -45,11 +45,13 @@ class PiscoEstimator:
     tau: radius (int or per-axis tuple); kernel_shape: "ellipsoid" (Sec. V-B) or "rect".
     reduction: grid-reduction factor f (Sec. V-D); iters: power iterations (Sec. V-E).
     masked_gram: the exact Gram of the masked calibration matrix instead of Sec. V-A's FFT route.
+    block_pi: two-vector block power iteration with Rayleigh-Ritz (small-gap pixels).
     """
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
-                 stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False):
+                 stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False,
+                 block_pi=False):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -61,6 +63,8 @@ class PiscoEstimator:
         flags = (B.PISCO_FLAG_HOST_IO if host_io else 0) | precision_flags(precision)
         if masked_gram:
             flags |= B.PISCO_FLAG_MASKED_GRAM
+        if block_pi:
+            flags |= B.PISCO_FLAG_BLOCK_PI
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
                                     reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
                                     gemm_splits)
@@ -141,6 +145,14 @@ class PiscoEstimator:
         view = _DevView(ptr, (nbytes // item,), ts)
         self.stream.synchronize()
         return torch.as_tensor(view, device="cuda").clone()
+
+    def support_mask(self, eig: torch.Tensor, threshold=0.05) -> torch.Tensor:
+        """uint8 mask of the reduced-grid pixels with eigenvalue below threshold (inside the object)."""
+        mask = torch.empty(eig.shape, dtype=torch.uint8, device=eig.device)
+        st = B.pisco_support_mask(eig.data_ptr(), eig.numel(), threshold, mask.data_ptr(), self.stream.cuda_stream)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_support_mask")
+        return mask
 
     def close(self):
         if getattr(self, "_plan", None):
