@@ -193,3 +193,39 @@ def teacher_pairs(teacher: PiscoEstimator, calibs, eig_max=0.05):
         xs.append(features(teacher).index_select(0, keep))
         ts.append(targets(teacher).index_select(0, keep))
     return torch.cat(xs), torch.cat(ts)
+
+
+def generated_pairs(teacher: PiscoEstimator, seeds, eig_max=0.05, **gen):
+    """teacher_pairs over volumes drawn by phantoms_torch.make_calib (one volume on the device at
+    a time); gen: grid, Q, calib_shape and the generator's options."""
+    from .phantoms_torch import make_calib
+    xs, ts = [], []
+    for s in seeds:
+        calib, _ = make_calib(gen["grid"], gen["Q"], gen["calib_shape"], seed=int(s),
+                              **{k: v for k, v in gen.items() if k not in ("grid", "Q", "calib_shape")})
+        x, t = teacher_pairs(teacher, [calib], eig_max=eig_max)
+        xs.append(x)
+        ts.append(t)
+        del calib
+    return torch.cat(xs), torch.cat(ts)
+
+
+def train_warm_start(grid, Q, calib_shape, tau, reduction, train_seeds, val_seeds, kernel_shape="ellipsoid",
+                     hidden=128, epochs=6, batch=8192, lr=5e-4, teacher_iters=200, seed=0, log=None):
+    """Train a warm-start network on volumes the estimator itself labels (teacher: the same
+    estimator with teacher_iters power iterations), select it on the validation volumes.
+    Returns (net, info)."""
+    teacher = PiscoEstimator(grid, calib_shape, Q, tau, kernel_shape=kernel_shape, reduction=reduction,
+                             iters=teacher_iters)
+    gen = dict(grid=grid, Q=Q, calib_shape=calib_shape)
+    X, T = generated_pairs(teacher, train_seeds, **gen)
+    Xv, Tv = generated_pairs(teacher, val_seeds, **gen)
+    teacher.close()
+    net = WarmStartNet(Q, hidden, seed=seed, max_batch=batch)
+    hist = net.fit(X, T, epochs=epochs, batch=batch, lr=lr, seed=seed, val=(Xv, Tv))
+    info = dict(train_pairs=int(X.shape[0]), val_pairs=int(Xv.shape[0]), loss=hist,
+                val_direction_error=net.val_history, train_volumes=len(train_seeds),
+                val_volumes=len(val_seeds))
+    if log:
+        log(info)
+    return net, info

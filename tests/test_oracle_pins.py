@@ -487,3 +487,16 @@ def test_start_vector_offset_draws_the_next_counters():
     a = O.start_vectors(7, 3, 4, offset=8)
     b = O.start_vectors(7, 3, 8)
     np.testing.assert_array_equal(a, b[:, 4:])
+
+
+def test_gpu_recipe_generator_equals_numpy_recipe_without_noise():
+    """phantoms_torch draws the same parameters as phantoms.make_case; without noise the
+    calibration blocks agree to rounding (evaluated here on the CPU device)."""
+    torch = pytest.importorskip("torch")
+    from paper_2302_13431_gb300.phantoms import make_case
+    from paper_2302_13431_gb300.phantoms_torch import make_calib
+    for grid, Q, cs in (((32, 40), 4, (12, 10)), ((16, 12, 14), 3, (8, 6, 8))):
+        ref = make_case(grid, Q, cs, seed=5, noise=0.0).calib
+        got, _ = make_calib(grid, Q, cs, seed=5, noise=0.0, device="cpu")
+        got = got.numpy()
+        assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
