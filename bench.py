@@ -210,6 +210,17 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
+# DRAM bytes (read + write) per launch of each op's main kernel on the 2D 256x256 Q=32
+# workload, from one ncu --set full capture (cold caches); an op whose kernel changed since
+# its capture has no entry
+NCU_TRAFFIC = {
+    "eig_jacobi": (54784, "ncu --set full, jacobi_kernel<1>, 64x64 block"),
+    "eig_gemm_AX": (15700480, "ncu --set full, tc2_kernel<3,4>, A32 X 928x64x928 (head+tail operands)"),
+    "g_field_tc": (10471936, "ncu --set full, tc2_kernel<3,2>, G = E K 4096x1024x105"),
+    "g_herk_tc": (2871808, "ncu --set full, tc2_kernel<3,2>, U W U^H 928x928x64"),
+}
+
+
 def n_lags(w):
     """|Lambda - Lambda| of the workload's kernel support (2D ellipse / rectangle)."""
     t = w["tau"]
@@ -402,7 +413,10 @@ def run_gpu(args):
     roof = dict(stages[dom]) if dom else {}
     roof.pop("ms_per_map", None)
     roof["kernel"] = dom
-    roof["traffic"] = None
+    tr = NCU_TRAFFIC.get(dom) if w is WORKLOAD else None
+    roof["traffic"] = tr[0] if tr else None
+    if tr:
+        roof["traffic_source"] = tr[1]
     roof["measured"] = "CUDA events around each launch of the op in the profiled single-map pass"
 
     line = {
