@@ -96,6 +96,7 @@ typedef struct {
   int tc_splits;          /* K splits of the tensor-core GEMMs (PISCO_FLAG_TC_*; 0: automatic) */
   int gemm_splits;        /* split-K cap of the CUDA-core block products (0: automatic, about
                              two CTAs per SM; small values suit batches of concurrent plans)  */
+  int gemm_tile;          /* tile of the CUDA-core block products: 0 automatic, 32 or 64      */
 } pisco_params;
 
 typedef struct pisco_plan_s* pisco_plan_t;

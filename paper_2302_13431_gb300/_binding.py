@@ -42,6 +42,7 @@ class pisco_params(ctypes.Structure):
         ("eig_iters", ctypes.c_int),
         ("tc_splits", ctypes.c_int),
         ("gemm_splits", ctypes.c_int),
+        ("gemm_tile", ctypes.c_int),
     ]
 
 
@@ -160,7 +161,7 @@ def pisco_status_string(status: int) -> str:
 
 def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid", null_threshold=0.05,
                 grid_reduction=1, power_iters=30, seed=0, flags=0, eig_block=0, eig_iters=0, tc_splits=0,
-                gemm_splits=0):
+                gemm_splits=0, gemm_tile=0):
     """pisco_params from (z,)y,x-ordered Python tuples (the array order); the struct is x,y,z."""
     nd = len(grid)
     pr = pisco_params()
@@ -181,6 +182,7 @@ def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid",
     pr.eig_iters = eig_iters
     pr.tc_splits = tc_splits
     pr.gemm_splits = gemm_splits
+    pr.gemm_tile = gemm_tile
     return pr
 
 

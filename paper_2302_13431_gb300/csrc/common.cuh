@@ -108,7 +108,7 @@ cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L,
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* splitk_ws,
-                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits = 0);
+                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits = 0, int tile = 0);
 
 // a2: block eigensolver pieces
 cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, cudaStream_t st);

@@ -239,9 +239,12 @@ __global__ void __launch_bounds__(256) cgemm64_kernel(char opA, char opB, int M,
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* ws,
-                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits) {
+                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits, int tile) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (M >= 48 && N >= 48 && K >= 4096) {  // large-K shapes only: the 32x32 kernel wins below
+  // automatic: 64x64 tiles only for large K (the 32x32 kernel has the lower latency for the
+  // skinny shapes of one solve); tile = 64 / 32 forces one (64x64 costs less SM time per flop)
+  const bool big = tile == 64 || (tile != 32 && M >= 48 && N >= 48 && K >= 4096);
+  if (big) {
     // 64 x 64 tiles; split K until ~1 CTA per SM, at most 16 slices of >= 2 k-steps each
     const int tiles2 = ((M + BM2 - 1) / BM2) * ((N + BN2 - 1) / BN2);
     const int kb = K > 0 ? (K + BK2 - 1) / BK2 : 1;
@@ -282,9 +285,9 @@ cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const c
 }
 
 template cudaError_t cgemm<float>(char, char, int, int, int, float2, const float2*, int, const float2*,
-                                  int, float2, float2*, int, float2*, size_t, int*, cudaStream_t, int);
+                                  int, float2, float2*, int, float2*, size_t, int*, cudaStream_t, int, int);
 template cudaError_t cgemm<double>(char, char, int, int, int, double2, const double2*, int,
                                    const double2*, int, double2, double2*, int, double2*, size_t, int*,
-                                   cudaStream_t, int);
+                                   cudaStream_t, int, int);
 
 }  // namespace pisco

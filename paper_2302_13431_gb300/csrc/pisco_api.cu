@@ -68,6 +68,7 @@ struct pisco_plan_s {
   // split operands of the TMA-fed tensor-core GEMMs (head/tail arrays) and split-K scratch
   int tc_splits_ax = 4, tc_splits_g = 1;
   int gemm_splits = 0;  // split-K cap of the CUDA-core block products (0: automatic)
+  int gemm_tile = 0;    // CUDA-core block product tile: 0 automatic, 32 or 64
   float *Ah = nullptr, *Al = nullptr, *Xh = nullptr, *Xl = nullptr;        // A32 and the block
   float *Eh = nullptr, *El = nullptr, *KTh = nullptr, *KTl = nullptr;      // E and the lag table
   float *UAh = nullptr, *UAl = nullptr, *UBh = nullptr, *UBl = nullptr;    // U diag(w), conj(U)^T
@@ -476,13 +477,13 @@ pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, co
   cudaStream_t st = pl->st;
   const int n = pl->n;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits));
+  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   if (m <= 96) {
     if (pl->chol_variant == 1)
       OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
     else
       OP("eig_chol", eig_chol_inv_warp(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
-    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, Yin, m, pl->Rinv, m, zero, Xout, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits));
+    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, Yin, m, pl->Rinv, m, zero, Xout, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   } else {
     OP("eig_chol", eig_chol(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, pl->dsc, diag_out, pl->dstatus, st));
     OP("eig_trsm", eig_trsm(Yin, pl->Rinv, pl->dsc, n, m, Xout, st));
@@ -501,7 +502,7 @@ cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y) {
                     pl->tc_splits_ax, pl->tc_ws, &pl->dstatus->flags, pl->st);
   }
   return cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, X, m, zero, Y, m, pl->ws32, pl->ws32_elems,
-                      pl->tiles, pl->st, pl->gemm_splits);
+                      pl->tiles, pl->st, pl->gemm_splits, pl->gemm_tile);
 }
 
 // Nullspace of the Gram (Sec. III-A, threshold footnote of Sec. III-B): orthogonal
@@ -547,9 +548,9 @@ pisco_status run_eig(pisco_plan_s* pl) {
   }
   // Rayleigh-Ritz on the block
   OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
-  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits));
+  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
-  OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits));
+  OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   // FP64 Rayleigh quotients of the Ritz vectors that decide the split
   OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st));
   OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
@@ -744,6 +745,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   if (pl->m < 2) { delete pl; return PISCO_ERR_ARG; }
   pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 8;
   pl->gemm_splits = p->gemm_splits > 0 ? std::min(p->gemm_splits, 64) : 0;
+  pl->gemm_tile = (p->gemm_tile == 32 || p->gemm_tile == 64) ? p->gemm_tile : 0;
   pl->masked = (p->flags & PISCO_FLAG_MASKED_GRAM) != 0;
   pl->block_pi = (p->flags & PISCO_FLAG_BLOCK_PI) != 0;
   if (pl->masked) {

@@ -51,7 +51,7 @@ class PiscoEstimator:
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
                  stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False,
-                 block_pi=False):
+                 block_pi=False, gemm_tile=0):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -67,7 +67,7 @@ class PiscoEstimator:
             flags |= B.PISCO_FLAG_BLOCK_PI
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
                                     reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
-                                    gemm_splits)
+                                    gemm_splits, gemm_tile)
         st, h = B.pisco_plan(self.params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
             raise B.PiscoError(st, "pisco_plan")
@@ -171,7 +171,7 @@ class PiscoBatch:
 
     specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
     kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision, tc_splits,
-    gemm_splits.
+    gemm_splits, gemm_tile.
     """
 
     def __init__(self, specs, stream=None):
@@ -187,7 +187,7 @@ class PiscoBatch:
                                         sp.get("iters", 30), sp.get("seed", 0),
                                         precision_flags(sp.get("precision", "fp32")),
                                         sp.get("eig_block", 0), sp.get("eig_iters", 0), sp.get("tc_splits", 0),
-                                        sp.get("gemm_splits", 0)))
+                                        sp.get("gemm_splits", 0), sp.get("gemm_tile", 0)))
         st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
             raise B.PiscoError(st, "pisco_batch_plan")
