@@ -320,7 +320,8 @@ def run_gpu(args):
     # ---- launch configuration of the batched form, picked by the autotuner (cached) ----
     nb = args.batch
     bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
-    tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0}, [])
+    tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
+                          "gram_df": False}, [])
     if args.tune:
         from paper_2302_13431_gb300.autotune import tune
         tuned, tune_table = tune([spec] * nb, calibs=bcal)
@@ -344,7 +345,7 @@ def run_gpu(args):
     est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
                          thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0,
                          precision=tuned["precision"], tc_splits=tuned["tc_splits"],
-                         gemm_splits=tuned["gemm_splits"], gemm_tile=tuned["gemm_tile"])
+                         gemm_splits=tuned["gemm_splits"], gemm_tile=tuned["gemm_tile"], gram_df=tuned["gram_df"])
     est.estimate_into(calibs[0], maps1, eig1)
     stats = est.stats()
     est.set_profiling(True)
@@ -441,7 +442,8 @@ def run_gpu(args):
         "single_map_same_precision": {"value": single[tuned["precision"]], "unit": "maps/s"},
         "precision_mode": tuned["precision"],
         "launch_config": dict(tuned, autotuned=bool(args.tune),
-                              candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}":
+                              candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
+                                                      f"{'/df' if r.get('gram_df') else ''}":
                                                       round(r["ms"], 3) for r in tune_table}),
         "wall_s": t_wall,
         "gpu_launches": int(binfo["launches"]) * args.steps,
@@ -485,7 +487,8 @@ def run_gpu_uneven(args):
     calibs_h = [make_case(sp["grid"], sp["num_coils"], sp["calib_shape"], seed=sp["data_seed"]).calib
                 for sp in specs]
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
-    tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0}, [])
+    tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
+                          "gram_df": False}, [])
     if args.tune:
         from paper_2302_13431_gb300.autotune import tune
         tuned, tune_table = tune(specs, calibs=calibs)
@@ -527,7 +530,8 @@ def run_gpu_uneven(args):
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision_mode": tuned["precision"],
         "launch_config": dict(tuned, autotuned=bool(args.tune),
-                              candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}":
+                              candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
+                                                      f"{'/df' if r.get('gram_df') else ''}":
                                                       round(r["ms"], 3) for r in tune_table}),
         "data": "synthetic",
         "config": {"workload": "96 uneven 2D slices (seeded shapes, see phantoms.uneven_slice_specs)",

@@ -74,6 +74,11 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
                                      smallest eigenvalues of G(x) are close: convergence set by
                                      the third eigenvalue (Sec. V-E's iteration on a block);
                                      twice the work of the plain iteration                    */
+#define PISCO_FLAG_GRAM_DF 0x40u  /* the FFT route of Sec. V-A in double-float arithmetic (each
+                                     value an unevaluated sum of two FP32 numbers, Dekker's
+                                     error-free products and Knuth's two-sum; about 48
+                                     significant bits) instead of FP64: GB300's FP64 rate is
+                                     about 1/58 of FP32.  The lag table and the Gram stay FP64. */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 

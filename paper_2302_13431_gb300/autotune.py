@@ -11,7 +11,8 @@ share the GPU:
 * `tc_splits`: K splits of the tensor-core block products (more splits shorten one product,
   fewer cost less SM time and reduction traffic);
 * `gemm_splits`: split-K cap of the CUDA-core block products (same trade-off);
-* `gemm_tile`: 32x32 or 64x64 output tiles for those products (lower latency vs less SM time).
+* `gemm_tile`: 32x32 or 64x64 output tiles for those products (lower latency vs less SM time);
+* `gram_df`: the Gram's FFT route in FP64 or in double-float arithmetic (pairs of FP32).
 
 Results are cached in a JSON file keyed by the device name, the shapes and the batch size.
 """
@@ -29,17 +30,17 @@ from .phantoms import make_case
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
-KNOB_KEYS = ("precision", "tc_splits", "gemm_splits", "gemm_tile")
+KNOB_KEYS = ("precision", "tc_splits", "gemm_splits", "gemm_tile", "gram_df")
 
 
 def candidates():
-    out = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0),
-           dict(precision="fp32", tc_splits=0, gemm_splits=2, gemm_tile=64),
-           dict(precision="tc_g", tc_splits=0, gemm_splits=2, gemm_tile=0)]
-    for ts in (1, 4):
-        for gs in (0, 2):
-            for gt in (0, 64):
-                out.append(dict(precision="tc_g_eig", tc_splits=ts, gemm_splits=gs, gemm_tile=gt))
+    out = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False),
+           dict(precision="fp32", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False),
+           dict(precision="tc_g", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False)]
+    for df in (False, True):
+        for ts in (1, 4):
+            for gs, gt in ((0, 0), (2, 64)):
+                out.append(dict(precision="tc_g_eig", tc_splits=ts, gemm_splits=gs, gemm_tile=gt, gram_df=df))
     return out
 
 

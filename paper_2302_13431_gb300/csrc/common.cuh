@@ -144,6 +144,13 @@ cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_s
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
                                const int* lag_ent, int nlag, float2* KT, cudaStream_t st);
 
+// the Gram's FFT route in double-float arithmetic (kernels_gram_df.cu); tables and buffers hold
+// {Re hi, Re lo, Im hi, Im lo} float quadruples in the storage of the FP64 path
+cudaError_t apply_axis_c2df(const float2* in, const void* M, void* out, AxisView v, cudaStream_t st);
+cudaError_t apply_axis_df(const void* in, const void* M, void* out, AxisView v, cudaStream_t st);
+cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st);
+cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, cudaStream_t st);
+
 // exact Gram of the masked calibration matrix (kernels_gram.cu): A (FP64 n x n), scale, A32
 cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo, const int* hi, const int* lam,
                         int L, const int* lag_ids, const int* lagc_ptr, const int* lag_ent, int nlag, const int* tau,

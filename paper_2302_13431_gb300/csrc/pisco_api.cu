@@ -57,6 +57,9 @@ struct pisco_plan_s {
   bool tc_g = false, tc_eig = false;
   bool masked = false;                 // PISCO_FLAG_MASKED_GRAM
   bool block_pi = false;               // PISCO_FLAG_BLOCK_PI
+  bool gram_df = false;                // PISCO_FLAG_GRAM_DF: double-float DFT tables below
+  float4 *fwdT_df = nullptr, *fwd_df[3] = {nullptr, nullptr, nullptr};
+  float4 *invT_df = nullptr, *inv_df[3] = {nullptr, nullptr, nullptr};
   int lam_lo[3] = {0, 0, 0}, lam_hi[3] = {0, 0, 0};
   int *d_lam = nullptr, *d_lag_ids = nullptr;
   int tc_terms = 3;
@@ -163,6 +166,16 @@ template <typename T>
 bool upload(pisco_plan_s* pl, T** p, const std::vector<T>& h) {
   if (!dalloc(pl, p, h.size())) return false;
   return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// FP64 table -> double-float {Re hi, Re lo, Im hi, Im lo}: hi = fl32(x), lo = fl32(x - hi)
+std::vector<float4> to_df(const std::vector<double2>& M) {
+  std::vector<float4> out(M.size());
+  for (size_t i = 0; i < M.size(); ++i) {
+    const float rh = (float)M[i].x, ih = (float)M[i].y;
+    out[i] = make_float4(rh, (float)(M[i].x - (double)rh), ih, (float)(M[i].y - (double)ih));
+  }
+  return out;
 }
 
 template <typename T>
@@ -445,6 +458,30 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
     return PISCO_OK;
   }
   const int* B = pl->B;
+  if (pl->gram_df) {
+    // the same passes in double-float arithmetic (FP64 storage reused; lags written in FP64)
+    const int np = pl->npairs;
+    OP("gram_dft_df", apply_axis_c2df(calib, pl->fwdT_df, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
+    OP("gram_dft_df", apply_axis_df(pl->gA, pl->fwd_df[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
+    const void* S = pl->gB;
+    if (pl->D == 3) {
+      OP("gram_dft_df", apply_axis_df(pl->gB, pl->fwd_df[0], pl->S, AxisView{Q, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
+      S = pl->S;
+    }
+    OP("gram_pair_products", gram_pair_products_df(S, Q, pl->nfreq, pl->P, st));
+    OP("gram_dft_df", apply_axis_df(pl->P, pl->invT_df, pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
+    if (pl->D == 3) {
+      OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->gB, AxisView{np, Lp[0], Lp[1], B[1], B[2]}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gB, pl->inv_df[0], pl->Rp, AxisView{np, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
+    } else {
+      OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->Rp, AxisView{np, 1, Lp[1], B[1], B[2]}, st));
+    }
+    OP("gram_scatter", gram_scatter_pairs_df(pl->Rp, Q, pl->nbox, pl->lags, st));
+    const int lag0 = (2 * pl->tau[0] * B[1] + 2 * pl->tau[1]) * B[2] + 2 * pl->tau[2];
+    OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st));
+    OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st));
+    return PISCO_OK;
+  }
   // forward zero-padded DFT of every channel: x, y, z
   OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwdT, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
   OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->fwd[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
@@ -748,6 +785,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->gemm_tile = (p->gemm_tile == 32 || p->gemm_tile == 64) ? p->gemm_tile : 0;
   pl->masked = (p->flags & PISCO_FLAG_MASKED_GRAM) != 0;
   pl->block_pi = (p->flags & PISCO_FLAG_BLOCK_PI) != 0;
+  pl->gram_df = (p->flags & PISCO_FLAG_GRAM_DF) != 0;
   if (pl->masked) {
     const int nvol = pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
     if (nvol > 12288) {
@@ -798,6 +836,14 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && upload(pl, &pl->gdftT, transposed(gdft_matrix(Nr[2], pl->tau[2]), Nr[2], B[2]));
   ok = ok && upload(pl, &pl->ydftT, transposed(ydft_matrix(Nr[2], Nc[2]), Nr[2], Nc[2]));
   ok = ok && upload(pl, &pl->interpT, transposed(interp_matrix(Nr[2], N[2]), N[2], Nr[2]));
+  if (pl->gram_df) {
+    ok = ok && upload(pl, &pl->fwdT_df, to_df(transposed(fwd_matrix(Lp[2], Nc[2]), Lp[2], Nc[2])));
+    ok = ok && upload(pl, &pl->invT_df, to_df(transposed(inv_matrix(Lp[2], pl->tau[2]), B[2], Lp[2])));
+    for (int d = 0; d < 2; ++d) {
+      ok = ok && upload(pl, &pl->fwd_df[d], to_df(fwd_matrix(Lp[d], Nc[d])));
+      ok = ok && upload(pl, &pl->inv_df[d], to_df(inv_matrix(Lp[d], pl->tau[d])));
+    }
+  }
   ok = ok && upload(pl, &pl->d_lag_of_ij, pl->lag_of_ij);
   ok = ok && upload(pl, &pl->d_lag_ptr, pl->lag_ptr) && upload(pl, &pl->d_lag_ent, pl->lag_ent);
   ok = ok && upload(pl, &pl->d_lagc_ptr, pl->lagc_ptr) && upload(pl, &pl->d_lag_ids, pl->lag_ids) &&

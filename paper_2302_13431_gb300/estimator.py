@@ -46,12 +46,13 @@ class PiscoEstimator:
     reduction: grid-reduction factor f (Sec. V-D); iters: power iterations (Sec. V-E).
     masked_gram: the exact Gram of the masked calibration matrix instead of Sec. V-A's FFT route.
     block_pi: two-vector block power iteration with Rayleigh-Ritz (small-gap pixels).
+    gram_df: the Gram's FFT route in double-float instead of FP64 arithmetic.
     """
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
                  stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False,
-                 block_pi=False, gemm_tile=0):
+                 block_pi=False, gemm_tile=0, gram_df=False):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -65,6 +66,8 @@ class PiscoEstimator:
             flags |= B.PISCO_FLAG_MASKED_GRAM
         if block_pi:
             flags |= B.PISCO_FLAG_BLOCK_PI
+        if gram_df:
+            flags |= B.PISCO_FLAG_GRAM_DF
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
                                     reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
                                     gemm_splits, gemm_tile)
@@ -171,7 +174,7 @@ class PiscoBatch:
 
     specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
     kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision, tc_splits,
-    gemm_splits, gemm_tile.
+    gemm_splits, gemm_tile, gram_df.
     """
 
     def __init__(self, specs, stream=None):
@@ -185,7 +188,8 @@ class PiscoBatch:
                                         sp["tau"], sp.get("kernel_shape", "ellipsoid"),
                                         sp.get("thr", 0.05), sp.get("reduction", 1),
                                         sp.get("iters", 30), sp.get("seed", 0),
-                                        precision_flags(sp.get("precision", "fp32")),
+                                        precision_flags(sp.get("precision", "fp32"))
+                                        | (B.PISCO_FLAG_GRAM_DF if sp.get("gram_df") else 0),
                                         sp.get("eig_block", 0), sp.get("eig_iters", 0), sp.get("tc_splits", 0),
                                         sp.get("gemm_splits", 0), sp.get("gemm_tile", 0)))
         st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)

@@ -297,3 +297,27 @@ def test_single_pass_tf32_error_is_reported(name):
     assert e["k_ok"]
     assert e["G"] <= 2e-3
     assert np.isfinite(r["maps"]).all()
+
+
+# ---- the Gram's FFT route in double-float arithmetic (PISCO_FLAG_GRAM_DF) ----------------------
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_double_float_gram_matches_explicit_CtC_and_maps(name):
+    grid, Q, cs, tau, shape, red, iters, phase = CASES[name]
+    case, ref = _oracle(name, 0)
+    est = PiscoEstimator(grid, cs, Q, tau, kernel_shape=shape, reduction=red, iters=iters, gram_df=True)
+    maps, eig = est(torch.from_numpy(case.calib).cuda())
+    torch.cuda.synchronize()
+    C = ref["C"]
+    A_ref = C.conj().T @ C
+    n = A_ref.shape[0]
+    A = est.debug_buffer(B.PISCO_BUF_GRAM).cpu().numpy().reshape(n, n)
+    err = np.abs(A - A_ref).max() / np.abs(A_ref).max()
+    print(f"{name}: double-float Gram max error / max|A| = {err:.2e}")
+    assert err <= 1e-11, err
+    assert est.info()["k"] == ref["U_sig"].shape[1]
+    r = dict(case=case, ref=ref, grid=grid, red=red)
+    m = _gated_mask(r).reshape(-1)
+    a = maps.cpu().numpy().reshape(Q, -1).T
+    b = ref["maps"].reshape(Q, -1).T
+    assert np.linalg.norm((_align(a) - _align(b))[m]) / np.linalg.norm(b[m]) <= 1e-4
+    est.close()
