@@ -384,22 +384,43 @@ def run_gpu(args):
     binfo = batch.info()
 
     # ---- end to end: host buffers in and out, copies inside the timed region ----
+    # two batch objects in flight (step s's device->host copies overlap step s+1's estimates),
+    # each step's inputs copied from pinned host memory and its maps and eigenvalues copied back;
+    # host-clock timing around the whole loop (the work runs on the batches' private streams)
     pin_c = [torch.from_numpy(calibs_h[i % N_CASES]).pin_memory().numpy() for i in range(nb)]
-    hmaps = [torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64).pin_memory().numpy() for _ in range(nb)]
-    heig = [torch.empty(red, dtype=torch.float32).pin_memory().numpy() for _ in range(nb)]
-    for i in range(min(args.warmup, 3)):
-        batch.estimate_host(pin_c, hmaps, heig)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.steps):
-        batch.estimate_host(pin_c, hmaps, heig)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-    e2e_value = whole_job_rate(nb * args.steps, world, e2e_ms)
+    batch2 = PiscoBatch([dict(spec, **tuned)] * nb)
+    outs = []
+    for _ in range(2):
+        outs.append(([torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64).pin_memory().numpy() for _ in range(nb)],
+                     [torch.empty(red, dtype=torch.float32).pin_memory().numpy() for _ in range(nb)]))
+    pair = (batch, batch2)
+
+    def e2e_steps(k):
+        for s_ in range(k):
+            pair[s_ % 2].launch_host(pin_c, *outs[s_ % 2])
+            if s_ > 0:
+                pair[(s_ - 1) % 2].wait()
+        pair[(k - 1) % 2].wait()
+
+    def blocking_steps(k):
+        for _ in range(k):
+            batch.estimate_host(pin_c, *outs[0])
+
+    e2e_modes = {}
+    for mode, fn in (("two_in_flight", e2e_steps), ("blocking", blocking_steps)):
+        fn(max(args.warmup, 3) + 1)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        fn(args.steps)
+        torch.cuda.synchronize()
+        ms = max_over_ranks((time.perf_counter() - t0) * 1e3, dist, "cuda")
+        e2e_modes[mode] = whole_job_rate(nb * args.steps, world, ms)
+    e2e_mode = max(e2e_modes, key=e2e_modes.get)
+    e2e_value = e2e_modes[e2e_mode]
+    hmaps, heig = outs[0]
+    batch2.close()
     batch.close()
 
     peaks = _peaks()
@@ -449,7 +470,9 @@ def run_gpu(args):
         "gpu_launches": int(binfo["launches"]) * args.steps,
         "e2e": {"value": e2e_value, "unit": "maps/s",
                 "h2d_bytes_per_step": int(sum(c.nbytes for c in pin_c)),
-                "d2h_bytes_per_step": int(sum(m.nbytes for m in hmaps) + sum(e.nbytes for e in heig))},
+                "d2h_bytes_per_step": int(sum(m.nbytes for m in hmaps) + sum(e.nbytes for e in heig)),
+                "mode": e2e_mode, "modes": e2e_modes,
+                "timing": "host clock around all steps, device synchronised at both ends"},
         "roofline": roof,
         "clocks": clocks,
         "eig": {"k": stats["signal_dim"], "block": stats["eig_block"], "iters": stats["eig_iters"],
@@ -510,20 +533,36 @@ def run_gpu_uneven(args):
     npix_red = sum((sp["grid"][0] // 4) * (sp["grid"][1] // 4) for sp in specs)
     binfo = batch.info()
     statuses = list(batch.last_item_status)
-    # end to end through host buffers
+    # end to end through host buffers: two batch objects in flight (as in the 2D workload)
     pin_c = [torch.from_numpy(c).pin_memory().numpy() for c in calibs_h]
-    hmaps = [torch.empty(tuple(m.shape), dtype=torch.complex64).pin_memory().numpy() for m in maps]
-    heig = [torch.empty(tuple(e.shape), dtype=torch.float32).pin_memory().numpy() for e in eigs]
-    for _ in range(min(args.warmup, 3)):
-        batch.estimate_host(pin_c, hmaps, heig)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        batch.estimate_host(pin_c, hmaps, heig)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value = len(specs) * args.steps / (e0.elapsed_time(e1) / 1e3)
+    batch2 = PiscoBatch(specs)
+    outs = [([torch.empty(tuple(m.shape), dtype=torch.complex64).pin_memory().numpy() for m in maps],
+             [torch.empty(tuple(e.shape), dtype=torch.float32).pin_memory().numpy() for e in eigs]) for _ in range(2)]
+    pair = (batch, batch2)
+
+    def e2e_steps(k):
+        for s_ in range(k):
+            pair[s_ % 2].launch_host(pin_c, *outs[s_ % 2])
+            if s_ > 0:
+                pair[(s_ - 1) % 2].wait()
+        pair[(k - 1) % 2].wait()
+
+    def blocking_steps(k):
+        for _ in range(k):
+            batch.estimate_host(pin_c, *outs[0])
+
+    e2e_modes = {}
+    for mode, fn in (("two_in_flight", e2e_steps), ("blocking", blocking_steps)):
+        fn(max(args.warmup, 3) + 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn(args.steps)
+        torch.cuda.synchronize()
+        e2e_modes[mode] = len(specs) * args.steps / (time.perf_counter() - t0)
+    e2e_mode = max(e2e_modes, key=e2e_modes.get)
+    e2e_value = e2e_modes[e2e_mode]
+    hmaps, heig = outs[0]
+    batch2.close()
     batch.close()
     line = {
         "metric": UNEVEN_METRIC, "value": value, "unit": "slices/s", "n_gpus": 1, "steps": args.steps,
@@ -542,7 +581,8 @@ def run_gpu_uneven(args):
         "gpu_launches": int(binfo["launches"]) * args.steps,
         "e2e": {"value": e2e_value, "unit": "slices/s",
                 "h2d_bytes_per_step": int(sum(c.nbytes for c in pin_c)),
-                "d2h_bytes_per_step": int(sum(m.nbytes for m in hmaps) + sum(e.nbytes for e in heig))},
+                "d2h_bytes_per_step": int(sum(m.nbytes for m in hmaps) + sum(e.nbytes for e in heig)),
+                "mode": e2e_mode, "modes": e2e_modes},
         "clocks": clocks, "workspace_bytes_batch": binfo["workspace_bytes"],
     }
     print(json.dumps(line), flush=True)

@@ -74,11 +74,13 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
                                      smallest eigenvalues of G(x) are close: convergence set by
                                      the third eigenvalue (Sec. V-E's iteration on a block);
                                      twice the work of the plain iteration                    */
-#define PISCO_FLAG_GRAM_DF 0x40u  /* the FFT route of Sec. V-A in double-float arithmetic (each
+#define PISCO_FLAG_GRAM_DF 0x40u  /* the FFT route of Sec. V-A and the band products of the
+                                     FP64 Rayleigh quotients in double-float arithmetic (each
                                      value an unevaluated sum of two FP32 numbers, Dekker's
                                      error-free products and Knuth's two-sum; about 48
                                      significant bits) instead of FP64: GB300's FP64 rate is
-                                     about 1/58 of FP32.  The lag table and the Gram stay FP64. */
+                                     about 1/58 of FP32.  The lag table, the Gram and the
+                                     quotients are stored and compared in FP64.               */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 
@@ -212,6 +214,16 @@ pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, v
 pisco_status pisco_batch_estimate_host(pisco_batch_t b, const void* const* h_calib,
                                        void* const* h_maps, float* const* h_eig,
                                        pisco_status* item_status);
+/* The host-buffer call split in two, so that a caller can keep two batch objects in flight and
+ * overlap one step's host copies with the next step's computation: pisco_batch_launch_host
+ * enqueues the whole batch (host->device copies, estimates, device->host copies) on the batch's
+ * private stream and returns at once; pisco_batch_wait blocks until it has finished and fills
+ * item_status as pisco_batch_estimate_host does.  The host buffers must stay valid and
+ * untouched until the wait returns.  One launch per batch object may be in flight
+ * (PISCO_ERR_ARG for a second launch, or for a wait without a launch). */
+pisco_status pisco_batch_launch_host(pisco_batch_t b, const void* const* h_calib,
+                                     void* const* h_maps, float* const* h_eig);
+pisco_status pisco_batch_wait(pisco_batch_t b, pisco_status* item_status);
 pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t* workspace_bytes);
 pisco_status pisco_batch_item(pisco_batch_t b, int i, pisco_plan_t* plan);
 void pisco_batch_destroy(pisco_batch_t b);

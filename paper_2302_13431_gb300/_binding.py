@@ -112,6 +112,10 @@ def load():
     lib.pisco_batch_estimate.restype = ctypes.c_int
     lib.pisco_batch_estimate_host.argtypes = [vp, PP, PP, PP, P(ctypes.c_int)]
     lib.pisco_batch_estimate_host.restype = ctypes.c_int
+    lib.pisco_batch_launch_host.argtypes = [vp, PP, PP, PP]
+    lib.pisco_batch_launch_host.restype = ctypes.c_int
+    lib.pisco_batch_wait.argtypes = [vp, P(ctypes.c_int)]
+    lib.pisco_batch_wait.restype = ctypes.c_int
     lib.pisco_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
     lib.pisco_batch_info.restype = ctypes.c_int
     lib.pisco_batch_item.argtypes = [vp, ctypes.c_int, P(vp)]
@@ -270,6 +274,18 @@ def pisco_batch_estimate(batch, calibs, maps, eigs, host=False):
     stat = (ctypes.c_int * n)()
     fn = load().pisco_batch_estimate_host if host else load().pisco_batch_estimate
     st = fn(batch, _ptr_array(calibs), _ptr_array(maps), _ptr_array(eigs) if eigs is not None else None, stat)
+    return st, list(stat)
+
+
+def pisco_batch_launch_host(batch, calibs, maps, eigs):
+    """Enqueue a host-buffer batch call; the pointer arrays are kept alive by the caller."""
+    return load().pisco_batch_launch_host(batch, _ptr_array(calibs), _ptr_array(maps),
+                                          _ptr_array(eigs) if eigs is not None else None)
+
+
+def pisco_batch_wait(batch, n):
+    stat = (ctypes.c_int * n)()
+    st = load().pisco_batch_wait(batch, stat)
     return st, list(stat)
 
 

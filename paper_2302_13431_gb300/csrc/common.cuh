@@ -150,6 +150,8 @@ cudaError_t apply_axis_c2df(const float2* in, const void* M, void* out, AxisView
 cudaError_t apply_axis_df(const void* in, const void* M, void* out, AxisView v, cudaStream_t st);
 cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st);
 cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, cudaStream_t st);
+cudaError_t eig_band_matvec_df(const double2* A, const double2* Xb, int n, int nb, const int* band_idx, double2* Zb,
+                               cudaStream_t st);
 
 // exact Gram of the masked calibration matrix (kernels_gram.cu): A (FP64 n x n), scale, A32
 cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo, const int* hi, const int* lam,

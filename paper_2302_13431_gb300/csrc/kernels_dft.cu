@@ -6,6 +6,8 @@
 // the matrix row is a warp-wide broadcast.  Along the contiguous axis (inner == 1) consecutive
 // threads are consecutive outputs instead; those passes read a transposed matrix (AxisView::mt)
 // so that a warp's matrix loads stay contiguous while the input element is the broadcast.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pisco {
@@ -37,10 +39,50 @@ __global__ void __launch_bounds__(256) apply_axis_kernel(const Tin* __restrict__
   }
 }
 
+// FP32 contiguous-axis pass (inner == 1, transposed matrix) with a register tile of R rows:
+// each matrix element, loaded once (coalesced across the warp's outputs), serves R rows whose
+// input elements are warp-wide broadcasts.
+template <int R>
+__global__ void __launch_bounds__(256) apply_axis_rows_kernel(const float2* __restrict__ in,
+                                                              const float2* __restrict__ MT,
+                                                              float2* __restrict__ out, long long rows,
+                                                              int n_in, int n_out) {
+  const long long groups = (rows + R - 1) / R;
+  const long long total = groups * n_out;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(idx % n_out);
+    const long long r0 = (idx / n_out) * R;
+    float2 acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int i = 0; i < n_in; ++i) {
+      const float2 m = MT[(long long)i * n_out + o];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r0 + r < rows) cfma(acc[r], m, in[(r0 + r) * n_in + i]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r0 + r < rows) out[(r0 + r) * n_out + o] = acc[r];
+  }
+}
+
 template <typename Tin, typename C>
 static cudaError_t launch_apply(const Tin* in, const C* M, C* out, AxisView v, cudaStream_t st) {
   const long long total = v.batch * v.outer * (long long)v.n_out * v.inner;
   if (total <= 0) return cudaSuccess;
+  if constexpr (std::is_same<Tin, float2>::value && std::is_same<C, float2>::value) {
+    if (v.inner == 1 && v.mt && !v.pixel_major) {
+      constexpr int R = 4;
+      const long long rows = v.batch * v.outer;
+      long long blocks = (((rows + R - 1) / R) * v.n_out + 255) / 256;
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      apply_axis_rows_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(in, M, out, rows, v.n_in, v.n_out);
+      ++g_launches;
+      return cudaGetLastError();
+    }
+  }
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   apply_axis_kernel<Tin, C><<<(unsigned)blocks, 256, 0, st>>>(in, M, out, v);

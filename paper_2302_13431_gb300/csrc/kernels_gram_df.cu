@@ -141,3 +141,98 @@ cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags
 }
 
 }  // namespace pisco
+
+namespace pisco {
+namespace {
+
+// (ah, al) += a * x with a = (a_hi + a_lo) double-float and x exact in FP32
+__device__ __forceinline__ void df_fma1(float& ah, float& al, float a_hi, float a_lo, float x) {
+  const float p = a_hi * x;
+  float pe = fmaf(a_hi, x, -p);
+  pe = fmaf(a_lo, x, pe);
+  float s, e;
+  two_sum(ah, p, s, e);
+  e += al + pe;
+  quick_two_sum(s, e, ah, al);
+}
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  quick_two_sum(s, e, ah, al);
+}
+
+// Zb = A * Xb (the band products of the FP64 Rayleigh quotients) in double-float: A's FP64
+// entries split into two floats, the band vectors exact in FP32 (they come from the FP32 Ritz
+// block); one warp per row of A, only the band columns in use.  Zb written in FP64.
+template <int NBV>
+__global__ void __launch_bounds__(256) band_matvec_df_kernel(const double2* __restrict__ A,
+                                                             const double2* __restrict__ Xb, int n,
+                                                             const int* __restrict__ band_idx,
+                                                             double2* __restrict__ Zb) {
+  constexpr int KC = 512;
+  __shared__ float2 xs[KC * NBV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * 8 + warp;
+  int nbu = 0;
+#pragma unroll
+  for (int c = 0; c < NBV; ++c)
+    if (band_idx[c] >= 0) nbu = c + 1;
+  float arh[NBV], arl[NBV], aih[NBV], ail[NBV];
+#pragma unroll
+  for (int c = 0; c < NBV; ++c) arh[c] = arl[c] = aih[c] = ail[c] = 0.f;
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    const int kc = min(KC, n - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kc * NBV; e += blockDim.x) {
+      const double2 v = Xb[(long long)k0 * NBV + e];
+      xs[e] = make_float2((float)v.x, (float)v.y);  // exact: the band vectors are FP32 values
+    }
+    __syncthreads();
+    if (r < n) {
+      const double2* arow = A + (long long)r * n + k0;
+      for (int k = lane; k < kc; k += 32) {
+        const double2 a = arow[k];
+        const float ahx = (float)a.x, ahy = (float)a.y;
+        const float alx = (float)(a.x - (double)ahx), aly = (float)(a.y - (double)ahy);
+#pragma unroll
+        for (int c = 0; c < NBV; ++c) {
+          if (c < nbu) {
+            const float2 x = xs[k * NBV + c];
+            df_fma1(arh[c], arl[c], ahx, alx, x.x);     // Re += Re a Re x
+            df_fma1(arh[c], arl[c], -ahy, -aly, x.y);   //      - Im a Im x
+            df_fma1(aih[c], ail[c], ahx, alx, x.y);     // Im += Re a Im x
+            df_fma1(aih[c], ail[c], ahy, aly, x.x);     //      + Im a Re x
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NBV; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, arh[c], o), bl = __shfl_xor_sync(0xffffffffu, arl[c], o);
+      const float ch = __shfl_xor_sync(0xffffffffu, aih[c], o), cl = __shfl_xor_sync(0xffffffffu, ail[c], o);
+      df_add(arh[c], arl[c], bh, bl);
+      df_add(aih[c], ail[c], ch, cl);
+    }
+  }
+  if (r < n && lane == 0) {
+#pragma unroll
+    for (int c = 0; c < NBV; ++c)
+      Zb[(long long)r * NBV + c] = make_double2((double)arh[c] + (double)arl[c], (double)aih[c] + (double)ail[c]);
+  }
+}
+
+}  // namespace
+
+cudaError_t eig_band_matvec_df(const double2* A, const double2* Xb, int n, int nb, const int* band_idx, double2* Zb,
+                               cudaStream_t st) {
+  if (nb != 8) return cudaErrorInvalidValue;
+  band_matvec_df_kernel<8><<<(n + 7) / 8, 256, 0, st>>>(A, Xb, n, band_idx, Zb);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pisco

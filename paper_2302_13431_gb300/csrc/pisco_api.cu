@@ -592,7 +592,10 @@ pisco_status run_eig(pisco_plan_s* pl) {
   OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st));
   OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
   const double2 zone = make_double2(1.0, 0.0), zzero = make_double2(0.0, 0.0);
-  OP("eig_rayleigh_fp64", eig_band_matvec(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
+  if (pl->gram_df)
+    OP("eig_rayleigh_df", eig_band_matvec_df(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
+  else
+    OP("eig_rayleigh_fp64", eig_band_matvec(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
   (void)zone; (void)zzero;
   OP("eig_decide_fp64", eig_decide(pl->mu, m, pl->band, kNbMax, pl->Xb, pl->Zb, n, thr2, pl->Q, pl->gscale,
                 pl->w, pl->ritz, pl->dstatus, st));
@@ -1164,6 +1167,11 @@ struct pisco_batch_s {
   bool g_host = false;
   int launches = 0;
   bool warmed = false;  // one eager run first: kernel attributes are set outside any capture
+  // the launched, not yet waited-for call (pointers kept for status decoding and re-runs)
+  bool pending = false, pend_host = false;
+  std::vector<const void*> pend_in;
+  std::vector<void*> pend_out;
+  std::vector<float*> pend_eig;
 };
 
 static void batch_graph_reset(pisco_batch_s* b) {
@@ -1236,13 +1244,16 @@ pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_
 
 // capture (if the pointer set changed) and launch the whole batch; host_io: in/out are host
 // pointers (copied through each item's staging buffers inside the graph)
-static pisco_status batch_run(pisco_batch_s* b, const void* const* in, void* const* outp,
-                              float* const* eig, bool host_io, pisco_status* item_status) {
+// Enqueue the whole batch (capture on the second call with a new pointer set, replay after);
+// order_user: order the batch after the caller's stream and the caller's stream after it
+// (device buffers); host-buffer launches skip that so two batches can be in flight at once.
+static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* const* outp,
+                                 float* const* eig, bool host_io, bool order_user) {
   const int n = (int)b->items.size();
   for (int i = 0; i < n; ++i)
     if (!in[i] || !outp[i]) return PISCO_ERR_ARG;
-  if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess ||
-      cudaStreamWaitEvent(b->main, b->ev_in, 0) != cudaSuccess)
+  if (order_user && (cudaEventRecord(b->ev_in, b->user) != cudaSuccess ||
+                     cudaStreamWaitEvent(b->main, b->ev_in, 0) != cudaSuccess))
     return PISCO_ERR_CUDA;
   bool same = b->gexec && b->g_host == host_io && (int)b->g_in.size() == n;
   for (int i = 0; same && i < n; ++i)
@@ -1321,9 +1332,29 @@ static pisco_status batch_run(pisco_batch_s* b, const void* const* in, void* con
     }
   }
   if (b->gexec && cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
-  if (cudaEventRecord(b->ev_out, b->main) != cudaSuccess ||
-      cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
+  if (order_user && (cudaEventRecord(b->ev_out, b->main) != cudaSuccess ||
+                     cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess))
     return PISCO_ERR_CUDA;
+  b->pend_in.assign(in, in + n);
+  b->pend_out.assign(outp, outp + n);
+  b->pend_eig.assign(n, nullptr);
+  if (eig)
+    for (int i = 0; i < n; ++i) b->pend_eig[i] = eig[i];
+  b->pend_host = host_io;
+  b->pending = true;
+  return PISCO_OK;
+}
+
+// Wait for the launched batch, then decode every item's status (saturated items are re-run
+// alone with a larger block).
+static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
+  if (!b->pending) return PISCO_ERR_ARG;
+  b->pending = false;
+  const int n = (int)b->items.size();
+  const bool host_io = b->pend_host;
+  const void* const* in = b->pend_in.data();
+  void* const* outp = b->pend_out.data();
+  float* const* eig = b->pend_eig.data();
   if (cudaStreamSynchronize(b->main) != cudaSuccess) return PISCO_ERR_CUDA;
   pisco_status worst = PISCO_OK;
   for (int i = 0; i < n; ++i) {
@@ -1339,8 +1370,7 @@ static pisco_status batch_run(pisco_batch_s* b, const void* const* in, void* con
       if (pl->m < pl->m_max) {
         pl->m = std::min(pl->m * 2, pl->m_max);
         batch_graph_reset(b);
-        si = host_io ? pisco_estimate_host(pl, in[i], outp[i], eig ? eig[i] : nullptr)
-                     : pisco_estimate(pl, in[i], outp[i], eig ? eig[i] : nullptr);
+        si = host_io ? pisco_estimate_host(pl, in[i], outp[i], eig[i]) : pisco_estimate(pl, in[i], outp[i], eig[i]);
       } else {
         si = PISCO_ERR_NOT_CONVERGED;
       }
@@ -1435,14 +1465,29 @@ pisco_status pisco_support_mask(const float* d_eig, long long n, float threshold
 
 pisco_status pisco_batch_estimate(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,
                                   float* const* d_eig, pisco_status* item_status) {
-  if (!b || !d_calib || !d_maps) return PISCO_ERR_ARG;
-  return batch_run(b, d_calib, d_maps, d_eig, false, item_status);
+  if (!b || !d_calib || !d_maps || b->pending) return PISCO_ERR_ARG;
+  const pisco_status s = batch_launch(b, d_calib, d_maps, d_eig, false, true);
+  if (s != PISCO_OK) return s;
+  return batch_finish(b, item_status);
 }
 
 pisco_status pisco_batch_estimate_host(pisco_batch_t b, const void* const* h_calib, void* const* h_maps,
                                        float* const* h_eig, pisco_status* item_status) {
-  if (!b || !h_calib || !h_maps) return PISCO_ERR_ARG;
-  return batch_run(b, h_calib, h_maps, h_eig, true, item_status);
+  if (!b || !h_calib || !h_maps || b->pending) return PISCO_ERR_ARG;
+  const pisco_status s = batch_launch(b, h_calib, h_maps, h_eig, true, true);
+  if (s != PISCO_OK) return s;
+  return batch_finish(b, item_status);
+}
+
+pisco_status pisco_batch_launch_host(pisco_batch_t b, const void* const* h_calib, void* const* h_maps,
+                                     float* const* h_eig) {
+  if (!b || !h_calib || !h_maps || b->pending) return PISCO_ERR_ARG;
+  return batch_launch(b, h_calib, h_maps, h_eig, true, false);
+}
+
+pisco_status pisco_batch_wait(pisco_batch_t b, pisco_status* item_status) {
+  if (!b) return PISCO_ERR_ARG;
+  return batch_finish(b, item_status);
 }
 
 pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t* workspace_bytes) {

@@ -220,6 +220,21 @@ class PiscoBatch:
             raise B.PiscoError(st, "pisco_batch_estimate_host")
         return st
 
+    def launch_host(self, calibs, maps, eigs=None):
+        """Enqueue a host-buffer call and return at once (pinned numpy buffers that stay untouched
+        until wait()); two batch objects can then overlap one step's copies with the next step."""
+        st = B.pisco_batch_launch_host(self._b, [c.ctypes.data for c in calibs], [m.ctypes.data for m in maps],
+                                       [e.ctypes.data for e in eigs] if eigs is not None else None)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_batch_launch_host")
+
+    def wait(self):
+        st, items = B.pisco_batch_wait(self._b, len(self.specs))
+        self.last_item_status = items
+        if st not in (B.PISCO_OK, B.PISCO_ERR_RANK):
+            raise B.PiscoError(st, "pisco_batch_wait")
+        return st
+
     def alloc_outputs(self, device="cuda"):
         maps, eigs = [], []
         for sp in self.specs:

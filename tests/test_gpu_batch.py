@@ -68,3 +68,30 @@ def test_batch_rejects_invalid_items():
     bad["calib_shape"] = (4, 4)
     with pytest.raises(B.PiscoError):
         PiscoBatch([SPECS[0], bad])
+
+
+def test_launch_and_wait_equal_the_blocking_host_call():
+    calibs_h = _inputs()
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+    cal = [pin(c) for c in calibs_h]
+    a, b = PiscoBatch(SPECS), PiscoBatch(SPECS)
+    ma = [pin(np.empty((s["num_coils"],) + tuple(s["grid"]), np.complex64)) for s in SPECS]
+    mb = [pin(np.empty((s["num_coils"],) + tuple(s["grid"]), np.complex64)) for s in SPECS]
+    ref = [np.empty((s["num_coils"],) + tuple(s["grid"]), np.complex64) for s in SPECS]
+    a.estimate_host(calibs_h, ref)
+    for step in range(4):  # ping-pong: two calls in flight
+        (a if step % 2 == 0 else b).launch_host(cal, ma if step % 2 == 0 else mb)
+        if step > 0:
+            (b if step % 2 == 0 else a).wait()
+    (b if 4 % 2 == 0 else a).wait()
+    for i in range(len(SPECS)):
+        np.testing.assert_array_equal(ma[i], ref[i])
+        np.testing.assert_array_equal(mb[i], ref[i])
+    a.launch_host(cal, ma)
+    with pytest.raises(B.PiscoError):
+        a.launch_host(cal, ma)  # one call in flight per batch object
+    a.wait()
+    with pytest.raises(B.PiscoError):
+        a.wait()                # nothing launched
+    a.close()
+    b.close()
