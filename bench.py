@@ -271,6 +271,21 @@ def roofline_for(op, prof, w, stats, peaks, precision):
         byts = 8.0 * Q * npix + 8.0 * Q * (w["grid"][1]) * (w["grid"][0] // w["reduction"])
         return dict(bound="hbm", achieved=byts / avg_s / 1e9, peak=peaks.get("hbm_gbs", 6800.0), unit="GB/s",
                     note="maps write + interpolated-row read")
+    if op == "eig_gemm_thin_fp32":
+        work = 8.0 * n * m * m                       # every thin block product is n x m x m
+        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                    note="CUDA-core complex block products (Y^H Y, Y R^-1, X^H Z, X V): 8 n m^2 flops each; "
+                         "latency-bound at one map")
+    if op in ("gram_dft_df", "gram_dft_fp64"):
+        Lp = w["calib"][0] + 2 * w["tau"]
+        nc, B = w["calib"][0], 4 * w["tau"] + 1
+        npair = Q * (Q + 1) // 2
+        cmacs = Q * nc * Lp * nc + Q * Lp * Lp * nc + npair * Lp * B * Lp + npair * B * B * Lp
+        passes = 4
+        return dict(bound="alu", achieved=8.0 * cmacs / passes / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
+                    unit="TFLOP/s (FP64-equivalent)",
+                    note="Gram DFT passes: FP64-equivalent flops per pass against the nominal FP64 peak"
+                         + ("; computed in double-float FP32 pairs" if op == "gram_dft_df" else ""))
     if op == "eig_jacobi":
         work = 8.0 * 2 * m * m * m * max(1, stats["jacobi_sweeps"])
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS / SMS, unit="TFLOP/s",

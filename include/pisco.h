@@ -99,7 +99,7 @@ typedef struct {
                              SplitMix64(seed*2^40 + j*2^8 + t), a 24-bit uniform in [-1,1)   */
   unsigned flags;         /* PISCO_FLAG_*                                                     */
   int eig_block;          /* block size of the nullspace eigensolver (0: automatic)           */
-  int eig_iters;          /* subspace iterations of the eigensolver (0: automatic)            */
+  int eig_iters;          /* subspace iterations of the eigensolver (0: automatic = 6)        */
   int tc_splits;          /* K splits of the tensor-core GEMMs (PISCO_FLAG_TC_*; 0: automatic) */
   int gemm_splits;        /* split-K cap of the CUDA-core block products (0: automatic, about
                              two CTAs per SM; small values suit batches of concurrent plans)  */
