@@ -81,6 +81,9 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
                                      significant bits) instead of FP64: GB300's FP64 rate is
                                      about 1/58 of FP32.  The lag table, the Gram and the
                                      quotients are stored and compared in FP64.               */
+#define PISCO_FLAG_TC_THIN 0x80u  /* with PISCO_FLAG_TC_EIG: also the thin block products of the
+                                     eigensolver (block Grams Y^H Y, Y R^-1, the Rayleigh-Ritz
+                                     products) on the tensor cores, same split precision      */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 

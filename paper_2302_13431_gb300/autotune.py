@@ -6,8 +6,8 @@ the fastest.  The knobs are ones whose best value depends on the shapes and on h
 share the GPU:
 
 * precision route: CUDA-core FP32 products, or split-TF32 tensor-core products for the G(x)
-  assembly only or also for the eigensolver's block products (all three meet the FP32 parity
-  gates; the one-pass TF32 routes do not and are never candidates);
+  assembly only, also for the eigensolver's A X products, or for every block product (all meet
+  the FP32 parity gates; the one-pass TF32 routes do not and are never candidates);
 * `tc_splits`: K splits of the tensor-core block products (more splits shorten one product,
   fewer cost less SM time and reduction traffic);
 * `gemm_splits`: split-K cap of the CUDA-core block products (same trade-off);
@@ -41,6 +41,7 @@ def candidates():
         for ts in (1, 4):
             for gs, gt in ((0, 0), (2, 64)):
                 out.append(dict(precision="tc_g_eig", tc_splits=ts, gemm_splits=gs, gemm_tile=gt, gram_df=df))
+            out.append(dict(precision="tc_all", tc_splits=ts, gemm_splits=0, gemm_tile=0, gram_df=df))
     return out
 
 

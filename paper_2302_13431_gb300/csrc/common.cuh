@@ -192,6 +192,7 @@ cudaError_t tc2_prepare();
 cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
                         cudaStream_t st);
 cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st);
+cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st);
 cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st);

@@ -286,6 +286,22 @@ __global__ void split_a_kernel(const float2* __restrict__ A, int lda, const floa
   }
 }
 
+// A' head/tail for A = conj(Y^T), Y K x M row-major (ldy): A'[i][2k] = Re Y[k][i],
+// A'[i][2k+1] = -Im Y[k][i]
+__global__ void split_at_kernel(const float2* __restrict__ Y, int ldy, int M, int K, float* __restrict__ hi,
+                                float* __restrict__ lo, int K2p) {
+  const long long total = (long long)M * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / M), i = (int)(e % M);
+    const float2 y = Y[(long long)k * ldy + i];
+    const float vx = y.x, vy = -y.y;
+    const float hx = head(vx), hy = head(vy);
+    const long long o = (long long)i * K2p + 2 * k;
+    *reinterpret_cast<float2*>(hi + o) = make_float2(hx, hy);
+    if (lo) *reinterpret_cast<float2*>(lo + o) = make_float2(head(vx - hx), head(vy - hy));
+  }
+}
+
 // B' head/tail rows (see the file comment); columns c >= N of the last tile are zero
 __global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, int K, int N, int Np,
                                float* __restrict__ hi, float* __restrict__ lo, int K2p) {
@@ -369,6 +385,12 @@ cudaError_t tc2_prepare() {
 cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
                         cudaStream_t st) {
   split_a_kernel<<<grid_for((long long)M * K), 256, 0, st>>>(A, lda, kscale, M, K, hi, lo, tc2_k2p(K));
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st) {
+  split_at_kernel<<<grid_for((long long)M * K), 256, 0, st>>>(Y, ldy, M, K, hi, lo, tc2_k2p(K));
   ++g_launches;
   return cudaGetLastError();
 }

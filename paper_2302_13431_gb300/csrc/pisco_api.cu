@@ -18,7 +18,8 @@ using namespace pisco;
 
 namespace {
 
-constexpr int kNbMax = 8;    // Ritz vectors refined in FP64 per decision
+constexpr int kNbMax = 8;       // Ritz vectors refined in FP64 per decision
+constexpr int kThinSplits = 8;  // K splits of the tensor-core m x m x n block Grams
 constexpr int kMmax = 128;   // largest eigensolver block
 
 struct DevBuf {
@@ -72,6 +73,8 @@ struct pisco_plan_s {
   int tc_splits_ax = 4, tc_splits_g = 1;
   int gemm_splits = 0;  // split-K cap of the CUDA-core block products (0: automatic)
   int gemm_tile = 0;    // CUDA-core block product tile: 0 automatic, 32 or 64
+  bool tc_thin = false; // thin block products (n x m x m, m x m x n) on the tensor cores too
+  float *TAh = nullptr, *TAl = nullptr, *TBh = nullptr, *TBl = nullptr;  // their split operands
   float *Ah = nullptr, *Al = nullptr, *Xh = nullptr, *Xl = nullptr;        // A32 and the block
   float *Eh = nullptr, *El = nullptr, *KTh = nullptr, *KTl = nullptr;      // E and the lag table
   float *UAh = nullptr, *UAl = nullptr, *UBh = nullptr, *UBl = nullptr;    // U diag(w), conj(U)^T
@@ -506,6 +509,25 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   return PISCO_OK;
 }
 
+// Thin block products on the tensor cores (PISCO_FLAG_TC_THIN): C = Y^H Z (m x m over n rows,
+// conj_a) or C = Y W (n x m by m x m), operands split into the plan's thin buffers
+cudaError_t thin_product(pisco_plan_s* pl, bool conj_a, const float2* Y, const float2* Z, float2* C) {
+  const int n = pl->n, m = pl->m;
+  const bool tt = pl->tc_terms == 3;
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  cudaError_t e;
+  if (conj_a) {
+    if ((e = tc2_split_at(Y, m, m, n, pl->TAh, tt ? pl->TAl : nullptr, pl->st)) != cudaSuccess) return e;
+    if ((e = tc2_split_b(Z, m, 0, n, m, pl->TBh, tt ? pl->TBl : nullptr, pl->st)) != cudaSuccess) return e;
+    return tc2_gemm(pl->tc_terms, m, m, n, pl->TAh, pl->TAl, pl->TBh, pl->TBl, one, zero, C, m, 0.f, 0, 0,
+                    kThinSplits, pl->tc_ws, &pl->dstatus->flags, pl->st);
+  }
+  if ((e = tc2_split_a(Y, m, nullptr, n, m, pl->TAh, tt ? pl->TAl : nullptr, pl->st)) != cudaSuccess) return e;
+  if ((e = tc2_split_b(Z, m, 0, m, m, pl->TBh, tt ? pl->TBl : nullptr, pl->st)) != cudaSuccess) return e;
+  return tc2_gemm(pl->tc_terms, n, m, m, pl->TAh, pl->TAl, pl->TBh, pl->TBl, one, zero, C, m, 0.f, 0, 0, 1, nullptr,
+                  &pl->dstatus->flags, pl->st);
+}
+
 // One Cholesky-QR pass: Xout = (Yin D^-1) L^-H with orthonormal columns.  dscale: optional
 // column scaling D (previous diag(R)); shift_rel: optional shift; acc_in: diag(R) of earlier
 // passes of the same factorisation; diag(R) of the whole factorisation goes to diag_out.
@@ -514,13 +536,19 @@ pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, co
   cudaStream_t st = pl->st;
   const int n = pl->n;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  if (pl->tc_thin)
+    OP("eig_gemm_thin_tc", thin_product(pl, true, Yin, Yin, pl->Gm));
+  else
+    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   if (m <= 96) {
     if (pl->chol_variant == 1)
       OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
     else
       OP("eig_chol", eig_chol_inv_warp(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
-    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, Yin, m, pl->Rinv, m, zero, Xout, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+    if (pl->tc_thin)
+      OP("eig_gemm_thin_tc", thin_product(pl, false, Yin, pl->Rinv, Xout));
+    else
+      OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, Yin, m, pl->Rinv, m, zero, Xout, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   } else {
     OP("eig_chol", eig_chol(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, pl->dsc, diag_out, pl->dstatus, st));
     OP("eig_trsm", eig_trsm(Yin, pl->Rinv, pl->dsc, n, m, Xout, st));
@@ -585,9 +613,15 @@ pisco_status run_eig(pisco_plan_s* pl) {
   }
   // Rayleigh-Ritz on the block
   OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
-  OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  if (pl->tc_thin)
+    OP("eig_gemm_thin_tc", thin_product(pl, true, pl->X, pl->Z, pl->Bm));
+  else
+    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
-  OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  if (pl->tc_thin)
+    OP("eig_gemm_thin_tc", thin_product(pl, false, pl->X, pl->Vj, pl->U));
+  else
+    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   // FP64 Rayleigh quotients of the Ritz vectors that decide the split
   OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st));
   OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
@@ -788,6 +822,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->eig_iters = p->eig_iters > 0 ? p->eig_iters : 6;
   pl->gemm_splits = p->gemm_splits > 0 ? std::min(p->gemm_splits, 64) : 0;
   pl->gemm_tile = (p->gemm_tile == 32 || p->gemm_tile == 64) ? p->gemm_tile : 0;
+  pl->tc_thin = (p->flags & PISCO_FLAG_TC_THIN) != 0 && (p->flags & PISCO_FLAG_TC_EIG) != 0;
   pl->masked = (p->flags & PISCO_FLAG_MASKED_GRAM) != 0;
   pl->block_pi = (p->flags & PISCO_FLAG_BLOCK_PI) != 0;
   pl->gram_df = (p->flags & PISCO_FLAG_GRAM_DF) != 0;
@@ -887,7 +922,14 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     const size_t lo_n = pl->tc_terms == 3 ? 1 : 0;
     pl->tc_ws_elems = std::max<size_t>((size_t)pl->tc_splits_ax * n * pl->m_max,
                                        pl->tc_splits_g > 1 ? (size_t)(pl->tc_splits_g * pl->npix_red * QQ) : 0);
+    if (pl->tc_thin) pl->tc_ws_elems = std::max<size_t>(pl->tc_ws_elems, (size_t)kThinSplits * pl->m_max * pl->m_max);
     ok = dalloc(pl, &pl->tc_ws, pl->tc_ws_elems);
+    if (ok && pl->tc_thin) {
+      const size_t ta = std::max((size_t)n * k2m, (size_t)pl->m_max * k2n);
+      const size_t tb = (size_t)2 * tc2_np(pl->m_max) * std::max(k2n, k2m);
+      ok = dalloc(pl, &pl->TAh, ta) && dalloc(pl, &pl->TAl, lo_n * ta + 1) && dalloc(pl, &pl->TBh, tb) &&
+           dalloc(pl, &pl->TBl, lo_n * tb + 1);
+    }
     if (ok && pl->tc_eig)
       ok = dalloc(pl, &pl->Ah, (size_t)n * k2n) && dalloc(pl, &pl->Al, lo_n * n * k2n + 1) &&
            dalloc(pl, &pl->Xh, (size_t)2 * tc2_np(pl->m_max) * k2n) &&

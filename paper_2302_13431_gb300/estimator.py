@@ -26,6 +26,8 @@ PRECISIONS = {
     "tc_g": (B.PISCO_FLAG_TC_GFIELD, "G(x) assembly on tensor cores, 3-pass split TF32"),
     "tc_g_eig": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_EIG,
                  "G(x) assembly and eigensolver block products on tensor cores, 3-pass split TF32"),
+    "tc_all": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_EIG | B.PISCO_FLAG_TC_THIN,
+               "G(x) assembly and every eigensolver block product on tensor cores, 3-pass split TF32"),
     "tc_g_1pass": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_1PASS, "G(x) assembly, single TF32 pass"),
     "tc_g_eig_1pass": (B.PISCO_FLAG_TC_GFIELD | B.PISCO_FLAG_TC_EIG | B.PISCO_FLAG_TC_1PASS,
                        "G(x) and eigensolver products, single TF32 pass"),

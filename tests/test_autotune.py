@@ -13,7 +13,7 @@ def test_candidates_exclude_single_pass_routes():
     assert len(cs) == len({tuple(sorted(c.items())) for c in cs})
     assert all(set(c) == set(KNOB_KEYS) for c in cs)
     assert all("1pass" not in c["precision"] for c in cs)
-    assert {c["precision"] for c in cs} == {"fp32", "tc_g", "tc_g_eig"}
+    assert {c["precision"] for c in cs} == {"fp32", "tc_g", "tc_g_eig", "tc_all"}
 
 
 @pytest.mark.gpu

@@ -272,7 +272,7 @@ def _errors(r):
                 eig=e_err, maps=map_err)
 
 
-@pytest.mark.parametrize("precision", ["tc_g", "tc_g_eig"])
+@pytest.mark.parametrize("precision", ["tc_g", "tc_g_eig", "tc_all"])
 @pytest.mark.parametrize("name", TC_CASES)
 def test_split_tf32_routes_meet_fp32_tolerances(name, precision):
     r = _run(name, precision=precision)
