@@ -229,7 +229,7 @@ def n_lags(w):
     return len({(a[0] - b[0], a[1] - b[1]) for a in pts for b in pts})
 
 
-def roofline_for(op, prof, w, stats, peaks, precision):
+def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False):
     """Algorithmic work per launch of one operation and its roofline."""
     Q, L = w["Q"], stats["filter_len"]
     n = Q * L
@@ -267,10 +267,20 @@ def roofline_for(op, prof, w, stats, peaks, precision):
         work = 8.0 * nr * (w["iters"] + 1) * Q * Q
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="per pixel (iters+1) Q x Q complex matvecs")
+    if op == "interp_final_norm" and not tc_interp:
+        work = 8.0 * Q * npix * (w["grid"][0] // w["reduction"])
+        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                    note="last interpolation axis fused with the per-pixel normalisation: per output pixel "
+                         "and coil one complex dot product of length N_r (64 flop per map byte written)")
     if op == "interp_final_norm":
-        byts = 8.0 * Q * npix + 8.0 * Q * (w["grid"][1]) * (w["grid"][0] // w["reduction"])
+        byts = 16.0 * Q * npix
         return dict(bound="hbm", achieved=byts / avg_s / 1e9, peak=peaks.get("hbm_gbs", 6800.0), unit="GB/s",
-                    note="maps write + interpolated-row read")
+                    note="per-pixel normalisation after the tensor-core interpolation: maps read + write")
+    if op == "interp_final_tc":
+        work = 8.0 * Q * npix * (w["grid"][0] // w["reduction"])
+        return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                    note="maps_q = M T_q, one batched complex GEMM (N x N_r) by (N_r x N) per coil, "
+                         "B-operand split included; " + tc_note)
     if op == "eig_gemm_thin_fp32":
         work = 8.0 * n * m * m                       # every thin block product is n x m x m
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
@@ -336,7 +346,7 @@ def run_gpu(args):
     nb = args.batch
     bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
     tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
-                          "gram_df": False}, [])
+                          "gram_df": False, "tc_interp": False}, [])
     if args.tune:
         from paper_2302_13431_gb300.autotune import tune
         tuned, tune_table = tune([spec] * nb, calibs=bcal)
@@ -360,7 +370,8 @@ def run_gpu(args):
     est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
                          thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0,
                          precision=tuned["precision"], tc_splits=tuned["tc_splits"],
-                         gemm_splits=tuned["gemm_splits"], gemm_tile=tuned["gemm_tile"], gram_df=tuned["gram_df"])
+                         gemm_splits=tuned["gemm_splits"], gemm_tile=tuned["gemm_tile"], gram_df=tuned["gram_df"],
+                         tc_interp=tuned.get("tc_interp", False))
     est.estimate_into(calibs[0], maps1, eig1)
     stats = est.stats()
     est.set_profiling(True)
@@ -441,7 +452,7 @@ def run_gpu(args):
     peaks = _peaks()
     stages = {}
     for op in prof:
-        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"])
+        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"], tuned.get("tc_interp", False))
         if r.get("achieved") is not None and r.get("peak"):
             r["frac"] = r["achieved"] / r["peak"]
         r["ms_per_map"] = prof[op][0] / nprof
@@ -479,7 +490,8 @@ def run_gpu(args):
         "precision_mode": tuned["precision"],
         "launch_config": dict(tuned, autotuned=bool(args.tune),
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
-                                                      f"{'/df' if r.get('gram_df') else ''}":
+                                                      f"{'/df' if r.get('gram_df') else ''}"
+                                                      f"{'/ti' if r.get('tc_interp') else ''}":
                                                       round(r["ms"], 3) for r in tune_table}),
         "wall_s": t_wall,
         "gpu_launches": int(binfo["launches"]) * args.steps,
@@ -526,7 +538,7 @@ def run_gpu_uneven(args):
                 for sp in specs]
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
     tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
-                          "gram_df": False}, [])
+                          "gram_df": False, "tc_interp": False}, [])
     if args.tune:
         from paper_2302_13431_gb300.autotune import tune
         tuned, tune_table = tune(specs, calibs=calibs)
@@ -585,7 +597,8 @@ def run_gpu_uneven(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision_mode": tuned["precision"],
         "launch_config": dict(tuned, autotuned=bool(args.tune),
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
-                                                      f"{'/df' if r.get('gram_df') else ''}":
+                                                      f"{'/df' if r.get('gram_df') else ''}"
+                                                      f"{'/ti' if r.get('tc_interp') else ''}":
                                                       round(r["ms"], 3) for r in tune_table}),
         "data": "synthetic",
         "config": {"workload": "96 uneven 2D slices (seeded shapes, see phantoms.uneven_slice_specs)",

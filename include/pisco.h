@@ -84,6 +84,10 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
 #define PISCO_FLAG_TC_THIN 0x80u  /* with PISCO_FLAG_TC_EIG: also the thin block products of the
                                      eigensolver (block Grams Y^H Y, Y R^-1, the Rayleigh-Ritz
                                      products) on the tensor cores, same split precision      */
+#define PISCO_FLAG_TC_INTERP 0x100u /* the last periodic-sinc interpolation pass (Sec. V-D) as one
+                                     batched tensor-core GEMM per estimate (maps_q = M T_q for
+                                     every coil, split TF32), followed by the per-pixel
+                                     normalisation of Sec. VI                                  */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 

@@ -12,7 +12,9 @@ share the GPU:
   fewer cost less SM time and reduction traffic);
 * `gemm_splits`: split-K cap of the CUDA-core block products (same trade-off);
 * `gemm_tile`: 32x32 or 64x64 output tiles for those products (lower latency vs less SM time);
-* `gram_df`: the Gram's FFT route in FP64 or in double-float arithmetic (pairs of FP32).
+* `gram_df`: the Gram's FFT route in FP64 or in double-float arithmetic (pairs of FP32);
+* `tc_interp`: the last interpolation pass as a batched split-TF32 tensor-core GEMM or as the
+  fused CUDA-core interpolate-and-normalise kernel (tried on the best of the others only).
 
 Results are cached in a JSON file keyed by the device name, the shapes and the batch size.
 """
@@ -30,18 +32,21 @@ from .phantoms import make_case
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
-KNOB_KEYS = ("precision", "tc_splits", "gemm_splits", "gemm_tile", "gram_df")
+KNOB_KEYS = ("precision", "tc_splits", "gemm_splits", "gemm_tile", "gram_df", "tc_interp")
+# knobs toggled one at a time on the best candidate after the main sweep
+REFINE = (("tc_interp", True),)
 
 
 def candidates():
-    out = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False),
-           dict(precision="fp32", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False),
-           dict(precision="tc_g", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False)]
+    base = dict(tc_interp=False)
+    out = [dict(base, precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False),
+           dict(base, precision="fp32", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False),
+           dict(base, precision="tc_g", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False)]
     for df in (False, True):
         for ts in (1, 4):
             for gs, gt in ((0, 0), (2, 64)):
-                out.append(dict(precision="tc_g_eig", tc_splits=ts, gemm_splits=gs, gemm_tile=gt, gram_df=df))
-            out.append(dict(precision="tc_all", tc_splits=ts, gemm_splits=0, gemm_tile=0, gram_df=df))
+                out.append(dict(base, precision="tc_g_eig", tc_splits=ts, gemm_splits=gs, gemm_tile=gt, gram_df=df))
+            out.append(dict(base, precision="tc_all", tc_splits=ts, gemm_splits=0, gemm_tile=0, gram_df=df))
     return out
 
 
@@ -99,6 +104,16 @@ def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None,
         if verbose:
             print(f"  autotune {c}: {ms:.2f} ms/step", flush=True)
     best = min(table, key=lambda r: r["ms"])
+    if cands is None:
+        for knob, val in REFINE:
+            c = {k: best[k] for k in KNOB_KEYS}
+            c[knob] = val
+            ms = _time_batch([dict(s, **c) for s in specs], calibs, steps, warmup)
+            table.append(dict(c, ms=ms))
+            if verbose:
+                print(f"  autotune {c}: {ms:.2f} ms/step", flush=True)
+            if ms < best["ms"]:
+                best = table[-1]
     config = {k: best[k] for k in KNOB_KEYS}
     if cache:
         db[key] = dict(config=config, table=table, seconds=time.time() - t0)

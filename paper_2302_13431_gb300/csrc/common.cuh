@@ -160,6 +160,8 @@ cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo
 cudaError_t gram_masked_prepare(int nvol);
 size_t gram_masked_smem(int nvol);
 
+cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st);
+
 // warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out, widths <= 128; w32 is the FP32
 // parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its FP16 copy (the
 // matrices are read from w16, the biases from w32)
@@ -191,11 +193,15 @@ int tc2_np(int N);
 cudaError_t tc2_prepare();
 cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
                         cudaStream_t st);
-cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st);
+cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st,
+                        int nbatch = 1, long long b_stride = 0);
 cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st);
+// nbatch > 1: gridDim.z runs nbatch products C_b = A B_b sharing A (B' items of 2 Np rows one
+// after another, C_b at C + b c_stride; no split-K)
 cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
-                     int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st);
+                     int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
+                     int nbatch = 1, long long c_stride = 0);
 
 // tensor-core complex GEMM (kernels_tc.cu): C = alpha*A*op(B) + beta*C (+ diag_val on columns
 // c % diag_stride == 0, c < diag_limit); A M x K row-major with optional per-k real scale;

@@ -151,3 +151,32 @@ cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long
 }
 
 }  // namespace pisco
+
+namespace pisco {
+
+// maps[q][x] /= ||maps[.][x]|| (sum of squares over the coils; zero pixels stay zero): the
+// normalisation of Sec. VI after a final interpolation pass that wrote unnormalised maps
+__global__ void normalize_maps_kernel(float2* __restrict__ maps, int Q, long long npix) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < npix; x += (long long)gridDim.x * blockDim.x) {
+    float n2 = 0.f;
+    for (int q = 0; q < Q; ++q) {
+      const float2 v = maps[(long long)q * npix + x];
+      n2 = fmaf(v.x, v.x, fmaf(v.y, v.y, n2));
+    }
+    const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
+    for (int q = 0; q < Q; ++q) {
+      const float2 v = maps[(long long)q * npix + x];
+      maps[(long long)q * npix + x] = make_float2(v.x * s, v.y * s);
+    }
+  }
+}
+
+cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st) {
+  long long b = (npix + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  normalize_maps_kernel<<<(unsigned)b, 256, 0, st>>>(maps, Q, npix);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pisco

@@ -108,8 +108,11 @@ struct Args {
   float2 alpha, beta;
   float diag_val;
   int diag_stride, diag_limit;
-  float2* ws;     // [splits][M][N] partial products when gridDim.z > 1
+  float2* ws;     // [splits][M][N] partial products when gridDim.z > 1 (split-K)
   int* err;
+  int batched;    // 1: gridDim.z indexes independent products sharing A (no split-K)
+  int b_rows;     // B' rows per batch item (2 Np)
+  long long c_stride;  // C elements per batch item
 };
 
 template <int NT, int STAGES>
@@ -128,8 +131,11 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNC;
   const int total = (g.K2 + BK - 1) / BK;
-  const int kb0 = blockIdx.z * g.kpb;
+  const int zb = g.batched ? (int)blockIdx.z : 0;          // batch item
+  const int kb0 = g.batched ? 0 : blockIdx.z * g.kpb;      // first K step of this split
   const int nk = min(g.kpb, total - kb0);
+  const int brow0 = zb * g.b_rows;                          // this item's rows of B'
+  float2* Cb = g.C + (long long)zb * g.c_stride;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -164,8 +170,8 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
       tma_2d(st, &tAh, kx, m0, fb);
       if (NT == 3) tma_2d(st + A_TILE, &tAl, kx, m0, fb);
       const uint32_t sb = st + (NT == 3 ? 2 * A_TILE : A_TILE);
-      tma_2d(sb, &tBh, kx, 2 * n0, fb);
-      if (NT == 3) tma_2d(sb + B_TILE, &tBl, kx, 2 * n0, fb);
+      tma_2d(sb, &tBh, kx, brow0 + 2 * n0, fb);
+      if (NT == 3) tma_2d(sb + B_TILE, &tBl, kx, brow0 + 2 * n0, fb);
     }
   } else if (warp == 1 && lane == 0 && nk > 0) {
     // MMA issuer: 4 MMAs of K = 8 per stage (x3 for the head/tail split)
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  if (gridDim.z > 1) {  // raw partial tile
+  if (gridDim.z > 1 && !g.batched) {  // raw partial tile
     float2* out = g.ws + (long long)blockIdx.z * g.M * g.N;
     for (int rr = warp; rr < BM; rr += 4) {
       const int gm = m0 + rr, gn = n0 + lane;
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     if (gm >= g.M || gn >= g.N) continue;
     const float2 a = tile[rr * 33 + lane];
     float2 o = make_float2(g.alpha.x * a.x - g.alpha.y * a.y, g.alpha.x * a.y + g.alpha.y * a.x);
-    float2* cp = g.C + (long long)gm * g.ldc + gn;
+    float2* cp = Cb + (long long)gm * g.ldc + gn;
     if (has_beta) {
       const float2 c = *cp;
       o.x += g.beta.x * c.x - g.beta.y * c.y;
@@ -304,15 +310,21 @@ __global__ void split_at_kernel(const float2* __restrict__ Y, int ldy, int M, in
 
 // B' head/tail rows (see the file comment); columns c >= N of the last tile are zero
 __global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, int K, int N, int Np,
-                               float* __restrict__ hi, float* __restrict__ lo, int K2p) {
-  const long long total = (long long)Np * K;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+                               float* __restrict__ hi, float* __restrict__ lo, int K2p, int nbatch,
+                               long long b_stride) {
+  const long long per = (long long)Np * K;
+  const long long total = per * nbatch;
+  for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < total; e0 += (long long)gridDim.x * blockDim.x) {
+    const long long bi = e0 / per, e = e0 % per;
+    const float2* Bb = B + bi * b_stride;
+    float* hb = hi + bi * (2LL * Np * K2p);
+    float* lb = lo ? lo + bi * (2LL * Np * K2p) : nullptr;
     const int c = (int)(e / K), k = (int)(e % K);
     float2 b = make_float2(0.f, 0.f);
     if (c < N) {
-      if (opB == 0) b = B[(long long)k * ldb + c];
+      if (opB == 0) b = Bb[(long long)k * ldb + c];
       else {
-        const float2 s = B[(long long)c * ldb + k];
+        const float2 s = Bb[(long long)c * ldb + k];
         b = make_float2(s.x, -s.y);
       }
     }
@@ -321,11 +333,11 @@ __global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, i
     const long long rim = (long long)(64 * t + 32 + cl) * K2p + 2 * k;
     const float2 vre = make_float2(b.x, -b.y), vim = make_float2(b.y, b.x);
     const float2 hre = make_float2(head(vre.x), head(vre.y)), him = make_float2(head(vim.x), head(vim.y));
-    *reinterpret_cast<float2*>(hi + rre) = hre;
-    *reinterpret_cast<float2*>(hi + rim) = him;
-    if (lo) {
-      *reinterpret_cast<float2*>(lo + rre) = make_float2(head(vre.x - hre.x), head(vre.y - hre.y));
-      *reinterpret_cast<float2*>(lo + rim) = make_float2(head(vim.x - him.x), head(vim.y - him.y));
+    *reinterpret_cast<float2*>(hb + rre) = hre;
+    *reinterpret_cast<float2*>(hb + rim) = him;
+    if (lb) {
+      *reinterpret_cast<float2*>(lb + rre) = make_float2(head(vre.x - hre.x), head(vre.y - hre.y));
+      *reinterpret_cast<float2*>(lb + rim) = make_float2(head(vim.x - him.x), head(vim.y - him.y));
     }
   }
 }
@@ -395,20 +407,23 @@ cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, floa
   return cudaGetLastError();
 }
 
-cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st) {
+cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st,
+                        int nbatch, long long b_stride) {
   const int Np = tc2_np(N);
-  split_b_kernel<<<grid_for((long long)Np * K), 256, 0, st>>>(B, ldb, opB, K, N, Np, hi, lo, tc2_k2p(K));
+  split_b_kernel<<<grid_for((long long)Np * K * nbatch), 256, 0, st>>>(B, ldb, opB, K, N, Np, hi, lo, tc2_k2p(K),
+                                                                      nbatch, b_stride);
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
-                     int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
+                     int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
+                     int nbatch, long long c_stride) {
+  if (M <= 0 || N <= 0 || nbatch < 1) return cudaSuccess;
   const int K2 = 2 * K, K2p = tc2_k2p(K), Np = tc2_np(N);
   const int total = (K2 + BK - 1) / BK;
-  if (splits < 1 || ws == nullptr) splits = 1;
+  if (splits < 1 || ws == nullptr || nbatch > 1) splits = 1;
   if (splits > total) splits = total > 0 ? total : 1;
   const int kpb = total > 0 ? (total + splits - 1) / splits : 0;
   if (kpb > 0) splits = (total + kpb - 1) / kpb;
@@ -417,10 +432,12 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   const float* bl = nterms == 3 ? Blo : Bhi;
   const int kcols = K2 > 0 ? K2 : 1;
   if (!encode_2d(&mAh, Ahi, kcols, M, K2p, BM) || !encode_2d(&mAl, al, kcols, M, K2p, BM) ||
-      !encode_2d(&mBh, Bhi, kcols, 2 * Np, K2p, 2 * BNC) || !encode_2d(&mBl, bl, kcols, 2 * Np, K2p, 2 * BNC))
+      !encode_2d(&mBh, Bhi, kcols, 2 * Np * nbatch, K2p, 2 * BNC) ||
+      !encode_2d(&mBl, bl, kcols, 2 * Np * nbatch, K2p, 2 * BNC))
     return cudaErrorInvalidValue;
-  Args g{M, N, K2, kpb, C, ldc, alpha, beta, diag_val, diag_stride, diag_limit, ws, err};
-  dim3 grid(Np / BNC, (M + BM - 1) / BM, splits);
+  Args g{M, N, K2, kpb, C, ldc, alpha, beta, diag_val, diag_stride, diag_limit, ws, err,
+         nbatch > 1 ? 1 : 0, 2 * Np, c_stride};
+  dim3 grid(Np / BNC, (M + BM - 1) / BM, nbatch > 1 ? nbatch : splits);
   // short K loops (<= 8 steps per CTA) keep 2 stages: half the shared memory, 2 CTAs per SM, so
   // one CTA's epilogue overlaps another's loads; long loops keep 4 stages in flight
   const bool deep = kpb > 8;

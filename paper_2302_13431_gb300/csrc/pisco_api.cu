@@ -74,6 +74,9 @@ struct pisco_plan_s {
   int gemm_splits = 0;  // split-K cap of the CUDA-core block products (0: automatic)
   int gemm_tile = 0;    // CUDA-core block product tile: 0 automatic, 32 or 64
   bool tc_thin = false; // thin block products (n x m x m, m x m x n) on the tensor cores too
+  bool tc_interp = false;  // last interpolation pass as a batched tensor-core GEMM
+  float *IAh = nullptr, *IAl = nullptr, *IBh = nullptr, *IBl = nullptr;
+  float2* interpA = nullptr;  // the last axis's interpolation matrix (split into IAh/IAl)
   float *TAh = nullptr, *TAl = nullptr, *TBh = nullptr, *TBl = nullptr;  // their split operands
   float *Ah = nullptr, *Al = nullptr, *Xh = nullptr, *Xl = nullptr;        // A32 and the block
   float *Eh = nullptr, *El = nullptr, *KTh = nullptr, *KTl = nullptr;      // E and the lag table
@@ -697,6 +700,25 @@ pisco_status run_interp(pisco_plan_s* pl, float2* maps) {
     return PISCO_OK;
   }
   OP("interp_axis", apply_axis_c(pl->V, pl->interpT, pl->I1, AxisView{Q, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1, 0, 1}, st));
+  if (pl->tc_interp) {
+    // maps_q = M T_q for every coil q (one batched tensor-core GEMM), then the per-pixel norm
+    const bool tt = pl->tc_terms == 3;
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    const float2* T = pl->I1;
+    if (pl->D == 3) {
+      OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{Q, Nr[0], Nr[1], N[1], N[2]}, st));
+      T = pl->I2;
+    }
+    const int ax = pl->D == 3 ? 0 : 1;
+    const long long inner = pl->D == 3 ? (long long)N[1] * N[2] : N[2];
+    OP("interp_final_tc", tc2_split_b(T, (int)inner, 0, Nr[ax], (int)inner, pl->IBh, tt ? pl->IBl : nullptr, st, Q,
+                                      (long long)Nr[ax] * inner));
+    OP("interp_final_tc", tc2_gemm(pl->tc_terms, N[ax], (int)inner, Nr[ax], pl->IAh, pl->IAl, pl->IBh, pl->IBl, one,
+                                   zero, maps, (int)inner, 0.f, 0, 0, 1, nullptr, &pl->dstatus->flags, st, Q,
+                                   (long long)N[ax] * inner));
+    OP("interp_final_norm", normalize_maps(maps, Q, pl->npix, st));
+    return PISCO_OK;
+  }
   if (pl->D == 3) {
     OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{Q, Nr[0], Nr[1], N[1], N[2]}, st));
     OP("interp_final_norm", interp_final_normalize(pl->I2, pl->interp[0], Q, 0, Nr[0], N[0], (long long)N[1] * N[2], maps, st));
@@ -823,6 +845,12 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->gemm_splits = p->gemm_splits > 0 ? std::min(p->gemm_splits, 64) : 0;
   pl->gemm_tile = (p->gemm_tile == 32 || p->gemm_tile == 64) ? p->gemm_tile : 0;
   pl->tc_thin = (p->flags & PISCO_FLAG_TC_THIN) != 0 && (p->flags & PISCO_FLAG_TC_EIG) != 0;
+  pl->tc_interp = (p->flags & PISCO_FLAG_TC_INTERP) != 0 && p->grid_reduction > 1;
+  if (pl->tc_interp && tc2_prepare() != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return PISCO_ERR_CUDA;
+  }
   pl->masked = (p->flags & PISCO_FLAG_MASKED_GRAM) != 0;
   pl->block_pi = (p->flags & PISCO_FLAG_BLOCK_PI) != 0;
   pl->gram_df = (p->flags & PISCO_FLAG_GRAM_DF) != 0;
@@ -955,6 +983,18 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->eig_tmp, (size_t)pl->npix_red);
   ok = ok && dalloc(pl, &pl->I1, (size_t)Q * Nr[0] * Nr[1] * N[2]);
   ok = ok && dalloc(pl, &pl->I2, (size_t)Q * Nr[0] * N[1] * N[2]);
+  if (ok && pl->tc_interp) {
+    // last interpolation axis: 0 in 3D, 1 in 2D (the axis kernels run the faster ones)
+    const int ax = pl->D == 3 ? 0 : 1;
+    const long long inner = pl->D == 3 ? (long long)N[1] * N[2] : N[2];
+    const size_t k2 = (size_t)tc2_k2p(Nr[ax]);
+    const size_t lo_n = pl->tc_terms == 3 ? 1 : 0;
+    const size_t nb = (size_t)Q * 2 * tc2_np((int)inner) * k2;
+    ok = upload(pl, &pl->interpA, interp_matrix(Nr[ax], N[ax])) && dalloc(pl, &pl->IAh, (size_t)N[ax] * k2) &&
+         dalloc(pl, &pl->IAl, lo_n * N[ax] * k2 + 1) && dalloc(pl, &pl->IBh, nb) && dalloc(pl, &pl->IBl, lo_n * nb + 1);
+    ok = ok && tc2_split_a(pl->interpA, Nr[ax], nullptr, N[ax], Nr[ax], pl->IAh, lo_n ? pl->IAl : nullptr,
+                           nullptr) == cudaSuccess;
+  }
   ok = ok && dalloc(pl, &pl->dstatus, 1);
   ok = ok && dalloc(pl, &pl->calib_stage, (size_t)Q * Nc[0] * Nc[1] * Nc[2]);
   if (ok && (p->flags & PISCO_FLAG_HOST_IO)) {

@@ -49,12 +49,13 @@ class PiscoEstimator:
     masked_gram: the exact Gram of the masked calibration matrix instead of Sec. V-A's FFT route.
     block_pi: two-vector block power iteration with Rayleigh-Ritz (small-gap pixels).
     gram_df: the Gram's FFT route in double-float instead of FP64 arithmetic.
+    tc_interp: the last interpolation pass as one batched split-TF32 tensor-core GEMM.
     """
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
                  stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False,
-                 block_pi=False, gemm_tile=0, gram_df=False):
+                 block_pi=False, gemm_tile=0, gram_df=False, tc_interp=False):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -70,6 +71,8 @@ class PiscoEstimator:
             flags |= B.PISCO_FLAG_BLOCK_PI
         if gram_df:
             flags |= B.PISCO_FLAG_GRAM_DF
+        if tc_interp:
+            flags |= B.PISCO_FLAG_TC_INTERP
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
                                     reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
                                     gemm_splits, gemm_tile)
@@ -176,7 +179,7 @@ class PiscoBatch:
 
     specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
     kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision, tc_splits,
-    gemm_splits, gemm_tile, gram_df.
+    gemm_splits, gemm_tile, gram_df, tc_interp.
     """
 
     def __init__(self, specs, stream=None):
@@ -191,7 +194,8 @@ class PiscoBatch:
                                         sp.get("thr", 0.05), sp.get("reduction", 1),
                                         sp.get("iters", 30), sp.get("seed", 0),
                                         precision_flags(sp.get("precision", "fp32"))
-                                        | (B.PISCO_FLAG_GRAM_DF if sp.get("gram_df") else 0),
+                                        | (B.PISCO_FLAG_GRAM_DF if sp.get("gram_df") else 0)
+                                        | (B.PISCO_FLAG_TC_INTERP if sp.get("tc_interp") else 0),
                                         sp.get("eig_block", 0), sp.get("eig_iters", 0), sp.get("tc_splits", 0),
                                         sp.get("gemm_splits", 0), sp.get("gemm_tile", 0)))
         st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)

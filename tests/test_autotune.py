@@ -26,8 +26,8 @@ def test_tune_picks_the_fastest_and_caches(tmp_path):
     from paper_2302_13431_gb300.phantoms import make_case
     specs = [dict(grid=(64, 64), calib_shape=(24, 24), num_coils=8, tau=3, reduction=2, iters=20)] * 3
     cache = str(tmp_path / "tune.json")
-    cands = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False),
-             dict(precision="tc_g_eig", tc_splits=4, gemm_splits=2, gemm_tile=64, gram_df=True)]
+    cands = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False, tc_interp=False),
+             dict(precision="tc_g_eig", tc_splits=4, gemm_splits=2, gemm_tile=64, gram_df=True, tc_interp=True)]
     cfg, table = tune(specs, steps=2, warmup=2, cache=cache, cands=cands)
     assert cfg == {k: min(table, key=lambda r: r["ms"])[k] for k in KNOB_KEYS}
     cfg2, table2 = tune(specs, cache=cache, cands=cands)  # cached: no re-timing
@@ -39,7 +39,7 @@ def test_tune_picks_the_fastest_and_caches(tmp_path):
     for i in range(3):
         est = PiscoEstimator((64, 64), (24, 24), 8, 3, reduction=2, iters=20, precision=cfg["precision"],
                              tc_splits=cfg["tc_splits"], gemm_splits=cfg["gemm_splits"], gemm_tile=cfg["gemm_tile"],
-                             gram_df=cfg["gram_df"])
+                             gram_df=cfg["gram_df"], tc_interp=cfg["tc_interp"])
         m1, e1 = est(calibs[i])
         torch.cuda.synchronize()
         assert torch.equal(m1, maps[i]) and torch.equal(e1, eigs[i])

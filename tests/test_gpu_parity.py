@@ -321,3 +321,31 @@ def test_double_float_gram_matches_explicit_CtC_and_maps(name):
     b = ref["maps"].reshape(Q, -1).T
     assert np.linalg.norm((_align(a) - _align(b))[m]) / np.linalg.norm(b[m]) <= 1e-4
     est.close()
+
+
+# ---- the last interpolation pass on the tensor cores (PISCO_FLAG_TC_INTERP) --------------------
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+def test_tensor_core_interpolation_matches_oracle_and_fp32_route(name):
+    """maps_q = M T_q as one batched split-TF32 GEMM, then the per-pixel normalisation: the same
+    map gate as the FP32 route, and within 1e-5 of the FP32 route's maps on the gated pixels.
+    (2d_small_rect has no grid reduction, so the flag leaves its path unchanged.)"""
+    grid, Q, cs, tau, shape, red, iters, phase = CASES[name]
+    case, ref = _oracle(name, 0)
+    est = PiscoEstimator(grid, cs, Q, tau, kernel_shape=shape, reduction=red, iters=iters, tc_interp=True)
+    maps, eig = est(torch.from_numpy(case.calib).cuda())
+    torch.cuda.synchronize()
+    r0 = _run(name)
+    r = dict(case=case, ref=ref, grid=grid, red=red)
+    m = _gated_mask(r).reshape(-1)
+    a = maps.cpu().numpy().reshape(Q, -1).T
+    b = ref["maps"].reshape(Q, -1).T
+    a0 = r0["maps"].reshape(Q, -1).T
+    err = np.linalg.norm((_align(a) - _align(b))[m]) / np.linalg.norm(b[m])
+    d32 = np.linalg.norm((a - a0)[m]) / np.linalg.norm(a0[m])
+    print(f"{name}: tc interp maps error vs oracle {err:.2e}, vs FP32 route {d32:.2e}")
+    assert err <= 1e-4, err
+    assert d32 <= 1e-5, d32
+    nrm = np.linalg.norm(a, axis=1)
+    assert np.all((np.abs(nrm - 1) < 1e-5) | (nrm == 0))
+    np.testing.assert_array_equal(eig.cpu().numpy(), r0["eig"])
+    est.close()
