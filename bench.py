@@ -347,7 +347,9 @@ def run_gpu(args):
     bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
     tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
                           "gram_df": False, "tc_interp": False}, [])
-    if args.tune:
+    if args.launch_config:
+        tuned = dict(tuned, **json.loads(args.launch_config))
+    elif args.tune:
         from paper_2302_13431_gb300.autotune import tune
         tuned, tune_table = tune([spec] * nb, calibs=bcal)
     # ---- plain FP32 PISCO, one plan, one map per call (per-slice launches): comparison point ----
@@ -488,7 +490,7 @@ def run_gpu(args):
                                           "launches), CUDA-core FP32 products, same iterations"},
         "single_map_same_precision": {"value": single[tuned["precision"]], "unit": "maps/s"},
         "precision_mode": tuned["precision"],
-        "launch_config": dict(tuned, autotuned=bool(args.tune),
+        "launch_config": dict(tuned, autotuned=bool(args.tune) and not args.launch_config,
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
                                                       f"{'/df' if r.get('gram_df') else ''}"
                                                       f"{'/ti' if r.get('tc_interp') else ''}":
@@ -539,7 +541,9 @@ def run_gpu_uneven(args):
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
     tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
                           "gram_df": False, "tc_interp": False}, [])
-    if args.tune:
+    if args.launch_config:
+        tuned = dict(tuned, **json.loads(args.launch_config))
+    elif args.tune:
         from paper_2302_13431_gb300.autotune import tune
         tuned, tune_table = tune(specs, calibs=calibs)
     specs = [dict(sp, **tuned) for sp in specs]
@@ -595,7 +599,7 @@ def run_gpu_uneven(args):
         "metric": UNEVEN_METRIC, "value": value, "unit": "slices/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision_mode": tuned["precision"],
-        "launch_config": dict(tuned, autotuned=bool(args.tune),
+        "launch_config": dict(tuned, autotuned=bool(args.tune) and not args.launch_config,
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
                                                       f"{'/df' if r.get('gram_df') else ''}"
                                                       f"{'/ti' if r.get('tc_interp') else ''}":
@@ -722,6 +726,9 @@ def main():
                     help="with --no-tune: fp32 | tc_g | tc_g_eig | tc_g_1pass | tc_g_eig_1pass")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (which picks precision route and split factors, cached)")
+    ap.add_argument("--launch-config", default="",
+                    help="JSON object of launch knobs (precision, tc_splits, gemm_splits, gemm_tile, gram_df, "
+                         "tc_interp) used instead of the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "pisco":
         args.warmup = 3

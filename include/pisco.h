@@ -88,6 +88,11 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
                                      batched tensor-core GEMM per estimate (maps_q = M T_q for
                                      every coil, split TF32), followed by the per-pixel
                                      normalisation of Sec. VI                                  */
+#define PISCO_FLAG_G_DENSE 0x200u   /* with PISCO_FLAG_TC_GFIELD in 2D: evaluate the lag sums of
+                                     G(x) (Sec. V-C) as the dense tensor-core product
+                                     E(x, d) K(d, pq) instead of the default separable DFT
+                                     passes over the lag rows and columns (3D always uses the
+                                     dense product)                                           */
 #define PISCO_FLAG_TC_1PASS 0x8u  /* with TC_GFIELD / TC_EIG: one TF32 pass per product (about
                                      11 significant bits) instead of three; for error studies */
 

@@ -24,6 +24,7 @@ PISCO_FLAG_BLOCK_PI = 0x20
 PISCO_FLAG_GRAM_DF = 0x40
 PISCO_FLAG_TC_THIN = 0x80
 PISCO_FLAG_TC_INTERP = 0x100
+PISCO_FLAG_G_DENSE = 0x200
 (PISCO_BUF_LAGS, PISCO_BUF_GRAM, PISCO_BUF_SIGNAL, PISCO_BUF_WEIGHTS, PISCO_BUF_RITZ, PISCO_BUF_G,
  PISCO_BUF_V, PISCO_BUF_Y, PISCO_BUF_BLOCK, PISCO_BUF_RITZ32, PISCO_BUF_SCALE) = range(11)
 

@@ -149,9 +149,15 @@ cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* 
 cudaError_t apply_axis_c2df(const float2* in, const void* M, void* out, AxisView v, cudaStream_t st);
 cudaError_t apply_axis_df(const void* in, const void* M, void* out, AxisView v, cudaStream_t st);
 cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st);
-cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, cudaStream_t st);
-cudaError_t eig_band_matvec_df(const double2* A, const double2* Xb, int n, int nb, const int* band_idx, double2* Zb,
-                               cudaStream_t st);
+// the lag table is written twice: FP64 (lags) and double-float (lags_df, for the expansion)
+cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, void* lags_df, cudaStream_t st);
+// A kept as double-float quadruples (no FP64 arithmetic per entry); A32 = A / scale
+cudaError_t gram_expand_df(const void* lags_df, const int* lag_of_ij, int Q, int L, int nbox, const double* scale,
+                           void* A, float2* A32, cudaStream_t st);
+cudaError_t df_to_fp64(const void* in, long long count, double2* out, cudaStream_t st);
+// a_df: A holds double-float quadruples, else FP64
+cudaError_t eig_band_matvec_df(const void* A, bool a_df, const double2* Xb, int n, int nb, const int* band_idx,
+                               double2* Zb, cudaStream_t st);
 
 // exact Gram of the masked calibration matrix (kernels_gram.cu): A (FP64 n x n), scale, A32
 cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo, const int* hi, const int* lam,
@@ -161,6 +167,21 @@ cudaError_t gram_masked_prepare(int nvol);
 size_t gram_masked_smem(int nvol);
 
 cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st);
+
+// 2D double-float Gram pairs stage fused per pair (kernels_gram_df.cu): pair product, both
+// inverse lag passes, lag table lags[(p,q)][B1*B2] for p <= q in FP64 and in double-float
+constexpr int kPairsInverseDfMaxSmem = 200 * 1024;
+bool gram_pairs_inverse_df_supported(int Lp1, int Lp2, int B1, int B2);
+cudaError_t gram_pairs_inverse_df(const void* S, int Q, int Lp1, int Lp2, const void* invT2, int B2, const void* inv1,
+                                  int B1, double2* lags, void* lags_df, cudaStream_t st);
+
+// 2D G(x) from the collapsed lag kernel KT[nlag][Q*Q] by two separable DFT passes
+// (kernels_gassembly.cu); row_ptr[B1+1] groups the lags by row, lag_b2 their column
+constexpr int kGfieldSep2MaxSmem = 200 * 1024;
+bool gassembly_field_sep2_supported(int nlag, int Nr1, int B1, int Nr2, int B2);
+cudaError_t gassembly_field_sep2(const float2* KT, int Q, int nlag, const int* row_ptr, const int* lag_b2,
+                                 const float2* E1, int Nr1, int B1, const float2* E2, int B2, int Nr2,
+                                 float lam_size, float2* G, cudaStream_t st);
 
 // warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out, widths <= 128; w32 is the FP32
 // parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its FP16 copy (the

@@ -147,3 +147,127 @@ cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* 
 }
 
 }  // namespace pisco
+
+namespace pisco {
+
+// 2D G(x) from the collapsed lag kernel by two separable DFT passes (the zero-padded lag sums of
+// Sec. V-C evaluated on the reduced grid).  With the lags of Lambda - Lambda sorted by their
+// row b1, then column b2 (row r holds lags row_ptr[r] .. row_ptr[r+1]-1),
+//     S_r(x2)       = sum_{l in row r} KT[l][pq] E2[x2][b2_l],
+//     G[x1,x2][pq]  = |Lambda| delta_pq - sum_r E1[x1][r] S_r(x2),
+// with E_a[j][t] = exp(+i 2 pi (t - 2 tau_a) (j - Nr_a/2)/Nr_a).  A CTA owns 32 consecutive pairs
+// and 8*XPT columns x2: it stages the pairs' lag kernel, both exponential tables and the lag
+// columns in shared memory with one coalesced sweep; each thread then keeps the row sums of its
+// pair and XPT columns in registers, and a warp stores 32 consecutive pairs (256 B) of a pixel.
+template <int NB, int XPT>
+__global__ void __launch_bounds__(256) gfield_sep2_kernel(const float2* __restrict__ KT, int Q, int nlag,
+                                                          const int* __restrict__ row_ptr,
+                                                          const int* __restrict__ lag_b2,
+                                                          const float2* __restrict__ E1, int Nr1,
+                                                          const float2* __restrict__ E2, int B2, int Nr2,
+                                                          float lam_size, float2* __restrict__ G) {
+  extern __shared__ float2 sm[];
+  float2* e1s = sm;                          // [Nr1][NB]
+  float2* e2s = e1s + Nr1 * NB;              // [Nr2][B2]
+  float2* ks = e2s + Nr2 * B2;               // [nlag][32]
+  int* b2s = reinterpret_cast<int*>(ks + nlag * 32);  // [nlag]
+  const int QQ = Q * Q;
+  const int pq0 = blockIdx.x * 32;
+  for (int i = threadIdx.x; i < Nr1 * NB; i += blockDim.x) e1s[i] = E1[i];
+  for (int i = threadIdx.x; i < Nr2 * B2; i += blockDim.x) e2s[i] = E2[i];
+  for (int i = threadIdx.x; i < nlag * 32; i += blockDim.x) {
+    const int l = i >> 5, j = i & 31;
+    ks[i] = pq0 + j < QQ ? KT[(long long)l * QQ + pq0 + j] : make_float2(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i < nlag; i += blockDim.x) b2s[i] = lag_b2[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pq = pq0 + lane;
+  const bool live = pq < QQ;
+  const int x2b = (blockIdx.y * 8 + warp) * XPT;
+  int x2c[XPT];
+#pragma unroll
+  for (int x = 0; x < XPT; ++x) x2c[x] = min(x2b + x, Nr2 - 1) * B2;
+  float2 S[NB][XPT];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+#pragma unroll
+    for (int x = 0; x < XPT; ++x) S[r][x] = make_float2(0.f, 0.f);
+    const int l1 = row_ptr[r + 1];
+#pragma unroll 4
+    for (int l = row_ptr[r]; l < l1; ++l) {
+      const float2 k = ks[l * 32 + lane];
+      const int b2 = b2s[l];
+#pragma unroll
+      for (int x = 0; x < XPT; ++x) {
+        const float2 e = e2s[x2c[x] + b2];
+        S[r][x].x = fmaf(k.x, e.x, fmaf(-k.y, e.y, S[r][x].x));
+        S[r][x].y = fmaf(k.x, e.y, fmaf(k.y, e.x, S[r][x].y));
+      }
+    }
+  }
+  const float diag = (live && pq / Q == pq % Q) ? lam_size : 0.f;
+  for (int x1 = 0; x1 < Nr1; ++x1) {
+    float2 g[XPT];
+#pragma unroll
+    for (int x = 0; x < XPT; ++x) g[x] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      const float2 e = e1s[x1 * NB + r];
+#pragma unroll
+      for (int x = 0; x < XPT; ++x) {
+        g[x].x = fmaf(e.x, S[r][x].x, fmaf(-e.y, S[r][x].y, g[x].x));
+        g[x].y = fmaf(e.x, S[r][x].y, fmaf(e.y, S[r][x].x, g[x].y));
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < XPT; ++x) {
+      const int x2 = x2b + x;
+      if (live && x2 < Nr2) G[((long long)x1 * Nr2 + x2) * QQ + pq] = make_float2(diag - g[x].x, -g[x].y);
+    }
+  }
+}
+
+size_t gfield_sep2_smem(int nlag, int Nr1, int B1, int Nr2, int B2) {
+  return ((size_t)Nr1 * B1 + (size_t)Nr2 * B2 + (size_t)nlag * 32) * sizeof(float2) + (size_t)nlag * sizeof(int);
+}
+
+namespace {
+constexpr int kSepXPT = 2;
+template <int NB>
+cudaError_t launch_sep2(const float2* KT, int Q, int nlag, const int* row_ptr, const int* lag_b2, const float2* E1,
+                        int Nr1, const float2* E2, int B2, int Nr2, float lam_size, float2* G, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(gfield_sep2_kernel<NB, kSepXPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kGfieldSep2MaxSmem);
+    attr_set = true;
+  }
+  const dim3 grid((unsigned)((Q * Q + 31) / 32), (unsigned)((Nr2 + 8 * kSepXPT - 1) / (8 * kSepXPT)));
+  gfield_sep2_kernel<NB, kSepXPT><<<grid, 256, gfield_sep2_smem(nlag, Nr1, NB, Nr2, B2), st>>>(
+      KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G);
+  ++g_launches;
+  return cudaGetLastError();
+}
+}  // namespace
+
+bool gassembly_field_sep2_supported(int nlag, int Nr1, int B1, int Nr2, int B2) {
+  return (B1 == 5 || B1 == 9 || B1 == 13 || B1 == 17 || B1 == 21 || B1 == 25) &&
+         gfield_sep2_smem(nlag, Nr1, B1, Nr2, B2) <= (size_t)kGfieldSep2MaxSmem;
+}
+
+cudaError_t gassembly_field_sep2(const float2* KT, int Q, int nlag, const int* row_ptr, const int* lag_b2,
+                                 const float2* E1, int Nr1, int B1, const float2* E2, int B2, int Nr2,
+                                 float lam_size, float2* G, cudaStream_t st) {
+  switch (B1) {
+    case 5: return launch_sep2<5>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    case 9: return launch_sep2<9>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    case 13: return launch_sep2<13>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    case 17: return launch_sep2<17>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    case 21: return launch_sep2<21>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    case 25: return launch_sep2<25>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pisco

@@ -95,7 +95,8 @@ __global__ void pair_products_df_kernel(const dfc* __restrict__ S, int Q, long l
 }
 
 // lags[(p,q)][t] = Rp[pair][t] as FP64 (hi + lo is exact in FP64)
-__global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int nbox, double2* __restrict__ lags) {
+__global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int nbox, double2* __restrict__ lags,
+                                        dfc* __restrict__ lags_df) {
   const int pair = blockIdx.x;
   int p = 0, base = 0;
   while (pair >= base + (Q - p)) { base += Q - p; ++p; }
@@ -103,6 +104,95 @@ __global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int n
   for (int t = threadIdx.x; t < nbox; t += blockDim.x) {
     const dfc v = Rp[(long long)pair * nbox + t];
     lags[((long long)p * Q + q) * nbox + t] = make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+    lags_df[((long long)p * Q + q) * nbox + t] = v;
+  }
+}
+
+// 2D pairs stage of the double-float Gram, fused per pair (p <= q): the frequency-domain product
+// conj(S_p) S_q, the inverse lag transform along the contiguous axis (Lp2 -> B2) and then along
+// axis 1 (Lp1 -> B1), all in shared memory, and the FP64 lag table of the pair.  Each output
+// accumulates its terms in the order of the unfused axis passes (bitwise the same result).
+// invT2: [Lp2][B2] (transposed), inv1: [B1][Lp1].
+__global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __restrict__ S, int Q, int Lp1, int Lp2,
+                                                               const dfc* __restrict__ invT2, int B2,
+                                                               const dfc* __restrict__ inv1, int B1,
+                                                               double2* __restrict__ lags, dfc* __restrict__ lags_df) {
+  extern __shared__ dfc dsm[];
+  const int ldp = Lp2 | 1;  // odd row stride (in 16-byte words): conflict-free column reads
+  dfc* P = dsm;                       // [Lp1][ldp]
+  dfc* T = P + Lp1 * ldp;             // [Lp1][B2]
+  dfc* m2 = T + Lp1 * B2;             // [Lp2][B2]
+  dfc* m1 = m2 + Lp2 * B2;            // [B1][Lp1]
+  const int pair = blockIdx.x;
+  int p = 0, base = 0;
+  while (pair >= base + (Q - p)) { base += Q - p; ++p; }
+  const int q = p + (pair - base);
+  const long long nfreq = (long long)Lp1 * Lp2;
+  const dfc* Sp = S + p * nfreq;
+  const dfc* Sq = S + q * nfreq;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < Lp2 * B2; i += nt) m2[i] = invT2[i];
+  for (int i = tid; i < B1 * Lp1; i += nt) m1[i] = inv1[i];
+  for (int f = tid; f < Lp1 * Lp2; f += nt) {
+    dfc acc{0.f, 0.f, 0.f, 0.f};
+    df_cfmac(acc, Sp[f], Sq[f]);
+    P[(f / Lp2) * ldp + f % Lp2] = acc;
+  }
+  __syncthreads();
+  for (int o = tid; o < Lp1 * B2; o += nt) {
+    const int f1 = o / B2, b2 = o % B2;
+    const dfc* prow = P + f1 * ldp;
+    dfc acc{0.f, 0.f, 0.f, 0.f};
+    for (int f2 = 0; f2 < Lp2; ++f2) df_cfma(acc, m2[f2 * B2 + b2], prow[f2]);
+    T[o] = acc;
+  }
+  __syncthreads();
+  const long long ob = ((long long)p * Q + q) * B1 * B2;
+  for (int o = tid; o < B1 * B2; o += nt) {
+    const int b1 = o / B2, b2 = o % B2;
+    const dfc* mrow = m1 + b1 * Lp1;
+    dfc acc{0.f, 0.f, 0.f, 0.f};
+    for (int f1 = 0; f1 < Lp1; ++f1) df_cfma(acc, mrow[f1], T[f1 * B2 + b2]);
+    lags[ob + o] = make_double2((double)acc.rh + (double)acc.rl, (double)acc.ih + (double)acc.il);
+    lags_df[ob + o] = acc;
+  }
+}
+
+size_t pairs_inverse_df_smem(int Lp1, int Lp2, int B1, int B2) {
+  return ((size_t)Lp1 * (Lp2 | 1) + (size_t)Lp1 * B2 + (size_t)Lp2 * B2 + (size_t)B1 * Lp1) * sizeof(dfc);
+}
+
+// A[(p,i),(q,j)] = R_pq[m_i - m_j] (Hermitian mirror for p > q) kept in double-float, and
+// A32 = A / scale in FP32, from the double-float lag table: no FP64 arithmetic per entry
+__global__ void gram_expand_df_kernel(const dfc* __restrict__ lags_df, const int* __restrict__ lag_of_ij, int Q,
+                                      int L, int nbox, const double* __restrict__ scale, dfc* __restrict__ A,
+                                      float2* __restrict__ A32) {
+  const long long n = (long long)Q * L;
+  const float inv = (float)(1.0 / *scale);
+  const long long total = n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int col = (int)(idx % n);
+    const int row = (int)(idx / n);
+    const int p = row / L, i = row % L;
+    const int q = col / L, j = col % L;
+    dfc v;
+    if (p <= q) {
+      v = lags_df[((long long)p * Q + q) * nbox + lag_of_ij[i * L + j]];
+    } else {
+      v = lags_df[((long long)q * Q + p) * nbox + lag_of_ij[j * L + i]];
+      v.ih = -v.ih;
+      v.il = -v.il;
+    }
+    A[idx] = v;
+    A32[idx] = make_float2(fmaf(v.rh, inv, v.rl * inv), fmaf(v.ih, inv, v.il * inv));
+  }
+}
+
+__global__ void df_to_fp64_kernel(const dfc* __restrict__ in, long long count, double2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const dfc v = in[i];
+    out[i] = make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
   }
 }
 
@@ -134,8 +224,43 @@ cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P
   ++g_launches;
   return cudaGetLastError();
 }
-cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, cudaStream_t st) {
-  scatter_pairs_df_kernel<<<Q * (Q + 1) / 2, 128, 0, st>>>(static_cast<const dfc*>(Rp), Q, nbox, lags);
+cudaError_t gram_expand_df(const void* lags_df, const int* lag_of_ij, int Q, int L, int nbox, const double* scale,
+                           void* A, float2* A32, cudaStream_t st) {
+  const long long n = (long long)Q * L;
+  long long blocks = (n * n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  gram_expand_df_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const dfc*>(lags_df), lag_of_ij, Q, L, nbox,
+                                                          scale, static_cast<dfc*>(A), A32);
+  ++g_launches;
+  return cudaGetLastError();
+}
+cudaError_t df_to_fp64(const void* in, long long count, double2* out, cudaStream_t st) {
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  df_to_fp64_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const dfc*>(in), count, out);
+  ++g_launches;
+  return cudaGetLastError();
+}
+bool gram_pairs_inverse_df_supported(int Lp1, int Lp2, int B1, int B2) {
+  return pairs_inverse_df_smem(Lp1, Lp2, B1, B2) <= (size_t)kPairsInverseDfMaxSmem;
+}
+cudaError_t gram_pairs_inverse_df(const void* S, int Q, int Lp1, int Lp2, const void* invT2, int B2, const void* inv1,
+                                  int B1, double2* lags, void* lags_df, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(pairs_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairsInverseDfMaxSmem);
+    attr_set = true;
+  }
+  pairs_inverse_df_kernel<<<Q * (Q + 1) / 2, 256, pairs_inverse_df_smem(Lp1, Lp2, B1, B2), st>>>(
+      static_cast<const dfc*>(S), Q, Lp1, Lp2, static_cast<const dfc*>(invT2), B2, static_cast<const dfc*>(inv1), B1,
+      lags, static_cast<dfc*>(lags_df));
+  ++g_launches;
+  return cudaGetLastError();
+}
+cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, void* lags_df, cudaStream_t st) {
+  scatter_pairs_df_kernel<<<Q * (Q + 1) / 2, 128, 0, st>>>(static_cast<const dfc*>(Rp), Q, nbox, lags,
+                                                           static_cast<dfc*>(lags_df));
   ++g_launches;
   return cudaGetLastError();
 }
@@ -162,18 +287,62 @@ __device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl)
   quick_two_sum(s, e, ah, al);
 }
 
-// Zb = A * Xb (the band products of the FP64 Rayleigh quotients) in double-float: A's FP64
-// entries split into two floats, the band vectors exact in FP32 (they come from the FP32 Ritz
-// block); one warp per row of A, only the band columns in use.  Zb written in FP64.
-template <int NBV>
-__global__ void __launch_bounds__(256) band_matvec_df_kernel(const double2* __restrict__ A,
+// an entry of A as double-float parts: FP64 storage is split here, double-float storage read as is
+__device__ __forceinline__ void split_entry(const double2& a, float& rh, float& rl, float& ih, float& il) {
+  rh = (float)a.x;
+  ih = (float)a.y;
+  rl = (float)(a.x - (double)rh);
+  il = (float)(a.y - (double)ih);
+}
+__device__ __forceinline__ void split_entry(const float4& a, float& rh, float& rl, float& ih, float& il) {
+  rh = a.x;
+  rl = a.y;
+  ih = a.z;
+  il = a.w;
+}
+
+// Zb = A * Xb (the band products of the FP64 Rayleigh quotients) in double-float: A's entries as
+// hi + lo float pairs, the band vectors exact in FP32 (they come from the FP32 Ritz block).  Four
+// warps share a row (interleaved 32-wide k slices), each lane accumulates the used band columns
+// (NBU, a compile-time count so the 2 NBU accumulator chains interleave) with the next A entry
+// already in flight; the warp partials are combined in a fixed order.  Zb written in FP64.
+constexpr int kBandKC = 512;      // k values of Xb staged per pass
+constexpr int kBandSplit = 4;     // warps per row
+constexpr int kBandRows = 2;      // rows per CTA (8 warps)
+
+template <int NBV, int NBU, typename TA>
+__device__ __forceinline__ void band_rows_accumulate(const TA* __restrict__ arow, const float2* xs, int kc, int k,
+                                                     float (&arh)[NBV], float (&arl)[NBV], float (&aih)[NBV],
+                                                     float (&ail)[NBV]) {
+  constexpr int STEP = 32 * kBandSplit;
+  if (k >= kc) return;
+  TA nxt = arow[k];
+  for (; k < kc; k += STEP) {
+    const TA cur = nxt;
+    if (k + STEP < kc) nxt = arow[k + STEP];
+    float ahx, alx, ahy, aly;
+    split_entry(cur, ahx, alx, ahy, aly);
+#pragma unroll
+    for (int c = 0; c < NBU; ++c) {
+      const float2 x = xs[k * NBV + c];
+      df_fma1(arh[c], arl[c], ahx, alx, x.x);     // Re += Re a Re x
+      df_fma1(aih[c], ail[c], ahx, alx, x.y);     // Im += Re a Im x
+      df_fma1(arh[c], arl[c], -ahy, -aly, x.y);   //      - Im a Im x
+      df_fma1(aih[c], ail[c], ahy, aly, x.x);     //      + Im a Re x
+    }
+  }
+}
+
+template <int NBV, typename TA>
+__global__ void __launch_bounds__(256) band_matvec_df_kernel(const TA* __restrict__ A,
                                                              const double2* __restrict__ Xb, int n,
                                                              const int* __restrict__ band_idx,
                                                              double2* __restrict__ Zb) {
-  constexpr int KC = 512;
-  __shared__ float2 xs[KC * NBV];
+  __shared__ float2 xs[kBandKC * NBV];
+  __shared__ float4 part[kBandRows][kBandSplit][NBV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r = blockIdx.x * 8 + warp;
+  const int rl = warp / kBandSplit, ks = warp % kBandSplit;
+  const int r = blockIdx.x * kBandRows + rl;
   int nbu = 0;
 #pragma unroll
   for (int c = 0; c < NBV; ++c)
@@ -181,8 +350,8 @@ __global__ void __launch_bounds__(256) band_matvec_df_kernel(const double2* __re
   float arh[NBV], arl[NBV], aih[NBV], ail[NBV];
 #pragma unroll
   for (int c = 0; c < NBV; ++c) arh[c] = arl[c] = aih[c] = ail[c] = 0.f;
-  for (int k0 = 0; k0 < n; k0 += KC) {
-    const int kc = min(KC, n - k0);
+  for (int k0 = 0; k0 < n; k0 += kBandKC) {
+    const int kc = min(kBandKC, n - k0);
     __syncthreads();
     for (int e = threadIdx.x; e < kc * NBV; e += blockDim.x) {
       const double2 v = Xb[(long long)k0 * NBV + e];
@@ -190,21 +359,18 @@ __global__ void __launch_bounds__(256) band_matvec_df_kernel(const double2* __re
     }
     __syncthreads();
     if (r < n) {
-      const double2* arow = A + (long long)r * n + k0;
-      for (int k = lane; k < kc; k += 32) {
-        const double2 a = arow[k];
-        const float ahx = (float)a.x, ahy = (float)a.y;
-        const float alx = (float)(a.x - (double)ahx), aly = (float)(a.y - (double)ahy);
-#pragma unroll
-        for (int c = 0; c < NBV; ++c) {
-          if (c < nbu) {
-            const float2 x = xs[k * NBV + c];
-            df_fma1(arh[c], arl[c], ahx, alx, x.x);     // Re += Re a Re x
-            df_fma1(arh[c], arl[c], -ahy, -aly, x.y);   //      - Im a Im x
-            df_fma1(aih[c], ail[c], ahx, alx, x.y);     // Im += Re a Im x
-            df_fma1(aih[c], ail[c], ahy, aly, x.x);     //      + Im a Re x
-          }
-        }
+      const TA* arow = A + (long long)r * n + k0;
+      const int k = ks * 32 + lane;
+      switch (nbu) {
+        case 1: band_rows_accumulate<NBV, 1>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 2: band_rows_accumulate<NBV, 2>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 3: band_rows_accumulate<NBV, 3>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 4: band_rows_accumulate<NBV, 4>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 5: band_rows_accumulate<NBV, 5>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 6: band_rows_accumulate<NBV, 6>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 7: band_rows_accumulate<NBV, 7>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 8: band_rows_accumulate<NBV, 8>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        default: break;
       }
     }
   }
@@ -218,19 +384,38 @@ __global__ void __launch_bounds__(256) band_matvec_df_kernel(const double2* __re
       df_add(aih[c], ail[c], ch, cl);
     }
   }
-  if (r < n && lane == 0) {
+  if (lane == 0) {
 #pragma unroll
-    for (int c = 0; c < NBV; ++c)
-      Zb[(long long)r * NBV + c] = make_double2((double)arh[c] + (double)arl[c], (double)aih[c] + (double)ail[c]);
+    for (int c = 0; c < NBV; ++c) part[rl][ks][c] = make_float4(arh[c], arl[c], aih[c], ail[c]);
+  }
+  __syncthreads();
+  // combine the k slices in a fixed order: one thread per (row, band column)
+  if (threadIdx.x < kBandRows * NBV) {
+    const int rr = threadIdx.x / NBV, c = threadIdx.x % NBV;
+    const int row = blockIdx.x * kBandRows + rr;
+    if (row < n) {
+      float4 acc = part[rr][0][c];
+#pragma unroll
+      for (int w = 1; w < kBandSplit; ++w) {
+        const float4 v = part[rr][w][c];
+        df_add(acc.x, acc.y, v.x, v.y);
+        df_add(acc.z, acc.w, v.z, v.w);
+      }
+      Zb[(long long)row * NBV + c] = make_double2((double)acc.x + (double)acc.y, (double)acc.z + (double)acc.w);
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t eig_band_matvec_df(const double2* A, const double2* Xb, int n, int nb, const int* band_idx, double2* Zb,
-                               cudaStream_t st) {
+cudaError_t eig_band_matvec_df(const void* A, bool a_df, const double2* Xb, int n, int nb, const int* band_idx,
+                               double2* Zb, cudaStream_t st) {
   if (nb != 8) return cudaErrorInvalidValue;
-  band_matvec_df_kernel<8><<<(n + 7) / 8, 256, 0, st>>>(A, Xb, n, band_idx, Zb);
+  const unsigned grid = (unsigned)((n + kBandRows - 1) / kBandRows);
+  if (a_df)
+    band_matvec_df_kernel<8, float4><<<grid, 256, 0, st>>>(static_cast<const float4*>(A), Xb, n, band_idx, Zb);
+  else
+    band_matvec_df_kernel<8, double2><<<grid, 256, 0, st>>>(static_cast<const double2*>(A), Xb, n, band_idx, Zb);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -75,6 +76,11 @@ struct pisco_plan_s {
   int gemm_tile = 0;    // CUDA-core block product tile: 0 automatic, 32 or 64
   bool tc_thin = false; // thin block products (n x m x m, m x m x n) on the tensor cores too
   bool tc_interp = false;  // last interpolation pass as a batched tensor-core GEMM
+  bool a_df = false;       // A holds double-float quadruples (double-float Gram route, unmasked)
+  void* lags_df = nullptr;
+  double2* A64 = nullptr;  // FP64 Gram built from the double-float one on request (debug accessor)
+  bool g_sep = false;      // 2D G(x) from KT by separable DFT passes instead of the dense lag GEMM
+  int *d_sep_rows = nullptr, *d_sep_b2 = nullptr;
   float *IAh = nullptr, *IAl = nullptr, *IBh = nullptr, *IBl = nullptr;
   float2* interpA = nullptr;  // the last axis's interpolation matrix (split into IAh/IAl)
   float *TAh = nullptr, *TAl = nullptr, *TBh = nullptr, *TBl = nullptr;  // their split operands
@@ -474,6 +480,10 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
       OP("gram_dft_df", apply_axis_df(pl->gB, pl->fwd_df[0], pl->S, AxisView{Q, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
       S = pl->S;
     }
+    if (pl->D == 2 && gram_pairs_inverse_df_supported(Lp[1], Lp[2], B[1], B[2])) {
+      OP("gram_pairs_df", gram_pairs_inverse_df(S, Q, Lp[1], Lp[2], pl->invT_df, B[2], pl->inv_df[1], B[1], pl->lags,
+                                                pl->lags_df, st));
+    } else {
     OP("gram_pair_products", gram_pair_products_df(S, Q, pl->nfreq, pl->P, st));
     OP("gram_dft_df", apply_axis_df(pl->P, pl->invT_df, pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
     if (pl->D == 3) {
@@ -482,10 +492,11 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
     } else {
       OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->Rp, AxisView{np, 1, Lp[1], B[1], B[2]}, st));
     }
-    OP("gram_scatter", gram_scatter_pairs_df(pl->Rp, Q, pl->nbox, pl->lags, st));
+    OP("gram_scatter", gram_scatter_pairs_df(pl->Rp, Q, pl->nbox, pl->lags, pl->lags_df, st));
+    }
     const int lag0 = (2 * pl->tau[0] * B[1] + 2 * pl->tau[1]) * B[2] + 2 * pl->tau[2];
     OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st));
-    OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st));
+    OP("gram_expand", gram_expand_df(pl->lags_df, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st));
     return PISCO_OK;
   }
   // forward zero-padded DFT of every channel: x, y, z
@@ -630,7 +641,7 @@ pisco_status run_eig(pisco_plan_s* pl) {
   OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
   const double2 zone = make_double2(1.0, 0.0), zzero = make_double2(0.0, 0.0);
   if (pl->gram_df)
-    OP("eig_rayleigh_df", eig_band_matvec_df(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
+    OP("eig_rayleigh_df", eig_band_matvec_df(pl->A, pl->a_df, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
   else
     OP("eig_rayleigh_fp64", eig_band_matvec(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
   (void)zone; (void)zzero;
@@ -657,6 +668,11 @@ pisco_status run_gfield(pisco_plan_s* pl) {
     OP("g_herk_tc", tc2_gemm(pl->tc_terms, n, n, pl->m, pl->UAh, pl->UAl, pl->UBh, pl->UBl, one, zero, pl->A32, n,
                              0.f, 0, 0, 1, nullptr, err, st));
     OP("g_collapse", gassembly_collapse(pl->A32, n, Q, pl->L, pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->KT, st));
+    if (pl->g_sep) {
+      OP("g_field_sep", gassembly_field_sep2(pl->KT, Q, pl->nlag, pl->d_sep_rows, pl->d_sep_b2, pl->gdft[1], Nr[1], B[1],
+                                             pl->gdft[2], B[2], Nr[2], (float)pl->L, pl->G, st));
+      return PISCO_OK;
+    }
     OP("g_field_tc", tc2_split_b(pl->KT, (int)QQ, 0, pl->nlag, (int)QQ, pl->KTh, tt ? pl->KTl : nullptr, st));
     OP("g_field_tc", tc2_gemm(pl->tc_terms, (int)pl->npix_red, (int)QQ, pl->nlag, pl->Eh, pl->El, pl->KTh, pl->KTl,
                               mone, zero, pl->G, (int)QQ, (float)pl->L, Q + 1, (int)QQ, pl->tc_splits_g, pl->tc_ws,
@@ -922,6 +938,8 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->gA, gA) && dalloc(pl, &pl->gB, gB);
   ok = ok && dalloc(pl, &pl->S, (size_t)Q * pl->nfreq) && dalloc(pl, &pl->P, (size_t)np * pl->nfreq);
   ok = ok && dalloc(pl, &pl->Rp, (size_t)np * pl->nbox) && dalloc(pl, &pl->lags, (size_t)Q * Q * pl->nbox);
+  pl->a_df = pl->gram_df && !pl->masked;
+  if (pl->a_df) ok = ok && dalloc(pl, reinterpret_cast<double2**>(&pl->lags_df), (size_t)Q * Q * pl->nbox);
   ok = ok && dalloc(pl, &pl->A, (size_t)n * n) && dalloc(pl, &pl->A32, (size_t)n * n);
   // eigensolver (sized for the largest block)
   const int M = pl->m_max;
@@ -962,7 +980,23 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
       ok = dalloc(pl, &pl->Ah, (size_t)n * k2n) && dalloc(pl, &pl->Al, lo_n * n * k2n + 1) &&
            dalloc(pl, &pl->Xh, (size_t)2 * tc2_np(pl->m_max) * k2n) &&
            dalloc(pl, &pl->Xl, lo_n * 2 * tc2_np(pl->m_max) * k2n + 1);
-    if (ok && pl->tc_g) {
+    pl->g_sep = pl->tc_g && pl->D == 2 && (p->flags & PISCO_FLAG_G_DENSE) == 0 &&
+                gassembly_field_sep2_supported(pl->nlag, Nr[1], B[1], Nr[2], B[2]);
+    if (ok && pl->g_sep) {
+      // lags grouped by row b1 (lag_ids ascend in b1, then b2)
+      std::vector<int> rows(B[1] + 1, 0), b2(pl->nlag);
+      for (int l = 0; l < pl->nlag; ++l) {
+        const int t = pl->lag_ids[l];
+        rows[(t / B[2]) % B[1] + 1]++;
+        b2[l] = t % B[2];
+      }
+      for (int r = 0; r < B[1]; ++r) rows[r + 1] += rows[r];
+      const size_t k2m2 = (size_t)tc2_k2p(pl->m_max);
+      ok = upload(pl, &pl->d_sep_rows, rows) && upload(pl, &pl->d_sep_b2, b2) &&
+           dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->UAh, (size_t)n * k2m2) &&
+           dalloc(pl, &pl->UAl, lo_n * n * k2m2 + 1) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m2) &&
+           dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m2 + 1);
+    } else if (ok && pl->tc_g) {
       const size_t k2l = (size_t)tc2_k2p(pl->nlag);
       ok = upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
            dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->Eh, (size_t)pl->npix_red * k2l) &&
@@ -1140,7 +1174,19 @@ pisco_status pisco_debug_buffer(pisco_plan_t pl, int which, void** dptr, size_t*
   const size_t n = pl->n;
   switch (which) {
     case PISCO_BUF_LAGS: *dptr = pl->lags; *bytes = sizeof(double2) * (size_t)pl->Q * pl->Q * pl->nbox; break;
-    case PISCO_BUF_GRAM: *dptr = pl->A; *bytes = sizeof(double2) * n * n; break;
+    case PISCO_BUF_GRAM:
+      if (pl->a_df) {
+        // the double-float Gram as FP64 (hi + lo is exact in FP64), built on request
+        if (!pl->A64 && !dalloc(pl, &pl->A64, n * n)) return PISCO_ERR_OOM;
+        if (df_to_fp64(pl->A, (long long)(n * n), pl->A64, pl->st) != cudaSuccess ||
+            cudaStreamSynchronize(pl->st) != cudaSuccess)
+          return PISCO_ERR_CUDA;
+        *dptr = pl->A64;
+      } else {
+        *dptr = pl->A;
+      }
+      *bytes = sizeof(double2) * n * n;
+      break;
     case PISCO_BUF_SIGNAL: *dptr = pl->U; *bytes = sizeof(float2) * n * pl->m; break;
     case PISCO_BUF_WEIGHTS: *dptr = pl->w; *bytes = sizeof(float) * pl->m; break;
     case PISCO_BUF_RITZ: *dptr = pl->ritz; *bytes = sizeof(double) * pl->m; break;
@@ -1243,6 +1289,11 @@ struct pisco_batch_s {
   cudaStream_t main = nullptr;   // private non-blocking stream: capture and graph launch
   cudaStream_t user = nullptr;   // the caller's stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // host-I/O graphs: recorded once every item's compute is done, before the device->host
+  // copies; the next host-I/O graph of another batch waits on it (compute chained, copies of
+  // one batch overlapping the compute of the next)
+  cudaEvent_t ev_compute = nullptr;
+  std::vector<cudaEvent_t> joinc;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> g_in;
@@ -1258,6 +1309,11 @@ struct pisco_batch_s {
   std::vector<float*> pend_eig;
 };
 
+// the compute-done event of the last host-I/O graph launched by any batch
+std::mutex g_chain_mu;
+cudaEvent_t g_chain_ev = nullptr;
+const pisco_batch_s* g_chain_owner = nullptr;
+
 static void batch_graph_reset(pisco_batch_s* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -1272,8 +1328,17 @@ void pisco_batch_destroy(pisco_batch_t b) {
   if (!b) return;
   if (b->main) cudaStreamSynchronize(b->main);
   batch_graph_reset(b);
+  {
+    std::lock_guard<std::mutex> lk(g_chain_mu);
+    if (g_chain_owner == b) {
+      g_chain_owner = nullptr;
+      g_chain_ev = nullptr;
+    }
+  }
   if (b->main) cudaStreamDestroy(b->main);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_compute) cudaEventDestroy(b->ev_compute);
+  for (auto e : b->joinc) if (e) cudaEventDestroy(e);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (auto* pl : b->items) pisco_destroy(pl);
   for (auto s : b->streams) if (s) cudaStreamDestroy(s);
@@ -1296,21 +1361,25 @@ pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_
   if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_compute, cudaEventDisableTiming) != cudaSuccess) {
     pisco_batch_destroy(b);
     return PISCO_ERR_CUDA;
   }
   for (int i = 0; i < count; ++i) {
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, evc = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evc, cudaEventDisableTiming) != cudaSuccess) {
       if (st) cudaStreamDestroy(st);
+      if (ev) cudaEventDestroy(ev);
       pisco_batch_destroy(b);
       return PISCO_ERR_CUDA;
     }
     b->streams.push_back(st);
     b->join.push_back(ev);
+    b->joinc.push_back(evc);
     pisco_params pi = params[i];
     pi.flags |= PISCO_FLAG_HOST_IO;
     pisco_plan_t pl = nullptr;
@@ -1386,7 +1455,18 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
       s = run_all(pl, pl->calib_stage, maps_dst, eig_dst);  // counts its launches from zero
       if (s != PISCO_OK) break;
       total_launches += g_launches;
+      if (host_io && (cudaEventRecord(b->joinc[i], st) != cudaSuccess ||
+                      cudaStreamWaitEvent(b->main, b->joinc[i], 0) != cudaSuccess)) { s = PISCO_ERR_CUDA; break; }
+    }
+    // an event-record node of the graph (external: visible to waits outside the capture)
+    if (s == PISCO_OK && host_io &&
+        cudaEventRecordWithFlags(b->ev_compute, b->main, cudaEventRecordExternal) != cudaSuccess)
+      s = PISCO_ERR_CUDA;
+    for (int i = 0; i < n && s == PISCO_OK; ++i) {
+      pisco_plan_s* pl = b->items[i];
+      cudaStream_t st = pl->st;
       if (host_io) {
+        float* eig_dst = eig && eig[i] ? pl->io_eig : nullptr;
         const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
         if (cudaMemcpyAsync(outp[i], pl->io_maps, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
         if (eig_dst && cudaMemcpyAsync(eig[i], pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost, st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
@@ -1415,7 +1495,16 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
       b->g_eig.push_back(eig ? eig[i] : nullptr);
     }
   }
-  if (b->gexec && cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+  if (b->gexec && host_io) {
+    std::lock_guard<std::mutex> lk(g_chain_mu);
+    if (g_chain_ev && g_chain_owner != b && cudaStreamWaitEvent(b->main, g_chain_ev, 0) != cudaSuccess)
+      return PISCO_ERR_CUDA;
+    if (cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+    g_chain_ev = b->ev_compute;
+    g_chain_owner = b;
+  } else if (b->gexec && cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) {
+    return PISCO_ERR_CUDA;
+  }
   if (order_user && (cudaEventRecord(b->ev_out, b->main) != cudaSuccess ||
                      cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess))
     return PISCO_ERR_CUDA;

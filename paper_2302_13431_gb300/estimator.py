@@ -50,12 +50,15 @@ class PiscoEstimator:
     block_pi: two-vector block power iteration with Rayleigh-Ritz (small-gap pixels).
     gram_df: the Gram's FFT route in double-float instead of FP64 arithmetic.
     tc_interp: the last interpolation pass as one batched split-TF32 tensor-core GEMM.
+    g_dense: with a tensor-core G(x) route in 2D, the dense lag product instead of the separable
+    DFT passes.
     """
 
     def __init__(self, grid, calib_shape, num_coils, tau, kernel_shape="ellipsoid", thr=0.05,
                  reduction=1, iters=30, seed=0, host_io=False, eig_block=0, eig_iters=0,
                  stream=None, precision="fp32", tc_splits=0, gemm_splits=0, masked_gram=False,
-                 block_pi=False, gemm_tile=0, gram_df=False, tc_interp=False):
+                 block_pi=False, gemm_tile=0, gram_df=False, tc_interp=False,
+                 g_dense=False):
         if not torch.cuda.is_available():
             raise RuntimeError("PiscoEstimator needs a CUDA GPU (no CPU fallback)")
         self.grid = tuple(int(g) for g in grid)
@@ -73,6 +76,8 @@ class PiscoEstimator:
             flags |= B.PISCO_FLAG_GRAM_DF
         if tc_interp:
             flags |= B.PISCO_FLAG_TC_INTERP
+        if g_dense:
+            flags |= B.PISCO_FLAG_G_DENSE
         self.params = B.make_params(self.grid, self.calib_shape, self.Q, tau, kernel_shape, thr,
                                     reduction, iters, seed, flags, eig_block, eig_iters, tc_splits,
                                     gemm_splits, gemm_tile)
