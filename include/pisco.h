@@ -216,7 +216,9 @@ pisco_status pisco_profile_entry(pisco_plan_t plan, int idx, const char** name, 
  * layouts of pisco_estimate (d_eig may be NULL, or hold NULL entries).  An item whose signal
  * dimension saturates its eigensolver block is re-run alone with a larger block.  Returns the
  * most severe item status.  The _host variant takes host pointers (pinned memory for full
- * copy bandwidth) and copies inside the graph.  pisco_batch_item exposes item i's plan for
+ * copy bandwidth): the host->device copies are enqueued on the batch's stream ahead of the graph,
+ * the device->host copies right after it (copy-engine copies that overlap the computation of
+ * the next host-I/O batch, which is ordered after this batch's computation).  pisco_batch_item exposes item i's plan for
  * pisco_plan_info / pisco_debug_buffer / pisco_get_stats (owned by the batch). */
 typedef struct pisco_batch_s* pisco_batch_t;
 pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_stream,
@@ -235,6 +237,12 @@ pisco_status pisco_batch_estimate_host(pisco_batch_t b, const void* const* h_cal
  * (PISCO_ERR_ARG for a second launch, or for a wait without a launch). */
 pisco_status pisco_batch_launch_host(pisco_batch_t b, const void* const* h_calib,
                                      void* const* h_maps, float* const* h_eig);
+/* pisco_batch_estimate split the same way: the batch is enqueued after the work already on the
+ * plan's (caller's) stream, that stream is made to wait for its completion, and the call
+ * returns without synchronising; pisco_batch_wait decodes the item statuses.  A caller keeps
+ * the GPU fed by launching the next batch object before waiting for this one. */
+pisco_status pisco_batch_launch(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,
+                                float* const* d_eig);
 pisco_status pisco_batch_wait(pisco_batch_t b, pisco_status* item_status);
 pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t* workspace_bytes);
 pisco_status pisco_batch_item(pisco_batch_t b, int i, pisco_plan_t* plan);

@@ -117,6 +117,8 @@ def load():
     lib.pisco_batch_estimate_host.restype = ctypes.c_int
     lib.pisco_batch_launch_host.argtypes = [vp, PP, PP, PP]
     lib.pisco_batch_launch_host.restype = ctypes.c_int
+    lib.pisco_batch_launch.argtypes = [vp, PP, PP, PP]
+    lib.pisco_batch_launch.restype = ctypes.c_int
     lib.pisco_batch_wait.argtypes = [vp, P(ctypes.c_int)]
     lib.pisco_batch_wait.restype = ctypes.c_int
     lib.pisco_batch_info.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)]
@@ -284,6 +286,12 @@ def pisco_batch_launch_host(batch, calibs, maps, eigs):
     """Enqueue a host-buffer batch call; the pointer arrays are kept alive by the caller."""
     return load().pisco_batch_launch_host(batch, _ptr_array(calibs), _ptr_array(maps),
                                           _ptr_array(eigs) if eigs is not None else None)
+
+
+def pisco_batch_launch(batch, calibs, maps, eigs):
+    """Enqueue a device-buffer batch call (ordered on the batch's caller stream)."""
+    return load().pisco_batch_launch(batch, _ptr_array(calibs), _ptr_array(maps),
+                                     _ptr_array(eigs) if eigs is not None else None)
 
 
 def pisco_batch_wait(batch, n):

@@ -1289,11 +1289,10 @@ struct pisco_batch_s {
   cudaStream_t main = nullptr;   // private non-blocking stream: capture and graph launch
   cudaStream_t user = nullptr;   // the caller's stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  // host-I/O graphs: recorded once every item's compute is done, before the device->host
-  // copies; the next host-I/O graph of another batch waits on it (compute chained, copies of
-  // one batch overlapping the compute of the next)
+  // host-I/O graphs: recorded after the graph (every item's compute done), before the
+  // device->host copies; the next host-I/O graph of another batch waits on it (compute
+  // chained, the copies of one batch overlapping the compute of the next)
   cudaEvent_t ev_compute = nullptr;
-  std::vector<cudaEvent_t> joinc;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> g_in;
@@ -1338,7 +1337,6 @@ void pisco_batch_destroy(pisco_batch_t b) {
   if (b->main) cudaStreamDestroy(b->main);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_compute) cudaEventDestroy(b->ev_compute);
-  for (auto e : b->joinc) if (e) cudaEventDestroy(e);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (auto* pl : b->items) pisco_destroy(pl);
   for (auto s : b->streams) if (s) cudaStreamDestroy(s);
@@ -1368,18 +1366,15 @@ pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_
   }
   for (int i = 0; i < count; ++i) {
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr, evc = nullptr;
+    cudaEvent_t ev = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&evc, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       if (st) cudaStreamDestroy(st);
-      if (ev) cudaEventDestroy(ev);
       pisco_batch_destroy(b);
       return PISCO_ERR_CUDA;
     }
     b->streams.push_back(st);
     b->join.push_back(ev);
-    b->joinc.push_back(evc);
     pisco_params pi = params[i];
     pi.flags |= PISCO_FLAG_HOST_IO;
     pisco_plan_t pl = nullptr;
@@ -1447,33 +1442,21 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
       cudaStream_t st = pl->st;
       if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
       const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
-      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                          st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
+      // host I/O: the host->device copies are issued outside the graph, ahead of it
+      if (!host_io && cudaMemcpyAsync(pl->calib_stage, in[i], cb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        s = PISCO_ERR_CUDA;
+        break;
+      }
       float2* maps_dst = host_io ? pl->io_maps : (float2*)outp[i];
       float* eig_dst = eig && eig[i] ? (host_io ? pl->io_eig : eig[i]) : nullptr;
       pl->ev_used = 0;
       s = run_all(pl, pl->calib_stage, maps_dst, eig_dst);  // counts its launches from zero
       if (s != PISCO_OK) break;
       total_launches += g_launches;
-      if (host_io && (cudaEventRecord(b->joinc[i], st) != cudaSuccess ||
-                      cudaStreamWaitEvent(b->main, b->joinc[i], 0) != cudaSuccess)) { s = PISCO_ERR_CUDA; break; }
-    }
-    // an event-record node of the graph (external: visible to waits outside the capture)
-    if (s == PISCO_OK && host_io &&
-        cudaEventRecordWithFlags(b->ev_compute, b->main, cudaEventRecordExternal) != cudaSuccess)
-      s = PISCO_ERR_CUDA;
-    for (int i = 0; i < n && s == PISCO_OK; ++i) {
-      pisco_plan_s* pl = b->items[i];
-      cudaStream_t st = pl->st;
-      if (host_io) {
-        float* eig_dst = eig && eig[i] ? pl->io_eig : nullptr;
-        const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
-        if (cudaMemcpyAsync(outp[i], pl->io_maps, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
-        if (eig_dst && cudaMemcpyAsync(eig[i], pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost, st) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
-      }
       if (cudaEventRecord(b->join[i], st) != cudaSuccess ||
           cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
     }
+    // host I/O: the copies stay outside the graph (issued around each launch)
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->main, &g);
     if (s != PISCO_OK || ec != cudaSuccess || !g) {
@@ -1496,12 +1479,31 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
     }
   }
   if (b->gexec && host_io) {
+    // inputs staged, compute chained after the previous host-I/O batch's compute, then this
+    // batch's output copies on its own stream (copy-engine copies overlap the next compute)
+    // the inputs first, so that they are staged while the previous batch still computes
+    for (int i = 0; i < n; ++i) {
+      pisco_plan_s* pl = b->items[i];
+      const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
+      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, cudaMemcpyHostToDevice, b->main) != cudaSuccess)
+        return PISCO_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lk(g_chain_mu);
     if (g_chain_ev && g_chain_owner != b && cudaStreamWaitEvent(b->main, g_chain_ev, 0) != cudaSuccess)
       return PISCO_ERR_CUDA;
-    if (cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+    if (cudaGraphLaunch(b->gexec, b->main) != cudaSuccess || cudaEventRecord(b->ev_compute, b->main) != cudaSuccess)
+      return PISCO_ERR_CUDA;
     g_chain_ev = b->ev_compute;
     g_chain_owner = b;
+    for (int i = 0; i < n; ++i) {
+      pisco_plan_s* pl = b->items[i];
+      const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
+      if (cudaMemcpyAsync(outp[i], pl->io_maps, mb, cudaMemcpyDeviceToHost, b->main) != cudaSuccess)
+        return PISCO_ERR_CUDA;
+      if (eig && eig[i] &&
+          cudaMemcpyAsync(eig[i], pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost, b->main) != cudaSuccess)
+        return PISCO_ERR_CUDA;
+    }
   } else if (b->gexec && cudaGraphLaunch(b->gexec, b->main) != cudaSuccess) {
     return PISCO_ERR_CUDA;
   }
@@ -1656,6 +1658,12 @@ pisco_status pisco_batch_launch_host(pisco_batch_t b, const void* const* h_calib
                                      float* const* h_eig) {
   if (!b || !h_calib || !h_maps || b->pending) return PISCO_ERR_ARG;
   return batch_launch(b, h_calib, h_maps, h_eig, true, false);
+}
+
+pisco_status pisco_batch_launch(pisco_batch_t b, const void* const* d_calib, void* const* d_maps,
+                                float* const* d_eig) {
+  if (!b || !d_calib || !d_maps || b->pending) return PISCO_ERR_ARG;
+  return batch_launch(b, d_calib, d_maps, d_eig, false, true);
 }
 
 pisco_status pisco_batch_wait(pisco_batch_t b, pisco_status* item_status) {

@@ -231,6 +231,15 @@ class PiscoBatch:
             raise B.PiscoError(st, "pisco_batch_estimate_host")
         return st
 
+    def launch(self, calibs, maps, eigs=None):
+        """Enqueue a device-buffer call (after the work on the batch's stream, which then waits for
+        it) and return at once; wait() decodes the statuses.  Two batch objects launched in turn
+        keep the GPU busy while the host prepares the next launch."""
+        st = B.pisco_batch_launch(self._b, [c.data_ptr() for c in calibs], [m.data_ptr() for m in maps],
+                                  [e.data_ptr() if e is not None else 0 for e in eigs] if eigs is not None else None)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_batch_launch")
+
     def launch_host(self, calibs, maps, eigs=None):
         """Enqueue a host-buffer call and return at once (pinned numpy buffers that stay untouched
         until wait()); two batch objects can then overlap one step's copies with the next step."""

@@ -95,3 +95,31 @@ def test_launch_and_wait_equal_the_blocking_host_call():
         a.wait()                # nothing launched
     a.close()
     b.close()
+
+
+def test_device_launch_and_wait_in_turn_equal_the_blocking_call():
+    """pisco_batch_launch / pisco_batch_wait on device buffers, two batch objects launched in turn
+    on one stream with a stream write between steps: every step equals the blocking call."""
+    dcal = [torch.from_numpy(c).cuda() for c in _inputs()]
+    a, b = PiscoBatch(SPECS), PiscoBatch(SPECS)
+    ref_m, ref_e = a.alloc_outputs()
+    a.estimate_into(dcal, ref_m, ref_e)
+    io = [a.alloc_outputs(), b.alloc_outputs()]
+    scratch = torch.zeros(1 << 20, device="cuda")
+    for step in range(5):
+        scratch.add_(1.0)  # work on the caller's stream between steps
+        (a, b)[step % 2].launch(dcal, *io[step % 2])
+        if step > 0:
+            (a, b)[(step - 1) % 2].wait()
+    (a, b)[4 % 2].wait()
+    torch.cuda.synchronize()
+    for k in range(2):
+        for i in range(len(SPECS)):
+            assert torch.equal(io[k][0][i], ref_m[i]) and torch.equal(io[k][1][i], ref_e[i])
+    assert float(scratch[0]) == 5.0
+    a.launch(dcal, *io[0])
+    with pytest.raises(B.PiscoError):
+        a.launch(dcal, *io[0])  # one call in flight per batch object
+    a.wait()
+    a.close()
+    b.close()
