@@ -218,6 +218,9 @@ NCU_TRAFFIC = {
     "eig_gemm_AX": (15700480, "ncu --set full, tc2_kernel<3,4>, A32 X 928x64x928 (head+tail operands)"),
     "g_field_tc": (10471936, "ncu --set full, tc2_kernel<3,2>, G = E K 4096x1024x105"),
     "g_herk_tc": (2871808, "ncu --set full, tc2_kernel<3,2>, U W U^H 928x928x64"),
+    "eig_gemm_thin_fp32": (601856, "ncu dram__bytes_read.sum + dram__bytes_write.sum, cgemm64_kernel<float>, "
+                                   "mean of 3 launches of the timed batched step (X^H Y, X R^-1 shapes, n = 928, "
+                                   "m = 64; 4-map batch, same per-map shapes as the 64-map workload)"),
 }
 
 
@@ -229,8 +232,11 @@ def n_lags(w):
     return len({(a[0] - b[0], a[1] - b[1]) for a in pts for b in pts})
 
 
-def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False):
-    """Algorithmic work per launch of one operation and its roofline."""
+def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=None):
+    """Algorithmic work of one operation and its roofline.  Ops made of one kernel launch per
+    product divide one product's work by the average launch time; ops whose profiled calls also
+    include operand-split kernels (tensor-core routes) divide one map's work by one map's time
+    (nmaps = maps in the profiled pass)."""
     Q, L = w["Q"], stats["filter_len"]
     n = Q * L
     m = stats["eig_block"]
@@ -238,6 +244,7 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False):
     npix = w["grid"][0] * w["grid"][1]
     total_ms, count = prof[op]
     avg_s = total_ms / count / 1e3
+    map_s = total_ms / nmaps / 1e3 if nmaps else avg_s
     terms = 1 if "1pass" in precision else 3
     tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
     tc_note = (f"tcgen05 kind::tf32, {terms} TF32 pass(es) per product (the tensor pipe executes "
@@ -246,18 +253,20 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False):
     if op == "eig_gemm_AX":
         work = 8.0 * n * n * m                       # complex MAC = 8 real flops
         if "eig" in precision:
-            return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
-                        note="complex GEMM A(n x n) X(n x m); " + tc_note)
+            prods = stats.get("eig_iters", 6) + 1    # orthogonal iteration + the Rayleigh-Ritz product
+            return dict(bound="tensor", achieved=work * prods / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                        note=f"complex GEMM A(n x n) X(n x m), {prods} per map (per-map work / per-map time, "
+                             "the one split of A included); " + tc_note)
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="FP32 CUDA-core complex GEMM A(n x n) X(n x m); peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
     if op == "g_field_tc":
         work = 8.0 * nr * Q * Q * n_lags(w)
-        return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+        return dict(bound="tensor", achieved=work / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
                     note="G[x][pq] = sum_l E[x][l] K[l][pq]: complex GEMM (N_r x |Lambda-Lambda|) by "
                          "(|Lambda-Lambda| x Q^2); " + tc_note)
     if op == "g_herk_tc":
         work = 8.0 * n * n * m
-        return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+        return dict(bound="tensor", achieved=work / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
                     note="P = U diag(w) U^H: complex GEMM (n x m) by (m x n); " + tc_note)
     if op == "eig_rayleigh_fp64":
         work = 8.0 * n * n * 16
@@ -278,7 +287,7 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False):
                     note="per-pixel normalisation after the tensor-core interpolation: maps read + write")
     if op == "interp_final_tc":
         work = 8.0 * Q * npix * (w["grid"][0] // w["reduction"])
-        return dict(bound="tensor", achieved=work / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+        return dict(bound="tensor", achieved=work / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
                     note="maps_q = M T_q, one batched complex GEMM (N x N_r) by (N_r x N) per coil, "
                          "B-operand split included; " + tc_note)
     if op == "eig_gemm_thin_fp32":
@@ -286,12 +295,30 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False):
         return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="CUDA-core complex block products (Y^H Y, Y R^-1, X^H Z, X V): 8 n m^2 flops each; "
                          "latency-bound at one map")
+    if op == "gram_pairs_df":
+        Lp = w["calib"][0] + 2 * w["tau"]
+        B = 4 * w["tau"] + 1
+        npair = Q * (Q + 1) // 2
+        cmacs = npair * (Lp * Lp + Lp * B * Lp + B * B * Lp)
+        return dict(bound="alu", achieved=8.0 * cmacs / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
+                    unit="TFLOP/s (FP64-equivalent)",
+                    note="Gram pair stage fused per coil pair (pair product + both inverse lag passes), "
+                         "FP64-equivalent flops against the nominal FP64 peak; computed in double-float FP32 pairs")
+    if op == "g_field_sep":
+        nr1, nr2 = w["grid"][0] // w["reduction"], w["grid"][1] // w["reduction"]
+        B = 4 * w["tau"] + 1
+        work = 8.0 * Q * Q * (n_lags(w) * nr2 + B * nr1 * nr2)
+        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                    note="G(x) lag sums as two separable DFT passes per coil pair (lags -> rows x columns, "
+                         "rows -> pixels); also writes the 33.5 MB pixel-major G")
     if op in ("gram_dft_df", "gram_dft_fp64"):
         Lp = w["calib"][0] + 2 * w["tau"]
         nc, B = w["calib"][0], 4 * w["tau"] + 1
         npair = Q * (Q + 1) // 2
         cmacs = Q * nc * Lp * nc + Q * Lp * Lp * nc + npair * Lp * B * Lp + npair * B * B * Lp
         passes = 4
+        if "gram_pairs_df" in prof:  # the inverse passes run inside the fused pair stage
+            cmacs, passes = Q * nc * Lp * nc + Q * Lp * Lp * nc, 2
         return dict(bound="alu", achieved=8.0 * cmacs / passes / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
                     unit="TFLOP/s (FP64-equivalent)",
                     note="Gram DFT passes: FP64-equivalent flops per pass against the nominal FP64 peak"
@@ -475,7 +502,7 @@ def run_gpu(args):
     peaks = _peaks()
     stages = {}
     for op in prof:
-        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"], tuned.get("tc_interp", False))
+        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"], tuned.get("tc_interp", False), nprof)
         if r.get("achieved") is not None and r.get("peak"):
             r["frac"] = r["achieved"] / r["peak"]
         r["ms_per_map"] = prof[op][0] / nprof
