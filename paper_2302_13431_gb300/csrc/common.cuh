@@ -172,6 +172,10 @@ cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st)
 // inverse lag passes, lag table lags[(p,q)][B1*B2] for p <= q in FP64 and in double-float
 constexpr int kPairsInverseDfMaxSmem = 200 * 1024;
 bool gram_pairs_inverse_df_supported(int Lp1, int Lp2, int B1, int B2);
+// 2D double-float forward stage fused per coil: S[q][Lp1][Lp2] from calib[q][Nc1][Nc2]
+bool gram_forward_df_supported(int Nc1, int Nc2, int Lp1, int Lp2);
+cudaError_t gram_forward_df(const float2* calib, int Q, int Nc1, int Nc2, const void* fwdT2, int Lp2, const void* fwd1,
+                            int Lp1, void* S, cudaStream_t st);
 cudaError_t gram_pairs_inverse_df(const void* S, int Q, int Lp1, int Lp2, const void* invT2, int B2, const void* inv1,
                                   int B1, double2* lags, void* lags_df, cudaStream_t st);
 

@@ -158,6 +158,52 @@ __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __rest
   }
 }
 
+// 2D forward stage of the double-float Gram, fused per coil: the zero-padded DFT of one coil's
+// calibration along the contiguous axis (Nc2 -> Lp2), then along axis 1 (Nc1 -> Lp1), with the
+// calibration, the intermediate and both tables in shared memory.  Each output accumulates its
+// terms in the order of the unfused axis passes (bitwise the same spectrum).
+// fwdT2: [Nc2][Lp2] (transposed), fwd1: [Lp1][Nc1]; S: [Q][Lp1][Lp2].
+__global__ void __launch_bounds__(256) forward_df_kernel(const float2* __restrict__ calib, int Nc1, int Nc2,
+                                                         const dfc* __restrict__ fwdT2, int Lp2,
+                                                         const dfc* __restrict__ fwd1, int Lp1, dfc* __restrict__ S) {
+  extern __shared__ dfc fsm[];
+  dfc* T = fsm;                                  // [Nc1][Lp2]
+  dfc* m2 = T + Nc1 * Lp2;                       // [Nc2][Lp2]
+  dfc* m1 = m2 + Nc2 * Lp2;                      // [Lp1][Nc1]
+  float2* cs = reinterpret_cast<float2*>(m1 + Lp1 * Nc1);  // [Nc1][Nc2]
+  const int q = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float2* cq = calib + (long long)q * Nc1 * Nc2;
+  for (int i = tid; i < Nc1 * Nc2; i += nt) cs[i] = cq[i];
+  for (int i = tid; i < Nc2 * Lp2; i += nt) m2[i] = fwdT2[i];
+  for (int i = tid; i < Lp1 * Nc1; i += nt) m1[i] = fwd1[i];
+  __syncthreads();
+  for (int o = tid; o < Nc1 * Lp2; o += nt) {
+    const int x1 = o / Lp2, f2 = o % Lp2;
+    const float2* crow = cs + x1 * Nc2;
+    dfc acc{0.f, 0.f, 0.f, 0.f};
+    for (int x2 = 0; x2 < Nc2; ++x2) {
+      const float2 v = crow[x2];
+      df_cfma(acc, m2[x2 * Lp2 + f2], dfc{v.x, 0.f, v.y, 0.f});
+    }
+    T[o] = acc;
+  }
+  __syncthreads();
+  dfc* out = S + (long long)q * Lp1 * Lp2;
+  for (int o = tid; o < Lp1 * Lp2; o += nt) {
+    const int f1 = o / Lp2, f2 = o % Lp2;
+    const dfc* mrow = m1 + f1 * Nc1;
+    dfc acc{0.f, 0.f, 0.f, 0.f};
+    for (int x1 = 0; x1 < Nc1; ++x1) df_cfma(acc, mrow[x1], T[x1 * Lp2 + f2]);
+    out[o] = acc;
+  }
+}
+
+size_t forward_df_smem(int Nc1, int Nc2, int Lp1, int Lp2) {
+  return ((size_t)Nc1 * Lp2 + (size_t)Nc2 * Lp2 + (size_t)Lp1 * Nc1) * sizeof(dfc) +
+         (size_t)Nc1 * Nc2 * sizeof(float2);
+}
+
 size_t pairs_inverse_df_smem(int Lp1, int Lp2, int B1, int B2) {
   return ((size_t)Lp1 * (Lp2 | 1) + (size_t)Lp1 * B2 + (size_t)Lp2 * B2 + (size_t)B1 * Lp1) * sizeof(dfc);
 }
@@ -239,6 +285,21 @@ cudaError_t df_to_fp64(const void* in, long long count, double2* out, cudaStream
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   df_to_fp64_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const dfc*>(in), count, out);
+  ++g_launches;
+  return cudaGetLastError();
+}
+bool gram_forward_df_supported(int Nc1, int Nc2, int Lp1, int Lp2) {
+  return forward_df_smem(Nc1, Nc2, Lp1, Lp2) <= (size_t)kPairsInverseDfMaxSmem;
+}
+cudaError_t gram_forward_df(const float2* calib, int Q, int Nc1, int Nc2, const void* fwdT2, int Lp2, const void* fwd1,
+                            int Lp1, void* S, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(forward_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairsInverseDfMaxSmem);
+    attr_set = true;
+  }
+  forward_df_kernel<<<Q, 256, forward_df_smem(Nc1, Nc2, Lp1, Lp2), st>>>(
+      calib, Nc1, Nc2, static_cast<const dfc*>(fwdT2), Lp2, static_cast<const dfc*>(fwd1), Lp1, static_cast<dfc*>(S));
   ++g_launches;
   return cudaGetLastError();
 }

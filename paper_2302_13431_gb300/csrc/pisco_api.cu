@@ -473,8 +473,12 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   if (pl->gram_df) {
     // the same passes in double-float arithmetic (FP64 storage reused; lags written in FP64)
     const int np = pl->npairs;
-    OP("gram_dft_df", apply_axis_c2df(calib, pl->fwdT_df, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
-    OP("gram_dft_df", apply_axis_df(pl->gA, pl->fwd_df[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
+    if (pl->D == 2 && gram_forward_df_supported(Nc[1], Nc[2], Lp[1], Lp[2])) {
+      OP("gram_dft_df", gram_forward_df(calib, Q, Nc[1], Nc[2], pl->fwdT_df, Lp[2], pl->fwd_df[1], Lp[1], pl->gB, st));
+    } else {
+      OP("gram_dft_df", apply_axis_c2df(calib, pl->fwdT_df, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gA, pl->fwd_df[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
+    }
     const void* S = pl->gB;
     if (pl->D == 3) {
       OP("gram_dft_df", apply_axis_df(pl->gB, pl->fwd_df[0], pl->S, AxisView{Q, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
