@@ -117,9 +117,6 @@ cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_r
                      cudaStream_t st);
 cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, int m, float2* X,
                      cudaStream_t st);
-cudaError_t eig_chol_inv_warp(const float2* Gm, int m, const float* dscale, float shift_rel,
-                              const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
-                              cudaStream_t st);
 cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, float shift_rel,
                                  const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
                                  cudaStream_t st);

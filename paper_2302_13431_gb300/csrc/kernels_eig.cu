@@ -365,123 +365,6 @@ __global__ void __launch_bounds__(256) chol_inv_blocked_kernel(const float2* __r
   if (tid == 0 && s_clamp && status) atomicOr(&status->flags, (int)ST_CHOL);
 }
 
-// Single-warp Cholesky-QR factor (m <= 96): same inputs, scaling, shift and floor rules as
-// chol_inv_blocked_kernel and the same outputs (Rinv = D^-1 L^-H, diag(R)).  One warp owns the
-// whole factorisation, so its m pivot steps are ordered by __syncwarp only (no block
-// barriers): the right-looking update touches the lower triangle with lanes striding the
-// rows, and L^-1 is formed row by row with lanes striding the columns.
-__global__ void __launch_bounds__(32) chol_inv_warp_kernel(const float2* __restrict__ Gm, int m,
-                                                           const float* __restrict__ dscale,
-                                                           float shift_rel,
-                                                           const float* __restrict__ acc_in,
-                                                           float2* __restrict__ Rinv,
-                                                           float* __restrict__ diagR,
-                                                           DevStatus* status) {
-  extern __shared__ float2 sm[];
-  float2* A = sm;                                    // m*m (lower triangle: L)
-  float2* Li = A + m * m;                            // m*m (lower triangle: L^-1)
-  float* ds = reinterpret_cast<float*>(Li + m * m);  // m
-  float* pv = ds + m;                                // m
-  const int lane = threadIdx.x;
-  float mx = 0.f;
-  if (dscale)
-    for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(dscale[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  for (int i = lane; i < m; i += 32) {
-    float d = 1.f;
-    if (dscale) d = fminf(fmaxf(fmaxf(fabsf(dscale[i]), 1e-6f * mx), 1e-18f), 1e18f);
-    if (!(d > 0.f) || !(d < 1e30f)) d = 1.f;
-    ds[i] = d;
-  }
-  __syncwarp();
-  float md = 0.f, tr = 0.f;
-  for (int r = 0; r < m; ++r) {
-    const float dr = ds[r];
-    for (int c = lane; c <= r; c += 32) {
-      const float2 g = Gm[r * m + c];
-      const float sc = 1.f / (dr * ds[c]);
-      A[r * m + c] = make_float2(g.x * sc, g.y * sc);
-      if (c == r) { md = fmaxf(md, g.x * sc); tr += g.x * sc; }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
-    tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  }
-  const float shift = shift_rel * tr;
-  const float floor_piv = (md + shift > 1e-30f) ? (md + shift) * 1e-12f : 1.0f;
-  __syncwarp();
-  int clamped = 0;
-  for (int j = 0; j < m; ++j) {
-    const float d = A[j * m + j].x + shift;
-    const bool clamp = !(d > floor_piv);
-    clamped |= clamp;
-    const float piv = sqrtf(clamp ? floor_piv : d);
-    const float inv = 1.f / piv;
-    for (int i = j + 1 + lane; i < m; i += 32) {
-      const float2 v = A[i * m + j];
-      A[i * m + j] = make_float2(v.x * inv, v.y * inv);
-    }
-    if (lane == 0) pv[j] = piv;
-    __syncwarp();
-    // trailing lower triangle: rows i > j (lanes stride i), columns j < k <= i
-    for (int i = j + 1 + lane; i < m; i += 32) {
-      const float2 a = A[i * m + j];
-      for (int k = j + 1; k <= i; ++k) {
-        const float2 b = A[k * m + j];
-        float2 g = A[i * m + k];
-        const float2 p = cmulc(a, b);
-        g.x -= p.x; g.y -= p.y;
-        A[i * m + k] = g;
-      }
-    }
-    __syncwarp();
-  }
-  // L^-1 row by row: Li[r][c] = (delta_rc - sum_{c<=k<r} L[r][k] Li[k][c]) / L[r][r]
-  for (int r = 0; r < m; ++r) {
-    const float di = 1.f / pv[r];
-    for (int c = lane; c <= r; c += 32) {
-      float2 acc = make_float2(r == c ? 1.f : 0.f, 0.f);
-      for (int k = c; k < r; ++k) {
-        const float2 l = A[r * m + k];
-        const float2 x = Li[k * m + c];
-        acc.x -= l.x * x.x - l.y * x.y;
-        acc.y -= l.x * x.y + l.y * x.x;
-      }
-      Li[r * m + c] = make_float2(acc.x * di, acc.y * di);
-    }
-    __syncwarp();
-  }
-  for (int i = lane; i < m; i += 32) diagR[i] = pv[i] * ds[i] * (acc_in ? acc_in[i] : 1.f);
-  // Rinv[r][c] = conj(Li[c][r]) / d_r (upper triangular)
-  for (int r = 0; r < m; ++r) {
-    const float id = 1.f / ds[r];
-    for (int c = lane; c < m; c += 32) {
-      float2 v = make_float2(0.f, 0.f);
-      if (c >= r) { const float2 x = Li[c * m + r]; v = make_float2(x.x * id, -x.y * id); }
-      Rinv[r * m + c] = v;
-    }
-  }
-  if (clamped && status) atomicOr(&status->flags, (int)ST_CHOL);
-}
-
-cudaError_t eig_chol_inv_warp(const float2* Gm, int m, const float* dscale, float shift_rel,
-                              const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
-                              cudaStream_t st) {
-  if (m > 96) return cudaErrorInvalidValue;
-  const size_t smem = 2 * (size_t)m * m * sizeof(float2) + 2 * m * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(chol_inv_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
-  chol_inv_warp_kernel<<<1, 32, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, Rinv, diagR, status);
-  ++g_launches;
-  return cudaGetLastError();
-}
-
 // One thread per row r: x L^H = y with y = Y[r] D^-1, i.e. for c = 0..m-1
 //   x_c = (y_c - sum_{k<c} x_k conj(L[c][k])) / L[c][c].
 template <int MP>

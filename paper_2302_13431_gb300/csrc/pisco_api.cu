@@ -38,7 +38,6 @@ struct pisco_plan_s {
   int N[3], Nc[3], tau[3], Nr[3], Lp[3], B[3];
   int Q = 0, L = 0, n = 0, nbox = 0, npairs = 0;
   int m = 0, m_max = 0, eig_iters = 10;
-  int chol_variant = 1;  // 1: blocked 256-thread factor (default), 0: single-warp factor
   long long npix = 0, npix_red = 0, nfreq = 0;
   std::vector<int> lam;        // L x 3 (z,y,x)
   std::vector<int> lag_of_ij;  // L x L
@@ -559,10 +558,7 @@ pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, co
   else
     OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
   if (m <= 96) {
-    if (pl->chol_variant == 1)
-      OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
-    else
-      OP("eig_chol", eig_chol_inv_warp(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
+    OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
     if (pl->tc_thin)
       OP("eig_gemm_thin_tc", thin_product(pl, false, Yin, pl->Rinv, Xout));
     else
@@ -902,7 +898,6 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     delete pl;
     return PISCO_ERR_CUDA;
   }
-  if (const char* cv = getenv("PISCO_CHOL")) pl->chol_variant = atoi(cv);
 
   const int Q = pl->Q, n = pl->n, np = pl->npairs;
   const int* Nc = pl->Nc;

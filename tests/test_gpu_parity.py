@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, stage by stage and
 end to end, on seeded synthetic data.
 
-Tolerances (derived from the arithmetic; the design doc lists them):
+Tolerances (derived from the arithmetic of each stage):
   * Gram (FP64 on both sides): max |A_gpu - A_oracle| <= 1e-11 * max|A|.
   * signal dimension k: exact (integer decision taken on FP64 Rayleigh quotients).
   * signal projector U U^H (FP32 subspace iteration): max abs entry error <= 2e-5.
