@@ -300,7 +300,7 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
         B = 4 * w["tau"] + 1
         npair = Q * (Q + 1) // 2
         cmacs = npair * (Lp * Lp + Lp * B * Lp + B * B * Lp)
-        return dict(bound="alu", achieved=8.0 * cmacs / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
+        return dict(bound="alu", achieved=8.0 * cmacs / map_s / 1e12, peak=FP64_PEAK_TFLOPS,
                     unit="TFLOP/s (FP64-equivalent)",
                     note="Gram pair stage fused per coil pair (pair product + both inverse lag passes), "
                          "FP64-equivalent flops against the nominal FP64 peak; computed in double-float FP32 pairs")
@@ -308,7 +308,7 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
         nr1, nr2 = w["grid"][0] // w["reduction"], w["grid"][1] // w["reduction"]
         B = 4 * w["tau"] + 1
         work = 8.0 * Q * Q * (n_lags(w) * nr2 + B * nr1 * nr2)
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+        return dict(bound="alu", achieved=work / map_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="G(x) lag sums as two separable DFT passes per coil pair (lags -> rows x columns, "
                          "rows -> pixels); also writes the 33.5 MB pixel-major G")
     if op in ("gram_dft_df", "gram_dft_fp64"):
