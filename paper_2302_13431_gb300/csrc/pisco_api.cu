@@ -1292,6 +1292,8 @@ struct pisco_batch_s {
   // device->host copies; the next host-I/O graph of another batch waits on it (compute
   // chained, the copies of one batch overlapping the compute of the next)
   cudaEvent_t ev_compute = nullptr;
+  cudaStream_t in_st = nullptr;  // host-I/O input copies (kept apart from the output copies)
+  cudaEvent_t ev_staged = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> g_in;
@@ -1336,6 +1338,11 @@ void pisco_batch_destroy(pisco_batch_t b) {
   if (b->main) cudaStreamDestroy(b->main);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_compute) cudaEventDestroy(b->ev_compute);
+  if (b->in_st) {
+    cudaStreamSynchronize(b->in_st);
+    cudaStreamDestroy(b->in_st);
+  }
+  if (b->ev_staged) cudaEventDestroy(b->ev_staged);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (auto* pl : b->items) pisco_destroy(pl);
   for (auto s : b->streams) if (s) cudaStreamDestroy(s);
@@ -1359,7 +1366,9 @@ pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_
       cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_compute, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_compute, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->in_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_staged, cudaEventDisableTiming) != cudaSuccess) {
     pisco_batch_destroy(b);
     return PISCO_ERR_CUDA;
   }
@@ -1480,13 +1489,18 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
   if (b->gexec && host_io) {
     // inputs staged, compute chained after the previous host-I/O batch's compute, then this
     // batch's output copies on its own stream (copy-engine copies overlap the next compute)
-    // the inputs first, so that they are staged while the previous batch still computes
+    // the inputs first, on their own stream (not queued behind this batch's pending output
+    // copies), so that they are staged while the previous batch still computes
+    if (cudaEventRecord(b->ev_staged, b->main) != cudaSuccess || cudaStreamWaitEvent(b->in_st, b->ev_staged, 0) != cudaSuccess)
+      return PISCO_ERR_CUDA;
     for (int i = 0; i < n; ++i) {
       pisco_plan_s* pl = b->items[i];
       const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
-      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, cudaMemcpyHostToDevice, b->main) != cudaSuccess)
+      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, cudaMemcpyHostToDevice, b->in_st) != cudaSuccess)
         return PISCO_ERR_CUDA;
     }
+    if (cudaEventRecord(b->ev_staged, b->in_st) != cudaSuccess || cudaStreamWaitEvent(b->main, b->ev_staged, 0) != cudaSuccess)
+      return PISCO_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_chain_mu);
     if (g_chain_ev && g_chain_owner != b && cudaStreamWaitEvent(b->main, g_chain_ev, 0) != cudaSuccess)
       return PISCO_ERR_CUDA;
