@@ -85,7 +85,7 @@ struct AxisView {
   int n_in;          // transformed axis length on input
   int n_out;         // transformed axis length on output
   long long inner;   // product of the axis lengths after the transformed axis
-  int pixel_major;   // 1 (needs outer == 1): write out[(o*inner + ii)*batch + b] instead
+  int pixel_major = 0;  // 1 (needs outer == 1): write out[(o*inner + ii)*batch + b] instead
   int mt = 0;        // 1: the matrix is stored transposed, M[i][o] ([n_in][n_out]); for
                      // inner == 1 passes this makes a warp's matrix reads contiguous
 };
