@@ -38,7 +38,6 @@ WORKLOAD_DESC = ("2D 256x256 grid, Q=32, 32x32 centred calibration, ellipsoidal 
 METRIC = "maps/s (2D 256x256 Q=32 PISCO map sets per second)"
 N_CASES = 8
 L2_FLUSH_BYTES = 256 << 20
-ORACLE_PIX_STRIDE = 8   # the CPU sample runs the per-pixel stages on every 8th reduced pixel
 
 # measured peaks (generated file) and nominal unit counts (GB300: 152 SMs, 2070 MHz)
 SMS, SM_MAX_MHZ = 152, 2070.0
@@ -143,64 +142,68 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-# CPU oracle (bounded sample of one map)
+# CPU oracle: whole map sets of the workload on the host cores
 # ------------------------------------------------------------------------------------------
-def oracle_sample_seconds(calib):
-    """Time the FP64 oracle on one map of the workload: Gram/SVD and interpolation in full,
-    the per-pixel stages (G(x) = H^H H, power iteration, phase) on every
-    ORACLE_PIX_STRIDE-th reduced pixel, extrapolated to the full reduced grid.  Returns the
-    estimated seconds per map and the measured seconds."""
-    from oracle import pisco_oracle as O
+ORACLE_MAPS = 3   # whole map sets the GPU arm's cpu_baseline leg runs (and checks the GPU against)
+
+
+def make_cases(rank):
+    from paper_2302_13431_gb300.phantoms import make_case
     w = WORKLOAD
-    red = tuple(g // w["reduction"] for g in w["grid"])
-    t0 = time.perf_counter()
-    lam = O.kernel_support((w["tau"],) * 2, w["shape"])
-    C = O.calibration_matrix(calib, lam, rows="full")
-    Vn, Us, sig = O.nullspace_svd(C, w["thr"])
-    t1 = time.perf_counter()
-    xs = O.grid_points(red)
-    sel = np.arange(0, xs.shape[0], ORACLE_PIX_STRIDE)
-    G = O.G_direct(Vn, lam, w["Q"], xs[sel])
-    v0 = O.start_vectors(0, xs.shape[0], w["Q"])[sel]
-    v, lmb, res = O.power_iteration(G, v0, w["iters"], lam.shape[0])
-    y = O.apodised_lowres(calib, xs[sel])
-    va = O.phase_align(v, y)
-    t2 = time.perf_counter()
-    full = np.zeros((xs.shape[0], w["Q"]), complex)
-    full[sel] = va
-    maps = O.normalize_maps(O.sinc_interp(full, red, w["grid"]))
-    t3 = time.perf_counter()
-    est = (t1 - t0) + (t2 - t1) * ORACLE_PIX_STRIDE + (t3 - t2)
-    return est, t3 - t0
+    return [make_case(w["grid"], w["Q"], w["calib"], seed=sd, phase="poly4") for sd in rank_seeds(rank)]
 
 
-def oracle_sample_desc():
-    return (f"FP64 numpy oracle on one map of the workload: C + SVD + interpolation in full, "
-            f"per-pixel G(x)/power iteration/phase on 1/{ORACLE_PIX_STRIDE} of the 4096 reduced "
-            f"pixels, time extrapolated to the full reduced grid")
+def oracle_whole_maps(calibs, pool=None):
+    """The FP64 oracle (oracle/pisco_oracle.py, every stage, no sampling, no extrapolation) on each
+    calibration block, its per-pixel stages spread over a pool of single-threaded host processes.
+    Returns (results, seconds per map, worker count)."""
+    from oracle import runner
+    w = WORKLOAD
+    own = pool is None
+    if own:
+        pool = runner.make_pool()
+    try:
+        refs = [runner.estimate_parallel(c, w["grid"], w["tau"], shape=w["shape"], thr=w["thr"],
+                                         reduction=w["reduction"], iters=w["iters"], seed=0, pool=pool[0],
+                                         workers=pool[1]) for c in calibs]
+    finally:
+        if own:
+            pool[0].close()
+            pool[0].join()
+    return refs, [r["seconds"] for r in refs], pool[1]
+
+
+def oracle_desc(nmaps, workers):
+    return (f"FP64 numpy oracle, {nmaps} whole map set(s) of the workload (explicit C, FP64 SVD, per-pixel "
+            f"G(x) = H^H H, power iteration, phase, sinc interpolation, normalisation; no sampling, no "
+            f"extrapolation), per-pixel stages on {workers} single-threaded host processes")
 
 
 def run_reference(args):
+    """The oracle as the reference arm: one whole map set per step, timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import runner
     calibs = make_inputs(0)
-    for i in range(args.warmup):
-        oracle_sample_seconds(calibs[i % N_CASES])
-    tot_est, tot_meas = 0.0, 0.0
-    for i in range(args.steps):
-        e, m = oracle_sample_seconds(calibs[i % N_CASES])
-        tot_est += e
-        tot_meas += m
-    value = args.steps / tot_est
+    pool = runner.make_pool()
+    try:
+        oracle_whole_maps([calibs[i % N_CASES] for i in range(args.warmup)], pool)
+        t0 = time.perf_counter()
+        _, secs, workers = oracle_whole_maps([calibs[i % N_CASES] for i in range(args.steps)], pool)
+        wall = time.perf_counter() - t0
+    finally:
+        pool[0].close()
+        pool[0].join()
+    value = args.steps / sum(secs)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "maps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tot_est / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC},
-        "cpu_baseline": {"value": value, "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": oracle_sample_desc(), "measured_s": tot_meas},
+        "cpu_baseline": {"value": value, "unit": "maps/s", "cores": workers, "kind": "oracle",
+                         "sample": oracle_desc(1, workers) + " per step", "timed_s": wall},
         "e2e": {"value": value, "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -381,7 +384,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2302_13431_gb300.estimator import PiscoBatch, PiscoEstimator
     w = WORKLOAD
-    calibs_h = make_inputs(rank)
+    cases = make_cases(rank)
+    calibs_h = [c.calib for c in cases]
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
     red = tuple(g // w["reduction"] for g in w["grid"])
     nr = red[0] * red[1]
@@ -460,6 +464,10 @@ def run_gpu(args):
     tot_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     value = whole_job_rate(nb * args.steps, world, tot_ms)
     binfo = batch.info()
+    # every item of both batch objects must have succeeded; the first maps go to the accuracy check
+    statuses = list(pair[0].last_item_status) + list(pair[1].last_item_status)
+    n_check = min(ORACLE_MAPS, nb)
+    check_out = [(bmaps[i].cpu().numpy(), beigs[i].cpu().numpy()) for i in range(n_check)]
 
     # ---- end to end: host buffers in and out, copies inside the timed region ----
     # two batch objects in flight (step s's device->host copies overlap step s+1's estimates),
@@ -521,7 +529,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "precision": ("FP64 Gram and FP64 threshold split of the nullspace; " +
+        "precision": (("double-float (FP32 pairs, ~48-bit) Gram" if tuned.get("gram_df") else "FP64 Gram") +
+                      " and FP64-certified threshold split of the nullspace; " +
                       {"fp32": "FP32 CUDA-core products elsewhere"}.get(
                           tuned["precision"], "split-precision TF32 tensor-core products (FP32 accumulate) for "
                           + ("G(x) assembly and the eigensolver block products" if "eig" in tuned["precision"]
@@ -544,7 +553,7 @@ def run_gpu(args):
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
                                                       f"{'/df' if r.get('gram_df') else ''}"
                                                       f"{'/ti' if r.get('tc_interp') else ''}":
-                                                      round(r["ms"], 3) for r in tune_table}),
+                                                      (round(r["ms"], 3) if r["ms"] is not None else "rejected") for r in tune_table}),
         "wall_s": t_wall,
         "gpu_launches": int(binfo["launches"]) * args.steps,
         "e2e": {"value": e2e_value, "unit": "maps/s",
@@ -559,14 +568,31 @@ def run_gpu(args):
         "stages": {k: stages[k] for k in sorted(stages, key=lambda k: -stages[k]["ms_per_map"])},
         "workspace_bytes_batch": binfo["workspace_bytes"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_s = 3
-        tot = 0.0
-        for i in range(n_s):
-            e, _ = oracle_sample_seconds(calibs_h[i % N_CASES])
-            tot += e
-        line["cpu_baseline"] = {"value": n_s / tot, "unit": "maps/s", "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": oracle_sample_desc() + f"; {n_s} maps"}
+    line["item_status_counts"] = {str(k): statuses.count(k) for k in sorted(set(statuses))}
+    failed = [k for k in statuses if k != 0]
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle on whole map sets: the CPU baseline (N=1) and the accuracy of the timed route
+        from oracle import runner
+        refs, secs, workers = oracle_whole_maps([c.calib for c in cases[:n_check]])
+        errs = [runner.gated_errors(mo, eo, ref, cases[i].rho, w["reduction"])
+                for i, ((mo, eo), ref) in enumerate(zip(check_out, refs))]
+        ks = [r["k"] for r in refs]
+        line["accuracy"] = {
+            "map_err": max(e["map_err"] for e in errs), "eig_err": max(e["eig_err"] for e in errs),
+            "gates": {"map_err": 1e-4, "eig_err": 1e-5},
+            "maps_checked": n_check, "signal_dims_oracle": ks,
+            "against": "FP64 oracle whole maps; relative L2 after per-pixel channel-1 phase alignment inside "
+                       "the object support eroded by 2 px at pixels with eigen-gap > 1e-3; eigenvalue max "
+                       "abs error on the same reduced pixels"}
+        if world == 1:
+            line["cpu_baseline"] = {"value": len(secs) / sum(secs), "unit": "maps/s", "cores": workers,
+                                    "kind": "oracle", "sample": oracle_desc(len(secs), workers)}
+        if not (line["accuracy"]["map_err"] <= 1e-4 and line["accuracy"]["eig_err"] <= 1e-5):
+            line["value"] = None
+            line["invalid"] = "accuracy gate failed"
+    if failed:
+        line["value"] = None
+        line["invalid"] = f"{len(failed)} item(s) did not return PISCO_OK"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -615,7 +641,7 @@ def run_gpu_uneven(args):
     value = len(specs) * args.steps / (tot_ms / 1e3)
     npix_red = sum((sp["grid"][0] // 4) * (sp["grid"][1] // 4) for sp in specs)
     binfo = batch.info()
-    statuses = list(batch.last_item_status)
+    statuses = list(batch.last_item_status) + list(batch2.last_item_status)
     # end to end through host buffers: two batch objects in flight (as in the 2D workload)
     pin_c = [torch.from_numpy(c).pin_memory().numpy() for c in calibs_h]
     outs = [([torch.empty(tuple(m.shape), dtype=torch.complex64).pin_memory().numpy() for m in maps],
@@ -653,7 +679,7 @@ def run_gpu_uneven(args):
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
                                                       f"{'/df' if r.get('gram_df') else ''}"
                                                       f"{'/ti' if r.get('tc_interp') else ''}":
-                                                      round(r["ms"], 3) for r in tune_table}),
+                                                      (round(r["ms"], 3) if r["ms"] is not None else "rejected") for r in tune_table}),
         "data": "synthetic",
         "config": {"workload": "96 uneven 2D slices (seeded shapes, see phantoms.uneven_slice_specs)",
                    "batch": len(specs), "step": "one CUDA-graph launch estimating all 96 slices (two batch objects launched in turn, "
@@ -668,6 +694,10 @@ def run_gpu_uneven(args):
                 "mode": e2e_mode, "modes": e2e_modes},
         "clocks": clocks, "workspace_bytes_batch": binfo["workspace_bytes"],
     }
+    failed = [k for k in statuses if k != 0]
+    if failed:
+        line["value"] = None
+        line["invalid"] = f"{len(failed)} item(s) did not return PISCO_OK"
     print(json.dumps(line), flush=True)
     return 0
 

@@ -44,7 +44,11 @@ typedef enum {
   PISCO_ERR_RANK = 4,           /* R < Q-1: the necessary condition of Sec. III-B fails.  The
                                    outputs are still written (they are not identifiable).    */
   PISCO_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired                         */
-  PISCO_ERR_NOT_CONVERGED = 6,  /* block eigensolver saturated even at the largest block     */
+  PISCO_ERR_NOT_CONVERGED = 6,  /* block eigensolver saturated even at the largest block, or
+                                   the FP64 residual bounds do not certify the threshold split
+                                   (Sec. III-B footnote) after the largest automatic iteration
+                                   count (or after an explicit eig_iters).  The outputs are
+                                   still written with the uncertified split.                 */
   PISCO_ERR_UNSUPPORTED = 7,    /* valid request outside what this build implements          */
   PISCO_ERR_TOO_LARGE = 8       /* request needs more than the fixed scratch of
                                    pisco_gram_lags_noalloc (nothing was launched)            */
@@ -111,7 +115,8 @@ typedef struct {
                              SplitMix64(seed*2^40 + j*2^8 + t), a 24-bit uniform in [-1,1)   */
   unsigned flags;         /* PISCO_FLAG_*                                                     */
   int eig_block;          /* block size of the nullspace eigensolver (0: automatic)           */
-  int eig_iters;          /* subspace iterations of the eigensolver (0: automatic = 6)        */
+  int eig_iters;          /* subspace iterations of the eigensolver (0: automatic: 6, doubled
+                             up to 48 while the split is not certified; > 0: fixed)          */
   int tc_splits;          /* K splits of the tensor-core GEMMs (PISCO_FLAG_TC_*; 0: automatic) */
   int gemm_splits;        /* split-K cap of the CUDA-core block products (0: automatic, about
                              two CTAs per SM; small values suit batches of concurrent plans)  */
@@ -193,6 +198,10 @@ typedef struct {
   int signal_dim;     /* k = Q|Lambda| - R                                                 */
   int filter_len;     /* |Lambda|                                                          */
   int warm_fallback;  /* pixels re-solved from the plain start (warm start only)            */
+  double cert_margin; /* certificate of the threshold split: min over the Ritz values decided
+                         in FP64 of (|mu - theta| - b) / theta, theta = thr^2 lambda_1 and b
+                         the FP64 residual (Kato-Temple) bound; > 0 means certified        */
+  double band_resid;  /* largest FP64 residual ||A x - mu x|| / lambda_1 of those vectors   */
 } pisco_stats;
 pisco_status pisco_get_stats(pisco_plan_t plan, pisco_stats* out);
 

@@ -61,6 +61,8 @@ class pisco_stats(ctypes.Structure):
         ("signal_dim", ctypes.c_int),
         ("filter_len", ctypes.c_int),
         ("warm_fallback", ctypes.c_int),
+        ("cert_margin", ctypes.c_double),
+        ("band_resid", ctypes.c_double),
     ]
 
 

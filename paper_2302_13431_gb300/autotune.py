@@ -16,6 +16,10 @@ share the GPU:
 * `tc_interp`: the last interpolation pass as a batched split-TF32 tensor-core GEMM or as the
   fused CUDA-core interpolate-and-normalise kernel (tried on the best of the others only).
 
+A candidate counts only if it passes a correctness gate on the tuning batch: every item returns
+PISCO_OK, with the same signal dimension as the first candidate (plain FP32) and eigenvalue maps
+within 1e-4 of it; candidates that fail are listed with ms = None and never chosen.
+
 Results are cached in a JSON file keyed by the device name, the shapes and the batch size.
 """
 from __future__ import annotations
@@ -59,20 +63,37 @@ def _shape_key(specs, batch_note=""):
     return f"{dev}|{len(specs)} items|{h}{batch_note}"
 
 
-def _time_batch(specs, calibs, steps, warmup):
+def _time_batch(specs, calibs, steps, warmup, ref=None):
+    """(ms per step, outputs) of one candidate, or (None, reason) when it fails the gate against
+    `ref` (the outputs of the reference candidate: per-item signal dimensions and eigenvalue maps)."""
+    from . import _binding as B
     batch = PiscoBatch(specs)
     maps, eigs = batch.alloc_outputs()
     try:
-        for _ in range(warmup):
-            batch.estimate_into(calibs, maps, eigs)
+        try:
+            for _ in range(warmup):
+                batch.estimate_into(calibs, maps, eigs)
+        except B.PiscoError as e:
+            return None, f"batch call failed: {e}"
         torch.cuda.synchronize()
+        st = list(batch.last_item_status)
+        if any(x != B.PISCO_OK for x in st):
+            return None, f"item statuses {st}"
+        ks = [batch.item_stats(i)["signal_dim"] for i in range(len(specs))]
+        out = (ks, [e.clone() for e in eigs])
+        if ref is not None:
+            if ks != ref[0]:
+                return None, f"signal dims {ks} != {ref[0]}"
+            d = max(float((a - b).abs().max()) for a, b in zip(eigs, ref[1]))
+            if not d <= 1e-4:
+                return None, f"eigenvalue maps differ by {d:.2e}"
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
             batch.estimate_into(calibs, maps, eigs)
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / steps, out
     finally:
         batch.close()
 
@@ -97,22 +118,28 @@ def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None,
                   for i, s in enumerate(specs)]
     table = []
     t0 = time.time()
+    ref = None
     for c in (cands or candidates()):
         sp = [dict(s, **c) for s in specs]
-        ms = _time_batch(sp, calibs, steps, warmup)
-        table.append(dict(c, ms=ms))
+        ms, out = _time_batch(sp, calibs, steps, warmup, ref)
+        table.append(dict(c, ms=ms) if ms is not None else dict(c, ms=None, rejected=out))
+        if ms is not None and ref is None:
+            ref = out
         if verbose:
-            print(f"  autotune {c}: {ms:.2f} ms/step", flush=True)
-    best = min(table, key=lambda r: r["ms"])
+            print(f"  autotune {c}: {ms if ms is None else round(ms, 3)} ms/step", flush=True)
+    ok = [r for r in table if r["ms"] is not None]
+    if not ok:
+        raise RuntimeError("autotune: no candidate passed the correctness gate: " + repr(table))
+    best = min(ok, key=lambda r: r["ms"])
     if cands is None:
         for knob, val in REFINE:
             c = {k: best[k] for k in KNOB_KEYS}
             c[knob] = val
-            ms = _time_batch([dict(s, **c) for s in specs], calibs, steps, warmup)
-            table.append(dict(c, ms=ms))
+            ms, out = _time_batch([dict(s, **c) for s in specs], calibs, steps, warmup, ref)
+            table.append(dict(c, ms=ms) if ms is not None else dict(c, ms=None, rejected=out))
             if verbose:
-                print(f"  autotune {c}: {ms:.2f} ms/step", flush=True)
-            if ms < best["ms"]:
+                print(f"  autotune {c}: {ms} ms/step", flush=True)
+            if ms is not None and ms < best["ms"]:
                 best = table[-1]
     config = {k: best[k] for k in KNOB_KEYS}
     if cache:

@@ -64,6 +64,7 @@ enum : int {
   ST_CHOL = 4,          // non-positive pivot clamped in a Cholesky factorisation
   ST_ZERO = 8,          // calibration data identically zero
   ST_TIMEOUT = 16,      // a bounded wait of a tensor-core kernel expired
+  ST_UNCERTIFIED = 32,  // FP64 residual bounds do not certify the threshold split
 };
 struct DevStatus {
   int flags;            // ST_* bits
@@ -72,6 +73,8 @@ struct DevStatus {
   int jacobi_sweeps;    // sweeps used by the last small eigensolve
   double lambda_max;    // largest eigenvalue of C^H C (FP64 Rayleigh quotient)
   int ws_fallback;      // pixels re-solved after the warm start's residual gate
+  double cert_margin;   // min over the band of (|mu - theta| - bound) / theta (certificate)
+  double band_resid;    // max FP64 residual of the band vectors / lambda_1
 };
 
 // ---------------------------------------------------------------------------------------
@@ -124,7 +127,6 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
                        float skip_rel, DevStatus* status, cudaStream_t st);
 cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, const int* band_idx,
                             double2* Zb, cudaStream_t st);
-cudaError_t eig_pow(float* d, int m, float e, cudaStream_t st);
 cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
                             cudaStream_t st);
 cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, int nb_max,

@@ -683,18 +683,6 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
   return cudaGetLastError();
 }
 
-// d <- |d|^e (rescales diag(R) of `cur` Gram products to the next group's product count)
-__global__ void pow_kernel(float* d, int m, float e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) d[i] = powf(fabsf(d[i]), e);
-}
-
-cudaError_t eig_pow(float* d, int m, float e, cudaStream_t st) {
-  pow_kernel<<<(m + 127) / 128, 128, 0, st>>>(d, m, e);
-  ++g_launches;
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------------------
 // FP64 decision.  band_idx[0] = 0 (the top Ritz vector fixes lambda_1); the others are the
 // Ritz vectors whose FP32 Ritz value lies within a factor 4 of the FP32 threshold, closest
@@ -811,6 +799,16 @@ cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, 
 
 // FP64 Rayleigh quotients mu~_c = Re(x_c^H A x_c) / (x_c^H x_c) of the band vectors, then the
 // threshold split on the FP64 values (band) and the FP32 values (far from the threshold).
+//
+// Certificate of the split.  For a Hermitian A and a unit vector x with Rayleigh quotient mu
+// and residual r = ||A x - mu x||, some eigenvalue lies in [mu - r, mu + r]; when every other
+// eigenvalue is at least g away from mu (g > r), that eigenvalue lies within r^2 / (g - r) of mu
+// (Kato-Temple).  Each band vector's FP64 residual gives the bound b_c = min(r_c, r_c^2/(g_c - r_c))
+// with g_c the distance to the nearest other Ritz value (less that value's own bound when it is
+// a band value); theta = thr^2 lambda_1 inherits thr^2 b_0 from lambda_1.  The split is certified
+// when every band value satisfies |mu_c - theta| > b_c + thr^2 b_0 and every Ritz value decided
+// in FP32 lies outside [theta / 1.001, 1.001 theta] (FP32 Ritz values of the scaled Gram carry
+// errors of order 1e-7 lambda_1, i.e. 4e-5 theta at thr = 0.05).  Otherwise ST_UNCERTIFIED.
 __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ mu, int m,
                                                      const int* __restrict__ band_idx, int nb_max,
                                                      const double2* __restrict__ Xb,
@@ -819,10 +817,12 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
                                                      const double* __restrict__ scale,
                                                      float* __restrict__ w,
                                                      double* __restrict__ ritz, DevStatus* status) {
-  __shared__ double num[32], den[32];
+  __shared__ double num[32], den[32], res[32], bnd[32];
   __shared__ double s_lmax;
+  __shared__ int s_uncert;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) s_uncert = 0;
   // one warp per band column (8 warps, loop over columns)
   for (int c = warp; c < nb_max; c += blockDim.x / 32) {
     double a = 0.0, b = 0.0;
@@ -835,7 +835,20 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
       a += __shfl_xor_sync(0xffffffffu, a, o);
       b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    if (lane == 0) { num[c] = a; den[c] = b; }
+    // FP64 residual of the normalised vector: ||z - mu x||^2 / ||x||^2, summed directly
+    const double muc = b > 0.0 ? a / b : 0.0;
+    double e = 0.0;
+    for (int r = lane; r < n; r += 32) {
+      const double2 x = Xb[(long long)r * nb_max + c], z = Zb[(long long)r * nb_max + c];
+      const double dx = z.x - muc * x.x, dy = z.y - muc * x.y;
+      e += dx * dx + dy * dy;
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) {
+      num[c] = a;
+      den[c] = b;
+      res[c] = b > 0.0 ? sqrt(e / b) : 0.0;
+    }
   }
   __syncthreads();
   if (tid == 0) s_lmax = den[0] > 0.0 ? num[0] / den[0] : 0.0;
@@ -854,6 +867,38 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
     w[j] = sig ? 1.f : 0.f;
   }
   __syncthreads();
+  // first bounds: the plain residual bound of every band value (neighbours' bounds below)
+  if (tid < nb_max) bnd[tid] = res[tid];
+  __syncthreads();
+  if (tid < nb_max && band_idx[tid] >= 0 && den[tid] > 0.0) {
+    const int c = tid, jc = band_idx[c];
+    const double mc = ritz[jc], rc = res[c];
+    double g = 1e300;
+    for (int j = 0; j < m; ++j) {
+      if (j == jc) continue;
+      double d = fabs(mc - ritz[j]);
+      for (int c2 = 0; c2 < nb_max; ++c2)
+        if (band_idx[c2] == j && den[c2] > 0.0) d -= res[c2];
+      g = fmin(g, d);
+    }
+    double bc = rc;
+    if (g > rc) bc = fmin(rc, rc * rc / (g - rc));
+    bnd[c] = bc;
+  }
+  __syncthreads();
+  if (tid < m && lmax > 0.0) {
+    const int j = tid;
+    int c = -1;
+    for (int c2 = 0; c2 < nb_max; ++c2)
+      if (band_idx[c2] == j && den[c2] > 0.0) c = c2;
+    const double v = ritz[j];
+    bool ok;
+    if (c == 0) ok = true;  // lambda_1 itself: its bound enters through theta
+    else if (c > 0) ok = fabs(v - theta) > bnd[c] + thr2 * bnd[0];
+    else ok = (v > 1.001 * theta) || (v < theta / 1.001);
+    if (!ok) atomicOr(&s_uncert, 1);
+  }
+  __syncthreads();
   if (tid == 0) {
     int k = 0;
     for (int j = 0; j < m; ++j) k += (w[j] > 0.f);
@@ -863,12 +908,22 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
     if (k > m - guard && !(flags & ST_ZERO)) flags |= ST_SATURATED;
     const int R = n - k;
     if (R < Q - 1) flags |= ST_RANK;
+    if (s_uncert && !(flags & ST_ZERO)) flags |= ST_UNCERTIFIED;
+    // smallest relative certificate margin over the band (for reporting)
+    double margin = 1e300, rmax = 0.0;
+    for (int c = 1; c < nb_max; ++c) {
+      if (band_idx[c] < 0 || !(den[c] > 0.0)) continue;
+      margin = fmin(margin, (fabs(ritz[band_idx[c]] - theta) - bnd[c] - thr2 * bnd[0]) / theta);
+      rmax = fmax(rmax, res[c]);
+    }
     atomicOr(&status->flags, flags);
     status->k = k;
     int nb = 0;
     for (int c = 0; c < nb_max; ++c) nb += (band_idx[c] >= 0);
     status->nband = nb;
     status->lambda_max = lmax;
+    status->cert_margin = lmax > 0.0 ? margin : 0.0;
+    status->band_resid = lmax > 0.0 ? rmax / lmax : 0.0;
   }
 }
 

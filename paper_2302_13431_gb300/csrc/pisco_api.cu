@@ -22,6 +22,7 @@ namespace {
 constexpr int kNbMax = 8;       // Ritz vectors refined in FP64 per decision
 constexpr int kThinSplits = 8;  // K splits of the tensor-core m x m x n block Grams
 constexpr int kMmax = 128;   // largest eigensolver block
+constexpr int kItersMax = 48;  // largest automatic subspace iteration count
 
 struct DevBuf {
   void* p = nullptr;
@@ -446,6 +447,17 @@ void graph_reset(pisco_plan_s* pl) {
   pl->g_m = -1;
 }
 
+// the eigensolver's block size and iteration count, which a captured graph bakes in
+int solve_key(const pisco_plan_s* pl) { return pl->m * 1024 + pl->eig_iters; }
+
+// An uncertified split with the automatic iteration count: double the subspace iterations (up
+// to kItersMax) for this and later estimates.  Returns false when no retry is left.
+bool retry_iters(pisco_plan_s* pl) {
+  if (pl->prm.eig_iters > 0 || pl->eig_iters >= kItersMax) return false;
+  pl->eig_iters = std::min(2 * pl->eig_iters, kItersMax);
+  return true;
+}
+
 #define OP(tag, x)                                   \
   do {                                               \
     const int i__ = prof_begin(pl, tag);             \
@@ -557,7 +569,7 @@ pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, co
     OP("eig_gemm_thin_tc", thin_product(pl, true, Yin, Yin, pl->Gm));
   else
     OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
-  if (m <= 96) {
+  if (m <= 64) {
     OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
     if (pl->tc_thin)
       OP("eig_gemm_thin_tc", thin_product(pl, false, Yin, pl->Rinv, Xout));
@@ -585,45 +597,48 @@ cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y) {
 }
 
 // Nullspace of the Gram (Sec. III-A, threshold footnote of Sec. III-B): orthogonal
-// iteration on an m-column block in FP32, two Gram products per orthonormalisation with the
-// block rescaled by the square of the previous diag(R) (keeps Cholesky-QR well conditioned),
+// iteration on an m-column block in FP32, one Gram product per orthonormalisation with the
+// block rescaled by the previous Ritz values or diag(R) (keeps Cholesky-QR well conditioned),
 // one Rayleigh-Ritz at the end, and the threshold split decided on FP64 Rayleigh quotients
-// against the FP64 Gram.
+// against the FP64 Gram, with FP64 residuals certifying the decision.
+//
+// The start is a Rayleigh-Ritz step on an orthonormalised random block: the first product
+// A X0 of a random block spans the dominant directions so unevenly (condition number up to
+// lambda_1/lambda_m, 1e4 and more on these spectra) that even shifted Cholesky-QR leaves a
+// block at the FP32 limit of the next pass; the Ritz vectors of the random block instead give
+// an equilibrated first product A X0 V diag(mu)^-1.
 pisco_status run_eig(pisco_plan_s* pl) {
   cudaStream_t st = pl->st;
   const int n = pl->n, m = pl->m;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
   const double thr2 = pl->prm.null_threshold * pl->prm.null_threshold;
   pisco_status s;
-  // random start; the first product can be ill conditioned -> shifted Cholesky-QR + two passes
   OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
   if (pl->tc_eig)  // the Gram's TF32 head/tail split, shared by every block product of the solve
     OP("eig_gemm_AX", tc2_split_a(pl->A32, n, nullptr, n, n, pl->Ah, pl->tc_terms == 3 ? pl->Al : nullptr, st));
-  OP("eig_gemm_AX", ax_product(pl, pl->Y, pl->Z));
-  const float shift = 11.0f * ((float)m * n + (float)m * (m + 1)) * 5.9604645e-8f;
-  if ((s = cholqr(pl, pl->Z, pl->Y, m, nullptr, shift, nullptr, pl->dR1)) != PISCO_OK) return s;
-  if ((s = cholqr(pl, pl->Y, pl->Z, m, nullptr, 0.f, pl->dR1, pl->dR0)) != PISCO_OK) return s;
-  if ((s = cholqr(pl, pl->Z, pl->X, m, nullptr, 0.f, pl->dR0, pl->dR1)) != PISCO_OK) return s;
-  float* dprev = pl->dR1;
-  float* dnext = pl->dR0;
-  // orthogonal iteration: X <- orth(A^2 X diag(R)^-2) (the last group may be a single product)
-  // dprev approximates lambda^cur for the block columns (diag(R) of `cur` products)
-  int left = pl->eig_iters - 1, cur = 1;
-  while (left > 0) {
-    // one Gram product per orthonormalisation: with two, the squared dynamic range of the
-    // noise-level columns (~(1e-5)^2) exceeds what FP32 Cholesky-QR can resolve
-    const int g = 1;
+  // X0 = orth(random block): well conditioned (kappa ~ (1 + sqrt(m/n)) / (1 - sqrt(m/n)))
+  if ((s = cholqr(pl, pl->Y, pl->X, m, nullptr, 0.f, nullptr, pl->dR1)) != PISCO_OK) return s;
+  // Rayleigh-Ritz of the start block: Z = A X0, B = X0^H Z = V diag(mu) V^H, A (X0 V) = Z V
+  OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
+  if (pl->tc_thin)
+    OP("eig_gemm_thin_tc", thin_product(pl, true, pl->X, pl->Z, pl->Bm));
+  else
+    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
+  if (pl->tc_thin)
+    OP("eig_gemm_thin_tc", thin_product(pl, false, pl->Z, pl->Vj, pl->Y));
+  else
+    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->Z, m, pl->Vj, m, zero, pl->Y, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  // first power step: X1 = orth(A X0 V diag(mu)^-1)
+  if ((s = cholqr(pl, pl->Y, pl->X, m, pl->mu, 0.f, nullptr, pl->dR0)) != PISCO_OK) return s;
+  float* dprev = pl->dR0;
+  float* dnext = pl->dR1;
+  // orthogonal iteration: X <- orth(A X diag(R)^-1), diag(R) of the previous orthonormalisation
+  // approximating the Ritz values of the block columns
+  for (int it = 1; it < pl->eig_iters; ++it) {
     OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Y));
-    const float2* src = pl->Y;
-    if (g == 2) {
-      OP("eig_gemm_AX", ax_product(pl, pl->Y, pl->Z));
-      src = pl->Z;
-    }
-    if (g != cur) OP("eig_misc", eig_pow(dprev, m, (float)g / (float)cur, st));
-    cur = g;
-    if ((s = cholqr(pl, src, pl->X, m, dprev, 0.f, nullptr, dnext)) != PISCO_OK) return s;
+    if ((s = cholqr(pl, pl->Y, pl->X, m, dprev, 0.f, nullptr, dnext)) != PISCO_OK) return s;
     std::swap(dprev, dnext);
-    left -= g;
   }
   // Rayleigh-Ritz on the block
   OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
@@ -1071,9 +1086,9 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
   d_calib = pl->calib_stage;
   for (;;) {
     const bool same_as_graph = pl->gexec && pl->g_calib == d_calib && pl->g_maps == d_maps &&
-                               pl->g_eig == d_eig && pl->g_m == pl->m && pl->g_prof == pl->prof;
+                               pl->g_eig == d_eig && pl->g_m == solve_key(pl) && pl->g_prof == pl->prof;
     const bool same_as_eager = pl->eager_calib == d_calib && pl->eager_maps == d_maps &&
-                               pl->eager_eig == d_eig && pl->eager_m == pl->m && pl->eager_prof == pl->prof;
+                               pl->eager_eig == d_eig && pl->eager_m == solve_key(pl) && pl->eager_prof == pl->prof;
     // profiled calls always run eagerly: their per-operation events time individual launches
     if (pl->use_graph && !pl->prof && !same_as_graph && same_as_eager) {
       // capture the path once the same arguments have run eagerly (attributes set, sizes settled)
@@ -1090,7 +1105,7 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
             cudaGraphInstantiate(&pl->gexec, g, 0) == cudaSuccess) {
           pl->graph = g;
           pl->g_calib = d_calib; pl->g_maps = d_maps; pl->g_eig = d_eig;
-          pl->g_m = pl->m; pl->g_prof = pl->prof;
+          pl->g_m = solve_key(pl); pl->g_prof = pl->prof;
           pl->g_launches = g_launches;
           pl->g_events = pl->ev_used;
         } else {
@@ -1105,7 +1120,7 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
       }
     }
     const bool replay = pl->use_graph && !pl->prof && pl->gexec && pl->g_calib == d_calib && pl->g_maps == d_maps &&
-                        pl->g_eig == d_eig && pl->g_m == pl->m && pl->g_prof == pl->prof;
+                        pl->g_eig == d_eig && pl->g_m == solve_key(pl) && pl->g_prof == pl->prof;
     if (replay) {
       // order the graph after earlier work on the caller's stream, and the caller after it
       if (cudaEventRecord(pl->ev_in, pl->st) != cudaSuccess ||
@@ -1125,7 +1140,7 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
       pl->last_launches = g_launches;
       if (pl->prof) prof_collect(pl, pl->ev_used);
       pl->eager_calib = d_calib; pl->eager_maps = d_maps; pl->eager_eig = d_eig;
-      pl->eager_m = pl->m; pl->eager_prof = pl->prof;
+      pl->eager_m = solve_key(pl); pl->eager_prof = pl->prof;
     }
     const DevStatus h = *pl->hstatus;
     pl->last_status = h;
@@ -1134,9 +1149,10 @@ pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, 
       pl->m = std::min(pl->m * 2, pl->m_max);
       continue;
     }
+    if ((h.flags & ST_UNCERTIFIED) && !(h.flags & ST_SATURATED) && retry_iters(pl)) continue;
     pl->last_k = h.k;
     pl->last_R = pl->n - h.k;
-    if (h.flags & ST_SATURATED) return PISCO_ERR_NOT_CONVERGED;
+    if (h.flags & (ST_SATURATED | ST_UNCERTIFIED)) return PISCO_ERR_NOT_CONVERGED;
     if (h.flags & ST_RANK) return PISCO_ERR_RANK;
     return PISCO_OK;
   }
@@ -1211,6 +1227,8 @@ pisco_status pisco_get_stats(pisco_plan_t pl, pisco_stats* out) {
   out->signal_dim = pl->last_k;
   out->filter_len = pl->L;
   out->warm_fallback = pl->ws_on ? pl->last_status.ws_fallback : 0;
+  out->cert_margin = pl->last_status.cert_margin;
+  out->band_resid = pl->last_status.band_resid;
   return PISCO_OK;
 }
 
@@ -1562,10 +1580,15 @@ static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
       } else {
         si = PISCO_ERR_NOT_CONVERGED;
       }
+    } else if ((h.flags & ST_UNCERTIFIED) && retry_iters(pl)) {
+      // the split is not certified yet: redo this item alone with more subspace iterations
+      batch_graph_reset(b);
+      si = host_io ? pisco_estimate_host(pl, in[i], outp[i], eig[i]) : pisco_estimate(pl, in[i], outp[i], eig[i]);
     } else {
       pl->last_k = h.k;
       pl->last_R = pl->n - h.k;
-      if (h.flags & ST_RANK) si = PISCO_ERR_RANK;
+      if (h.flags & ST_UNCERTIFIED) si = PISCO_ERR_NOT_CONVERGED;
+      else if (h.flags & ST_RANK) si = PISCO_ERR_RANK;
     }
     if (item_status) item_status[i] = si;
     if (si != PISCO_OK && (worst == PISCO_OK || worst == PISCO_ERR_RANK)) worst = si;

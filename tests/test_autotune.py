@@ -29,6 +29,7 @@ def test_tune_picks_the_fastest_and_caches(tmp_path):
     cands = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False, tc_interp=False),
              dict(precision="tc_g_eig", tc_splits=4, gemm_splits=2, gemm_tile=64, gram_df=True, tc_interp=True)]
     cfg, table = tune(specs, steps=2, warmup=2, cache=cache, cands=cands)
+    assert all(r["ms"] is not None for r in table), table  # both candidates pass the correctness gate
     assert cfg == {k: min(table, key=lambda r: r["ms"])[k] for k in KNOB_KEYS}
     cfg2, table2 = tune(specs, cache=cache, cands=cands)  # cached: no re-timing
     assert cfg2 == cfg and table2 == table

@@ -36,7 +36,7 @@ def test_batch_equals_single_plans_device_and_host():
     for rep in range(3):  # eager, capture, replay
         batch.estimate_into(calibs, maps, eigs)
         torch.cuda.synchronize()
-        assert all(s in (B.PISCO_OK, B.PISCO_ERR_RANK) for s in batch.last_item_status)
+        assert all(s == B.PISCO_OK for s in batch.last_item_status), batch.last_item_status
         single_launches = 0
         for i, sp in enumerate(SPECS):
             est = PiscoEstimator(sp["grid"], sp["calib_shape"], sp["num_coils"], sp["tau"],
