@@ -334,9 +334,12 @@ pisco_status pisco_warm_start_features(const void* d_y, int Q, long long npix, f
 pisco_status pisco_set_warm_start(pisco_plan_t plan, pisco_mlp_t mlp, int iters, float gate,
                                   int fallback_iters);
 
-/* The dense complex contraction behind PISCO_FLAG_TC_GFIELD / PISCO_FLAG_TC_EIG, exposed for
- * testing and reuse: C = alpha * A * op(B) + beta * C on the tensor cores (tcgen05, TF32
- * operands, FP32 accumulation in tensor memory).
+/* The dense complex contraction behind PISCO_FLAG_TC_GFIELD / PISCO_FLAG_TC_EIG /
+ * PISCO_FLAG_TC_INTERP, exposed for testing and reuse: C = alpha * A * op(B) + beta * C on the
+ * tensor cores (tcgen05, TF32 operands, FP32 accumulation in tensor memory).  The operands are
+ * first split into TF32 head/tail arrays in the caller's workspace (the tensor core's K-major
+ * layout), then TMA loads feed a shared-memory ring consumed by tcgen05.mma.  K may be split over
+ * `splits` CTAs per tile (partials summed in a fixed order, deterministic).
  *   nterms: 3 = each FP32 operand split into a TF32 head and tail, three products per entry
  *           (close to FP32 accuracy); 1 = one TF32 product (about 11 significant bits);
  *   A: device complex64 M x K, row-major, leading dimension lda >= K;
@@ -344,20 +347,12 @@ pisco_status pisco_set_warm_start(pisco_plan_t plan, pisco_mlp_t mlp, int iters,
  *   opB 1: op(B) = conj(Bs^T) with Bs device complex64 N x K row-major, ldb >= K;
  *   C: device complex64 M x N row-major, ldc >= N, read when beta != 0, written;
  *   alpha, beta: host float[2] (real, imaginary);
+ *   d_workspace: device, 16-byte aligned, at least
+ *           pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, splits) bytes;
  *   d_status: optional device int; bit 16 is OR-ed in if a bounded device wait expired.
- * All device pointers 8-byte aligned (PISCO_ERR_ARG otherwise, nothing launched).  Enqueued on
+ * A, B, C 8-byte aligned (PISCO_ERR_ARG otherwise, nothing launched).  Enqueued on
  * `cuda_stream`; returns without synchronising.  The first call sets kernel attributes, so
  * make it outside stream capture. */
-pisco_status pisco_tc_cgemm(int nterms, int M, int N, int K, const float* alpha, const void* d_A,
-                            int lda, const void* d_B, int ldb, int opB, const float* beta, void* d_C,
-                            int ldc, int* d_status, void* cuda_stream);
-
-/* The same product through the pipelined kernel the estimator uses: the operands are first split
- * into TF32 head/tail arrays in the caller's workspace (the tensor core's K-major layout), then
- * TMA loads feed a 4-stage shared-memory ring consumed by tcgen05.mma.  K may be split over
- * `splits` CTAs per tile (partials summed in a fixed order, deterministic).  d_workspace: device,
- * 16-byte aligned, at least pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, splits) bytes
- * (PISCO_ERR_ARG otherwise).  Other arguments as pisco_tc_cgemm. */
 size_t pisco_tc_cgemm_pipelined_workspace(int nterms, int M, int N, int K, int splits);
 pisco_status pisco_tc_cgemm_pipelined(int nterms, int M, int N, int K, const float* alpha,
                                       const void* d_A, int lda, const void* d_B, int ldb, int opB,

@@ -131,10 +131,6 @@ def load():
     lib.pisco_batch_destroy.restype = None
     lib.pisco_gram_lags_noalloc.argtypes = [P(pisco_params), vp, vp, vp]
     lib.pisco_gram_lags_noalloc.restype = ctypes.c_int
-    lib.pisco_tc_cgemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_float), vp,
-                                   ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_float), vp,
-                                   ctypes.c_int, vp, vp]
-    lib.pisco_tc_cgemm.restype = ctypes.c_int
     lib.pisco_tc_cgemm_pipelined_workspace.argtypes = [ctypes.c_int] * 5
     lib.pisco_tc_cgemm_pipelined_workspace.restype = ctypes.c_size_t
     lib.pisco_tc_cgemm_pipelined.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -316,15 +312,6 @@ def pisco_batch_item(batch, i):
 
 def pisco_batch_destroy(batch):
     load().pisco_batch_destroy(batch)
-
-
-def pisco_tc_cgemm(nterms, M, N, K, alpha, d_A, lda, d_B, ldb, opB, beta, d_C, ldc, d_status=0, stream=0):
-    """C = alpha*A*op(B) + beta*C on the tensor cores (see include/pisco.h); alpha, beta complex."""
-    a = (ctypes.c_float * 2)(float(complex(alpha).real), float(complex(alpha).imag))
-    b = (ctypes.c_float * 2)(float(complex(beta).real), float(complex(beta).imag))
-    return load().pisco_tc_cgemm(nterms, M, N, K, a, ctypes.c_void_p(d_A), lda, ctypes.c_void_p(d_B), ldb, opB,
-                                 b, ctypes.c_void_p(d_C), ldc, ctypes.c_void_p(d_status or 0),
-                                 ctypes.c_void_p(stream))
 
 
 def _fptr(a):

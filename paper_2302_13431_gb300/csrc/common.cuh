@@ -227,14 +227,6 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
                      int nbatch = 1, long long c_stride = 0);
 
-// tensor-core complex GEMM (kernels_tc.cu): C = alpha*A*op(B) + beta*C (+ diag_val on columns
-// c % diag_stride == 0, c < diag_limit); A M x K row-major with optional per-k real scale;
-// opB 0: B K x N row-major, 1: conj of an N x K row-major array; nterms 3 (head/tail split TF32)
-// or 1 (TF32); err gets bit 16 on a bounded-wait expiry
-cudaError_t tc_gemm_prepare();
-cudaError_t tc_cgemm(int nterms, int M, int N, int K, float2 alpha, const float2* A, int lda,
-                     const float* kscale, const float2* B, int ldb, int opB, float2 beta, float2* C,
-                     int ldc, float diag_val, int diag_stride, int diag_limit, int* err, cudaStream_t st);
 
 // a4+a5: power iteration with the phase step
 cudaError_t power_iteration_block2(const float2* G, const float2* Y, int Q, long long npix, int iters,

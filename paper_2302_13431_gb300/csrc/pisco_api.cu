@@ -908,7 +908,7 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   pl->tc_g = (p->flags & PISCO_FLAG_TC_GFIELD) != 0;
   pl->tc_eig = (p->flags & PISCO_FLAG_TC_EIG) != 0;
   pl->tc_terms = (p->flags & PISCO_FLAG_TC_1PASS) ? 1 : 3;
-  if ((pl->tc_g || pl->tc_eig) && (tc_gemm_prepare() != cudaSuccess || tc2_prepare() != cudaSuccess)) {
+  if ((pl->tc_g || pl->tc_eig) && tc2_prepare() != cudaSuccess) {
     cudaGetLastError();
     delete pl;
     return PISCO_ERR_CUDA;
@@ -1594,24 +1594,6 @@ static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
     if (si != PISCO_OK && (worst == PISCO_OK || worst == PISCO_ERR_RANK)) worst = si;
   }
   return worst;
-}
-
-pisco_status pisco_tc_cgemm(int nterms, int M, int N, int K, const float* alpha, const void* d_A, int lda,
-                            const void* d_B, int ldb, int opB, const float* beta, void* d_C, int ldc,
-                            int* d_status, void* cuda_stream) {
-  if (M < 0 || N < 0 || K < 0 || (nterms != 1 && nterms != 3) || (opB != 0 && opB != 1)) return PISCO_ERR_ARG;
-  if (M == 0 || N == 0) return PISCO_OK;
-  if (!d_C || !alpha || !beta || (K > 0 && (!d_A || !d_B))) return PISCO_ERR_ARG;  // K = 0: A, B unread
-  if (lda < K || ldc < N || ldb < (opB == 0 ? N : K)) return PISCO_ERR_ARG;
-  if (((uintptr_t)d_A | (uintptr_t)d_B | (uintptr_t)d_C) & 7) return PISCO_ERR_ARG;
-  if (tc_gemm_prepare() != cudaSuccess) {
-    cudaGetLastError();
-    return PISCO_ERR_CUDA;
-  }
-  const cudaError_t e = tc_cgemm(nterms, M, N, K, make_float2(alpha[0], alpha[1]), (const float2*)d_A, lda,
-                                 nullptr, (const float2*)d_B, ldb, opB, make_float2(beta[0], beta[1]),
-                                 (float2*)d_C, ldc, 0.f, 0, 0, d_status, (cudaStream_t)cuda_stream);
-  return e == cudaSuccess ? PISCO_OK : PISCO_ERR_CUDA;
 }
 
 // workspace layout of pisco_tc_cgemm_pipelined: A' head, A' tail, B' head, B' tail, partials

@@ -23,9 +23,8 @@ def _rand(rng, *shape):
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
 
 
-def _run(nterms, A, Bm, opB, alpha=1.0, beta=0.0, C0=None, pipelined=None):
-    """pipelined: None = the staging kernel (pisco_tc_cgemm); an int = the TMA-fed kernel with
-    that many K splits (pisco_tc_cgemm_pipelined)."""
+def _run(nterms, A, Bm, opB, alpha=1.0, beta=0.0, C0=None, pipelined=1):
+    """The TMA-fed tensor-core GEMM (pisco_tc_cgemm_pipelined) with `pipelined` K splits."""
     M, K = A.shape
     N = Bm.shape[1] if opB == 0 else Bm.shape[0]
     dA = torch.from_numpy(A).cuda()
@@ -34,22 +33,18 @@ def _run(nterms, A, Bm, opB, alpha=1.0, beta=0.0, C0=None, pipelined=None):
                                                                                  device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    if pipelined is None:
-        st = B.pisco_tc_cgemm(nterms, M, N, K, alpha, dA.data_ptr(), K, dB.data_ptr(), Bm.shape[1], opB, beta,
-                              dC.data_ptr(), N, status.data_ptr(), stream)
-    else:
-        nb = B.pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, pipelined)
-        ws = torch.empty(max(nb, 16), dtype=torch.uint8, device="cuda")
-        st = B.pisco_tc_cgemm_pipelined(nterms, M, N, K, alpha, dA.data_ptr(), K, dB.data_ptr(), Bm.shape[1], opB,
-                                        beta, dC.data_ptr(), N, pipelined, ws.data_ptr(), nb, status.data_ptr(),
-                                        stream)
+    nb = B.pisco_tc_cgemm_pipelined_workspace(nterms, M, N, K, pipelined)
+    ws = torch.empty(max(nb, 16), dtype=torch.uint8, device="cuda")
+    st = B.pisco_tc_cgemm_pipelined(nterms, M, N, K, alpha, dA.data_ptr(), K, dB.data_ptr(), Bm.shape[1], opB,
+                                    beta, dC.data_ptr(), N, pipelined, ws.data_ptr(), nb, status.data_ptr(),
+                                    stream)
     assert st == B.PISCO_OK
     torch.cuda.synchronize()
     assert int(status.item()) == 0
     return dC.cpu().numpy()
 
 
-def _check(nterms, A, Bm, opB, alpha=1.0, beta=0.0, C0=None, pipelined=None):
+def _check(nterms, A, Bm, opB, alpha=1.0, beta=0.0, C0=None, pipelined=1):
     A64 = A.astype(np.complex128)
     opb = Bm.astype(np.complex128) if opB == 0 else Bm.astype(np.complex128).conj().T
     ref = alpha * (A64 @ opb)
@@ -94,10 +89,13 @@ def test_tc_gemm_alpha_beta_and_empty_K():
 def test_tc_gemm_rejects_bad_arguments():
     d = torch.zeros(64, dtype=torch.complex64, device="cuda")
     p = d.data_ptr()
-    assert B.pisco_tc_cgemm(2, 4, 4, 4, 1, p, 4, p, 4, 0, 0, p, 4) == B.PISCO_ERR_ARG
-    assert B.pisco_tc_cgemm(3, 4, 4, 4, 1, p, 3, p, 4, 0, 0, p, 4) == B.PISCO_ERR_ARG  # lda < K
-    assert B.pisco_tc_cgemm(3, 4, 4, 4, 1, p + 4, 4, p, 4, 0, 0, p, 4) == B.PISCO_ERR_ARG  # misaligned
-    assert B.pisco_tc_cgemm(3, 0, 4, 4, 1, 0, 4, 0, 4, 0, 0, 0, 4) == B.PISCO_OK  # empty: nothing to do
+    ws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    w, nb = ws.data_ptr(), ws.numel()
+    assert B.pisco_tc_cgemm_pipelined(2, 4, 4, 4, 1, p, 4, p, 4, 0, 0, p, 4, 1, w, nb) == B.PISCO_ERR_ARG
+    assert B.pisco_tc_cgemm_pipelined(3, 4, 4, 4, 1, p, 3, p, 4, 0, 0, p, 4, 1, w, nb) == B.PISCO_ERR_ARG  # lda < K
+    assert B.pisco_tc_cgemm_pipelined(3, 4, 4, 4, 1, p + 4, 4, p, 4, 0, 0, p, 4, 1, w, nb) == B.PISCO_ERR_ARG
+    assert B.pisco_tc_cgemm_pipelined(3, 4, 4, 4, 1, p, 4, p, 4, 0, 0, p, 4, 1, w, 16) == B.PISCO_ERR_ARG  # small ws
+    assert B.pisco_tc_cgemm_pipelined(3, 0, 4, 4, 1, 0, 4, 0, 4, 0, 0, 0, 4, 1, w, nb) == B.PISCO_OK  # empty
 
 
 @pytest.mark.parametrize("splits", [1, 4])
