@@ -216,15 +216,7 @@ def run_reference(args):
 # DRAM bytes (read + write) per launch of each op's main kernel on the 2D 256x256 Q=32
 # workload, from one ncu --set full capture (cold caches); an op whose kernel changed since
 # its capture has no entry
-NCU_TRAFFIC = {
-    "eig_jacobi": (54784, "ncu --set full, jacobi_kernel<1>, 64x64 block"),
-    "eig_gemm_AX": (15700480, "ncu --set full, tc2_kernel<3,4>, A32 X 928x64x928 (head+tail operands)"),
-    "g_field_tc": (10471936, "ncu --set full, tc2_kernel<3,2>, G = E K 4096x1024x105"),
-    "g_herk_tc": (2871808, "ncu --set full, tc2_kernel<3,2>, U W U^H 928x928x64"),
-    "eig_gemm_thin_fp32": (601856, "ncu dram__bytes_read.sum + dram__bytes_write.sum, cgemm64_kernel<float>, "
-                                   "mean of 3 launches of the timed batched step (X^H Y, X R^-1 shapes, n = 928, "
-                                   "m = 64; 4-map batch, same per-map shapes as the 64-map workload)"),
-}
+NCU_TRAFFIC = {}
 
 
 def n_lags(w):
@@ -235,11 +227,12 @@ def n_lags(w):
     return len({(a[0] - b[0], a[1] - b[1]) for a in pts for b in pts})
 
 
-def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=None):
-    """Algorithmic work of one operation and its roofline.  Ops made of one kernel launch per
-    product divide one product's work by the average launch time; ops whose profiled calls also
-    include operand-split kernels (tensor-core routes) divide one map's work by one map's time
-    (nmaps = maps in the profiled pass)."""
+def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=None, mpl=1):
+    """Algorithmic work of one operation and its roofline.  prof[op] = (total ms, launches) over
+    `nmaps` map sets, each launch covering `mpl` map sets (the items of a batched pass).  Ops made
+    of one launch per product divide one launch's work (mpl products) by the average launch time;
+    ops whose calls also include operand-split kernels (tensor-core routes) divide one map's work
+    by the time per map."""
     Q, L = w["Q"], stats["filter_len"]
     n = Q * L
     m = stats["eig_block"]
@@ -250,9 +243,12 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
     map_s = total_ms / nmaps / 1e3 if nmaps else avg_s
     terms = 1 if "1pass" in precision else 3
     tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
+    inst_peak = FP32_PEAK_TFLOPS / 2   # FP32 instructions (an FMA is one) per second, in T/s
     tc_note = (f"tcgen05 kind::tf32, {terms} TF32 pass(es) per product (the tensor pipe executes "
                f"{terms}x the algorithmic flops); peak = measured dense bf16 x {TF32_PER_BF16:.3f} "
                "(nominal tf32/bf16 ratio 1.1/2.25)")
+    df_note = ("double-float arithmetic: 60 FP32 instructions per complex multiply-add (4 error-free "
+               "products of 15 instructions); peak = 152 SMs x 128 FP32 lanes x 2070 MHz instructions/s")
     if op == "eig_gemm_AX":
         work = 8.0 * n * n * m                       # complex MAC = 8 real flops
         if "eig" in precision:
@@ -260,7 +256,7 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
             return dict(bound="tensor", achieved=work * prods / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
                         note=f"complex GEMM A(n x n) X(n x m), {prods} per map (per-map work / per-map time, "
                              "the one split of A included); " + tc_note)
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+        return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="FP32 CUDA-core complex GEMM A(n x n) X(n x m); peak = 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
     if op == "g_field_tc":
         work = 8.0 * nr * Q * Q * n_lags(w)
@@ -272,21 +268,25 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
         return dict(bound="tensor", achieved=work / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
                     note="P = U diag(w) U^H: complex GEMM (n x m) by (m x n); " + tc_note)
     if op == "eig_rayleigh_fp64":
-        work = 8.0 * n * n * 16
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    note="FP64 complex GEMM A(n x n) Xb(n x 16); peak = GB300 nominal FP64")
+        work = 8.0 * n * n * 8
+        return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    note="FP64 complex GEMM A(n x n) Xb(n x 8); peak = GB300 nominal FP64")
+    if op == "eig_rayleigh_df":
+        cm = 1.0 * n * n * stats.get("nband", 8)
+        return dict(bound="alu", achieved=60.0 * cm * mpl / avg_s / 1e12, peak=inst_peak, unit="Tinst/s",
+                    note=f"A(n x n) times the {stats.get('nband', 8)} band vectors in use; " + df_note)
     if op == "power_iteration":
         work = 8.0 * nr * (w["iters"] + 1) * Q * Q
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+        return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="per pixel (iters+1) Q x Q complex matvecs")
     if op == "interp_final_norm" and not tc_interp:
         work = 8.0 * Q * npix * (w["grid"][0] // w["reduction"])
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+        return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
                     note="last interpolation axis fused with the per-pixel normalisation: per output pixel "
                          "and coil one complex dot product of length N_r (64 flop per map byte written)")
     if op == "interp_final_norm":
         byts = 16.0 * Q * npix
-        return dict(bound="hbm", achieved=byts / avg_s / 1e9, peak=peaks.get("hbm_gbs", 6800.0), unit="GB/s",
+        return dict(bound="hbm", achieved=byts * mpl / avg_s / 1e9, peak=peaks.get("hbm_gbs", 6800.0), unit="GB/s",
                     note="per-pixel normalisation after the tensor-core interpolation: maps read + write")
     if op == "interp_final_tc":
         work = 8.0 * Q * npix * (w["grid"][0] // w["reduction"])
@@ -295,18 +295,20 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
                          "B-operand split included; " + tc_note)
     if op == "eig_gemm_thin_fp32":
         work = 8.0 * n * m * m                       # every thin block product is n x m x m
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                    note="CUDA-core complex block products (Y^H Y, Y R^-1, X^H Z, X V): 8 n m^2 flops each; "
-                         "latency-bound at one map")
+        return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                    note="CUDA-core complex block products (Y^H Y, Y R^-1, X^H Z, Z V, X V): 8 n m^2 flops each")
+    if op == "eig_gemm_thin_tc":
+        work = 8.0 * n * m * m
+        return dict(bound="tensor", achieved=work * mpl / (avg_s * 3) / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                    note="tensor-core thin block products (each launch triple: two operand splits + the GEMM); "
+                         + tc_note)
     if op == "gram_pairs_df":
         Lp = w["calib"][0] + 2 * w["tau"]
         B = 4 * w["tau"] + 1
         npair = Q * (Q + 1) // 2
         cmacs = npair * (Lp * Lp + Lp * B * Lp + B * B * Lp)
-        return dict(bound="alu", achieved=8.0 * cmacs / map_s / 1e12, peak=FP64_PEAK_TFLOPS,
-                    unit="TFLOP/s (FP64-equivalent)",
-                    note="Gram pair stage fused per coil pair (pair product + both inverse lag passes), "
-                         "FP64-equivalent flops against the nominal FP64 peak; computed in double-float FP32 pairs")
+        return dict(bound="alu", achieved=60.0 * cmacs * mpl / avg_s / 1e12, peak=inst_peak, unit="Tinst/s",
+                    note="Gram pair stage fused per coil pair (pair product + both inverse lag passes); " + df_note)
     if op == "g_field_sep":
         nr1, nr2 = w["grid"][0] // w["reduction"], w["grid"][1] // w["reduction"]
         B = 4 * w["tau"] + 1
@@ -321,16 +323,17 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
         cmacs = Q * nc * Lp * nc + Q * Lp * Lp * nc + npair * Lp * B * Lp + npair * B * B * Lp
         passes = 4
         if "gram_pairs_df" in prof:  # the inverse passes run inside the fused pair stage
-            cmacs, passes = Q * nc * Lp * nc + Q * Lp * Lp * nc, 2
-        return dict(bound="alu", achieved=8.0 * cmacs / passes / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
-                    unit="TFLOP/s (FP64-equivalent)",
-                    note="Gram DFT passes: FP64-equivalent flops per pass against the nominal FP64 peak"
-                         + ("; computed in double-float FP32 pairs" if op == "gram_dft_df" else ""))
+            cmacs, passes = Q * nc * Lp * nc + Q * Lp * Lp * nc, 1
+        if op == "gram_dft_df":
+            return dict(bound="alu", achieved=60.0 * cmacs / passes * mpl / avg_s / 1e12, peak=inst_peak,
+                        unit="Tinst/s", note="Gram forward DFT of every coil; " + df_note)
+        return dict(bound="alu", achieved=8.0 * cmacs / passes * mpl / avg_s / 1e12, peak=FP64_PEAK_TFLOPS,
+                    unit="TFLOP/s", note="Gram DFT passes in FP64 against the nominal FP64 peak")
     if op == "eig_jacobi":
         work = 8.0 * 2 * m * m * m * max(1, stats["jacobi_sweeps"])
-        return dict(bound="alu", achieved=work / avg_s / 1e12, peak=FP32_PEAK_TFLOPS / SMS, unit="TFLOP/s",
-                    note="one-CTA Jacobi: peak is one SM's FP32 rate")
-    byts = 0.0
+        return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP32_PEAK_TFLOPS * min(mpl, SMS) / SMS,
+                    unit="TFLOP/s", note="one-CTA Jacobi per map set: peak is the FP32 rate of the SMs the launch "
+                                         "occupies (one per map set)")
     return dict(bound="latency", achieved=None, peak=None, unit=None, note=f"no roofline formula for {op}")
 
 
@@ -398,7 +401,7 @@ def run_gpu(args):
     nb = args.batch
     bcal = [calibs[i % N_CASES].clone() for i in range(nb)]
     tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
-                          "gram_df": False, "tc_interp": False}, [])
+                          "gram_df": False, "tc_interp": False, "batch_group": 0}, [])
     if args.launch_config:
         tuned = dict(tuned, **json.loads(args.launch_config))
     elif args.tune:
@@ -420,26 +423,23 @@ def run_gpu(args):
         single[prec] = len(ms) / (sum(ms) / 1e3)
         e1.close()
     plain_value = single["fp32"]
-    # ---- op profile of one map (eager launches, CUDA events around each operation) ----
-    est = PiscoEstimator(w["grid"], w["calib"], w["Q"], w["tau"], kernel_shape=w["shape"],
-                         thr=w["thr"], reduction=w["reduction"], iters=w["iters"], seed=0,
-                         precision=tuned["precision"], tc_splits=tuned["tc_splits"],
-                         gemm_splits=tuned["gemm_splits"], gemm_tile=tuned["gemm_tile"], gram_df=tuned["gram_df"],
-                         tc_interp=tuned.get("tc_interp", False))
-    est.estimate_into(calibs[0], maps1, eig1)
-    stats = est.stats()
-    est.set_profiling(True)
-    est.estimate_into(calibs[0], maps1, eig1)
-    est.estimate_into(calibs[0], maps1, eig1)
-    est.profile_reset()
-    for i in range(min(args.steps, 20)):
+    # ---- op profile of the batched step: the same batch configuration run eagerly, CUDA events
+    #      around every operation (each one launch over a group's items) ----
+    pb = PiscoBatch([dict(spec, **tuned)] * nb)
+    pio = (bcal,) + tuple(pb.alloc_outputs())
+    pb.estimate_into(*pio)
+    stats = pb.item_stats(0)
+    groups = pb.groups()
+    pb.set_profiling(True)
+    pb.estimate_into(*pio)
+    pb.profile_reset()
+    nprof = min(args.steps, 10)
+    for i in range(nprof):
         flush.zero_()
-        est.estimate_into(calibs[i % N_CASES], maps1, eig1)
+        pb.estimate_into(*pio)
     torch.cuda.synchronize()
-    prof = est.profile()
-    nprof = min(args.steps, 20)
-    est.set_profiling(False)
-    est.close()
+    prof = pb.profile()
+    pb.close()
 
     # ---- batched form: one step = one CUDA-graph launch over `batch` maps ----
     batch = PiscoBatch([dict(spec, **tuned)] * nb)
@@ -510,20 +510,23 @@ def run_gpu(args):
     peaks = _peaks()
     stages = {}
     for op in prof:
-        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"], tuned.get("tc_interp", False), nprof)
+        r = roofline_for(op, prof, w, stats, peaks, tuned["precision"], tuned.get("tc_interp", False),
+                         nb * nprof, groups["largest"])
         if r.get("achieved") is not None and r.get("peak"):
             r["frac"] = r["achieved"] / r["peak"]
-        r["ms_per_map"] = prof[op][0] / nprof
+        r["ms_per_step"] = prof[op][0] / nprof
+        r["launches_per_step"] = prof[op][1] / nprof
         stages[op] = r
     dom = max(prof, key=lambda k: prof[k][0]) if prof else None
     roof = dict(stages[dom]) if dom else {}
-    roof.pop("ms_per_map", None)
+    roof.pop("ms_per_step", None)
     roof["kernel"] = dom
     tr = NCU_TRAFFIC.get(dom) if w is WORKLOAD else None
     roof["traffic"] = tr[0] if tr else None
     if tr:
         roof["traffic_source"] = tr[1]
-    roof["measured"] = "CUDA events around each launch of the op in the profiled single-map pass"
+    roof["measured"] = (f"CUDA events around each launch of the op in eager runs of the timed batch configuration "
+                        f"({groups['groups']} group(s), largest {groups['largest']} map sets per launch)")
 
     line = {
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
@@ -552,7 +555,7 @@ def run_gpu(args):
         "launch_config": dict(tuned, autotuned=bool(args.tune) and not args.launch_config,
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
                                                       f"{'/df' if r.get('gram_df') else ''}"
-                                                      f"{'/ti' if r.get('tc_interp') else ''}":
+                                                      f"{'/ti' if r.get('tc_interp') else ''}/b{r.get('batch_group', 0)}":
                                                       (round(r["ms"], 3) if r["ms"] is not None else "rejected") for r in tune_table}),
         "wall_s": t_wall,
         "gpu_launches": int(binfo["launches"]) * args.steps,
@@ -565,7 +568,8 @@ def run_gpu(args):
         "clocks": clocks,
         "eig": {"k": stats["signal_dim"], "block": stats["eig_block"], "iters": stats["eig_iters"],
                 "jacobi_sweeps": stats["jacobi_sweeps"], "fp64_band": stats["nband"]},
-        "stages": {k: stages[k] for k in sorted(stages, key=lambda k: -stages[k]["ms_per_map"])},
+        "stages": {k: stages[k] for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])},
+        "groups": groups,
         "workspace_bytes_batch": binfo["workspace_bytes"],
     }
     line["item_status_counts"] = {str(k): statuses.count(k) for k in sorted(set(statuses))}
@@ -616,7 +620,7 @@ def run_gpu_uneven(args):
                 for sp in specs]
     calibs = [torch.from_numpy(c).cuda() for c in calibs_h]
     tuned, tune_table = ({"precision": args.precision, "tc_splits": 0, "gemm_splits": 0, "gemm_tile": 0,
-                          "gram_df": False, "tc_interp": False}, [])
+                          "gram_df": False, "tc_interp": False, "batch_group": 0}, [])
     if args.launch_config:
         tuned = dict(tuned, **json.loads(args.launch_config))
     elif args.tune:
@@ -678,7 +682,7 @@ def run_gpu_uneven(args):
         "launch_config": dict(tuned, autotuned=bool(args.tune) and not args.launch_config,
                               candidates_ms_per_step={f"{r['precision']}/tc{r['tc_splits']}/g{r['gemm_splits']}/t{r['gemm_tile']}"
                                                       f"{'/df' if r.get('gram_df') else ''}"
-                                                      f"{'/ti' if r.get('tc_interp') else ''}":
+                                                      f"{'/ti' if r.get('tc_interp') else ''}/b{r.get('batch_group', 0)}":
                                                       (round(r["ms"], 3) if r["ms"] is not None else "rejected") for r in tune_table}),
         "data": "synthetic",
         "config": {"workload": "96 uneven 2D slices (seeded shapes, see phantoms.uneven_slice_specs)",

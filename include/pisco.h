@@ -121,6 +121,12 @@ typedef struct {
   int gemm_splits;        /* split-K cap of the CUDA-core block products (0: automatic, about
                              two CTAs per SM; small values suit batches of concurrent plans)  */
   int gemm_tile;          /* tile of the CUDA-core block products: 0 automatic, 32 or 64      */
+  int batch_group;        /* batches (pisco_batch_plan): most items of identical parameters that
+                             one batched pass estimates together, every stage one launch over
+                             all of them (0: automatic = 64; 1: one launch chain per item).
+                             Batched passes need PISCO_FLAG_TC_GFIELD and neither
+                             PISCO_FLAG_MASKED_GRAM nor PISCO_FLAG_BLOCK_PI; other items run
+                             one chain each.  Ignored by pisco_plan.                          */
 } pisco_params;
 
 typedef struct pisco_plan_s* pisco_plan_t;
@@ -216,19 +222,24 @@ pisco_status pisco_profile_entry(pisco_plan_t plan, int idx, const char** name, 
                                  int* count);
 
 /* Batches of independent estimates (many slices or volumes, sizes and coil counts may
- * differ).  pisco_batch_plan builds one plan per item (params[i], with its own workspace and
- * stream).  pisco_batch_estimate captures every item's path into ONE CUDA graph whose
- * per-item branches run concurrently on the GPU (the small latency-bound kernels of different
- * items then occupy different SMs), launches it on `cuda_stream`, synchronises once and
- * reports each item's status in item_status[i] (may be NULL).  The graph is replayed while
+ * differ; the database setting of Sec. I).  pisco_batch_plan groups the items: items of identical
+ * parameters (up to params.batch_group of them) share one plan whose passes run every stage as
+ * ONE launch over all of them (item-strided workspace; each item's result is bitwise the one
+ * pisco_estimate gives it alone), other items get a plan each.  pisco_batch_estimate captures
+ * every group's pass into ONE CUDA graph whose branches (one per group) run concurrently on the
+ * GPU, launches it on `cuda_stream`, synchronises once and reports each item's status in
+ * item_status[i] (may be NULL).  The graph is replayed while
  * the pointer arrays stay the same.  Pointer arrays hold `count` device pointers with the
  * layouts of pisco_estimate (d_eig may be NULL, or hold NULL entries).  An item whose signal
- * dimension saturates its eigensolver block is re-run alone with a larger block.  Returns the
+ * dimension saturates its eigensolver block, or whose threshold split is not certified yet with
+ * the automatic iteration count, is re-run alone with a larger block or more iterations (its
+ * group keeps the larger setting for later calls).  Returns the
  * most severe item status.  The _host variant takes host pointers (pinned memory for full
  * copy bandwidth): the host->device copies are enqueued on the batch's stream ahead of the graph,
  * the device->host copies right after it (copy-engine copies that overlap the computation of
  * the next host-I/O batch, which is ordered after this batch's computation).  pisco_batch_item exposes item i's plan for
- * pisco_plan_info / pisco_debug_buffer / pisco_get_stats (owned by the batch). */
+ * pisco_plan_info / pisco_debug_buffer / pisco_get_stats (owned by the batch; for an item of a
+ * group, a one-item view into the group's workspace). */
 typedef struct pisco_batch_s* pisco_batch_t;
 pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_stream,
                               pisco_batch_t* out);
@@ -255,6 +266,17 @@ pisco_status pisco_batch_launch(pisco_batch_t b, const void* const* d_calib, voi
 pisco_status pisco_batch_wait(pisco_batch_t b, pisco_status* item_status);
 pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t* workspace_bytes);
 pisco_status pisco_batch_item(pisco_batch_t b, int i, pisco_plan_t* plan);
+/* Operation timing of a batch (as pisco_set_profiling for one plan): while enabled, batch calls
+ * run eagerly (no graph) and every operation of every group's pass, each one launch over the
+ * group's items, is bracketed by CUDA events on the group's stream; totals per operation name
+ * are summed over the groups and enumerated by pisco_batch_profile_entry (idx = 0, 1, ... until
+ * PISCO_ERR_ARG).  pisco_batch_groups reports the number of groups and the items of the
+ * largest. */
+pisco_status pisco_batch_set_profiling(pisco_batch_t b, int enable);
+pisco_status pisco_batch_profile_reset(pisco_batch_t b);
+pisco_status pisco_batch_profile_entry(pisco_batch_t b, int idx, const char** name, double* total_ms,
+                                       int* count);
+pisco_status pisco_batch_groups(pisco_batch_t b, int* groups, int* largest);
 void pisco_batch_destroy(pisco_batch_t b);
 
 /* Allocation-free variant of stage (a).  The paper has no counterpart: this entry point
@@ -354,6 +376,12 @@ pisco_status pisco_set_warm_start(pisco_plan_t plan, pisco_mlp_t mlp, int iters,
  * `cuda_stream`; returns without synchronising.  The first call sets kernel attributes, so
  * make it outside stream capture. */
 size_t pisco_tc_cgemm_pipelined_workspace(int nterms, int M, int N, int K, int splits);
+/* Test hook of the bounded device waits (the paper has no counterpart): while enabled, the
+ * tensor-core products launched by this process issue none of their shared-memory loads and
+ * give up waiting after about 10 ms, so every such launch ends with its wait expired (bit 16 of
+ * the status word: pisco_estimate returns PISCO_ERR_TIMEOUT) and its tensor memory freed.
+ * Nothing else changes; disabling it restores normal products.  Not for production use. */
+void pisco_test_stall_tensor_loads(int enable);
 pisco_status pisco_tc_cgemm_pipelined(int nterms, int M, int N, int K, const float* alpha,
                                       const void* d_A, int lda, const void* d_B, int ldb, int opB,
                                       const float* beta, void* d_C, int ldc, int splits,

@@ -38,7 +38,7 @@ import numpy as np
 
 __all__ = [
     "kernel_support", "difference_set", "calibration_matrix", "nullspace_svd",
-    "filter_response", "G_direct", "jacobi_eigh", "splitmix64", "start_vectors",
+    "nullspace_gram_eigh", "filter_response", "G_direct", "jacobi_eigh", "splitmix64", "start_vectors",
     "power_iteration", "apodised_lowres", "phase_align", "sinc_interp_matrix",
     "sinc_interp", "normalize_maps", "estimate", "grid_points",
 ]
@@ -144,6 +144,22 @@ def nullspace_svd(C, thr=0.05):
     V = Vh.conj().T
     null = sig < thr * sig[0]
     return V[:, null], V[:, ~null], sig
+
+
+def nullspace_gram_eigh(C, thr=0.05):
+    """The split of nullspace_svd from the FP64 Hermitian eigendecomposition of the Gram C^H C
+    (LAPACK) instead of an SVD of C: the eigenvalues are the squared singular values, so
+    sigma_n < thr*sigma_1 reads lambda_n < thr^2 lambda_1 (rounding below zero clipped to 0).
+    For calibration matrices with many rows (3D: (Nc+2 tau)^3), whose SVD with the full left
+    basis is too large.  Returns (V_null, U_signal, sigma) in decreasing order as nullspace_svd.
+    """
+    A = C.conj().T @ C
+    w, V = np.linalg.eigh(0.5 * (A + A.conj().T))
+    order = np.argsort(w)[::-1]
+    w = np.clip(w[order], 0.0, None)
+    V = V[:, order]
+    null = w < thr * thr * w[0]
+    return V[:, null], V[:, ~null], np.sqrt(w)
 
 
 # ----------------------------------------------------------------------------------------

@@ -47,6 +47,7 @@ class pisco_params(ctypes.Structure):
         ("tc_splits", ctypes.c_int),
         ("gemm_splits", ctypes.c_int),
         ("gemm_tile", ctypes.c_int),
+        ("batch_group", ctypes.c_int),
     ]
 
 
@@ -127,6 +128,17 @@ def load():
     lib.pisco_batch_info.restype = ctypes.c_int
     lib.pisco_batch_item.argtypes = [vp, ctypes.c_int, P(vp)]
     lib.pisco_batch_item.restype = ctypes.c_int
+    lib.pisco_test_stall_tensor_loads.argtypes = [ctypes.c_int]
+    lib.pisco_test_stall_tensor_loads.restype = None
+    lib.pisco_batch_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.pisco_batch_set_profiling.restype = ctypes.c_int
+    lib.pisco_batch_profile_reset.argtypes = [vp]
+    lib.pisco_batch_profile_reset.restype = ctypes.c_int
+    lib.pisco_batch_profile_entry.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), P(ctypes.c_double),
+                                              P(ctypes.c_int)]
+    lib.pisco_batch_profile_entry.restype = ctypes.c_int
+    lib.pisco_batch_groups.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int)]
+    lib.pisco_batch_groups.restype = ctypes.c_int
     lib.pisco_batch_destroy.argtypes = [vp]
     lib.pisco_batch_destroy.restype = None
     lib.pisco_gram_lags_noalloc.argtypes = [P(pisco_params), vp, vp, vp]
@@ -169,7 +181,7 @@ def pisco_status_string(status: int) -> str:
 
 def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid", null_threshold=0.05,
                 grid_reduction=1, power_iters=30, seed=0, flags=0, eig_block=0, eig_iters=0, tc_splits=0,
-                gemm_splits=0, gemm_tile=0):
+                gemm_splits=0, gemm_tile=0, batch_group=0):
     """pisco_params from (z,)y,x-ordered Python tuples (the array order); the struct is x,y,z."""
     nd = len(grid)
     pr = pisco_params()
@@ -191,6 +203,7 @@ def make_params(grid, calib, num_coils, kernel_radius, kernel_shape="ellipsoid",
     pr.tc_splits = tc_splits
     pr.gemm_splits = gemm_splits
     pr.gemm_tile = gemm_tile
+    pr.batch_group = batch_group
     return pr
 
 
@@ -302,6 +315,36 @@ def pisco_batch_info(batch):
     c, l, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
     st = load().pisco_batch_info(batch, ctypes.byref(c), ctypes.byref(l), ctypes.byref(w))
     return st, c.value, l.value, w.value
+
+
+def pisco_test_stall_tensor_loads(enable: bool):
+    """Test hook: tensor-core products withhold their loads so their bounded waits expire."""
+    load().pisco_test_stall_tensor_loads(1 if enable else 0)
+
+
+def pisco_batch_set_profiling(batch, enable: bool):
+    return load().pisco_batch_set_profiling(batch, 1 if enable else 0)
+
+
+def pisco_batch_profile_reset(batch):
+    return load().pisco_batch_profile_reset(batch)
+
+
+def pisco_batch_profile(batch):
+    """{name: (total_ms, count)} of the batch's operations (summed over its groups)."""
+    out = {}
+    i = 0
+    name, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int()
+    while load().pisco_batch_profile_entry(batch, i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt)) == PISCO_OK:
+        out[name.value.decode()] = (ms.value, cnt.value)
+        i += 1
+    return out
+
+
+def pisco_batch_groups(batch):
+    g, mx = ctypes.c_int(), ctypes.c_int()
+    st = load().pisco_batch_groups(batch, ctypes.byref(g), ctypes.byref(mx))
+    return st, g.value, mx.value
 
 
 def pisco_batch_item(batch, i):

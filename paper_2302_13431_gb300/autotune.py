@@ -14,7 +14,9 @@ share the GPU:
 * `gemm_tile`: 32x32 or 64x64 output tiles for those products (lower latency vs less SM time);
 * `gram_df`: the Gram's FFT route in FP64 or in double-float arithmetic (pairs of FP32);
 * `tc_interp`: the last interpolation pass as a batched split-TF32 tensor-core GEMM or as the
-  fused CUDA-core interpolate-and-normalise kernel (tried on the best of the others only).
+  fused CUDA-core interpolate-and-normalise kernel (tried on the best of the others only);
+* `batch_group`: how many items of identical parameters one batched pass estimates (0: all of
+  them, up to 64; 1: one launch chain per item; tried on the best of the others only).
 
 A candidate counts only if it passes a correctness gate on the tuning batch: every item returns
 PISCO_OK, with the same signal dimension as the first candidate (plain FP32) and eigenvalue maps
@@ -36,13 +38,13 @@ from .phantoms import make_case
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
-KNOB_KEYS = ("precision", "tc_splits", "gemm_splits", "gemm_tile", "gram_df", "tc_interp")
+KNOB_KEYS = ("precision", "tc_splits", "gemm_splits", "gemm_tile", "gram_df", "tc_interp", "batch_group")
 # knobs toggled one at a time on the best candidate after the main sweep
-REFINE = (("tc_interp", True),)
+REFINE = (("tc_interp", True), ("batch_group", 1), ("batch_group", 16), ("batch_group", 32))
 
 
 def candidates():
-    base = dict(tc_interp=False)
+    base = dict(tc_interp=False, batch_group=0)
     out = [dict(base, precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False),
            dict(base, precision="fp32", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False),
            dict(base, precision="tc_g", tc_splits=0, gemm_splits=2, gemm_tile=64, gram_df=False)]
@@ -134,6 +136,8 @@ def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None,
     if cands is None:
         for knob, val in REFINE:
             c = {k: best[k] for k in KNOB_KEYS}
+            if c[knob] == val:
+                continue
             c[knob] = val
             ms, out = _time_batch([dict(s, **c) for s in specs], calibs, steps, warmup, ref)
             table.append(dict(c, ms=ms) if ms is not None else dict(c, ms=None, rejected=out))

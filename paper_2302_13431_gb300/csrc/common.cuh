@@ -96,12 +96,27 @@ cudaError_t apply_axis_c2z(const float2* in, const double2* M, double2* out, Axi
 cudaError_t apply_axis_z(const double2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
 cudaError_t apply_axis_c(const float2* in, const float2* M, float2* out, AxisView v, cudaStream_t st);
 
-// a1: pair products and Gram expansion
-cudaError_t gram_pair_products(const double2* S, int Q, long long nfreq, double2* P, cudaStream_t st);
-cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* lags, cudaStream_t st);
-cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* scale, cudaStream_t st);
+// a1: pair products and Gram expansion.  `it.n` independent Grams per launch (grid z or y is
+// the item); item i of each per-item buffer starts i * stride elements after item 0.
+struct GramItems {
+  int n = 1;
+  long long calib = 0;   // calibration blocks
+  long long S = 0;       // spectra [Q][nfreq]
+  long long P = 0;       // pair products [npairs][nfreq]
+  long long Rp = 0;      // pair lag boxes [npairs][nbox]
+  long long lags = 0;    // lag tables [Q][Q][nbox] (FP64 and double-float)
+  long long A = 0;       // Gram and its FP32 copy (entries)
+  long long scale = 0;
+};
+cudaError_t gram_pair_products(const double2* S, int Q, long long nfreq, double2* P, cudaStream_t st,
+                               const GramItems& it = GramItems{});
+cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* lags, cudaStream_t st,
+                               const GramItems& it = GramItems{});
+cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* scale, cudaStream_t st,
+                       const GramItems& it = GramItems{});
 cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L, int nbox,
-                        const double* scale, double2* A, float2* A32, cudaStream_t st);
+                        const double* scale, double2* A, float2* A32, cudaStream_t st,
+                        const GramItems& it = GramItems{});
 
 // dense complex GEMM: C = alpha*op(A)*op(B) + beta*C, row-major, op in {'N','C'}
 // Split-K partials go to splitk_ws (ws_elems entries); tile_count must hold 4096 zeroed ints
@@ -111,29 +126,44 @@ cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L,
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* splitk_ws,
-                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits = 0, int tile = 0);
+                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits = 0, int tile = 0,
+                  int items = 1, long long sA = 0, long long sB = 0, long long sC = 0);
 
-// a2: block eigensolver pieces
+// a2: block eigensolver pieces.  Every launcher runs `it.n` independent solves in one launch
+// (grid dimension z, or y for the multi-CTA kernels, indexes the item); item i of a per-item
+// buffer starts i * stride elements after item 0.
+struct EigItems {
+  int n = 1;              // items
+  long long mm = 0;       // m x m blocks (Gram of the block, Rinv / L, Rayleigh-Ritz matrix)
+  long long vj = 0;       // Jacobi output + scratch (2 m_max^2)
+  long long vec = 0;      // m-vectors (scalings, diag(R), Ritz values, weights, FP64 Ritz values)
+  long long nm = 0;       // n x m blocks
+  long long nb = 0;       // band blocks (n x 8)
+  long long band = 0;     // band index vectors
+  long long a = 0;        // FP64 / double-float Gram (entries)
+  long long scale = 0;    // Gram scale
+};
 cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, cudaStream_t st);
 cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_rel,
                      const float* acc_in, float2* L, float* dout, float* diagR, DevStatus* status,
-                     cudaStream_t st);
+                     cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, int m, float2* X,
-                     cudaStream_t st);
+                     cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, float shift_rel,
                                  const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
-                       float skip_rel, DevStatus* status, cudaStream_t st);
+                       float skip_rel, DevStatus* status, cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, const int* band_idx,
-                            double2* Zb, cudaStream_t st);
+                            double2* Zb, cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
-                            cudaStream_t st);
+                            cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, int nb_max,
-                            double2* Xb, cudaStream_t st);
+                            double2* Xb, cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_decide(const float* mu, int m, const int* band_idx, int nb_max, const double2* Xb,
                        const double2* Zb, int n, double thr2, int Q, const double* scale,
-                       float* weights, double* ritz, DevStatus* status, cudaStream_t st);
+                       float* weights, double* ritz, DevStatus* status, cudaStream_t st,
+                       const EigItems& it = EigItems{});
 
 // a3: collapsed kernel and G field
 cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int m,
@@ -141,22 +171,25 @@ cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int 
                              cudaStream_t st);
 cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_size, cudaStream_t st);
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
-                               const int* lag_ent, int nlag, float2* KT, cudaStream_t st);
+                               const int* lag_ent, int nlag, float2* KT, cudaStream_t st, int items = 1,
+                               long long sP = 0, long long sKT = 0);
 
 // the Gram's FFT route in double-float arithmetic (kernels_gram_df.cu); tables and buffers hold
 // {Re hi, Re lo, Im hi, Im lo} float quadruples in the storage of the FP64 path
 cudaError_t apply_axis_c2df(const float2* in, const void* M, void* out, AxisView v, cudaStream_t st);
 cudaError_t apply_axis_df(const void* in, const void* M, void* out, AxisView v, cudaStream_t st);
-cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st);
+cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st,
+                                  const GramItems& it = GramItems{});
 // the lag table is written twice: FP64 (lags) and double-float (lags_df, for the expansion)
-cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, void* lags_df, cudaStream_t st);
+cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, void* lags_df, cudaStream_t st,
+                                  const GramItems& it = GramItems{});
 // A kept as double-float quadruples (no FP64 arithmetic per entry); A32 = A / scale
 cudaError_t gram_expand_df(const void* lags_df, const int* lag_of_ij, int Q, int L, int nbox, const double* scale,
-                           void* A, float2* A32, cudaStream_t st);
+                           void* A, float2* A32, cudaStream_t st, const GramItems& it = GramItems{});
 cudaError_t df_to_fp64(const void* in, long long count, double2* out, cudaStream_t st);
 // a_df: A holds double-float quadruples, else FP64
 cudaError_t eig_band_matvec_df(const void* A, bool a_df, const double2* Xb, int n, int nb, const int* band_idx,
-                               double2* Zb, cudaStream_t st);
+                               double2* Zb, cudaStream_t st, const EigItems& it = EigItems{});
 
 // exact Gram of the masked calibration matrix (kernels_gram.cu): A (FP64 n x n), scale, A32
 cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo, const int* hi, const int* lam,
@@ -165,7 +198,8 @@ cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo
 cudaError_t gram_masked_prepare(int nvol);
 size_t gram_masked_smem(int nvol);
 
-cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st);
+cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st, int items = 1, long long sM = 0,
+                           float2* const* maps_tab = nullptr);
 
 // 2D double-float Gram pairs stage fused per pair (kernels_gram_df.cu): pair product, both
 // inverse lag passes, lag table lags[(p,q)][B1*B2] for p <= q in FP64 and in double-float
@@ -174,9 +208,10 @@ bool gram_pairs_inverse_df_supported(int Lp1, int Lp2, int B1, int B2);
 // 2D double-float forward stage fused per coil: S[q][Lp1][Lp2] from calib[q][Nc1][Nc2]
 bool gram_forward_df_supported(int Nc1, int Nc2, int Lp1, int Lp2);
 cudaError_t gram_forward_df(const float2* calib, int Q, int Nc1, int Nc2, const void* fwdT2, int Lp2, const void* fwd1,
-                            int Lp1, void* S, cudaStream_t st);
+                            int Lp1, void* S, cudaStream_t st, const GramItems& it = GramItems{});
 cudaError_t gram_pairs_inverse_df(const void* S, int Q, int Lp1, int Lp2, const void* invT2, int B2, const void* inv1,
-                                  int B1, double2* lags, void* lags_df, cudaStream_t st);
+                                  int B1, double2* lags, void* lags_df, cudaStream_t st,
+                                  const GramItems& it = GramItems{});
 
 // 2D G(x) from the collapsed lag kernel KT[nlag][Q*Q] by two separable DFT passes
 // (kernels_gassembly.cu); row_ptr[B1+1] groups the lags by row, lag_b2 their column
@@ -184,7 +219,8 @@ constexpr int kGfieldSep2MaxSmem = 200 * 1024;
 bool gassembly_field_sep2_supported(int nlag, int Nr1, int B1, int Nr2, int B2);
 cudaError_t gassembly_field_sep2(const float2* KT, int Q, int nlag, const int* row_ptr, const int* lag_b2,
                                  const float2* E1, int Nr1, int B1, const float2* E2, int B2, int Nr2,
-                                 float lam_size, float2* G, cudaStream_t st);
+                                 float lam_size, float2* G, cudaStream_t st, int items = 1, long long sKT = 0,
+                                 long long sG = 0);
 
 // warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out, widths <= 128; w32 is the FP32
 // parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its FP16 copy (the
@@ -215,17 +251,25 @@ cudaError_t mlp_features(const float2* Y, int Q, long long npix, float* X, cudaS
 int tc2_k2p(int K);
 int tc2_np(int N);
 cudaError_t tc2_prepare();
+// test hook: while set, tensor-core GEMM launches issue no TMA loads and wait ~10 ms at most, so
+// their bounded waits expire with nothing in flight (bit 16 of err, TMEM freed as always)
+void tc2_set_stall(bool on);
+// The split kernels take `items` independent operands (inputs item_stride elements apart, the
+// split arrays one after another).
 cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
-                        cudaStream_t st);
+                        cudaStream_t st, int items = 1, long long a_stride = 0, long long w_stride = 0);
 cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st,
                         int nbatch = 1, long long b_stride = 0);
-cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st);
-// nbatch > 1: gridDim.z runs nbatch products C_b = A B_b sharing A (B' items of 2 Np rows one
-// after another, C_b at C + b c_stride; no split-K)
+cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st,
+                         int items = 1, long long y_stride = 0);
+// nbatch > 1: gridDim.z runs nbatch products C_b = A_b B_b (B' items of 2 Np rows one after
+// another; A shared, or with a_per_item one A' of M rows per item; C_b at C + b c_stride, or at
+// c_tab[b / c_div] + (b % c_div) c_stride; no split-K)
 cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
-                     int nbatch = 1, long long c_stride = 0);
+                     int nbatch = 1, long long c_stride = 0, int a_per_item = 0, float2* const* c_tab = nullptr,
+                     int c_div = 1, int b_per_item = 1);
 
 
 // a4+a5: power iteration with the phase step
@@ -241,14 +285,21 @@ struct PiOpts {
   int* flags = nullptr;
   int* count = nullptr;
   const int* only = nullptr;
+  // independent estimates in one launch (grid y = item): G, Y, V of item i start i * sG, sY, sV
+  // elements after item 0; its eigenvalues go to eig_tab[i] (or eig + i * sE)
+  int items = 1;
+  long long sG = 0, sY = 0, sV = 0, sE = 0;
+  float* const* eig_tab = nullptr;
 };
 cudaError_t power_iteration(const float2* G, const float2* Y, int Q, long long npix, int iters,
                             float lam_size, unsigned long long seed, float2* V, float* eig,
                             cudaStream_t st, const PiOpts& opt = PiOpts{});
 
 // a6: final interpolation pass along the slowest axis fused with unit-norm normalisation
+// (items independent outputs: T of item i at T + i * sT, maps at maps_tab[i] or maps + i * sM)
 cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long long outer_dummy,
                                    int n_in, int n_out, long long inner, float2* maps,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int items = 1, long long sT = 0, long long sM = 0,
+                                   float2* const* maps_tab = nullptr);
 
 }  // namespace pisco

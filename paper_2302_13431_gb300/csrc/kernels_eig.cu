@@ -59,8 +59,18 @@ __global__ void __launch_bounds__(256) chol_kernel(const float2* __restrict__ Gm
                                                    float2* __restrict__ Lout,
                                                    float* __restrict__ dout,
                                                    float* __restrict__ diagR,
-                                                   DevStatus* status) {
+                                                   DevStatus* status, EigItems it) {
   extern __shared__ float2 sm[];
+  {
+    const int i = blockIdx.z;
+    Gm += i * it.mm;
+    if (dscale) dscale += i * it.vec;
+    if (acc_in) acc_in += i * it.vec;
+    Lout += i * it.mm;
+    dout += i * it.vec;
+    diagR += i * it.vec;
+    if (status) status += i;
+  }
   float2* Lm = sm;                                   // m*m
   float* ds = reinterpret_cast<float*>(Lm + m * m);  // m (scaling)
   float* dg = ds + m;                                // m (pivots)
@@ -161,8 +171,17 @@ __global__ void __launch_bounds__(256) chol_inv_blocked_kernel(const float2* __r
                                                                const float* __restrict__ acc_in,
                                                                float2* __restrict__ Rinv,
                                                                float* __restrict__ diagR,
-                                                               DevStatus* status) {
+                                                               DevStatus* status, EigItems it) {
   extern __shared__ float2 sm[];
+  {
+    const int i = blockIdx.z;
+    Gm += i * it.mm;
+    if (dscale) dscale += i * it.vec;
+    if (acc_in) acc_in += i * it.vec;
+    Rinv += i * it.mm;
+    diagR += i * it.vec;
+    if (status) status += i;
+  }
   const int NB = (m + CB - 1) / CB, M = NB * CB;
   float2* A = sm;                                    // M*M, L in the lower triangle
   float2* Li = A + M * M;                            // M*M, L^-1 (lower)
@@ -371,8 +390,12 @@ template <int MP>
 __global__ void __launch_bounds__(128) trsm_rows_kernel(const float2* __restrict__ Y,
                                                         const float2* __restrict__ Lg,
                                                         const float* __restrict__ ds, int n, int m,
-                                                        float2* __restrict__ X) {
+                                                        float2* __restrict__ X, EigItems it) {
   extern __shared__ float2 sm[];
+  Y += blockIdx.y * it.nm;
+  Lg += blockIdx.y * it.mm;
+  ds += blockIdx.y * it.vec;
+  X += blockIdx.y * it.nm;
   float2* Ls = sm;                                       // m*m
   float* dinv = reinterpret_cast<float*>(Ls + m * m);    // m
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ls[e] = Lg[e];
@@ -408,8 +431,12 @@ __global__ void __launch_bounds__(128) trsm_rows_kernel(const float2* __restrict
 __global__ void __launch_bounds__(256) trsm_rows_warp_kernel(const float2* __restrict__ Y,
                                                              const float2* __restrict__ Lg,
                                                              const float* __restrict__ ds, int n,
-                                                             int m, float2* __restrict__ X) {
+                                                             int m, float2* __restrict__ X, EigItems it) {
   extern __shared__ float2 sm[];
+  Y += blockIdx.y * it.nm;
+  Lg += blockIdx.y * it.mm;
+  ds += blockIdx.y * it.vec;
+  X += blockIdx.y * it.nm;
   float2* Ls = sm;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ls[e] = Lg[e];
   __syncthreads();
@@ -463,7 +490,7 @@ __global__ void __launch_bounds__(256) trsm_rows_warp_kernel(const float2* __res
 
 cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_rel,
                      const float* acc_in, float2* L, float* dout, float* diagR, DevStatus* status,
-                     cudaStream_t st) {
+                     cudaStream_t st, const EigItems& it) {
   if (m > 128) return cudaErrorInvalidValue;
   const size_t smem = (size_t)m * m * sizeof(float2) + 2 * m * sizeof(float);
   static bool attr_set = false;
@@ -471,15 +498,15 @@ cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_r
     cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  chol_kernel<<<1, 256, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, L, dout, diagR, status);
+  chol_kernel<<<dim3(1, 1, it.n), 256, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, L, dout, diagR, status, it);
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, float shift_rel,
                                  const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
-                                 cudaStream_t st) {
-  if (m > 96) return cudaErrorInvalidValue;
+                                 cudaStream_t st, const EigItems& it) {
+  if (m > 64) return cudaErrorInvalidValue;  // the panel step covers 64 rows
   const int M = ((m + CB - 1) / CB) * CB;
   const size_t smem = 2 * (size_t)M * M * sizeof(float2) + 2 * M * sizeof(float);
   static bool attr_set = false;
@@ -487,13 +514,14 @@ cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, f
     cudaFuncSetAttribute(chol_inv_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  chol_inv_blocked_kernel<<<1, 256, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, Rinv, diagR, status);
+  chol_inv_blocked_kernel<<<dim3(1, 1, it.n), 256, smem, st>>>(Gm, m, dscale, shift_rel, acc_in, Rinv, diagR,
+                                                              status, it);
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, int m, float2* X,
-                     cudaStream_t st) {
+                     cudaStream_t st, const EigItems& it) {
   if (m > 128) return cudaErrorInvalidValue;
   const size_t smem = (size_t)m * m * sizeof(float2) + m * sizeof(float);
   static bool attr_set = false;
@@ -504,13 +532,13 @@ cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, i
     attr_set = true;
   }
   if (m <= 32) {
-    trsm_rows_kernel<32><<<(n + 127) / 128, 128, smem, st>>>(Y, L, ds, n, m, X);
+    trsm_rows_kernel<32><<<dim3((n + 127) / 128, it.n), 128, smem, st>>>(Y, L, ds, n, m, X, it);
   } else if (m <= 64) {
-    trsm_rows_kernel<64><<<(n + 127) / 128, 128, smem, st>>>(Y, L, ds, n, m, X);
+    trsm_rows_kernel<64><<<dim3((n + 127) / 128, it.n), 128, smem, st>>>(Y, L, ds, n, m, X, it);
   } else {
     int blocks = (n + 7) / 8;
     if (blocks > 152) blocks = 152;
-    trsm_rows_warp_kernel<<<blocks, 256, smem, st>>>(Y, L, ds, n, m, X);
+    trsm_rows_warp_kernel<<<dim3(blocks, it.n), 256, smem, st>>>(Y, L, ds, n, m, X, it);
   }
   ++g_launches;
   return cudaGetLastError();
@@ -532,8 +560,13 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
                                                      float* __restrict__ mu,
                                                      float2* __restrict__ Vout,
                                                      float2* __restrict__ Vg, int max_sweeps,
-                                                     float skip_rel, DevStatus* status) {
+                                                     float skip_rel, DevStatus* status, EigItems it) {
   extern __shared__ float2 sm[];
+  Bin += blockIdx.z * it.mm;
+  mu += blockIdx.z * it.vec;
+  Vout += blockIdx.z * it.vj;
+  Vg += blockIdx.z * it.vj;
+  if (status) status += blockIdx.z;
   float2* Bs = sm;                                         // m*m
   float2* Vw = VSMEM ? (Bs + m * m) : Vg;                  // m*m
   float* rc = reinterpret_cast<float*>(Bs + (VSMEM ? 2 : 1) * m * m);  // c, s*er, s*ei per pair (+pad)
@@ -663,7 +696,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
 }
 
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
-                       float skip_rel, DevStatus* status, cudaStream_t st) {
+                       float skip_rel, DevStatus* status, cudaStream_t st, const EigItems& it) {
   // V must have room for 2*m*m entries: [0, m*m) output, [m*m, 2*m*m) scratch
   const bool vsmem = m <= 96;
   const size_t smem = (size_t)(vsmem ? 2 : 1) * m * m * sizeof(float2) + 4 * (m / 2) * sizeof(float) +
@@ -676,9 +709,11 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
   }
   const int threads = 512;
   if (vsmem)
-    jacobi_kernel<true><<<1, threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps, skip_rel, status);
+    jacobi_kernel<true><<<dim3(1, 1, it.n), threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps,
+                                                                 skip_rel, status, it);
   else
-    jacobi_kernel<false><<<1, threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps, skip_rel, status);
+    jacobi_kernel<false><<<dim3(1, 1, it.n), threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps,
+                                                                  skip_rel, status, it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -689,7 +724,9 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
 // (in log distance) first, -1 padded.
 // ---------------------------------------------------------------------------------------
 __global__ void select_band_kernel(const float* __restrict__ mu, int m, double thr2, int nb_max,
-                                   int* __restrict__ band_idx) {
+                                   int* __restrict__ band_idx, EigItems it) {
+  mu += blockIdx.z * it.vec;
+  band_idx += blockIdx.z * it.band;
   // candidate j >= 1 with |log2(mu_j/theta)| <= 2; rank by (distance, index); the nb_max-1
   // nearest fill band_idx[1..]
   const int j = threadIdx.x;
@@ -713,14 +750,18 @@ __global__ void select_band_kernel(const float* __restrict__ mu, int m, double t
 }
 
 cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
-                            cudaStream_t st) {
-  select_band_kernel<<<1, 128, 0, st>>>(mu, m, thr2, nb_max, band_idx);
+                            cudaStream_t st, const EigItems& it) {
+  select_band_kernel<<<dim3(1, 1, it.n), 128, 0, st>>>(mu, m, thr2, nb_max, band_idx, it);
   ++g_launches;
   return cudaGetLastError();
 }
 
 __global__ void gather_band_kernel(const float2* __restrict__ X, int n, int m,
-                                   const int* __restrict__ band_idx, int nb_max, double2* __restrict__ Xb) {
+                                   const int* __restrict__ band_idx, int nb_max, double2* __restrict__ Xb,
+                                   EigItems it) {
+  X += blockIdx.y * it.nm;
+  band_idx += blockIdx.y * it.band;
+  Xb += blockIdx.y * it.nb;
   const long long total = (long long)n * nb_max;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -731,10 +772,10 @@ __global__ void gather_band_kernel(const float2* __restrict__ X, int n, int m,
 }
 
 cudaError_t eig_gather_band(const float2* X, int n, int m, const int* band_idx, int nb_max,
-                            double2* Xb, cudaStream_t st) {
+                            double2* Xb, cudaStream_t st, const EigItems& it) {
   long long blocks = ((long long)n * nb_max + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  gather_band_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, n, m, band_idx, nb_max, Xb);
+  gather_band_kernel<<<dim3((unsigned)blocks, it.n), 256, 0, st>>>(X, n, m, band_idx, nb_max, Xb, it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -748,8 +789,12 @@ template <int NBV>
 __global__ void __launch_bounds__(256) band_matvec_kernel(const double2* __restrict__ A,
                                                           const double2* __restrict__ Xb, int n,
                                                           const int* __restrict__ band_idx,
-                                                          double2* __restrict__ Zb) {
+                                                          double2* __restrict__ Zb, EigItems it) {
   constexpr int KC = 256;  // rows of Xb per chunk (32 KiB of shared memory for 8 columns)
+  A += blockIdx.y * it.a;
+  Xb += blockIdx.y * it.nb;
+  band_idx += blockIdx.y * it.band;
+  Zb += blockIdx.y * it.nb;
   __shared__ double2 xs[KC * NBV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.x * 8 + warp;
@@ -790,9 +835,9 @@ __global__ void __launch_bounds__(256) band_matvec_kernel(const double2* __restr
 }
 
 cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, const int* band_idx,
-                            double2* Zb, cudaStream_t st) {
+                            double2* Zb, cudaStream_t st, const EigItems& it) {
   if (nb != 8) return cudaErrorInvalidValue;
-  band_matvec_kernel<8><<<(n + 7) / 8, 256, 0, st>>>(A, Xb, n, band_idx, Zb);
+  band_matvec_kernel<8><<<dim3((n + 7) / 8, it.n), 256, 0, st>>>(A, Xb, n, band_idx, Zb, it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -816,8 +861,20 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
                                                      double thr2, int Q,
                                                      const double* __restrict__ scale,
                                                      float* __restrict__ w,
-                                                     double* __restrict__ ritz, DevStatus* status) {
+                                                     double* __restrict__ ritz, DevStatus* status,
+                                                     EigItems it) {
   __shared__ double num[32], den[32], res[32], bnd[32];
+  {
+    const int i = blockIdx.z;
+    mu += i * it.vec;
+    band_idx += i * it.band;
+    Xb += i * it.nb;
+    Zb += i * it.nb;
+    scale += i * it.scale;
+    w += i * it.vec;
+    ritz += i * it.vec;
+    status += i;
+  }
   __shared__ double s_lmax;
   __shared__ int s_uncert;
   const int tid = threadIdx.x;
@@ -929,8 +986,9 @@ __global__ void __launch_bounds__(256) decide_kernel(const float* __restrict__ m
 
 cudaError_t eig_decide(const float* mu, int m, const int* band_idx, int nb_max, const double2* Xb,
                        const double2* Zb, int n, double thr2, int Q, const double* scale,
-                       float* weights, double* ritz, DevStatus* status, cudaStream_t st) {
-  decide_kernel<<<1, 256, 0, st>>>(mu, m, band_idx, nb_max, Xb, Zb, n, thr2, Q, scale, weights, ritz, status);
+                       float* weights, double* ritz, DevStatus* status, cudaStream_t st, const EigItems& it) {
+  decide_kernel<<<dim3(1, 1, it.n), 256, 0, st>>>(mu, m, band_idx, nb_max, Xb, Zb, n, thr2, Q, scale, weights,
+                                                 ritz, status, it);
   ++g_launches;
   return cudaGetLastError();
 }

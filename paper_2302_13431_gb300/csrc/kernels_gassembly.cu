@@ -116,7 +116,9 @@ namespace pisco {
 // K x N operand of the second GEMM, G[x][pq] = |Lambda| delta_pq - sum_l E[x][l] KT[l][pq].
 __global__ void collapse_lags_kernel(const float2* __restrict__ P, int n, int Q, int L,
                                      const int* __restrict__ lagc_ptr, const int* __restrict__ lag_ent,
-                                     int nlag, float2* __restrict__ KT) {
+                                     int nlag, float2* __restrict__ KT, long long sP, long long sKT) {
+  P += blockIdx.y * sP;
+  KT += blockIdx.y * sKT;
   const int QQ = Q * Q;
   const long long total = (long long)nlag * QQ;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -137,11 +139,14 @@ __global__ void collapse_lags_kernel(const float2* __restrict__ P, int n, int Q,
 }
 
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
-                               const int* lag_ent, int nlag, float2* KT, cudaStream_t st) {
+                               const int* lag_ent, int nlag, float2* KT, cudaStream_t st, int items, long long sP,
+                               long long sKT) {
   const long long total = (long long)nlag * Q * Q;
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  collapse_lags_kernel<<<(unsigned)blocks, 256, 0, st>>>(P, n, Q, L, lagc_ptr, lag_ent, nlag, KT);
+  blocks = (blocks + items - 1) / items;
+  collapse_lags_kernel<<<dim3((unsigned)blocks, items), 256, 0, st>>>(P, n, Q, L, lagc_ptr, lag_ent, nlag, KT, sP,
+                                                                      sKT);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -165,8 +170,11 @@ __global__ void __launch_bounds__(256) gfield_sep2_kernel(const float2* __restri
                                                           const int* __restrict__ lag_b2,
                                                           const float2* __restrict__ E1, int Nr1,
                                                           const float2* __restrict__ E2, int B2, int Nr2,
-                                                          float lam_size, float2* __restrict__ G) {
+                                                          float lam_size, float2* __restrict__ G, long long sKT,
+                                                          long long sG) {
   extern __shared__ float2 sm[];
+  KT += blockIdx.z * sKT;
+  G += blockIdx.z * sG;
   float2* e1s = sm;                          // [Nr1][NB]
   float2* e2s = e1s + Nr1 * NB;              // [Nr2][B2]
   float2* ks = e2s + Nr2 * B2;               // [nlag][32]
@@ -236,16 +244,17 @@ namespace {
 constexpr int kSepXPT = 2;
 template <int NB>
 cudaError_t launch_sep2(const float2* KT, int Q, int nlag, const int* row_ptr, const int* lag_b2, const float2* E1,
-                        int Nr1, const float2* E2, int B2, int Nr2, float lam_size, float2* G, cudaStream_t st) {
+                        int Nr1, const float2* E2, int B2, int Nr2, float lam_size, float2* G, cudaStream_t st,
+                        int items, long long sKT, long long sG) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(gfield_sep2_kernel<NB, kSepXPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kGfieldSep2MaxSmem);
     attr_set = true;
   }
-  const dim3 grid((unsigned)((Q * Q + 31) / 32), (unsigned)((Nr2 + 8 * kSepXPT - 1) / (8 * kSepXPT)));
+  const dim3 grid((unsigned)((Q * Q + 31) / 32), (unsigned)((Nr2 + 8 * kSepXPT - 1) / (8 * kSepXPT)), items);
   gfield_sep2_kernel<NB, kSepXPT><<<grid, 256, gfield_sep2_smem(nlag, Nr1, NB, Nr2, B2), st>>>(
-      KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G);
+      KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, sKT, sG);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -258,14 +267,14 @@ bool gassembly_field_sep2_supported(int nlag, int Nr1, int B1, int Nr2, int B2) 
 
 cudaError_t gassembly_field_sep2(const float2* KT, int Q, int nlag, const int* row_ptr, const int* lag_b2,
                                  const float2* E1, int Nr1, int B1, const float2* E2, int B2, int Nr2,
-                                 float lam_size, float2* G, cudaStream_t st) {
+                                 float lam_size, float2* G, cudaStream_t st, int items, long long sKT, long long sG) {
   switch (B1) {
-    case 5: return launch_sep2<5>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
-    case 9: return launch_sep2<9>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
-    case 13: return launch_sep2<13>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
-    case 17: return launch_sep2<17>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
-    case 21: return launch_sep2<21>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
-    case 25: return launch_sep2<25>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st);
+    case 5: return launch_sep2<5>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st, items, sKT, sG);
+    case 9: return launch_sep2<9>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st, items, sKT, sG);
+    case 13: return launch_sep2<13>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st, items, sKT, sG);
+    case 17: return launch_sep2<17>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st, items, sKT, sG);
+    case 21: return launch_sep2<21>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st, items, sKT, sG);
+    case 25: return launch_sep2<25>(KT, Q, nlag, row_ptr, lag_b2, E1, Nr1, E2, B2, Nr2, lam_size, G, st, items, sKT, sG);
     default: return cudaErrorInvalidValue;
   }
 }

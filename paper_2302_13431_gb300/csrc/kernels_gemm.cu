@@ -4,8 +4,10 @@
 // Used by the block eigensolver of stage (b): the n x n by n x m products with the Gram
 // (FP32 subspace iteration, FP64 Rayleigh quotients) and the thin n x m / m x m products of
 // the Rayleigh-Ritz and Cholesky-QR steps.  The shapes are skinny (m = 32..128), so a CTA
-// owns a 32 x 32 output tile and K is split across grid.z until the grid covers the 152 SMs;
-// split partials are reduced in a second deterministic pass.
+// owns a 32 x 32 (or 64 x 64) output tile and K is split across CTAs until the grid covers the
+// 152 SMs; the last CTA of a tile sums the split partials in a fixed order.  `items`
+// independent products (operands sA, sB, sC elements apart) run in the same launch: grid.z is
+// item * splits + split.
 #include <algorithm>
 
 #include "common.cuh"
@@ -15,7 +17,7 @@ namespace pisco {
 namespace {
 constexpr int BM = 32, BN = 32, BK = 16;
 }  // namespace
-constexpr int kMaxTiles = 4096;  // tile counters the caller provides
+constexpr int kMaxTiles = 4096;  // tile counters the caller provides per item
 namespace {
 
 template <typename T>
@@ -24,14 +26,19 @@ __global__ void __launch_bounds__(256) cgemm_kernel(char opA, char opB, int M, i
                                                     int lda, const cpx<T>* __restrict__ B, int ldb,
                                                     cpx<T> beta, cpx<T>* __restrict__ C, int ldc,
                                                     cpx<T>* __restrict__ ws, int kchunk,
-                                                    int* __restrict__ tile_count) {
+                                                    int* __restrict__ tile_count, int splits,
+                                                    long long sA, long long sB, long long sC) {
   using Cx = cpx<T>;
   __shared__ Cx As[BK][BM + 1];
   __shared__ Cx Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-  const int kbeg = blockIdx.z * kchunk;
+  const int item = blockIdx.z / splits, split = blockIdx.z % splits;
+  A += item * sA;
+  B += item * sB;
+  C += item * sC;
+  const int kbeg = split * kchunk;
   const int kend = min(K, kbeg + kchunk);
   Cx acc[2][2];
 #pragma unroll
@@ -76,7 +83,7 @@ __global__ void __launch_bounds__(256) cgemm_kernel(char opA, char opB, int M, i
     }
     __syncthreads();
   }
-  if (gridDim.z == 1) {
+  if (splits == 1) {
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -101,8 +108,8 @@ __global__ void __launch_bounds__(256) cgemm_kernel(char opA, char opB, int M, i
   __threadfence();
   __syncthreads();
   __shared__ int s_last;
-  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tid == 0) s_last = (atomicAdd(&tile_count[tile], 1) == (int)gridDim.z - 1);
+  const int tile = item * kMaxTiles + blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid == 0) s_last = (atomicAdd(&tile_count[tile], 1) == splits - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(256) cgemm_kernel(char opA, char opB, int M, i
       const int gr = r0 + ty * 2 + i, gc = c0 + tx * 2 + j;
       if (gr >= M || gc >= N) continue;
       Cx sum = mk(T(0), T(0));
-      for (int z = 0; z < (int)gridDim.z; ++z) sum = cadd(sum, __ldcg(&ws[((long long)z * M + gr) * N + gc]));
+      for (int z = 0; z < splits; ++z) sum = cadd(sum, __ldcg(&ws[((long long)(item * splits + z) * M + gr) * N + gc]));
       Cx out = cmul(alpha, sum);
       if (beta.x != T(0) || beta.y != T(0)) out = cadd(out, cmul(beta, C[(long long)gr * ldc + gc]));
       C[(long long)gr * ldc + gc] = out;
@@ -134,14 +141,19 @@ __global__ void __launch_bounds__(256) cgemm64_kernel(char opA, char opB, int M,
                                                       int lda, const cpx<T>* __restrict__ B, int ldb,
                                                       cpx<T> beta, cpx<T>* __restrict__ C, int ldc,
                                                       cpx<T>* __restrict__ ws, int kchunk,
-                                                      int* __restrict__ tile_count) {
+                                                      int* __restrict__ tile_count, int splits,
+                                                      long long sA, long long sB, long long sC) {
   using Cx = cpx<T>;
   __shared__ Cx As[BK2][BM2 + 1];
   __shared__ Cx Bs[BK2][BN2 + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.y * BM2, c0 = blockIdx.x * BN2;
-  const int kbeg = blockIdx.z * kchunk;
+  const int item = blockIdx.z / splits, split = blockIdx.z % splits;
+  A += item * sA;
+  B += item * sB;
+  C += item * sC;
+  const int kbeg = split * kchunk;
   const int kend = min(K, kbeg + kchunk);
   Cx acc[4][4];
 #pragma unroll
@@ -181,7 +193,7 @@ __global__ void __launch_bounds__(256) cgemm64_kernel(char opA, char opB, int M,
     }
     __syncthreads();
   }
-  if (gridDim.z == 1) {
+  if (splits == 1) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -204,19 +216,19 @@ __global__ void __launch_bounds__(256) cgemm64_kernel(char opA, char opB, int M,
   __threadfence();
   __syncthreads();
   __shared__ int s_last;
-  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tid == 0) s_last = (atomicAdd(&tile_count[tile], 1) == (int)gridDim.z - 1);
+  const int tile = item * kMaxTiles + blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid == 0) s_last = (atomicAdd(&tile_count[tile], 1) == splits - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const int nz = gridDim.z;
+  const int nz = splits;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gr = r0 + ty + 16 * i, gc = c0 + tx + 16 * j;
       if (gr >= M || gc >= N) continue;
-      const cpx<T>* src = ws + (long long)gr * N + gc;
+      const cpx<T>* src = ws + (long long)item * splits * M * N + (long long)gr * N + gc;
       const long long stride = (long long)M * N;
       Cx s0 = mk(T(0), T(0)), s1 = s0, s2 = s0, s3 = s0;
       int z = 0;
@@ -239,8 +251,9 @@ __global__ void __launch_bounds__(256) cgemm64_kernel(char opA, char opB, int M,
 template <typename T>
 cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const cpx<T>* A, int lda,
                   const cpx<T>* B, int ldb, cpx<T> beta, cpx<T>* C, int ldc, cpx<T>* ws,
-                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits, int tile) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
+                  size_t ws_elems, int* tile_count, cudaStream_t st, int max_splits, int tile, int items,
+                  long long sA, long long sB, long long sC) {
+  if (M <= 0 || N <= 0 || items < 1) return cudaSuccess;
   // automatic: 64x64 tiles only for large K (the 32x32 kernel has the lower latency for the
   // skinny shapes of one solve); tile = 64 / 32 forces one (64x64 costs less SM time per flop)
   const bool big = tile == 64 || (tile != 32 && M >= 48 && N >= 48 && K >= 4096);
@@ -249,18 +262,20 @@ cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const c
     const int tiles2 = ((M + BM2 - 1) / BM2) * ((N + BN2 - 1) / BN2);
     const int kb = K > 0 ? (K + BK2 - 1) / BK2 : 1;
     int sp = 1;
+    // the split of one product does not depend on the batch (an item's result is the same
+    // whether it runs alone or in a batch)
     if (ws != nullptr && tile_count != nullptr && tiles2 <= kMaxTiles) {
       sp = (152 + tiles2 - 1) / tiles2;
       sp = std::min(sp, std::max(1, kb / 2));
       sp = std::min(sp, 16);
       if (max_splits > 0) sp = std::min(sp, max_splits);
-      while (sp > 1 && (size_t)sp * M * N > ws_elems) --sp;
+      while (sp > 1 && (size_t)sp * M * N * items > ws_elems) --sp;
     }
     const int kc = ((kb + sp - 1) / sp) * BK2;
     sp = K > 0 ? (K + kc - 1) / kc : 1;
-    dim3 grid2((N + BN2 - 1) / BN2, (M + BM2 - 1) / BM2, sp);
+    dim3 grid2((N + BN2 - 1) / BN2, (M + BM2 - 1) / BM2, sp * items);
     cgemm64_kernel<T><<<grid2, 256, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws,
-                                             kc, tile_count);
+                                             kc, tile_count, sp, sA, sB, sC);
     ++g_launches;
     return cudaGetLastError();
   }
@@ -272,22 +287,23 @@ cudaError_t cgemm(char opA, char opB, int M, int N, int K, cpx<T> alpha, const c
     if (splits > kblocks) splits = kblocks;
     if (splits > 64) splits = 64;
     if (max_splits > 0 && splits > max_splits) splits = max_splits;
-    while (splits > 1 && (size_t)splits * M * N > ws_elems) --splits;
+    while (splits > 1 && (size_t)splits * M * N * items > ws_elems) --splits;
     if (splits < 1) splits = 1;
   }
   const int kchunk = ((kblocks + splits - 1) / splits) * BK;
   splits = K > 0 ? (K + kchunk - 1) / kchunk : 1;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits * items);
   cgemm_kernel<T><<<grid, 256, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ws,
-                                        kchunk, tile_count);
+                                        kchunk, tile_count, splits, sA, sB, sC);
   ++g_launches;
   return cudaGetLastError();
 }
 
 template cudaError_t cgemm<float>(char, char, int, int, int, float2, const float2*, int, const float2*,
-                                  int, float2, float2*, int, float2*, size_t, int*, cudaStream_t, int, int);
+                                  int, float2, float2*, int, float2*, size_t, int*, cudaStream_t, int, int, int,
+                                  long long, long long, long long);
 template cudaError_t cgemm<double>(char, char, int, int, int, double2, const double2*, int,
                                    const double2*, int, double2, double2*, int, double2*, size_t, int*,
-                                   cudaStream_t, int, int);
+                                   cudaStream_t, int, int, int, long long, long long, long long);
 
 }  // namespace pisco

@@ -18,7 +18,9 @@ __device__ __forceinline__ void pair_of(int pair, int Q, int& p, int& q) {
 }
 
 __global__ void pair_products_kernel(const double2* __restrict__ S, int Q, long long nfreq,
-                                     double2* __restrict__ P) {
+                                     double2* __restrict__ P, GramItems it) {
+  S += blockIdx.z * it.S;
+  P += blockIdx.z * it.P;
   const int pair = blockIdx.y;
   int p, q;
   pair_of(pair, Q, p, q);
@@ -33,17 +35,20 @@ __global__ void pair_products_kernel(const double2* __restrict__ S, int Q, long 
   }
 }
 
-cudaError_t gram_pair_products(const double2* S, int Q, long long nfreq, double2* P, cudaStream_t st) {
+cudaError_t gram_pair_products(const double2* S, int Q, long long nfreq, double2* P, cudaStream_t st,
+                               const GramItems& it) {
   const int npairs = Q * (Q + 1) / 2;
   int bx = (int)((nfreq + 255) / 256);
   if (bx > 64) bx = 64;
-  pair_products_kernel<<<dim3(bx, npairs), 256, 0, st>>>(S, Q, nfreq, P);
+  pair_products_kernel<<<dim3(bx, npairs, it.n), 256, 0, st>>>(S, Q, nfreq, P, it);
   ++g_launches;
   return cudaGetLastError();
 }
 
 __global__ void scatter_pairs_kernel(const double2* __restrict__ Rp, int Q, int nbox,
-                                     double2* __restrict__ lags) {
+                                     double2* __restrict__ lags, GramItems it) {
+  Rp += blockIdx.y * it.Rp;
+  lags += blockIdx.y * it.lags;
   const int pair = blockIdx.x;
   int p, q;
   pair_of(pair, Q, p, q);
@@ -51,8 +56,9 @@ __global__ void scatter_pairs_kernel(const double2* __restrict__ Rp, int Q, int 
     lags[((long long)p * Q + q) * nbox + t] = Rp[(long long)pair * nbox + t];
 }
 
-cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* lags, cudaStream_t st) {
-  scatter_pairs_kernel<<<Q * (Q + 1) / 2, 128, 0, st>>>(Rpairs, Q, nbox, lags);
+cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* lags, cudaStream_t st,
+                               const GramItems& it) {
+  scatter_pairs_kernel<<<dim3(Q * (Q + 1) / 2, it.n), 128, 0, st>>>(Rpairs, Q, nbox, lags, it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -61,7 +67,9 @@ cudaError_t gram_scatter_pairs(const double2* Rpairs, int Q, int nbox, double2* 
 // The FP32 copy of the Gram is divided by it so that products of the iterated block stay in
 // FP32 range whatever the data scale.
 __global__ void gram_scale_kernel(const double2* __restrict__ lags, int Q, int nbox, int lag0,
-                                  double* __restrict__ scale) {
+                                  double* __restrict__ scale, GramItems it) {
+  lags += blockIdx.x * it.lags;
+  scale += blockIdx.x * it.scale;
   double mx = 0.0;
   for (int p = threadIdx.x; p < Q; p += 32) mx = fmax(mx, lags[((long long)p * Q + p) * nbox + lag0].x);
 #pragma unroll
@@ -69,8 +77,9 @@ __global__ void gram_scale_kernel(const double2* __restrict__ lags, int Q, int n
   if (threadIdx.x == 0) *scale = mx > 0.0 ? mx : 1.0;
 }
 
-cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* scale, cudaStream_t st) {
-  gram_scale_kernel<<<1, 32, 0, st>>>(lags, Q, nbox, lag0, scale);
+cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* scale, cudaStream_t st,
+                       const GramItems& it) {
+  gram_scale_kernel<<<it.n, 32, 0, st>>>(lags, Q, nbox, lag0, scale, it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -80,7 +89,11 @@ cudaError_t gram_scale(const double2* lags, int Q, int nbox, int lag0, double* s
 __global__ void gram_expand_kernel(const double2* __restrict__ lags,
                                    const int* __restrict__ lag_of_ij, int Q, int L, int nbox,
                                    const double* __restrict__ scale,
-                                   double2* __restrict__ A, float2* __restrict__ A32) {
+                                   double2* __restrict__ A, float2* __restrict__ A32, GramItems it) {
+  lags += blockIdx.y * it.lags;
+  scale += blockIdx.y * it.scale;
+  A += blockIdx.y * it.A;
+  A32 += blockIdx.y * it.A;
   const long long n = (long long)Q * L;
   const double inv = 1.0 / *scale;
   const long long total = n * n;
@@ -102,11 +115,12 @@ __global__ void gram_expand_kernel(const double2* __restrict__ lags,
 }
 
 cudaError_t gram_expand(const double2* lags, const int* lag_of_ij, int Q, int L, int nbox,
-                        const double* scale, double2* A, float2* A32, cudaStream_t st) {
+                        const double* scale, double2* A, float2* A32, cudaStream_t st, const GramItems& it) {
   const long long n = (long long)Q * L;
   long long blocks = (n * n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  gram_expand_kernel<<<(unsigned)blocks, 256, 0, st>>>(lags, lag_of_ij, Q, L, nbox, scale, A, A32);
+  blocks = (blocks + it.n - 1) / it.n;
+  gram_expand_kernel<<<dim3((unsigned)blocks, it.n), 256, 0, st>>>(lags, lag_of_ij, Q, L, nbox, scale, A, A32, it);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(256) apply_axis_df_kernel(const Tin* __restric
   }
 }
 
-__global__ void pair_products_df_kernel(const dfc* __restrict__ S, int Q, long long nfreq, dfc* __restrict__ P) {
+__global__ void pair_products_df_kernel(const dfc* __restrict__ S, int Q, long long nfreq, dfc* __restrict__ P,
+                                        GramItems it) {
+  S += blockIdx.z * it.S;
+  P += blockIdx.z * it.P;
   const int pair = blockIdx.y;
   int p = 0, base = 0;
   while (pair >= base + (Q - p)) { base += Q - p; ++p; }
@@ -96,7 +99,10 @@ __global__ void pair_products_df_kernel(const dfc* __restrict__ S, int Q, long l
 
 // lags[(p,q)][t] = Rp[pair][t] as FP64 (hi + lo is exact in FP64)
 __global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int nbox, double2* __restrict__ lags,
-                                        dfc* __restrict__ lags_df) {
+                                        dfc* __restrict__ lags_df, GramItems it) {
+  Rp += blockIdx.y * it.Rp;
+  lags += blockIdx.y * it.lags;
+  lags_df += blockIdx.y * it.lags;
   const int pair = blockIdx.x;
   int p = 0, base = 0;
   while (pair >= base + (Q - p)) { base += Q - p; ++p; }
@@ -116,8 +122,12 @@ __global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int n
 __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __restrict__ S, int Q, int Lp1, int Lp2,
                                                                const dfc* __restrict__ invT2, int B2,
                                                                const dfc* __restrict__ inv1, int B1,
-                                                               double2* __restrict__ lags, dfc* __restrict__ lags_df) {
+                                                               double2* __restrict__ lags, dfc* __restrict__ lags_df,
+                                                               GramItems it) {
   extern __shared__ dfc dsm[];
+  S += blockIdx.y * it.S;
+  lags += blockIdx.y * it.lags;
+  lags_df += blockIdx.y * it.lags;
   const int ldp = Lp2 | 1;  // odd row stride (in 16-byte words): conflict-free column reads
   dfc* P = dsm;                       // [Lp1][ldp]
   dfc* T = P + Lp1 * ldp;             // [Lp1][B2]
@@ -165,8 +175,11 @@ __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __rest
 // fwdT2: [Nc2][Lp2] (transposed), fwd1: [Lp1][Nc1]; S: [Q][Lp1][Lp2].
 __global__ void __launch_bounds__(256) forward_df_kernel(const float2* __restrict__ calib, int Nc1, int Nc2,
                                                          const dfc* __restrict__ fwdT2, int Lp2,
-                                                         const dfc* __restrict__ fwd1, int Lp1, dfc* __restrict__ S) {
+                                                         const dfc* __restrict__ fwd1, int Lp1, dfc* __restrict__ S,
+                                                         GramItems it) {
   extern __shared__ dfc fsm[];
+  calib += blockIdx.y * it.calib;
+  S += blockIdx.y * it.S;
   dfc* T = fsm;                                  // [Nc1][Lp2]
   dfc* m2 = T + Nc1 * Lp2;                       // [Nc2][Lp2]
   dfc* m1 = m2 + Nc2 * Lp2;                      // [Lp1][Nc1]
@@ -212,7 +225,11 @@ size_t pairs_inverse_df_smem(int Lp1, int Lp2, int B1, int B2) {
 // A32 = A / scale in FP32, from the double-float lag table: no FP64 arithmetic per entry
 __global__ void gram_expand_df_kernel(const dfc* __restrict__ lags_df, const int* __restrict__ lag_of_ij, int Q,
                                       int L, int nbox, const double* __restrict__ scale, dfc* __restrict__ A,
-                                      float2* __restrict__ A32) {
+                                      float2* __restrict__ A32, GramItems it) {
+  lags_df += blockIdx.y * it.lags;
+  scale += blockIdx.y * it.scale;
+  A += blockIdx.y * it.A;
+  A32 += blockIdx.y * it.A;
   const long long n = (long long)Q * L;
   const float inv = (float)(1.0 / *scale);
   const long long total = n * n;
@@ -262,21 +279,24 @@ cudaError_t apply_axis_c2df(const float2* in, const void* M, void* out, AxisView
 cudaError_t apply_axis_df(const void* in, const void* M, void* out, AxisView v, cudaStream_t st) {
   return launch_df<dfc>(static_cast<const dfc*>(in), M, out, v, st);
 }
-cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st) {
+cudaError_t gram_pair_products_df(const void* S, int Q, long long nfreq, void* P, cudaStream_t st,
+                                  const GramItems& it) {
   const int npairs = Q * (Q + 1) / 2;
   int bx = (int)((nfreq + 255) / 256);
   if (bx > 64) bx = 64;
-  pair_products_df_kernel<<<dim3(bx, npairs), 256, 0, st>>>(static_cast<const dfc*>(S), Q, nfreq, static_cast<dfc*>(P));
+  pair_products_df_kernel<<<dim3(bx, npairs, it.n), 256, 0, st>>>(static_cast<const dfc*>(S), Q, nfreq,
+                                                                  static_cast<dfc*>(P), it);
   ++g_launches;
   return cudaGetLastError();
 }
 cudaError_t gram_expand_df(const void* lags_df, const int* lag_of_ij, int Q, int L, int nbox, const double* scale,
-                           void* A, float2* A32, cudaStream_t st) {
+                           void* A, float2* A32, cudaStream_t st, const GramItems& it) {
   const long long n = (long long)Q * L;
   long long blocks = (n * n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  gram_expand_df_kernel<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const dfc*>(lags_df), lag_of_ij, Q, L, nbox,
-                                                          scale, static_cast<dfc*>(A), A32);
+  blocks = (blocks + it.n - 1) / it.n;
+  gram_expand_df_kernel<<<dim3((unsigned)blocks, it.n), 256, 0, st>>>(static_cast<const dfc*>(lags_df), lag_of_ij, Q,
+                                                                      L, nbox, scale, static_cast<dfc*>(A), A32, it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -292,14 +312,15 @@ bool gram_forward_df_supported(int Nc1, int Nc2, int Lp1, int Lp2) {
   return forward_df_smem(Nc1, Nc2, Lp1, Lp2) <= (size_t)kPairsInverseDfMaxSmem;
 }
 cudaError_t gram_forward_df(const float2* calib, int Q, int Nc1, int Nc2, const void* fwdT2, int Lp2, const void* fwd1,
-                            int Lp1, void* S, cudaStream_t st) {
+                            int Lp1, void* S, cudaStream_t st, const GramItems& it) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(forward_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairsInverseDfMaxSmem);
     attr_set = true;
   }
-  forward_df_kernel<<<Q, 256, forward_df_smem(Nc1, Nc2, Lp1, Lp2), st>>>(
-      calib, Nc1, Nc2, static_cast<const dfc*>(fwdT2), Lp2, static_cast<const dfc*>(fwd1), Lp1, static_cast<dfc*>(S));
+  forward_df_kernel<<<dim3(Q, it.n), 256, forward_df_smem(Nc1, Nc2, Lp1, Lp2), st>>>(
+      calib, Nc1, Nc2, static_cast<const dfc*>(fwdT2), Lp2, static_cast<const dfc*>(fwd1), Lp1, static_cast<dfc*>(S),
+      it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -307,21 +328,22 @@ bool gram_pairs_inverse_df_supported(int Lp1, int Lp2, int B1, int B2) {
   return pairs_inverse_df_smem(Lp1, Lp2, B1, B2) <= (size_t)kPairsInverseDfMaxSmem;
 }
 cudaError_t gram_pairs_inverse_df(const void* S, int Q, int Lp1, int Lp2, const void* invT2, int B2, const void* inv1,
-                                  int B1, double2* lags, void* lags_df, cudaStream_t st) {
+                                  int B1, double2* lags, void* lags_df, cudaStream_t st, const GramItems& it) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(pairs_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairsInverseDfMaxSmem);
     attr_set = true;
   }
-  pairs_inverse_df_kernel<<<Q * (Q + 1) / 2, 256, pairs_inverse_df_smem(Lp1, Lp2, B1, B2), st>>>(
+  pairs_inverse_df_kernel<<<dim3(Q * (Q + 1) / 2, it.n), 256, pairs_inverse_df_smem(Lp1, Lp2, B1, B2), st>>>(
       static_cast<const dfc*>(S), Q, Lp1, Lp2, static_cast<const dfc*>(invT2), B2, static_cast<const dfc*>(inv1), B1,
-      lags, static_cast<dfc*>(lags_df));
+      lags, static_cast<dfc*>(lags_df), it);
   ++g_launches;
   return cudaGetLastError();
 }
-cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, void* lags_df, cudaStream_t st) {
-  scatter_pairs_df_kernel<<<Q * (Q + 1) / 2, 128, 0, st>>>(static_cast<const dfc*>(Rp), Q, nbox, lags,
-                                                           static_cast<dfc*>(lags_df));
+cudaError_t gram_scatter_pairs_df(const void* Rp, int Q, int nbox, double2* lags, void* lags_df, cudaStream_t st,
+                                  const GramItems& it) {
+  scatter_pairs_df_kernel<<<dim3(Q * (Q + 1) / 2, it.n), 128, 0, st>>>(static_cast<const dfc*>(Rp), Q, nbox, lags,
+                                                                       static_cast<dfc*>(lags_df), it);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -398,8 +420,12 @@ template <int NBV, typename TA>
 __global__ void __launch_bounds__(256) band_matvec_df_kernel(const TA* __restrict__ A,
                                                              const double2* __restrict__ Xb, int n,
                                                              const int* __restrict__ band_idx,
-                                                             double2* __restrict__ Zb) {
+                                                             double2* __restrict__ Zb, EigItems it) {
   __shared__ float2 xs[kBandKC * NBV];
+  A += blockIdx.y * it.a;
+  Xb += blockIdx.y * it.nb;
+  band_idx += blockIdx.y * it.band;
+  Zb += blockIdx.y * it.nb;
   __shared__ float4 part[kBandRows][kBandSplit][NBV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rl = warp / kBandSplit, ks = warp % kBandSplit;
@@ -470,13 +496,13 @@ __global__ void __launch_bounds__(256) band_matvec_df_kernel(const TA* __restric
 }  // namespace
 
 cudaError_t eig_band_matvec_df(const void* A, bool a_df, const double2* Xb, int n, int nb, const int* band_idx,
-                               double2* Zb, cudaStream_t st) {
+                               double2* Zb, cudaStream_t st, const EigItems& it) {
   if (nb != 8) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)((n + kBandRows - 1) / kBandRows);
+  const dim3 grid((unsigned)((n + kBandRows - 1) / kBandRows), it.n);
   if (a_df)
-    band_matvec_df_kernel<8, float4><<<grid, 256, 0, st>>>(static_cast<const float4*>(A), Xb, n, band_idx, Zb);
+    band_matvec_df_kernel<8, float4><<<grid, 256, 0, st>>>(static_cast<const float4*>(A), Xb, n, band_idx, Zb, it);
   else
-    band_matvec_df_kernel<8, double2><<<grid, 256, 0, st>>>(static_cast<const double2*>(A), Xb, n, band_idx, Zb);
+    band_matvec_df_kernel<8, double2><<<grid, 256, 0, st>>>(static_cast<const double2*>(A), Xb, n, band_idx, Zb, it);
   ++g_launches;
   return cudaGetLastError();
 }

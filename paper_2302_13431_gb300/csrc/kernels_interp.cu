@@ -16,7 +16,10 @@ constexpr int QB = 32;  // coils held in registers per chunk
 __global__ void __launch_bounds__(128) interp_final_kernel(const float2* __restrict__ T,
                                                            const float2* __restrict__ M, int Q,
                                                            int n_in, int n_out, long long inner,
-                                                           float2* __restrict__ maps) {
+                                                           float2* __restrict__ maps, long long sT, long long sM,
+                                                           float2* const* __restrict__ maps_tab) {
+  T += blockIdx.y * sT;
+  maps = maps_tab ? maps_tab[blockIdx.y] : maps + blockIdx.y * sM;
   const long long total = (long long)n_out * inner;
   const long long plane_in = (long long)n_in * inner, plane_out = total;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -72,8 +75,11 @@ template <int QB>
 __global__ void __launch_bounds__(256) interp_tiled_kernel(const float2* __restrict__ T,
                                                            const float2* __restrict__ M, int Q,
                                                            int n_in, int n_out, long long inner,
-                                                           float2* __restrict__ maps) {
+                                                           float2* __restrict__ maps, long long sT, long long sM,
+                                                           float2* const* __restrict__ maps_tab) {
   constexpr int TO = 16, TI = 16, QC = 4;
+  T += blockIdx.z * sT;
+  maps = maps_tab ? maps_tab[blockIdx.z] : maps + blockIdx.z * sM;
   extern __shared__ float2 sm[];
   float2* Ms = sm;                      // TO * n_in
   float2* Ts = Ms + TO * n_in;          // QC * n_in * TI
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(256) interp_tiled_kernel(const float2* __restr
 
 cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long long /*unused*/,
                                    int n_in, int n_out, long long inner, float2* maps,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int items, long long sT, long long sM, float2* const* maps_tab) {
   if (M != nullptr && n_in <= 128 && Q <= 64) {
     const size_t smem = (size_t)(16 * n_in + 4 * n_in * 16) * sizeof(float2);
     static bool attr_set = false;
@@ -134,18 +140,20 @@ cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long
       cudaFuncSetAttribute(interp_tiled_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr_set = true;
     }
-    dim3 grid((unsigned)((inner + 15) / 16), (unsigned)((n_out + 15) / 16));
+    dim3 grid((unsigned)((inner + 15) / 16), (unsigned)((n_out + 15) / 16), items);
     if (Q <= 32)
-      interp_tiled_kernel<32><<<grid, 256, smem, st>>>(T, M, Q, n_in, n_out, inner, maps);
+      interp_tiled_kernel<32><<<grid, 256, smem, st>>>(T, M, Q, n_in, n_out, inner, maps, sT, sM, maps_tab);
     else
-      interp_tiled_kernel<64><<<grid, 256, smem, st>>>(T, M, Q, n_in, n_out, inner, maps);
+      interp_tiled_kernel<64><<<grid, 256, smem, st>>>(T, M, Q, n_in, n_out, inner, maps, sT, sM, maps_tab);
     ++g_launches;
     return cudaGetLastError();
   }
   const long long total = (long long)n_out * inner;
   long long blocks = (total + 127) / 128;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  interp_final_kernel<<<(unsigned)blocks, 128, 0, st>>>(T, M, Q, n_in, n_out, inner, maps);
+  blocks = (blocks + items - 1) / items;
+  interp_final_kernel<<<dim3((unsigned)blocks, items), 128, 0, st>>>(T, M, Q, n_in, n_out, inner, maps, sT, sM,
+                                                                      maps_tab);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -156,7 +164,9 @@ namespace pisco {
 
 // maps[q][x] /= ||maps[.][x]|| (sum of squares over the coils; zero pixels stay zero): the
 // normalisation of Sec. VI after a final interpolation pass that wrote unnormalised maps
-__global__ void normalize_maps_kernel(float2* __restrict__ maps, int Q, long long npix) {
+__global__ void normalize_maps_kernel(float2* __restrict__ maps, int Q, long long npix, long long sM,
+                                      float2* const* __restrict__ maps_tab) {
+  maps = maps_tab ? maps_tab[blockIdx.y] : maps + blockIdx.y * sM;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < npix; x += (long long)gridDim.x * blockDim.x) {
     float n2 = 0.f;
     for (int q = 0; q < Q; ++q) {
@@ -171,10 +181,12 @@ __global__ void normalize_maps_kernel(float2* __restrict__ maps, int Q, long lon
   }
 }
 
-cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st) {
+cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st, int items, long long sM,
+                           float2* const* maps_tab) {
   long long b = (npix + 255) / 256;
   if (b > 152 * 8) b = 152 * 8;
-  normalize_maps_kernel<<<(unsigned)b, 256, 0, st>>>(maps, Q, npix);
+  b = (b + items - 1) / items;
+  normalize_maps_kernel<<<dim3((unsigned)b, items), 256, 0, st>>>(maps, Q, npix, sM, maps_tab);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -43,6 +43,14 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
   __shared__ float2 vs[PIX * QP];
   __shared__ float red[PIX * 2];
   __shared__ int any_flag;
+  {
+    const int i = blockIdx.y;
+    G += i * opt.sG;
+    Y += i * opt.sY;
+    V += i * opt.sV;
+    if (opt.eig_tab) eig = opt.eig_tab[i];
+    else if (eig) eig += i * opt.sE;
+  }
   const int tid = threadIdx.x;
   const int xi = tid / QP, q = tid % QP;
   const long long x = (long long)blockIdx.x * PIX + xi;
@@ -265,7 +273,7 @@ static cudaError_t launch_pi(const float2* G, const float2* Y, int Q, long long 
                              const PiOpts& opt, cudaStream_t st) {
   constexpr int PIX = 256 / QP;
   const long long blocks = (npix + PIX - 1) / PIX;
-  pi_kernel<QP><<<(unsigned)blocks, 256, 0, st>>>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt);
+  pi_kernel<QP><<<dim3((unsigned)blocks, opt.items), 256, 0, st>>>(G, Y, Q, npix, iters, lam_size, seed, V, eig, opt);
   ++g_launches;
   return cudaGetLastError();
 }

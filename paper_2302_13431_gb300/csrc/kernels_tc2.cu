@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -35,6 +36,7 @@ constexpr uint32_t A_TILE = BM * BK * 4;        // 16384
 constexpr uint32_t B_TILE = 2 * BNC * BK * 4;   // 8192
 constexpr uint32_t TMEM_COLS = 64;
 constexpr long long kWait = 4000000000ll;       // ~2 s at 2 GHz
+constexpr long long kWaitStalled = 20000000ll;  // ~10 ms: the wait limit while loads are withheld
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -58,10 +60,10 @@ __device__ __forceinline__ bool bar_try(uint32_t b, uint32_t par) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t par) {
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t par, long long limit) {
   const long long t0 = clock64();
   while (!bar_try(b, par))
-    if (clock64() - t0 > kWait) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
@@ -110,9 +112,16 @@ struct Args {
   int diag_stride, diag_limit;
   float2* ws;     // [splits][M][N] partial products when gridDim.z > 1 (split-K)
   int* err;
-  int batched;    // 1: gridDim.z indexes independent products sharing A (no split-K)
+  int batched;    // 1: gridDim.z indexes independent products (no split-K)
   int b_rows;     // B' rows per batch item (2 Np)
   long long c_stride;  // C elements per batch item
+  int a_rows;     // 0: every batch item shares A'; else A' rows per batch item (A' per item)
+  float2* const* c_tab;  // non-null: C of batch item z is c_tab[z / c_div] + (z % c_div) * c_stride
+  int c_div;
+  int splits;     // K splits (gridDim.z = items * splits); partials of item b, split z at
+                  // ws + (b * splits + z) * M * N
+  long long wait_limit;  // clock cycles a bounded mbarrier wait may take
+  int no_loads;   // test hook: the producer issues no loads, so the waits on them expire
 };
 
 template <int NT, int STAGES>
@@ -131,11 +140,13 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNC;
   const int total = (g.K2 + BK - 1) / BK;
-  const int zb = g.batched ? (int)blockIdx.z : 0;          // batch item
-  const int kb0 = g.batched ? 0 : blockIdx.z * g.kpb;      // first K step of this split
+  const int zb = (int)blockIdx.z / g.splits;                // batch item
+  const int kb0 = ((int)blockIdx.z % g.splits) * g.kpb;    // first K step of this split
   const int nk = min(g.kpb, total - kb0);
   const int brow0 = zb * g.b_rows;                          // this item's rows of B'
-  float2* Cb = g.C + (long long)zb * g.c_stride;
+  const int arow0 = zb * g.a_rows + m0;                     // this tile's first row of A'
+  float2* Cb = g.c_tab ? g.c_tab[zb / g.c_div] + (long long)(zb % g.c_div) * g.c_stride
+                       : g.C + (long long)zb * g.c_stride;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -157,18 +168,18 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
-  if (warp == 0 && lane == 0 && nk > 0) {
+  if (warp == 0 && lane == 0 && nk > 0 && !g.no_loads) {
     // producer: TMA loads of the four tiles of every K step into the stage ring
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES, c = i / STAGES;
-      if (i >= STAGES) ok = bar_wait(empty0 + 8 * s, (uint32_t)((c - 1) & 1));
+      if (i >= STAGES) ok = bar_wait(empty0 + 8 * s, (uint32_t)((c - 1) & 1), g.wait_limit);
       if (!ok) break;
       const uint32_t st = base + s * STAGE;
       const uint32_t fb = full0 + 8 * s;
       bar_expect_tx(fb, STAGE);
       const int kx = (kb0 + i) * BK;
-      tma_2d(st, &tAh, kx, m0, fb);
-      if (NT == 3) tma_2d(st + A_TILE, &tAl, kx, m0, fb);
+      tma_2d(st, &tAh, kx, arow0, fb);
+      if (NT == 3) tma_2d(st + A_TILE, &tAl, kx, arow0, fb);
       const uint32_t sb = st + (NT == 3 ? 2 * A_TILE : A_TILE);
       tma_2d(sb, &tBh, kx, brow0 + 2 * n0, fb);
       if (NT == 3) tma_2d(sb + B_TILE, &tBl, kx, brow0 + 2 * n0, fb);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     // MMA issuer: 4 MMAs of K = 8 per stage (x3 for the head/tail split)
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES, c = i / STAGES;
-      ok = bar_wait(full0 + 8 * s, (uint32_t)(c & 1));
+      ok = bar_wait(full0 + 8 * s, (uint32_t)(c & 1), g.wait_limit);
       if (!ok) break;
       fence_after();
       const uint32_t st = base + s * STAGE;
@@ -197,7 +208,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   }
   __syncwarp();
   if (nk > 0) {
-    if (!bar_wait(accum, 0)) ok = false;
+    if (!bar_wait(accum, 0, g.wait_limit)) ok = false;
   }
   if (!ok && g.err) atomicOr(g.err, 16);
   fence_after();
@@ -223,7 +234,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  if (gridDim.z > 1 && !g.batched) {  // raw partial tile
+  if (g.splits > 1) {  // raw partial tile
     float2* out = g.ws + (long long)blockIdx.z * g.M * g.N;
     for (int rr = warp; rr < BM; rr += 4) {
       const int gm = m0 + rr, gn = n0 + lane;
@@ -248,11 +259,14 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   }
 }
 
-// C = alpha * sum_z ws[z] + beta * C (+ diag), partials summed in z order
+// C = alpha * sum_z ws[z] + beta * C (+ diag), partials summed in z order; grid y = batch item
+// (its partials at ws + item * splits * M * N, its C at C + item * c_stride)
 __global__ void splitk_reduce_kernel(const float2* __restrict__ ws, int splits, int M, int N, float2 alpha,
                                      float2 beta, float2* __restrict__ C, int ldc, float diag_val, int diag_stride,
-                                     int diag_limit) {
+                                     int diag_limit, long long c_stride) {
   const long long total = (long long)M * N;
+  ws += (long long)blockIdx.y * splits * total;
+  C += blockIdx.y * c_stride;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     float2 a = make_float2(0.f, 0.f);
     for (int z = 0; z < splits; ++z) {
@@ -273,20 +287,24 @@ __global__ void splitk_reduce_kernel(const float2* __restrict__ ws, int splits, 
   }
 }
 
-// A' head/tail: A'[m][2k] = Re(A[m][k] w_k), A'[m][2k+1] = Im(...), w_k = kscale[k] (or 1)
+// A' head/tail: A'[m][2k] = Re(A[m][k] w_k), A'[m][2k+1] = Im(...), w_k = kscale[k] (or 1);
+// `items` independent operands: A, kscale and A' advance by a_stride, w_stride and M * K2p
 __global__ void split_a_kernel(const float2* __restrict__ A, int lda, const float* __restrict__ kscale, int M, int K,
-                               float* __restrict__ hi, float* __restrict__ lo, int K2p) {
-  const long long total = (long long)M * K;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+                               float* __restrict__ hi, float* __restrict__ lo, int K2p, int items,
+                               long long a_stride, long long w_stride) {
+  const long long per = (long long)M * K;
+  const long long total = per * items;
+  for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < total; e0 += (long long)gridDim.x * blockDim.x) {
+    const long long it = e0 / per, e = e0 % per;
     const int m = (int)(e / K), k = (int)(e % K);
-    float2 v = A[(long long)m * lda + k];
+    float2 v = A[it * a_stride + (long long)m * lda + k];
     if (kscale) {
-      const float w = kscale[k];
+      const float w = kscale[it * w_stride + k];
       v.x *= w;
       v.y *= w;
     }
     const float hx = head(v.x), hy = head(v.y);
-    const long long o = (long long)m * K2p + 2 * k;
+    const long long o = it * ((long long)M * K2p) + (long long)m * K2p + 2 * k;
     *reinterpret_cast<float2*>(hi + o) = make_float2(hx, hy);
     if (lo) *reinterpret_cast<float2*>(lo + o) = make_float2(head(v.x - hx), head(v.y - hy));
   }
@@ -295,14 +313,16 @@ __global__ void split_a_kernel(const float2* __restrict__ A, int lda, const floa
 // A' head/tail for A = conj(Y^T), Y K x M row-major (ldy): A'[i][2k] = Re Y[k][i],
 // A'[i][2k+1] = -Im Y[k][i]
 __global__ void split_at_kernel(const float2* __restrict__ Y, int ldy, int M, int K, float* __restrict__ hi,
-                                float* __restrict__ lo, int K2p) {
-  const long long total = (long long)M * K;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+                                float* __restrict__ lo, int K2p, int items, long long y_stride) {
+  const long long per = (long long)M * K;
+  const long long total = per * items;
+  for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < total; e0 += (long long)gridDim.x * blockDim.x) {
+    const long long it = e0 / per, e = e0 % per;
     const int k = (int)(e / M), i = (int)(e % M);
-    const float2 y = Y[(long long)k * ldy + i];
+    const float2 y = Y[it * y_stride + (long long)k * ldy + i];
     const float vx = y.x, vy = -y.y;
     const float hx = head(vx), hy = head(vy);
-    const long long o = (long long)i * K2p + 2 * k;
+    const long long o = it * ((long long)M * K2p) + (long long)i * K2p + 2 * k;
     *reinterpret_cast<float2*>(hi + o) = make_float2(hx, hy);
     if (lo) *reinterpret_cast<float2*>(lo + o) = make_float2(head(vx - hx), head(vy - hy));
   }
@@ -343,6 +363,8 @@ __global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, i
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+// test hook (pisco_test_stall_tensor_loads): launches made while it is set withhold their loads
+std::atomic<int> g_tc2_stall{0};
 std::mutex g_encode_mu;
 
 bool encode_2d(CUtensorMap* map, const float* base, int cols, int rows, int ld_floats, int box_rows) {
@@ -378,6 +400,8 @@ unsigned grid_for(long long n) {
 
 }  // namespace
 
+void tc2_set_stall(bool on) { g_tc2_stall.store(on ? 1 : 0); }
+
 int tc2_k2p(int K) { return ((2 * K + 3) / 4) * 4; }
 int tc2_np(int N) { return ((N + BNC - 1) / BNC) * BNC; }
 
@@ -395,14 +419,17 @@ cudaError_t tc2_prepare() {
 }
 
 cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
-                        cudaStream_t st) {
-  split_a_kernel<<<grid_for((long long)M * K), 256, 0, st>>>(A, lda, kscale, M, K, hi, lo, tc2_k2p(K));
+                        cudaStream_t st, int items, long long a_stride, long long w_stride) {
+  split_a_kernel<<<grid_for((long long)M * K * items), 256, 0, st>>>(A, lda, kscale, M, K, hi, lo, tc2_k2p(K), items,
+                                                                     a_stride, w_stride);
   ++g_launches;
   return cudaGetLastError();
 }
 
-cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st) {
-  split_at_kernel<<<grid_for((long long)M * K), 256, 0, st>>>(Y, ldy, M, K, hi, lo, tc2_k2p(K));
+cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st, int items,
+                         long long y_stride) {
+  split_at_kernel<<<grid_for((long long)M * K * items), 256, 0, st>>>(Y, ldy, M, K, hi, lo, tc2_k2p(K), items,
+                                                                      y_stride);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -419,11 +446,13 @@ cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* 
 cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const float* Alo, const float* Bhi,
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
-                     int nbatch, long long c_stride) {
+                     int nbatch, long long c_stride, int a_per_item, float2* const* c_tab, int c_div,
+                     int b_per_item) {
   if (M <= 0 || N <= 0 || nbatch < 1) return cudaSuccess;
   const int K2 = 2 * K, K2p = tc2_k2p(K), Np = tc2_np(N);
   const int total = (K2 + BK - 1) / BK;
-  if (splits < 1 || ws == nullptr || nbatch > 1) splits = 1;
+  // split-K: also in batched mode (per item), never with a C table
+  if (splits < 1 || ws == nullptr || c_tab != nullptr) splits = 1;
   if (splits > total) splits = total > 0 ? total : 1;
   const int kpb = total > 0 ? (total + splits - 1) / splits : 0;
   if (kpb > 0) splits = (total + kpb - 1) / kpb;
@@ -431,13 +460,19 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   const float* al = nterms == 3 ? Alo : Ahi;
   const float* bl = nterms == 3 ? Blo : Bhi;
   const int kcols = K2 > 0 ? K2 : 1;
-  if (!encode_2d(&mAh, Ahi, kcols, M, K2p, BM) || !encode_2d(&mAl, al, kcols, M, K2p, BM) ||
-      !encode_2d(&mBh, Bhi, kcols, 2 * Np * nbatch, K2p, 2 * BNC) ||
-      !encode_2d(&mBl, bl, kcols, 2 * Np * nbatch, K2p, 2 * BNC))
+  const int arows = a_per_item && nbatch > 1 ? M * nbatch : M;
+  if (!encode_2d(&mAh, Ahi, kcols, arows, K2p, BM) || !encode_2d(&mAl, al, kcols, arows, K2p, BM) ||
+      !encode_2d(&mBh, Bhi, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC) ||
+      !encode_2d(&mBl, bl, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC))
     return cudaErrorInvalidValue;
   Args g{M, N, K2, kpb, C, ldc, alpha, beta, diag_val, diag_stride, diag_limit, ws, err,
-         nbatch > 1 ? 1 : 0, 2 * Np, c_stride};
-  dim3 grid(Np / BNC, (M + BM - 1) / BM, nbatch > 1 ? nbatch : splits);
+         nbatch > 1 ? 1 : 0, b_per_item ? 2 * Np : 0, c_stride, a_per_item && nbatch > 1 ? M : 0,
+         nbatch > 1 ? c_tab : nullptr,
+         c_div > 0 ? c_div : 1};
+  g.splits = splits;
+  g.no_loads = g_tc2_stall.load() ? 1 : 0;
+  g.wait_limit = g.no_loads ? kWaitStalled : kWait;
+  dim3 grid(Np / BNC, (M + BM - 1) / BM, nbatch * splits);
   // short K loops (<= 8 steps per CTA) keep 2 stages: half the shared memory, 2 CTAs per SM, so
   // one CTA's epilogue overlaps another's loads; long loops keep 4 stages in flight
   const bool deep = kpb > 8;
@@ -451,8 +486,8 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   ++g_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
-  splitk_reduce_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(ws, splits, M, N, alpha, beta, C, ldc, diag_val,
-                                                                   diag_stride, diag_limit);
+  splitk_reduce_kernel<<<dim3(grid_for((long long)M * N), nbatch), 256, 0, st>>>(
+      ws, splits, M, N, alpha, beta, C, ldc, diag_val, diag_stride, diag_limit, c_stride);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -34,6 +35,20 @@ struct DevBuf {
 struct pisco_plan_s {
   pisco_params prm;
   cudaStream_t st = nullptr;
+  // batched stages: one pass estimates `items` map sets of this shape; every per-item buffer
+  // holds the items one after another (item_elems: elements per item, keyed by the member's
+  // offset in this struct).  A view is a one-item plan into item i of a group's buffers.
+  int items = 1;
+  bool view = false;
+  std::unordered_map<size_t, std::pair<size_t, size_t>> item_elems;  // (elements, bytes) per item
+  // per-item inputs and outputs of a group (device tables, with the host copies they hold)
+  const float2** in_tab = nullptr;
+  float2** maps_tab = nullptr;
+  float** eig_tab = nullptr;
+  std::vector<const void*> h_in;
+  std::vector<void*> h_maps;
+  std::vector<float*> h_eig;
+  float2* X0 = nullptr;  // orthonormalised random start block (shared by the items)
   int D = 2;
   // internal axis order: [0] = z, [1] = y, [2] = x
   int N[3], Nc[3], tau[3], Nr[3], Lp[3], B[3];
@@ -163,8 +178,9 @@ struct pisco_plan_s {
 
 namespace {
 
+// a buffer shared by all items of the plan (tables, constants, counters)
 template <typename T>
-bool dalloc(pisco_plan_s* pl, T** p, size_t count) {
+bool dalloc_shared(pisco_plan_s* pl, T** p, size_t count) {
   if (count == 0) count = 1;
   void* q = nullptr;
   if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return false;
@@ -174,9 +190,25 @@ bool dalloc(pisco_plan_s* pl, T** p, size_t count) {
   return true;
 }
 
+// a per-item buffer of `count` elements per item (p is a member of *pl)
+template <typename T>
+bool dalloc(pisco_plan_s* pl, T** p, size_t count) {
+  if (count == 0) count = 1;
+  if (!dalloc_shared(pl, p, count * (size_t)pl->items)) return false;
+  pl->item_elems[(size_t)(reinterpret_cast<char*>(p) - reinterpret_cast<char*>(pl))] = {count, count * sizeof(T)};
+  return true;
+}
+
+// elements per item of the per-item buffer held by member `m` (0 for shared buffers)
+template <typename T>
+long long IS(const pisco_plan_s* pl, T* const& m) {
+  const auto it = pl->item_elems.find((size_t)(reinterpret_cast<const char*>(&m) - reinterpret_cast<const char*>(pl)));
+  return it == pl->item_elems.end() ? 0 : (long long)it->second.first;
+}
+
 template <typename T>
 bool upload(pisco_plan_s* pl, T** p, const std::vector<T>& h) {
-  if (!dalloc(pl, p, h.size())) return false;
+  if (!dalloc_shared(pl, p, h.size())) return false;
   return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
@@ -392,6 +424,7 @@ pisco_status validate(const pisco_params* p) {
   }
   if (p->eig_block < 0 || p->eig_block > kMmax || (p->eig_block % 2) != 0) return PISCO_ERR_ARG;
   if (p->eig_iters < 0 || p->eig_iters > 100) return PISCO_ERR_ARG;
+  if (p->batch_group < 0) return PISCO_ERR_ARG;
   return PISCO_OK;
 }
 
@@ -469,11 +502,28 @@ bool retry_iters(pisco_plan_s* pl) {
 // ---------------------------------------------------------------------------------------
 // the path
 // ---------------------------------------------------------------------------------------
+// strides of the Gram stage's per-item buffers (the axis passes write their outputs packed)
+GramItems gram_items(const pisco_plan_s* pl) {
+  GramItems it;
+  it.n = pl->items;
+  it.calib = IS(pl, pl->calib_stage);
+  it.S = (long long)pl->Q * pl->nfreq;
+  it.P = (long long)pl->npairs * pl->nfreq;
+  it.Rp = (long long)pl->npairs * pl->nbox;
+  it.lags = IS(pl, pl->lags);
+  it.A = IS(pl, pl->A);
+  it.scale = 1;
+  return it;
+}
+
 pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   cudaStream_t st = pl->st;
   const int Q = pl->Q;
   const int* Nc = pl->Nc;
   const int* Lp = pl->Lp;
+  const GramItems gi = gram_items(pl);
+  const long long QI = (long long)Q * pl->items;            // coils of all items
+  const long long NPI = (long long)pl->npairs * pl->items;  // coil pairs of all items
   if (pl->masked) {
     OP("gram_masked_fp64", gram_masked(calib, Q, Nc, pl->lam_lo, pl->lam_hi, pl->d_lam, pl->L, pl->d_lag_ids,
                                        pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->tau, pl->B, pl->A, pl->gscale,
@@ -483,117 +533,158 @@ pisco_status run_gram(pisco_plan_s* pl, const float2* calib) {
   const int* B = pl->B;
   if (pl->gram_df) {
     // the same passes in double-float arithmetic (FP64 storage reused; lags written in FP64)
-    const int np = pl->npairs;
     if (pl->D == 2 && gram_forward_df_supported(Nc[1], Nc[2], Lp[1], Lp[2])) {
-      OP("gram_dft_df", gram_forward_df(calib, Q, Nc[1], Nc[2], pl->fwdT_df, Lp[2], pl->fwd_df[1], Lp[1], pl->gB, st));
+      OP("gram_dft_df", gram_forward_df(calib, Q, Nc[1], Nc[2], pl->fwdT_df, Lp[2], pl->fwd_df[1], Lp[1], pl->gB, st, gi));
     } else {
-      OP("gram_dft_df", apply_axis_c2df(calib, pl->fwdT_df, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
-      OP("gram_dft_df", apply_axis_df(pl->gA, pl->fwd_df[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
+      OP("gram_dft_df", apply_axis_c2df(calib, pl->fwdT_df, pl->gA, AxisView{QI, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gA, pl->fwd_df[1], pl->gB, AxisView{QI, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
     }
     const void* S = pl->gB;
     if (pl->D == 3) {
-      OP("gram_dft_df", apply_axis_df(pl->gB, pl->fwd_df[0], pl->S, AxisView{Q, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gB, pl->fwd_df[0], pl->S, AxisView{QI, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
       S = pl->S;
     }
     if (pl->D == 2 && gram_pairs_inverse_df_supported(Lp[1], Lp[2], B[1], B[2])) {
       OP("gram_pairs_df", gram_pairs_inverse_df(S, Q, Lp[1], Lp[2], pl->invT_df, B[2], pl->inv_df[1], B[1], pl->lags,
-                                                pl->lags_df, st));
+                                                pl->lags_df, st, gi));
     } else {
-    OP("gram_pair_products", gram_pair_products_df(S, Q, pl->nfreq, pl->P, st));
-    OP("gram_dft_df", apply_axis_df(pl->P, pl->invT_df, pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
+    OP("gram_pair_products", gram_pair_products_df(S, Q, pl->nfreq, pl->P, st, gi));
+    OP("gram_dft_df", apply_axis_df(pl->P, pl->invT_df, pl->gA, AxisView{NPI, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
     if (pl->D == 3) {
-      OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->gB, AxisView{np, Lp[0], Lp[1], B[1], B[2]}, st));
-      OP("gram_dft_df", apply_axis_df(pl->gB, pl->inv_df[0], pl->Rp, AxisView{np, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->gB, AxisView{NPI, Lp[0], Lp[1], B[1], B[2]}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gB, pl->inv_df[0], pl->Rp, AxisView{NPI, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
     } else {
-      OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->Rp, AxisView{np, 1, Lp[1], B[1], B[2]}, st));
+      OP("gram_dft_df", apply_axis_df(pl->gA, pl->inv_df[1], pl->Rp, AxisView{NPI, 1, Lp[1], B[1], B[2]}, st));
     }
-    OP("gram_scatter", gram_scatter_pairs_df(pl->Rp, Q, pl->nbox, pl->lags, pl->lags_df, st));
+    OP("gram_scatter", gram_scatter_pairs_df(pl->Rp, Q, pl->nbox, pl->lags, pl->lags_df, st, gi));
     }
     const int lag0 = (2 * pl->tau[0] * B[1] + 2 * pl->tau[1]) * B[2] + 2 * pl->tau[2];
-    OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st));
-    OP("gram_expand", gram_expand_df(pl->lags_df, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st));
+    OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st, gi));
+    OP("gram_expand", gram_expand_df(pl->lags_df, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st, gi));
     return PISCO_OK;
   }
   // forward zero-padded DFT of every channel: x, y, z
-  OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwdT, pl->gA, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
-  OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->fwd[1], pl->gB, AxisView{Q, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
+  OP("gram_dft_fp64", apply_axis_c2z(calib, pl->fwdT, pl->gA, AxisView{QI, (long long)Nc[0] * Nc[1], Nc[2], Lp[2], 1, 0, 1}, st));
+  OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->fwd[1], pl->gB, AxisView{QI, Nc[0], Nc[1], Lp[1], Lp[2]}, st));
   const double2* S = pl->gB;
   if (pl->D == 3) {
-    OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->fwd[0], pl->S, AxisView{Q, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
+    OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->fwd[0], pl->S, AxisView{QI, 1, Nc[0], Lp[0], (long long)Lp[1] * Lp[2]}, st));
     S = pl->S;
   }
-  OP("gram_pair_products", gram_pair_products(S, Q, pl->nfreq, pl->P, st));
-  const int np = pl->npairs;
-  OP("gram_dft_fp64", apply_axis_z(pl->P, pl->invT, pl->gA, AxisView{np, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
+  OP("gram_pair_products", gram_pair_products(S, Q, pl->nfreq, pl->P, st, gi));
+  OP("gram_dft_fp64", apply_axis_z(pl->P, pl->invT, pl->gA, AxisView{NPI, (long long)Lp[0] * Lp[1], Lp[2], B[2], 1, 0, 1}, st));
   if (pl->D == 3) {
-    OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->gB, AxisView{np, Lp[0], Lp[1], B[1], B[2]}, st));
-    OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->inv[0], pl->Rp, AxisView{np, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
+    OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->gB, AxisView{NPI, Lp[0], Lp[1], B[1], B[2]}, st));
+    OP("gram_dft_fp64", apply_axis_z(pl->gB, pl->inv[0], pl->Rp, AxisView{NPI, 1, Lp[0], B[0], (long long)B[1] * B[2]}, st));
   } else {
-    OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->Rp, AxisView{np, 1, Lp[1], B[1], B[2]}, st));
+    OP("gram_dft_fp64", apply_axis_z(pl->gA, pl->inv[1], pl->Rp, AxisView{NPI, 1, Lp[1], B[1], B[2]}, st));
   }
-  OP("gram_scatter", gram_scatter_pairs(pl->Rp, Q, pl->nbox, pl->lags, st));
+  OP("gram_scatter", gram_scatter_pairs(pl->Rp, Q, pl->nbox, pl->lags, st, gi));
   const int lag0 = (2 * pl->tau[0] * B[1] + 2 * pl->tau[1]) * B[2] + 2 * pl->tau[2];
-  OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st));
-  OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st));
+  OP("gram_expand", gram_scale(pl->lags, Q, pl->nbox, lag0, pl->gscale, st, gi));
+  OP("gram_expand", gram_expand(pl->lags, pl->d_lag_of_ij, Q, pl->L, pl->nbox, pl->gscale, pl->A, pl->A32, st, gi));
   return PISCO_OK;
+}
+
+// strides of the eigensolver's per-item buffers
+EigItems eig_items(const pisco_plan_s* pl) {
+  EigItems it;
+  it.n = pl->items;
+  it.mm = IS(pl, pl->Gm);
+  it.vj = IS(pl, pl->Vj);
+  it.vec = IS(pl, pl->mu);
+  it.nm = IS(pl, pl->X);
+  it.nb = IS(pl, pl->Xb);
+  it.band = IS(pl, pl->band);
+  it.a = IS(pl, pl->A);
+  it.scale = IS(pl, pl->gscale);
+  return it;
 }
 
 // Thin block products on the tensor cores (PISCO_FLAG_TC_THIN): C = Y^H Z (m x m over n rows,
-// conj_a) or C = Y W (n x m by m x m), operands split into the plan's thin buffers
-cudaError_t thin_product(pisco_plan_s* pl, bool conj_a, const float2* Y, const float2* Z, float2* C) {
+// conj_a) or C = Y W (n x m by m x m), operands split into the plan's thin buffers; Y, Z, W, C
+// of item i are sY, sZ, sC elements after item 0 (sY = 0: one Y shared by the items)
+cudaError_t thin_product(pisco_plan_s* pl, bool conj_a, const float2* Y, const float2* Z, float2* C, long long sY,
+                         long long sZ, long long sC, int items) {
   const int n = pl->n, m = pl->m;
   const bool tt = pl->tc_terms == 3;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  const int ap = sY != 0 ? 1 : 0;
+  const int ai = sY != 0 ? items : 1;
   cudaError_t e;
   if (conj_a) {
-    if ((e = tc2_split_at(Y, m, m, n, pl->TAh, tt ? pl->TAl : nullptr, pl->st)) != cudaSuccess) return e;
-    if ((e = tc2_split_b(Z, m, 0, n, m, pl->TBh, tt ? pl->TBl : nullptr, pl->st)) != cudaSuccess) return e;
+    if ((e = tc2_split_at(Y, m, m, n, pl->TAh, tt ? pl->TAl : nullptr, pl->st, ai, sY)) != cudaSuccess) return e;
+    if ((e = tc2_split_b(Z, m, 0, n, m, pl->TBh, tt ? pl->TBl : nullptr, pl->st, items, sZ)) != cudaSuccess) return e;
     return tc2_gemm(pl->tc_terms, m, m, n, pl->TAh, pl->TAl, pl->TBh, pl->TBl, one, zero, C, m, 0.f, 0, 0,
-                    kThinSplits, pl->tc_ws, &pl->dstatus->flags, pl->st);
+                    kThinSplits, pl->tc_ws, &pl->dstatus->flags, pl->st, items, sC, ap);
   }
-  if ((e = tc2_split_a(Y, m, nullptr, n, m, pl->TAh, tt ? pl->TAl : nullptr, pl->st)) != cudaSuccess) return e;
-  if ((e = tc2_split_b(Z, m, 0, m, m, pl->TBh, tt ? pl->TBl : nullptr, pl->st)) != cudaSuccess) return e;
+  if ((e = tc2_split_a(Y, m, nullptr, n, m, pl->TAh, tt ? pl->TAl : nullptr, pl->st, ai, sY)) != cudaSuccess) return e;
+  if ((e = tc2_split_b(Z, m, 0, m, m, pl->TBh, tt ? pl->TBl : nullptr, pl->st, items, sZ)) != cudaSuccess) return e;
   return tc2_gemm(pl->tc_terms, n, m, m, pl->TAh, pl->TAl, pl->TBh, pl->TBl, one, zero, C, m, 0.f, 0, 0, 1, nullptr,
-                  &pl->dstatus->flags, pl->st);
+                  &pl->dstatus->flags, pl->st, items, sC, ap);
 }
 
-// One Cholesky-QR pass: Xout = (Yin D^-1) L^-H with orthonormal columns.  dscale: optional
-// column scaling D (previous diag(R)); shift_rel: optional shift; acc_in: diag(R) of earlier
-// passes of the same factorisation; diag(R) of the whole factorisation goes to diag_out.
-pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, const float* dscale,
-                    float shift_rel, const float* acc_in, float* diag_out) {
+// C = Y^H Z (m x m) or C = Y W (n x m by m x m) for every item: tensor cores or CUDA cores
+cudaError_t block_product(pisco_plan_s* pl, bool conj_a, const float2* Y, const float2* Z, float2* C, long long sY,
+                          long long sZ, long long sC, int items) {
+  if (pl->tc_thin) return thin_product(pl, conj_a, Y, Z, C, sY, sZ, sC, items);
+  const int n = pl->n, m = pl->m;
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  if (conj_a)
+    return cgemm<float>('C', 'N', m, m, n, one, Y, m, Z, m, zero, C, m, pl->ws32, pl->ws32_elems * pl->items,
+                        pl->tiles, pl->st, pl->gemm_splits, pl->gemm_tile, items, sY, sZ, sC);
+  return cgemm<float>('N', 'N', n, m, m, one, Y, m, Z, m, zero, C, m, pl->ws32, pl->ws32_elems * pl->items,
+                      pl->tiles, pl->st, pl->gemm_splits, pl->gemm_tile, items, sY, sZ, sC);
+}
+
+// Xout = (Yin D^-1) L^-H for the Cholesky factor L of the Hermitian matrix held in pl->Gm
+// (D^-1 Gm D^-1 = L L^H).  dscale: optional column scaling D; shift_rel: optional shift;
+// acc_in: diagonal of earlier factors of the same product; diag(L) D acc goes to diag_out.
+pisco_status chol_apply(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, const float* dscale,
+                        float shift_rel, const float* acc_in, float* diag_out, int items) {
   cudaStream_t st = pl->st;
   const int n = pl->n;
-  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  if (pl->tc_thin)
-    OP("eig_gemm_thin_tc", thin_product(pl, true, Yin, Yin, pl->Gm));
-  else
-    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, Yin, m, Yin, m, zero, pl->Gm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  EigItems it = eig_items(pl);
+  it.n = items;
+  const long long snm = IS(pl, pl->X), smm = IS(pl, pl->Gm);
   if (m <= 64) {
-    OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st));
-    if (pl->tc_thin)
-      OP("eig_gemm_thin_tc", thin_product(pl, false, Yin, pl->Rinv, Xout));
-    else
-      OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, Yin, m, pl->Rinv, m, zero, Xout, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+    OP("eig_chol", eig_chol_inv_blocked(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, diag_out, pl->dstatus, st, it));
+    OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, false, Yin, pl->Rinv, Xout, snm, smm, snm, items));
   } else {
-    OP("eig_chol", eig_chol(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, pl->dsc, diag_out, pl->dstatus, st));
-    OP("eig_trsm", eig_trsm(Yin, pl->Rinv, pl->dsc, n, m, Xout, st));
+    OP("eig_chol", eig_chol(pl->Gm, m, dscale, shift_rel, acc_in, pl->Rinv, pl->dsc, diag_out, pl->dstatus, st, it));
+    OP("eig_trsm", eig_trsm(Yin, pl->Rinv, pl->dsc, n, m, Xout, st, it));
   }
   return PISCO_OK;
 }
 
-// Y = A32 X (n x n by n x m): tensor cores (split TF32) or CUDA cores (FP32)
-cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y) {
-  const int n = pl->n, m = pl->m;
+// One Cholesky-QR pass: Xout = (Yin D^-1) L^-H with orthonormal columns, L L^H the Gram matrix
+// of Yin D^-1.  dscale: optional column scaling D (previous diag(R)); shift_rel: optional shift;
+// acc_in: diag(R) of earlier factors of the same product; diag(R) of the whole factorisation goes
+// to diag_out.  items: the plan's items (per-item Yin), or 1 for the shared start block.
+pisco_status cholqr(pisco_plan_s* pl, const float2* Yin, float2* Xout, int m, const float* dscale,
+                    float shift_rel, const float* acc_in, float* diag_out, int items) {
+  const long long snm = IS(pl, pl->X), smm = IS(pl, pl->Gm);
+  OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, true, Yin, Yin, pl->Gm, snm, snm, smm, items));
+  return chol_apply(pl, Yin, Xout, m, dscale, shift_rel, acc_in, diag_out, items);
+}
+
+// Y = A32 X (n x n by n x m) for every item: tensor cores (split TF32) or CUDA cores (FP32);
+// sX = 0: one X shared by the items
+cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y, long long sX) {
+  const int n = pl->n, m = pl->m, items = pl->items;
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  const long long snm = IS(pl, pl->X);
   if (pl->tc_eig) {
-    cudaError_t e = tc2_split_b(X, m, 0, n, m, pl->Xh, pl->tc_terms == 3 ? pl->Xl : nullptr, pl->st);
+    const int xi = sX != 0 ? items : 1;
+    cudaError_t e = tc2_split_b(X, m, 0, n, m, pl->Xh, pl->tc_terms == 3 ? pl->Xl : nullptr, pl->st, xi, sX);
     if (e != cudaSuccess) return e;
+    // sX == 0: every item multiplies the same block (B' of item 0 for all)
     return tc2_gemm(pl->tc_terms, n, m, n, pl->Ah, pl->Al, pl->Xh, pl->Xl, one, zero, Y, m, 0.f, 0, 0,
-                    pl->tc_splits_ax, pl->tc_ws, &pl->dstatus->flags, pl->st);
+                    pl->tc_splits_ax, pl->tc_ws, &pl->dstatus->flags, pl->st, items, snm, 1, nullptr, 1,
+                    sX != 0 ? 1 : 0);
   }
-  return cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, X, m, zero, Y, m, pl->ws32, pl->ws32_elems,
-                      pl->tiles, pl->st, pl->gemm_splits, pl->gemm_tile);
+  return cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, X, m, zero, Y, m, pl->ws32, pl->ws32_elems * pl->items,
+                      pl->tiles, pl->st, pl->gemm_splits, pl->gemm_tile, items, IS(pl, pl->A32), sX, snm);
 }
 
 // Nullspace of the Gram (Sec. III-A, threshold footnote of Sec. III-B): orthogonal
@@ -602,72 +693,60 @@ cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y) {
 // one Rayleigh-Ritz at the end, and the threshold split decided on FP64 Rayleigh quotients
 // against the FP64 Gram, with FP64 residuals certifying the decision.
 //
-// The start is a Rayleigh-Ritz step on an orthonormalised random block: the first product
-// A X0 of a random block spans the dominant directions so unevenly (condition number up to
-// lambda_1/lambda_m, 1e4 and more on these spectra) that even shifted Cholesky-QR leaves a
-// block at the FP32 limit of the next pass; the Ritz vectors of the random block instead give
-// an equilibrated first product A X0 V diag(mu)^-1.
+// The start equilibrates the first product: A X0 of an orthonormalised random block X0 spans the
+// dominant directions so unevenly (condition number up to lambda_1/lambda_m, 1e4 and more on
+// these spectra) that even shifted Cholesky-QR leaves a block at the FP32 limit of the next pass.
+// With B = X0^H A X0 = L L^H (positive definite: A is, X0 has full rank), Z L^-H with Z = A X0 has
+// about the square root of that condition number, well inside one FP32 Cholesky-QR pass, and
+// diag(L) times that pass's diag(R) is the diag(R) of the whole product (the next scaling).  X0
+// depends on the seed only, so the items of a batched pass share it.
 pisco_status run_eig(pisco_plan_s* pl) {
   cudaStream_t st = pl->st;
-  const int n = pl->n, m = pl->m;
-  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  const int n = pl->n, m = pl->m, items = pl->items;
   const double thr2 = pl->prm.null_threshold * pl->prm.null_threshold;
+  const EigItems it = eig_items(pl);
+  const long long snm = IS(pl, pl->X), smm = IS(pl, pl->Gm), svj = IS(pl, pl->Vj);
   pisco_status s;
   OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
   if (pl->tc_eig)  // the Gram's TF32 head/tail split, shared by every block product of the solve
-    OP("eig_gemm_AX", tc2_split_a(pl->A32, n, nullptr, n, n, pl->Ah, pl->tc_terms == 3 ? pl->Al : nullptr, st));
+    OP("eig_gemm_AX", tc2_split_a(pl->A32, n, nullptr, n, n, pl->Ah, pl->tc_terms == 3 ? pl->Al : nullptr, st, items,
+                                  IS(pl, pl->A32)));
   // X0 = orth(random block): well conditioned (kappa ~ (1 + sqrt(m/n)) / (1 - sqrt(m/n)))
-  if ((s = cholqr(pl, pl->Y, pl->X, m, nullptr, 0.f, nullptr, pl->dR1)) != PISCO_OK) return s;
-  // Rayleigh-Ritz of the start block: Z = A X0, B = X0^H Z = V diag(mu) V^H, A (X0 V) = Z V
-  OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
-  if (pl->tc_thin)
-    OP("eig_gemm_thin_tc", thin_product(pl, true, pl->X, pl->Z, pl->Bm));
-  else
-    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
-  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
-  if (pl->tc_thin)
-    OP("eig_gemm_thin_tc", thin_product(pl, false, pl->Z, pl->Vj, pl->Y));
-  else
-    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->Z, m, pl->Vj, m, zero, pl->Y, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
-  // first power step: X1 = orth(A X0 V diag(mu)^-1)
-  if ((s = cholqr(pl, pl->Y, pl->X, m, pl->mu, 0.f, nullptr, pl->dR0)) != PISCO_OK) return s;
-  float* dprev = pl->dR0;
-  float* dnext = pl->dR1;
+  if ((s = cholqr(pl, pl->Y, pl->X0, m, nullptr, 0.f, nullptr, pl->dR1, 1)) != PISCO_OK) return s;
+  // the equilibrated first power step: Z = A X0, B = X0^H Z = L L^H, Y = Z L^-H, X1 = orth(Y)
+  OP("eig_gemm_AX", ax_product(pl, pl->X0, pl->Z, 0));
+  OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, true, pl->X0, pl->Z, pl->Gm, 0, snm, smm, items));
+  if ((s = chol_apply(pl, pl->Z, pl->Y, m, nullptr, 0.f, nullptr, pl->dR0, items)) != PISCO_OK) return s;
+  if ((s = cholqr(pl, pl->Y, pl->X, m, nullptr, 0.f, pl->dR0, pl->dR1, items)) != PISCO_OK) return s;
+  float* dprev = pl->dR1;
+  float* dnext = pl->dR0;
   // orthogonal iteration: X <- orth(A X diag(R)^-1), diag(R) of the previous orthonormalisation
   // approximating the Ritz values of the block columns
-  for (int it = 1; it < pl->eig_iters; ++it) {
-    OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Y));
-    if ((s = cholqr(pl, pl->Y, pl->X, m, dprev, 0.f, nullptr, dnext)) != PISCO_OK) return s;
+  for (int k = 1; k < pl->eig_iters; ++k) {
+    OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Y, snm));
+    if ((s = cholqr(pl, pl->Y, pl->X, m, dprev, 0.f, nullptr, dnext, items)) != PISCO_OK) return s;
     std::swap(dprev, dnext);
   }
   // Rayleigh-Ritz on the block
-  OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z));
-  if (pl->tc_thin)
-    OP("eig_gemm_thin_tc", thin_product(pl, true, pl->X, pl->Z, pl->Bm));
-  else
-    OP("eig_gemm_thin_fp32", cgemm<float>('C', 'N', m, m, n, one, pl->X, m, pl->Z, m, zero, pl->Bm, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
-  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st));
-  if (pl->tc_thin)
-    OP("eig_gemm_thin_tc", thin_product(pl, false, pl->X, pl->Vj, pl->U));
-  else
-    OP("eig_gemm_thin_fp32", cgemm<float>('N', 'N', n, m, m, one, pl->X, m, pl->Vj, m, zero, pl->U, m, pl->ws32, pl->ws32_elems, pl->tiles, st, pl->gemm_splits, pl->gemm_tile));
+  OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z, snm));
+  OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, true, pl->X, pl->Z, pl->Bm, snm, snm, smm, items));
+  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st, it));
+  OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, false, pl->X, pl->Vj, pl->U, snm, svj, snm, items));
   // FP64 Rayleigh quotients of the Ritz vectors that decide the split
-  OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st));
-  OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st));
-  const double2 zone = make_double2(1.0, 0.0), zzero = make_double2(0.0, 0.0);
+  OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st, it));
+  OP("eig_misc", eig_gather_band(pl->U, n, m, pl->band, kNbMax, pl->Xb, st, it));
   if (pl->gram_df)
-    OP("eig_rayleigh_df", eig_band_matvec_df(pl->A, pl->a_df, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
+    OP("eig_rayleigh_df", eig_band_matvec_df(pl->A, pl->a_df, pl->Xb, n, kNbMax, pl->band, pl->Zb, st, it));
   else
-    OP("eig_rayleigh_fp64", eig_band_matvec(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st));
-  (void)zone; (void)zzero;
+    OP("eig_rayleigh_fp64", eig_band_matvec(pl->A, pl->Xb, n, kNbMax, pl->band, pl->Zb, st, it));
   OP("eig_decide_fp64", eig_decide(pl->mu, m, pl->band, kNbMax, pl->Xb, pl->Zb, n, thr2, pl->Q, pl->gscale,
-                pl->w, pl->ritz, pl->dstatus, st));
+                pl->w, pl->ritz, pl->dstatus, st, it));
   return PISCO_OK;
 }
 
 pisco_status run_gfield(pisco_plan_s* pl) {
   cudaStream_t st = pl->st;
-  const int Q = pl->Q;
+  const int Q = pl->Q, items = pl->items;
   const int* B = pl->B;
   const int* Nr = pl->Nr;
   const long long QQ = (long long)Q * Q;
@@ -678,22 +757,26 @@ pisco_status run_gfield(pisco_plan_s* pl) {
     int* err = &pl->dstatus->flags;
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f), mone = make_float2(-1.f, 0.f);
     const bool tt = pl->tc_terms == 3;
-    OP("g_herk_tc", tc2_split_a(pl->U, pl->m, pl->w, n, pl->m, pl->UAh, tt ? pl->UAl : nullptr, st));
-    OP("g_herk_tc", tc2_split_b(pl->U, pl->m, 1, pl->m, n, pl->UBh, tt ? pl->UBl : nullptr, st));
+    const long long snm = IS(pl, pl->U), snn = IS(pl, pl->A32), skt = IS(pl, pl->KT), sg = IS(pl, pl->G);
+    OP("g_herk_tc", tc2_split_a(pl->U, pl->m, pl->w, n, pl->m, pl->UAh, tt ? pl->UAl : nullptr, st, items, snm,
+                                IS(pl, pl->w)));
+    OP("g_herk_tc", tc2_split_b(pl->U, pl->m, 1, pl->m, n, pl->UBh, tt ? pl->UBl : nullptr, st, items, snm));
     OP("g_herk_tc", tc2_gemm(pl->tc_terms, n, n, pl->m, pl->UAh, pl->UAl, pl->UBh, pl->UBl, one, zero, pl->A32, n,
-                             0.f, 0, 0, 1, nullptr, err, st));
-    OP("g_collapse", gassembly_collapse(pl->A32, n, Q, pl->L, pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->KT, st));
+                             0.f, 0, 0, 1, nullptr, err, st, items, snn, 1));
+    OP("g_collapse", gassembly_collapse(pl->A32, n, Q, pl->L, pl->d_lagc_ptr, pl->d_lag_ent, pl->nlag, pl->KT, st,
+                                        items, snn, skt));
     if (pl->g_sep) {
       OP("g_field_sep", gassembly_field_sep2(pl->KT, Q, pl->nlag, pl->d_sep_rows, pl->d_sep_b2, pl->gdft[1], Nr[1], B[1],
-                                             pl->gdft[2], B[2], Nr[2], (float)pl->L, pl->G, st));
+                                             pl->gdft[2], B[2], Nr[2], (float)pl->L, pl->G, st, items, skt, sg));
       return PISCO_OK;
     }
-    OP("g_field_tc", tc2_split_b(pl->KT, (int)QQ, 0, pl->nlag, (int)QQ, pl->KTh, tt ? pl->KTl : nullptr, st));
+    OP("g_field_tc", tc2_split_b(pl->KT, (int)QQ, 0, pl->nlag, (int)QQ, pl->KTh, tt ? pl->KTl : nullptr, st, items, skt));
     OP("g_field_tc", tc2_gemm(pl->tc_terms, (int)pl->npix_red, (int)QQ, pl->nlag, pl->Eh, pl->El, pl->KTh, pl->KTl,
                               mone, zero, pl->G, (int)QQ, (float)pl->L, Q + 1, (int)QQ, pl->tc_splits_g, pl->tc_ws,
-                              err, st));
+                              err, st, items, sg));
     return PISCO_OK;
   }
+  if (items > 1) return PISCO_ERR_UNSUPPORTED;  // batched groups take the tensor-core G route
   OP("g_kernel", gassembly_kernel(pl->U, pl->w, Q, pl->L, pl->m, pl->d_lag_ptr, pl->d_lag_ent, pl->nbox, pl->K, st));
   OP("g_dft", apply_axis_c(pl->K, pl->gdftT, pl->T1, AxisView{QQ, (long long)B[0] * B[1], B[2], Nr[2], 1, 0, 1}, st));
   if (pl->D == 3) {
@@ -708,67 +791,87 @@ pisco_status run_gfield(pisco_plan_s* pl) {
 
 pisco_status run_lowres(pisco_plan_s* pl, const float2* calib) {
   cudaStream_t st = pl->st;
-  const int Q = pl->Q;
+  const long long QI = (long long)pl->Q * pl->items;  // the items' coils one after another
   const int* Nc = pl->Nc;
   const int* Nr = pl->Nr;
-  OP("lowres_dft", apply_axis_c(calib, pl->ydftT, pl->Ya, AxisView{Q, (long long)Nc[0] * Nc[1], Nc[2], Nr[2], 1, 0, 1}, st));
+  OP("lowres_dft", apply_axis_c(calib, pl->ydftT, pl->Ya, AxisView{QI, (long long)Nc[0] * Nc[1], Nc[2], Nr[2], 1, 0, 1}, st));
   if (pl->D == 3) {
-    OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yb, AxisView{Q, Nc[0], Nc[1], Nr[1], Nr[2]}, st));
-    OP("lowres_dft", apply_axis_c(pl->Yb, pl->ydft[0], pl->Yf, AxisView{Q, 1, Nc[0], Nr[0], (long long)Nr[1] * Nr[2]}, st));
+    OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yb, AxisView{QI, Nc[0], Nc[1], Nr[1], Nr[2]}, st));
+    OP("lowres_dft", apply_axis_c(pl->Yb, pl->ydft[0], pl->Yf, AxisView{QI, 1, Nc[0], Nr[0], (long long)Nr[1] * Nr[2]}, st));
   } else {
-    OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yf, AxisView{Q, 1, Nc[1], Nr[1], Nr[2]}, st));
+    OP("lowres_dft", apply_axis_c(pl->Ya, pl->ydft[1], pl->Yf, AxisView{QI, 1, Nc[1], Nr[1], Nr[2]}, st));
   }
   return PISCO_OK;
 }
 
+// maps: the output of a one-item plan; a group writes item i's maps to maps_tab[i]
 pisco_status run_interp(pisco_plan_s* pl, float2* maps) {
   cudaStream_t st = pl->st;
-  const int Q = pl->Q;
+  const int Q = pl->Q, items = pl->items;
+  const long long QI = (long long)Q * items;
   const int* N = pl->N;
   const int* Nr = pl->Nr;
+  float2* const* tab = items > 1 ? pl->maps_tab : nullptr;
   if (pl->prm.grid_reduction == 1) {
-    OP("interp_final_norm", interp_final_normalize(pl->V, nullptr, Q, 0, 1, 1, pl->npix, maps, st));
+    OP("interp_final_norm", interp_final_normalize(pl->V, nullptr, Q, 0, 1, 1, pl->npix, maps, st, items,
+                                                   IS(pl, pl->V), 0, tab));
     return PISCO_OK;
   }
-  OP("interp_axis", apply_axis_c(pl->V, pl->interpT, pl->I1, AxisView{Q, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1, 0, 1}, st));
+  OP("interp_axis", apply_axis_c(pl->V, pl->interpT, pl->I1, AxisView{QI, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1, 0, 1}, st));
   if (pl->tc_interp) {
     // maps_q = M T_q for every coil q (one batched tensor-core GEMM), then the per-pixel norm
     const bool tt = pl->tc_terms == 3;
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
     const float2* T = pl->I1;
     if (pl->D == 3) {
-      OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{Q, Nr[0], Nr[1], N[1], N[2]}, st));
+      OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{QI, Nr[0], Nr[1], N[1], N[2]}, st));
       T = pl->I2;
     }
     const int ax = pl->D == 3 ? 0 : 1;
     const long long inner = pl->D == 3 ? (long long)N[1] * N[2] : N[2];
-    OP("interp_final_tc", tc2_split_b(T, (int)inner, 0, Nr[ax], (int)inner, pl->IBh, tt ? pl->IBl : nullptr, st, Q,
+    OP("interp_final_tc", tc2_split_b(T, (int)inner, 0, Nr[ax], (int)inner, pl->IBh, tt ? pl->IBl : nullptr, st, (int)QI,
                                       (long long)Nr[ax] * inner));
     OP("interp_final_tc", tc2_gemm(pl->tc_terms, N[ax], (int)inner, Nr[ax], pl->IAh, pl->IAl, pl->IBh, pl->IBl, one,
-                                   zero, maps, (int)inner, 0.f, 0, 0, 1, nullptr, &pl->dstatus->flags, st, Q,
-                                   (long long)N[ax] * inner));
-    OP("interp_final_norm", normalize_maps(maps, Q, pl->npix, st));
+                                   zero, maps, (int)inner, 0.f, 0, 0, 1, nullptr, &pl->dstatus->flags, st, (int)QI,
+                                   (long long)N[ax] * inner, 0, tab, Q));
+    OP("interp_final_norm", normalize_maps(maps, Q, pl->npix, st, items, 0, tab));
     return PISCO_OK;
   }
   if (pl->D == 3) {
-    OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{Q, Nr[0], Nr[1], N[1], N[2]}, st));
-    OP("interp_final_norm", interp_final_normalize(pl->I2, pl->interp[0], Q, 0, Nr[0], N[0], (long long)N[1] * N[2], maps, st));
+    OP("interp_axis", apply_axis_c(pl->I1, pl->interp[1], pl->I2, AxisView{QI, Nr[0], Nr[1], N[1], N[2]}, st));
+    OP("interp_final_norm", interp_final_normalize(pl->I2, pl->interp[0], Q, 0, Nr[0], N[0], (long long)N[1] * N[2],
+                                                   maps, st, items, (long long)Q * Nr[0] * N[1] * N[2], 0, tab));
   } else {
-    OP("interp_final_norm", interp_final_normalize(pl->I1, pl->interp[1], Q, 0, Nr[1], N[1], N[2], maps, st));
+    OP("interp_final_norm", interp_final_normalize(pl->I1, pl->interp[1], Q, 0, Nr[1], N[1], N[2], maps, st, items,
+                                                   (long long)Q * Nr[1] * N[2], 0, tab));
   }
   return PISCO_OK;
 }
 
+// The whole path.  One-item plans read `calib` and write maps / eig directly; a group reads its
+// items' calibration blocks from calib_stage (staged by the batch launcher) and writes through
+// maps_tab / eig_tab (maps and eig unused).
 pisco_status run_all(pisco_plan_s* pl, const float2* calib, float2* maps, float* eig) {
   cudaStream_t st = pl->st;
+  const int items = pl->items;
   g_launches = 0;
-  CK(cudaMemsetAsync(pl->dstatus, 0, sizeof(DevStatus), st));
+  CK(cudaMemsetAsync(pl->dstatus, 0, sizeof(DevStatus) * items, st));
   pisco_status s;
   if ((s = run_gram(pl, calib)) != PISCO_OK) return s;
   if ((s = run_eig(pl)) != PISCO_OK) return s;
   if ((s = run_gfield(pl)) != PISCO_OK) return s;
   if ((s = run_lowres(pl, calib)) != PISCO_OK) return s;
-  if (pl->ws_on) {
+  if (items > 1) {
+    PiOpts o;
+    o.items = items;
+    o.sG = IS(pl, pl->G);
+    o.sY = IS(pl, pl->Yf);
+    o.sV = IS(pl, pl->V);
+    o.sE = IS(pl, pl->eig_tmp);
+    o.eig_tab = pl->eig_tab;
+    OP("power_iteration", power_iteration(pl->G, pl->Yf, pl->Q, pl->npix_red, pl->prm.power_iters, (float)pl->L,
+                                          pl->prm.seed, pl->V, pl->eig_tmp, st, o));
+  } else if (pl->ws_on) {
     // learned start vectors, fewer iterations, residual-gated re-solve from the plain start
     const MlpView mv{2 * pl->Q, pl->ws_H, 2 * pl->Q, pl->ws_w32, pl->ws_w16};
     OP("warm_start_mlp", mlp_features(pl->Yf, pl->Q, pl->npix_red, pl->ws_X, st));
@@ -795,7 +898,7 @@ pisco_status run_all(pisco_plan_s* pl, const float2* calib, float2* maps, float*
                                           pl->prm.seed, pl->V, eig ? eig : pl->eig_tmp, st));
   }
   if ((s = run_interp(pl, maps)) != PISCO_OK) return s;
-  CK(cudaMemcpyAsync(pl->hstatus, pl->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(pl->hstatus, pl->dstatus, sizeof(DevStatus) * items, cudaMemcpyDeviceToHost, st));
   return PISCO_OK;
 }
 
@@ -826,18 +929,22 @@ void pisco_destroy(pisco_plan_t pl) {
   if (pl->ev_in) cudaEventDestroy(pl->ev_in);
   if (pl->ev_out) cudaEventDestroy(pl->ev_out);
   for (cudaEvent_t e : pl->ev) cudaEventDestroy(e);
-  for (void* p : pl->allocs) cudaFree(p);
-  if (pl->hstatus) cudaFreeHost(pl->hstatus);
+  for (void* p : pl->allocs) cudaFree(p);  // a view owns only what was allocated for it
+  if (pl->hstatus && !pl->view) cudaFreeHost(pl->hstatus);
   delete pl;
 }
 
-pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* out) {
-  if (!out) return PISCO_ERR_ARG;
+}  // extern "C"
+
+// a plan whose passes estimate `items` map sets of the shape p at once (items == 1: pisco_plan)
+static pisco_status plan_create(const pisco_params* p, cudaStream_t cuda_stream, int items, pisco_plan_s** out) {
+  if (!out || items < 1) return PISCO_ERR_ARG;
   *out = nullptr;
   pisco_status s = validate(p);
   if (s != PISCO_OK) return s;
   pisco_plan_s* pl = new (std::nothrow) pisco_plan_s();
   if (!pl) return PISCO_ERR_OOM;
+  pl->items = items;
   pl->prm = *p;
   pl->st = (cudaStream_t)cuda_stream;
   pl->D = p->ndim;
@@ -964,7 +1071,8 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   ok = ok && dalloc(pl, &pl->mu, (size_t)M) && dalloc(pl, &pl->w, (size_t)M) && dalloc(pl, &pl->ritz, (size_t)M);
   ok = ok && dalloc(pl, &pl->band, (size_t)kNbMax);
   ok = ok && dalloc(pl, &pl->dR0, (size_t)M) && dalloc(pl, &pl->dR1, (size_t)M) && dalloc(pl, &pl->dsc, (size_t)M);
-  ok = ok && dalloc(pl, &pl->tiles, (size_t)4096);
+  ok = ok && dalloc(pl, &pl->tiles, (size_t)4096);  // split-K tile counters, 4096 per item
+  ok = ok && dalloc_shared(pl, &pl->X0, (size_t)n * M);
   ok = ok && dalloc(pl, &pl->gscale, (size_t)1);
   ok = ok && dalloc(pl, &pl->Xb, (size_t)n * kNbMax) && dalloc(pl, &pl->Zb, (size_t)n * kNbMax);
   pl->ws32_elems = (size_t)16 * n * M;
@@ -987,13 +1095,13 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     if (ok && pl->tc_thin) {
       const size_t ta = std::max((size_t)n * k2m, (size_t)pl->m_max * k2n);
       const size_t tb = (size_t)2 * tc2_np(pl->m_max) * std::max(k2n, k2m);
-      ok = dalloc(pl, &pl->TAh, ta) && dalloc(pl, &pl->TAl, lo_n * ta + 1) && dalloc(pl, &pl->TBh, tb) &&
-           dalloc(pl, &pl->TBl, lo_n * tb + 1);
+      ok = dalloc(pl, &pl->TAh, ta) && dalloc(pl, &pl->TAl, lo_n * ta) && dalloc(pl, &pl->TBh, tb) &&
+           dalloc(pl, &pl->TBl, lo_n * tb);
     }
     if (ok && pl->tc_eig)
-      ok = dalloc(pl, &pl->Ah, (size_t)n * k2n) && dalloc(pl, &pl->Al, lo_n * n * k2n + 1) &&
+      ok = dalloc(pl, &pl->Ah, (size_t)n * k2n) && dalloc(pl, &pl->Al, lo_n * n * k2n) &&
            dalloc(pl, &pl->Xh, (size_t)2 * tc2_np(pl->m_max) * k2n) &&
-           dalloc(pl, &pl->Xl, lo_n * 2 * tc2_np(pl->m_max) * k2n + 1);
+           dalloc(pl, &pl->Xl, lo_n * 2 * tc2_np(pl->m_max) * k2n);
     pl->g_sep = pl->tc_g && pl->D == 2 && (p->flags & PISCO_FLAG_G_DENSE) == 0 &&
                 gassembly_field_sep2_supported(pl->nlag, Nr[1], B[1], Nr[2], B[2]);
     if (ok && pl->g_sep) {
@@ -1008,16 +1116,16 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
       const size_t k2m2 = (size_t)tc2_k2p(pl->m_max);
       ok = upload(pl, &pl->d_sep_rows, rows) && upload(pl, &pl->d_sep_b2, b2) &&
            dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->UAh, (size_t)n * k2m2) &&
-           dalloc(pl, &pl->UAl, lo_n * n * k2m2 + 1) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m2) &&
-           dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m2 + 1);
+           dalloc(pl, &pl->UAl, lo_n * n * k2m2) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m2) &&
+           dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m2);
     } else if (ok && pl->tc_g) {
       const size_t k2l = (size_t)tc2_k2p(pl->nlag);
       ok = upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
-           dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->Eh, (size_t)pl->npix_red * k2l) &&
-           dalloc(pl, &pl->El, lo_n * pl->npix_red * k2l + 1) && dalloc(pl, &pl->KTh, (size_t)2 * tc2_np((int)QQ) * k2l) &&
-           dalloc(pl, &pl->KTl, lo_n * 2 * tc2_np((int)QQ) * k2l + 1) && dalloc(pl, &pl->UAh, (size_t)n * k2m) &&
-           dalloc(pl, &pl->UAl, lo_n * n * k2m + 1) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m) &&
-           dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m + 1);
+           dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc_shared(pl, &pl->Eh, (size_t)pl->npix_red * k2l) &&
+           dalloc_shared(pl, &pl->El, lo_n * pl->npix_red * k2l) && dalloc(pl, &pl->KTh, (size_t)2 * tc2_np((int)QQ) * k2l) &&
+           dalloc(pl, &pl->KTl, lo_n * 2 * tc2_np((int)QQ) * k2l) && dalloc(pl, &pl->UAh, (size_t)n * k2m) &&
+           dalloc(pl, &pl->UAl, lo_n * n * k2m) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m) &&
+           dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m);
       // the lag exponentials never change: split them once here
       ok = ok && tc2_split_a(pl->E, pl->nlag, nullptr, (int)pl->npix_red, pl->nlag, pl->Eh,
                              pl->tc_terms == 3 ? pl->El : nullptr, nullptr) == cudaSuccess;
@@ -1038,8 +1146,8 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     const size_t k2 = (size_t)tc2_k2p(Nr[ax]);
     const size_t lo_n = pl->tc_terms == 3 ? 1 : 0;
     const size_t nb = (size_t)Q * 2 * tc2_np((int)inner) * k2;
-    ok = upload(pl, &pl->interpA, interp_matrix(Nr[ax], N[ax])) && dalloc(pl, &pl->IAh, (size_t)N[ax] * k2) &&
-         dalloc(pl, &pl->IAl, lo_n * N[ax] * k2 + 1) && dalloc(pl, &pl->IBh, nb) && dalloc(pl, &pl->IBl, lo_n * nb + 1);
+    ok = upload(pl, &pl->interpA, interp_matrix(Nr[ax], N[ax])) && dalloc_shared(pl, &pl->IAh, (size_t)N[ax] * k2) &&
+         dalloc_shared(pl, &pl->IAl, lo_n * N[ax] * k2) && dalloc(pl, &pl->IBh, nb) && dalloc(pl, &pl->IBl, lo_n * nb);
     ok = ok && tc2_split_a(pl->interpA, Nr[ax], nullptr, N[ax], Nr[ax], pl->IAh, lo_n ? pl->IAl : nullptr,
                            nullptr) == cudaSuccess;
   }
@@ -1049,7 +1157,10 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     ok = dalloc(pl, &pl->io_calib, (size_t)Q * Nc[0] * Nc[1] * Nc[2]) &&
          dalloc(pl, &pl->io_maps, (size_t)(Q * pl->npix)) && dalloc(pl, &pl->io_eig, (size_t)pl->npix_red);
   }
-  if (ok) ok = cudaMallocHost((void**)&pl->hstatus, sizeof(DevStatus)) == cudaSuccess;
+  if (ok) ok = cudaMallocHost((void**)&pl->hstatus, sizeof(DevStatus) * items) == cudaSuccess;
+  if (ok && items > 1)
+    ok = dalloc_shared(pl, &pl->in_tab, (size_t)items) && dalloc_shared(pl, &pl->maps_tab, (size_t)items) &&
+         dalloc_shared(pl, &pl->eig_tab, (size_t)items);
   if (ok) ok = cudaStreamCreateWithFlags(&pl->cap_st, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&pl->ev_in, cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&pl->ev_out, cudaEventDisableTiming) == cudaSuccess;
@@ -1059,8 +1170,8 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
     if (ok) pl->ev.push_back(e);
     if (ok && (i & 1)) pl->ev_tag.push_back(nullptr);
   }
-  if (ok) ok = cudaMemset(pl->lags, 0, sizeof(double2) * (size_t)Q * Q * pl->nbox) == cudaSuccess;
-  if (ok) ok = cudaMemset(pl->tiles, 0, sizeof(int) * 4096) == cudaSuccess;
+  if (ok) ok = cudaMemset(pl->lags, 0, sizeof(double2) * (size_t)Q * Q * pl->nbox * items) == cudaSuccess;
+  if (ok) ok = cudaMemset(pl->tiles, 0, sizeof(int) * 4096 * items) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     pisco_destroy(pl);
@@ -1072,6 +1183,12 @@ pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* 
   }
   *out = pl;
   return PISCO_OK;
+}
+
+extern "C" {
+
+pisco_status pisco_plan(const pisco_params* p, void* cuda_stream, pisco_plan_t* out) {
+  return plan_create(p, (cudaStream_t)cuda_stream, 1, out);
 }
 
 pisco_status pisco_estimate(pisco_plan_t pl, const void* d_calib, void* d_maps, float* d_eig) {
@@ -1295,13 +1412,22 @@ pisco_status pisco_profile_entry(pisco_plan_t pl, int idx, const char** name, do
 }
 
 // ---------------------------------------------------------------------------------------
-// Batches: one sub-plan (own workspace and stream) per item, all items captured into one
-// CUDA graph whose branches run concurrently; replayed while the pointer sets stay the same.
+// Batches.  Items of identical parameters form groups of up to batch_group items; a group is
+// one plan whose passes run every stage once over all of its items (item-strided buffers,
+// per-item inputs and outputs through device pointer tables), and each of its items is
+// reached through a one-item view into the group's buffers (statuses, statistics, debug
+// buffers and re-runs of single items).  A group of one item is an ordinary plan.  All groups
+// are captured into one CUDA graph whose branches (one per group) run concurrently; it is
+// replayed while the pointer sets stay the same.
 // ---------------------------------------------------------------------------------------
 struct pisco_batch_s {
-  std::vector<pisco_plan_s*> items;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> join;
+  std::vector<pisco_plan_s*> items;    // per item: its one-item plan (a view, or the group itself)
+  std::vector<pisco_plan_s*> groups;   // owning: one plan per group
+  std::vector<pisco_plan_s*> views;    // owning: views of groups with more than one item
+  std::vector<int> group_of, slot_of;  // item -> group, item -> index inside its group
+  std::vector<std::vector<int>> members;  // group -> its items
+  std::vector<cudaStream_t> streams;   // one per group
+  std::vector<cudaEvent_t> join;       // one per group
   cudaEvent_t fork = nullptr;
   cudaStream_t main = nullptr;   // private non-blocking stream: capture and graph launch
   cudaStream_t user = nullptr;   // the caller's stream
@@ -1325,12 +1451,110 @@ struct pisco_batch_s {
   std::vector<const void*> pend_in;
   std::vector<void*> pend_out;
   std::vector<float*> pend_eig;
+  bool prof = false;  // operation timing: eager calls, events around every operation
 };
 
 // the compute-done event of the last host-I/O graph launched by any batch
 std::mutex g_chain_mu;
 cudaEvent_t g_chain_ev = nullptr;
 const pisco_batch_s* g_chain_owner = nullptr;
+
+namespace {
+
+constexpr int kAutoGroup = 64;
+
+bool same_params(const pisco_params& a, const pisco_params& b) {
+  bool s = a.ndim == b.ndim && a.num_coils == b.num_coils && a.kernel_shape == b.kernel_shape &&
+           a.null_threshold == b.null_threshold && a.grid_reduction == b.grid_reduction &&
+           a.power_iters == b.power_iters && a.seed == b.seed && a.flags == b.flags && a.eig_block == b.eig_block &&
+           a.eig_iters == b.eig_iters && a.tc_splits == b.tc_splits && a.gemm_splits == b.gemm_splits &&
+           a.gemm_tile == b.gemm_tile && a.batch_group == b.batch_group;
+  for (int d = 0; d < 3; ++d)
+    s = s && a.grid[d] == b.grid[d] && a.calib[d] == b.calib[d] && a.kernel_radius[d] == b.kernel_radius[d];
+  return s;
+}
+
+// items of these parameters may share a batched pass
+int group_cap(const pisco_params& p) {
+  if (!(p.flags & PISCO_FLAG_TC_GFIELD) || (p.flags & (PISCO_FLAG_MASKED_GRAM | PISCO_FLAG_BLOCK_PI))) return 1;
+  return p.batch_group > 0 ? p.batch_group : kAutoGroup;
+}
+
+// a one-item view of item i of group g: the group's plan state with every per-item buffer
+// pointer moved to item i; it shares the group's tables and owns nothing at creation
+pisco_plan_s* make_view(pisco_plan_s* g, int i, cudaStream_t st) {
+  pisco_plan_s* v = new (std::nothrow) pisco_plan_s(*g);
+  if (!v) return nullptr;
+  v->items = 1;
+  v->view = true;
+  v->allocs.clear();
+  v->ws_bytes = 0;
+  v->item_elems.clear();
+  v->in_tab = nullptr;
+  v->maps_tab = nullptr;
+  v->eig_tab = nullptr;
+  v->h_in.clear();
+  v->h_maps.clear();
+  v->h_eig.clear();
+  v->st = st;
+  v->ev.clear();
+  v->ev_tag.clear();
+  v->ev_used = 0;
+  v->prof = false;
+  v->cap_st = nullptr;
+  v->ev_in = v->ev_out = nullptr;
+  v->use_graph = false;
+  v->graph = nullptr;
+  v->gexec = nullptr;
+  v->g_m = -1;
+  v->eager_calib = nullptr;
+  v->prof_name.clear();
+  v->prof_ms.clear();
+  v->prof_cnt.clear();
+  v->hstatus = g->hstatus + i;
+  for (const auto& f : g->item_elems) {
+    char** field = reinterpret_cast<char**>(reinterpret_cast<char*>(v) + f.first);
+    *field += (size_t)i * f.second.second;
+  }
+  return v;
+}
+
+// uploads a group's pointer tables when the pointer set changed (no call of this batch is in
+// flight, so the previous graph no longer reads them)
+pisco_status set_tables(pisco_plan_s* g, const std::vector<const void*>& in, const std::vector<void*>& out,
+                        const std::vector<float*>& eig) {
+  if (g->items == 1) return PISCO_OK;
+  if (g->h_in == in && g->h_maps == out && g->h_eig == eig) return PISCO_OK;
+  const size_t n = (size_t)g->items;
+  if (cudaMemcpy(g->in_tab, in.data(), n * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g->maps_tab, out.data(), n * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(g->eig_tab, eig.data(), n * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PISCO_ERR_CUDA;
+  g->h_in = in;
+  g->h_maps = out;
+  g->h_eig = eig;
+  return PISCO_OK;
+}
+
+// calibration blocks of a group's items into its staging buffer, one launch
+__global__ void gather_inputs_kernel(const float2* const* __restrict__ src, float2* __restrict__ dst,
+                                     long long elems) {
+  const float2* s = src[blockIdx.y];
+  float2* d = dst + blockIdx.y * elems;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < elems; e += (long long)gridDim.x * blockDim.x)
+    d[e] = s[e];
+}
+
+pisco_status gather_inputs(pisco_plan_s* g) {
+  const long long elems = IS(g, g->calib_stage);
+  long long blocks = (elems + 255) / 256;
+  if (blocks > 64) blocks = 64;
+  gather_inputs_kernel<<<dim3((unsigned)blocks, g->items), 256, 0, g->st>>>(g->in_tab, g->calib_stage, elems);
+  ++g_launches;
+  return cudaGetLastError() == cudaSuccess ? PISCO_OK : PISCO_ERR_CUDA;
+}
+
+}  // namespace
 
 static void batch_graph_reset(pisco_batch_s* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -1362,7 +1586,8 @@ void pisco_batch_destroy(pisco_batch_t b) {
   }
   if (b->ev_staged) cudaEventDestroy(b->ev_staged);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
-  for (auto* pl : b->items) pisco_destroy(pl);
+  for (auto* v : b->views) pisco_destroy(v);
+  for (auto* pl : b->groups) pisco_destroy(pl);
   for (auto s : b->streams) if (s) cudaStreamDestroy(s);
   for (auto e : b->join) if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -1390,7 +1615,25 @@ pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_
     pisco_batch_destroy(b);
     return PISCO_ERR_CUDA;
   }
+  // groups of identical parameters, in item order
+  b->group_of.assign(count, -1);
+  b->slot_of.assign(count, 0);
   for (int i = 0; i < count; ++i) {
+    int g = -1;
+    for (int j = 0; j < (int)b->members.size() && g < 0; ++j) {
+      const int first = b->members[j][0];
+      if (same_params(params[first], params[i]) && (int)b->members[j].size() < group_cap(params[i])) g = j;
+    }
+    if (g < 0) {
+      g = (int)b->members.size();
+      b->members.emplace_back();
+    }
+    b->group_of[i] = g;
+    b->slot_of[i] = (int)b->members[g].size();
+    b->members[g].push_back(i);
+  }
+  b->items.assign(count, nullptr);
+  for (int g = 0; g < (int)b->members.size(); ++g) {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1401,23 +1644,121 @@ pisco_status pisco_batch_plan(const pisco_params* params, int count, void* cuda_
     }
     b->streams.push_back(st);
     b->join.push_back(ev);
-    pisco_params pi = params[i];
+    const std::vector<int>& mem = b->members[g];
+    pisco_params pi = params[mem[0]];
     pi.flags |= PISCO_FLAG_HOST_IO;
-    pisco_plan_t pl = nullptr;
-    pisco_status s = pisco_plan(&pi, st, &pl);
+    pisco_plan_s* pl = nullptr;
+    pisco_status s = plan_create(&pi, st, (int)mem.size(), &pl);
     if (s != PISCO_OK) {
       pisco_batch_destroy(b);
       return s;
     }
     pl->use_graph = false;
-    b->items.push_back(pl);
+    b->groups.push_back(pl);
+    if (mem.size() == 1) {
+      b->items[mem[0]] = pl;
+      continue;
+    }
+    for (int k = 0; k < (int)mem.size(); ++k) {
+      pisco_plan_s* v = make_view(pl, k, st);
+      if (!v) {
+        pisco_batch_destroy(b);
+        return PISCO_ERR_OOM;
+      }
+      b->views.push_back(v);
+      b->items[mem[k]] = v;
+    }
   }
   *out = b;
   return PISCO_OK;
 }
 
-// capture (if the pointer set changed) and launch the whole batch; host_io: in/out are host
-// pointers (copied through each item's staging buffers inside the graph)
+// the pointer tables of every group for this call (device or host I/O) and, per group, the
+// work of one pass: one-item groups copy their input and run as a plan; larger groups gather
+// their inputs (device I/O) and run one batched pass.  host_inline: issue the host copies of
+// host-I/O calls on the group streams too (eager first call); otherwise the caller does.
+static pisco_status enqueue_groups(pisco_batch_s* b, const void* const* in, void* const* outp, float* const* eig,
+                                   bool host_io, bool host_inline, int* launches) {
+  int total = 0;
+  for (int g = 0; g < (int)b->groups.size(); ++g) {
+    pisco_plan_s* gp = b->groups[g];
+    cudaStream_t st = gp->st;
+    if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) return PISCO_ERR_CUDA;
+    const std::vector<int>& mem = b->members[g];
+    const size_t cb = sizeof(float2) * (size_t)gp->Q * gp->Nc[0] * gp->Nc[1] * gp->Nc[2];
+    const size_t mb = sizeof(float2) * (size_t)gp->Q * gp->npix;
+    // inputs
+    for (int k = 0; k < (int)mem.size(); ++k) {
+      const int i = mem[k];
+      pisco_plan_s* it = b->items[i];
+      if (host_io && host_inline &&
+          cudaMemcpyAsync(it->calib_stage, in[i], cb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return PISCO_ERR_CUDA;
+      if (!host_io && mem.size() == 1 &&
+          cudaMemcpyAsync(it->calib_stage, in[i], cb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return PISCO_ERR_CUDA;
+    }
+    gp->ev_used = 0;
+    pisco_status s;
+    if (mem.size() == 1) {
+      const int i = mem[0];
+      float2* maps_dst = host_io ? gp->io_maps : (float2*)outp[i];
+      float* eig_dst = eig && eig[i] ? (host_io ? gp->io_eig : eig[i]) : nullptr;
+      s = run_all(gp, gp->calib_stage, maps_dst, eig_dst);
+      if (s != PISCO_OK) return s;
+      total += g_launches;
+    } else {
+      int extra = 0;
+      if (!host_io) {
+        g_launches = 0;
+        if ((s = gather_inputs(gp)) != PISCO_OK) return s;
+        extra = g_launches;
+      }
+      s = run_all(gp, gp->calib_stage, nullptr, nullptr);
+      if (s != PISCO_OK) return s;
+      total += g_launches + extra;
+    }
+    // host-I/O results of the eager call
+    if (host_io && host_inline) {
+      for (int k = 0; k < (int)mem.size(); ++k) {
+        const int i = mem[k];
+        pisco_plan_s* it = b->items[i];
+        if (cudaMemcpyAsync(outp[i], it->io_maps, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PISCO_ERR_CUDA;
+        if (eig && eig[i] &&
+            cudaMemcpyAsync(eig[i], it->io_eig, sizeof(float) * it->npix_red, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return PISCO_ERR_CUDA;
+      }
+    }
+    if (cudaEventRecord(b->join[g], st) != cudaSuccess || cudaStreamWaitEvent(b->main, b->join[g], 0) != cudaSuccess)
+      return PISCO_ERR_CUDA;
+  }
+  if (launches) *launches = total;
+  return PISCO_OK;
+}
+
+// the tables of every group with more than one item for this pointer set
+static pisco_status batch_tables(pisco_batch_s* b, const void* const* in, void* const* outp, float* const* eig,
+                                 bool host_io) {
+  for (int g = 0; g < (int)b->groups.size(); ++g) {
+    pisco_plan_s* gp = b->groups[g];
+    if (gp->items == 1) continue;
+    const std::vector<int>& mem = b->members[g];
+    std::vector<const void*> ti(mem.size());
+    std::vector<void*> tm(mem.size());
+    std::vector<float*> te(mem.size());
+    for (size_t k = 0; k < mem.size(); ++k) {
+      const int i = mem[k];
+      pisco_plan_s* it = b->items[i];
+      ti[k] = host_io ? it->calib_stage : in[i];
+      tm[k] = host_io ? (void*)it->io_maps : outp[i];
+      te[k] = eig && eig[i] ? (host_io ? it->io_eig : eig[i]) : nullptr;
+    }
+    const pisco_status s = set_tables(gp, ti, tm, te);
+    if (s != PISCO_OK) return s;
+  }
+  return PISCO_OK;
+}
+
 // Enqueue the whole batch (capture on the second call with a new pointer set, replay after);
 // order_user: order the batch after the caller's stream and the caller's stream after it
 // (device buffers); host-buffer launches skip that so two batches can be in flight at once.
@@ -1426,36 +1767,23 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
   const int n = (int)b->items.size();
   for (int i = 0; i < n; ++i)
     if (!in[i] || !outp[i]) return PISCO_ERR_ARG;
+  bool same = b->gexec && b->g_host == host_io && (int)b->g_in.size() == n && !b->prof;
+  for (int i = 0; same && i < n; ++i)
+    same = b->g_in[i] == in[i] && b->g_out[i] == outp[i] && b->g_eig[i] == (eig ? eig[i] : nullptr);
+  if (!same) {
+    // the tables of the new pointer set (the previous call has been waited for)
+    if (cudaStreamSynchronize(b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+    const pisco_status s = batch_tables(b, in, outp, eig, host_io);
+    if (s != PISCO_OK) return s;
+  }
   if (order_user && (cudaEventRecord(b->ev_in, b->user) != cudaSuccess ||
                      cudaStreamWaitEvent(b->main, b->ev_in, 0) != cudaSuccess))
     return PISCO_ERR_CUDA;
-  bool same = b->gexec && b->g_host == host_io && (int)b->g_in.size() == n;
-  for (int i = 0; same && i < n; ++i)
-    same = b->g_in[i] == in[i] && b->g_out[i] == outp[i] && b->g_eig[i] == (eig ? eig[i] : nullptr);
-  if (!same && !b->warmed) {
-    // first call: run every item eagerly on its own stream (same work as the graph)
-    pisco_status s = PISCO_OK;
+  if (!same && (!b->warmed || b->prof)) {
+    // first call (and profiled calls): every group eagerly on its own stream (same work as the graph)
     if (cudaEventRecord(b->fork, b->main) != cudaSuccess) return PISCO_ERR_CUDA;
-    for (int i = 0; i < n && s == PISCO_OK; ++i) {
-      pisco_plan_s* pl = b->items[i];
-      cudaStream_t st = pl->st;
-      if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) return PISCO_ERR_CUDA;
-      const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
-      if (cudaMemcpyAsync(pl->calib_stage, in[i], cb, host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                          st) != cudaSuccess) return PISCO_ERR_CUDA;
-      float2* maps_dst = host_io ? pl->io_maps : (float2*)outp[i];
-      float* eig_dst = eig && eig[i] ? (host_io ? pl->io_eig : eig[i]) : nullptr;
-      pl->ev_used = 0;
-      s = run_all(pl, pl->calib_stage, maps_dst, eig_dst);
-      if (s != PISCO_OK) return s;
-      if (host_io) {
-        const size_t mb = sizeof(float2) * (size_t)pl->Q * pl->npix;
-        if (cudaMemcpyAsync(outp[i], pl->io_maps, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PISCO_ERR_CUDA;
-        if (eig_dst && cudaMemcpyAsync(eig[i], pl->io_eig, sizeof(float) * pl->npix_red, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PISCO_ERR_CUDA;
-      }
-      if (cudaEventRecord(b->join[i], st) != cudaSuccess ||
-          cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess) return PISCO_ERR_CUDA;
-    }
+    const pisco_status s = enqueue_groups(b, in, outp, eig, host_io, true, nullptr);
+    if (s != PISCO_OK) return s;
     b->warmed = true;
   } else if (!same) {
     batch_graph_reset(b);
@@ -1463,26 +1791,8 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
     int total_launches = 0;
     pisco_status s = PISCO_OK;
     if (cudaEventRecord(b->fork, b->main) != cudaSuccess) s = PISCO_ERR_CUDA;
-    for (int i = 0; i < n && s == PISCO_OK; ++i) {
-      pisco_plan_s* pl = b->items[i];
-      cudaStream_t st = pl->st;
-      if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
-      const size_t cb = sizeof(float2) * (size_t)pl->Q * pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
-      // host I/O: the host->device copies are issued outside the graph, ahead of it
-      if (!host_io && cudaMemcpyAsync(pl->calib_stage, in[i], cb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-        s = PISCO_ERR_CUDA;
-        break;
-      }
-      float2* maps_dst = host_io ? pl->io_maps : (float2*)outp[i];
-      float* eig_dst = eig && eig[i] ? (host_io ? pl->io_eig : eig[i]) : nullptr;
-      pl->ev_used = 0;
-      s = run_all(pl, pl->calib_stage, maps_dst, eig_dst);  // counts its launches from zero
-      if (s != PISCO_OK) break;
-      total_launches += g_launches;
-      if (cudaEventRecord(b->join[i], st) != cudaSuccess ||
-          cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess) { s = PISCO_ERR_CUDA; break; }
-    }
     // host I/O: the copies stay outside the graph (issued around each launch)
+    if (s == PISCO_OK) s = enqueue_groups(b, in, outp, eig, host_io, false, &total_launches);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->main, &g);
     if (s != PISCO_OK || ec != cudaSuccess || !g) {
@@ -1551,8 +1861,10 @@ static pisco_status batch_launch(pisco_batch_s* b, const void* const* in, void* 
   return PISCO_OK;
 }
 
-// Wait for the launched batch, then decode every item's status (saturated items are re-run
-// alone with a larger block).
+// Wait for the launched batch, then decode every item's status.  Items whose eigensolver block
+// saturated, or whose split is not certified yet with the automatic iteration count, are re-run
+// alone (through their view) with a larger block or more iterations; their group adopts the
+// larger setting for later calls.
 static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
   if (!b->pending) return PISCO_ERR_ARG;
   b->pending = false;
@@ -1562,7 +1874,14 @@ static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
   void* const* outp = b->pend_out.data();
   float* const* eig = b->pend_eig.data();
   if (cudaStreamSynchronize(b->main) != cudaSuccess) return PISCO_ERR_CUDA;
+  if (b->prof)
+    for (pisco_plan_s* gp : b->groups) prof_collect(gp, gp->ev_used);
+  // a bounded wait of a batched tensor-core product reports on the group's first item
+  for (pisco_plan_s* gp : b->groups)
+    if (gp->items > 1 && (gp->hstatus[0].flags & ST_TIMEOUT))
+      for (int k = 1; k < gp->items; ++k) gp->hstatus[k].flags |= ST_TIMEOUT;
   pisco_status worst = PISCO_OK;
+  bool regroup = false;
   for (int i = 0; i < n; ++i) {
     pisco_plan_s* pl = b->items[i];
     const DevStatus h = *pl->hstatus;
@@ -1576,6 +1895,7 @@ static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
       if (pl->m < pl->m_max) {
         pl->m = std::min(pl->m * 2, pl->m_max);
         batch_graph_reset(b);
+        regroup = true;
         si = host_io ? pisco_estimate_host(pl, in[i], outp[i], eig[i]) : pisco_estimate(pl, in[i], outp[i], eig[i]);
       } else {
         si = PISCO_ERR_NOT_CONVERGED;
@@ -1583,6 +1903,7 @@ static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
     } else if ((h.flags & ST_UNCERTIFIED) && retry_iters(pl)) {
       // the split is not certified yet: redo this item alone with more subspace iterations
       batch_graph_reset(b);
+      regroup = true;
       si = host_io ? pisco_estimate_host(pl, in[i], outp[i], eig[i]) : pisco_estimate(pl, in[i], outp[i], eig[i]);
     } else {
       pl->last_k = h.k;
@@ -1592,6 +1913,21 @@ static pisco_status batch_finish(pisco_batch_s* b, pisco_status* item_status) {
     }
     if (item_status) item_status[i] = si;
     if (si != PISCO_OK && (worst == PISCO_OK || worst == PISCO_ERR_RANK)) worst = si;
+  }
+  if (regroup) {
+    // a group runs with the largest block and iteration count any of its items needed
+    for (int g = 0; g < (int)b->groups.size(); ++g) {
+      pisco_plan_s* gp = b->groups[g];
+      if (gp->items == 1) continue;
+      for (int i : b->members[g]) {
+        gp->m = std::max(gp->m, b->items[i]->m);
+        gp->eig_iters = std::max(gp->eig_iters, b->items[i]->eig_iters);
+      }
+      for (int i : b->members[g]) {
+        b->items[i]->m = gp->m;
+        b->items[i]->eig_iters = gp->eig_iters;
+      }
+    }
   }
   return worst;
 }
@@ -1647,6 +1983,8 @@ pisco_status pisco_tc_cgemm_pipelined(int nterms, int M, int N, int K, const flo
   return PISCO_OK;
 }
 
+void pisco_test_stall_tensor_loads(int enable) { tc2_set_stall(enable != 0); }
+
 pisco_status pisco_support_mask(const float* d_eig, long long n, float threshold, unsigned char* d_mask,
                                 void* cuda_stream) {
   if (n < 0 || !(threshold == threshold)) return PISCO_ERR_ARG;
@@ -1695,7 +2033,7 @@ pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t
   if (launches) *launches = b->launches;
   if (workspace_bytes) {
     size_t t = 0;
-    for (auto* pl : b->items) t += pl->ws_bytes;
+    for (auto* pl : b->groups) t += pl->ws_bytes;
     *workspace_bytes = t;
   }
   return PISCO_OK;
@@ -1704,6 +2042,53 @@ pisco_status pisco_batch_info(pisco_batch_t b, int* count, int* launches, size_t
 pisco_status pisco_batch_item(pisco_batch_t b, int i, pisco_plan_t* plan) {
   if (!b || !plan || i < 0 || i >= (int)b->items.size()) return PISCO_ERR_ARG;
   *plan = b->items[i];
+  return PISCO_OK;
+}
+
+pisco_status pisco_batch_set_profiling(pisco_batch_t b, int enable) {
+  if (!b || b->pending) return PISCO_ERR_ARG;
+  b->prof = enable != 0;
+  for (pisco_plan_s* gp : b->groups) gp->prof = b->prof;
+  return PISCO_OK;
+}
+
+pisco_status pisco_batch_profile_reset(pisco_batch_t b) {
+  if (!b) return PISCO_ERR_ARG;
+  for (pisco_plan_s* gp : b->groups) pisco_profile_reset(gp);
+  return PISCO_OK;
+}
+
+pisco_status pisco_batch_profile_entry(pisco_batch_t b, int idx, const char** name, double* total_ms, int* count) {
+  if (!b || idx < 0) return PISCO_ERR_ARG;
+  // the operation names of all groups in first-seen order, totals summed over the groups
+  std::vector<const char*> names;
+  for (pisco_plan_s* gp : b->groups)
+    for (const char* nm : gp->prof_name) {
+      bool seen = false;
+      for (const char* x : names) seen = seen || strcmp(x, nm) == 0;
+      if (!seen) names.push_back(nm);
+    }
+  if (idx >= (int)names.size()) return PISCO_ERR_ARG;
+  double ms = 0.0;
+  int cnt = 0;
+  for (pisco_plan_s* gp : b->groups)
+    for (size_t k = 0; k < gp->prof_name.size(); ++k)
+      if (strcmp(gp->prof_name[k], names[idx]) == 0) {
+        ms += gp->prof_ms[k];
+        cnt += gp->prof_cnt[k];
+      }
+  if (name) *name = names[idx];
+  if (total_ms) *total_ms = ms;
+  if (count) *count = cnt;
+  return PISCO_OK;
+}
+
+pisco_status pisco_batch_groups(pisco_batch_t b, int* groups, int* largest) {
+  if (!b) return PISCO_ERR_ARG;
+  int mx = 0;
+  for (pisco_plan_s* gp : b->groups) mx = std::max(mx, gp->items);
+  if (groups) *groups = (int)b->groups.size();
+  if (largest) *largest = mx;
   return PISCO_OK;
 }
 

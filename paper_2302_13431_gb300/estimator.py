@@ -184,7 +184,8 @@ class PiscoBatch:
 
     specs: list of dicts with keys grid, calib_shape, num_coils, tau and optionally
     kernel_shape, thr, reduction, iters, seed, eig_block, eig_iters, precision, tc_splits,
-    gemm_splits, gemm_tile, gram_df, tc_interp.
+    gemm_splits, gemm_tile, gram_df, tc_interp, batch_group (items of identical parameters
+    estimated by one batched pass; 0 automatic, 1 one launch chain per item).
     """
 
     def __init__(self, specs, stream=None):
@@ -202,7 +203,8 @@ class PiscoBatch:
                                         | (B.PISCO_FLAG_GRAM_DF if sp.get("gram_df") else 0)
                                         | (B.PISCO_FLAG_TC_INTERP if sp.get("tc_interp") else 0),
                                         sp.get("eig_block", 0), sp.get("eig_iters", 0), sp.get("tc_splits", 0),
-                                        sp.get("gemm_splits", 0), sp.get("gemm_tile", 0)))
+                                        sp.get("gemm_splits", 0), sp.get("gemm_tile", 0),
+                                        sp.get("batch_group", 0)))
         st, h = B.pisco_batch_plan(params, self.stream.cuda_stream)
         if st != B.PISCO_OK:
             raise B.PiscoError(st, "pisco_batch_plan")
@@ -280,6 +282,23 @@ class PiscoBatch:
         view = _DevView(ptr, (nbytes // int(ts[2:]),), ts)
         torch.cuda.synchronize()
         return torch.as_tensor(view, device="cuda").clone()
+
+    def set_profiling(self, enable=True):
+        """Eager calls with CUDA events around every operation of every group's pass."""
+        st = B.pisco_batch_set_profiling(self._b, enable)
+        if st != B.PISCO_OK:
+            raise B.PiscoError(st, "pisco_batch_set_profiling")
+
+    def profile_reset(self):
+        B.pisco_batch_profile_reset(self._b)
+
+    def profile(self):
+        """{operation: (total_ms, count)} summed over the groups since the last reset."""
+        return B.pisco_batch_profile(self._b)
+
+    def groups(self):
+        st, g, mx = B.pisco_batch_groups(self._b)
+        return dict(groups=g, largest=mx)
 
     def item_stats(self, i):
         st, h = B.pisco_batch_item(self._b, i)

@@ -26,8 +26,10 @@ def test_tune_picks_the_fastest_and_caches(tmp_path):
     from paper_2302_13431_gb300.phantoms import make_case
     specs = [dict(grid=(64, 64), calib_shape=(24, 24), num_coils=8, tau=3, reduction=2, iters=20)] * 3
     cache = str(tmp_path / "tune.json")
-    cands = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False, tc_interp=False),
-             dict(precision="tc_g_eig", tc_splits=4, gemm_splits=2, gemm_tile=64, gram_df=True, tc_interp=True)]
+    cands = [dict(precision="fp32", tc_splits=0, gemm_splits=0, gemm_tile=0, gram_df=False, tc_interp=False,
+                  batch_group=0),
+             dict(precision="tc_g_eig", tc_splits=4, gemm_splits=2, gemm_tile=64, gram_df=True, tc_interp=True,
+                  batch_group=0)]
     cfg, table = tune(specs, steps=2, warmup=2, cache=cache, cands=cands)
     assert all(r["ms"] is not None for r in table), table  # both candidates pass the correctness gate
     assert cfg == {k: min(table, key=lambda r: r["ms"])[k] for k in KNOB_KEYS}

@@ -159,6 +159,25 @@ def test_nullspace_svd_matches_lapack_eigh_of_gram():
     assert np.all(sig[:-1] >= sig[1:])
 
 
+@pytest.mark.parametrize("grid, Q, cs, tau", [((48, 48), 4, (16, 16), (2, 2)), ((12, 16, 12), 3, (8, 10, 8), (1, 2, 1))])
+def test_gram_eigh_route_equals_the_svd_route(grid, Q, cs, tau):
+    """nullspace_gram_eigh (eigendecomposition of C^H C) gives the SVD route's split: same k,
+    same signal projector, orthonormal null basis, singular values equal."""
+    case = make_case(grid, Q, cs, seed=9, phase="poly4")
+    lam = O.kernel_support(tau, "ellipsoid")
+    C = O.calibration_matrix(case.calib, lam, rows="full")
+    Vn, Us, sig = O.nullspace_svd(C, 0.05)
+    Vn2, Us2, sig2 = O.nullspace_gram_eigh(C, 0.05)
+    assert Us2.shape[1] == Us.shape[1] and Vn2.shape[1] == Vn.shape[1]
+    np.testing.assert_allclose(Us2 @ Us2.conj().T, Us @ Us.conj().T, atol=1e-9)
+    np.testing.assert_allclose(Vn2.conj().T @ Vn2, np.eye(Vn2.shape[1]), atol=1e-12)
+    k = Us.shape[1]
+    np.testing.assert_allclose(sig2[:k], sig[:k], rtol=1e-9)
+    # a threshold placed between two singular values moves the split by exactly one
+    thr = 0.5 * (sig[k - 1] + sig[k - 2]) / sig[0]
+    assert O.nullspace_gram_eigh(C, thr)[1].shape[1] == O.nullspace_svd(C, thr)[1].shape[1] == k - 1
+
+
 def test_threshold_is_strict_and_counts_missing_singular_values():
     # P < n: C has 2 rows and 4 columns -> at least 2 exactly-null directions
     C = np.array([[1.0, 0, 0, 0], [0, 0.05, 0, 0]], complex)
