@@ -91,6 +91,8 @@ struct AxisView {
   int pixel_major = 0;  // 1 (needs outer == 1): write out[(o*inner + ii)*batch + b] instead
   int mt = 0;        // 1: the matrix is stored transposed, M[i][o] ([n_in][n_out]); for
                      // inner == 1 passes this makes a warp's matrix reads contiguous
+  int pm_group = 0;  // pixel_major with batch = items x pm_group: item-major blocks, each
+                     // [n_out * inner][pm_group] (0: one block of the whole batch)
 };
 cudaError_t apply_axis_c2z(const float2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
 cudaError_t apply_axis_z(const double2* in, const double2* M, double2* out, AxisView v, cudaStream_t st);
@@ -170,6 +172,9 @@ cudaError_t gassembly_kernel(const float2* U, const float* w, int Q, int L, int 
                              const int* lag_ptr, const int* lag_ent, int nbox, float2* K,
                              cudaStream_t st);
 cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_size, cudaStream_t st);
+// the folded lag table KT [nlag][Q*Q] spread onto the lag box K [Q*Q][nbox] (zero where box_lag < 0)
+cudaError_t gassembly_scatter_box(const float2* KT, const int* box_lag, int QQ, int nbox, float2* K, cudaStream_t st,
+                                  int items = 1, long long sKT = 0, long long sK = 0);
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
                                const int* lag_ent, int nlag, float2* KT, cudaStream_t st, int items = 1,
                                long long sP = 0, long long sKT = 0);
@@ -269,7 +274,10 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
                      int nbatch = 1, long long c_stride = 0, int a_per_item = 0, float2* const* c_tab = nullptr,
-                     int c_div = 1, int b_per_item = 1);
+                     int c_div = 1, int b_per_item = 1, const float2* a_fp32 = nullptr, int lda_fp32 = 0);
+// a_fp32: A given as FP32 complex rows (leading dimension lda_fp32, even; items lda_fp32 * M apart
+// with a_per_item) and split into head and tail in shared memory (three passes only); Ahi/Alo unused
+bool tc2_conv_ok(int K, int lda_fp32, const void* a_fp32);
 
 
 // a4+a5: power iteration with the phase step

@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(256) apply_axis_kernel(const Tin* __restrict__
       C sv = mk(decltype(acc.x)(s.x), decltype(acc.x)(s.y));
       cfma(acc, row[(long long)i * mstep], sv);
     }
-    if (v.pixel_major)
+    if (v.pixel_major && v.pm_group > 0)
+      out[((bo / v.pm_group) * ((long long)v.n_out * v.inner) + (long long)o * v.inner + ii) * v.pm_group +
+          bo % v.pm_group] = acc;
+    else if (v.pixel_major)
       out[((long long)o * v.inner + ii) * v.batch + bo] = acc;
     else
       out[(bo * v.n_out + o) * v.inner + ii] = acc;

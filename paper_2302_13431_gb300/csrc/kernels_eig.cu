@@ -550,7 +550,9 @@ cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, i
 // (p,q) with b = B[p][q] = |b| e, the rotation J = [[c, -s e],[s conj(e), c]] with
 // t = tan(theta) = sign(z)/(|z| + sqrt(1+z^2)), z = (B[p][p]-B[q][q])/(2|b|), zeroes B[p][q].
 // A rotation is skipped when |b| <= 3e-7 sqrt(|B_pp B_qq|) + 3e-9 max|B_ii| (relative
-// accuracy for the small Ritz values); the solve stops after a sweep without rotations.
+// accuracy for the small Ritz values); the solve stops after a sweep whose rotations all had
+// |b| <= 2e-6 sqrt(|B_pp B_qq|) + 3e-9 max|B_ii| (rotations at that level only stir FP32 rounding
+// noise, which otherwise keeps a converged matrix rotating until the sweep limit).
 // The two-sided update of a round is applied per 2x2 block (pair i rows, pair j columns):
 // B_ij <- J_i^H B_ij J_j, one shared-memory pass; V <- V J likewise.  B and, when it fits
 // (m <= 96), V live in shared memory.  Output: mu (descending) and V with B V = V diag(mu).
@@ -615,14 +617,15 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
         float c = 1.f, ser = 0.f, sei = 0.f;
         int on = 0;
         const bool both_low = fabsf(app) < skip_below && fabsf(aqq) < skip_below;
-        if (!both_low && mag > 3e-7f * sqrtf(fmaxf(fabsf(app), noise) * fmaxf(fabsf(aqq), noise)) + abs_tol) {
+        const float rel = sqrtf(fmaxf(fabsf(app), noise) * fmaxf(fabsf(aqq), noise));
+        if (!both_low && mag > 3e-7f * rel + abs_tol) {
           const float z = (app - aqq) / (2.f * mag);
           const float t = (z >= 0.f ? 1.f : -1.f) / (fabsf(z) + sqrtf(1.f + z * z));
           c = rsqrtf(1.f + t * t);
           const float sn = t * c;
           ser = sn * bpq.x / mag; sei = sn * bpq.y / mag;
           on = 1;
-          s_rot = 1;
+          if (mag > 2e-6f * rel + abs_tol) s_rot = 1;
         }
         rc[4 * i] = c; rc[4 * i + 1] = ser; rc[4 * i + 2] = sei;
         act[i] = on;
@@ -720,14 +723,14 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
 
 // ---------------------------------------------------------------------------------------
 // FP64 decision.  band_idx[0] = 0 (the top Ritz vector fixes lambda_1); the others are the
-// Ritz vectors whose FP32 Ritz value lies within a factor 4 of the FP32 threshold, closest
+// Ritz vectors whose FP32 Ritz value lies within a factor 2 of the FP32 threshold, closest
 // (in log distance) first, -1 padded.
 // ---------------------------------------------------------------------------------------
 __global__ void select_band_kernel(const float* __restrict__ mu, int m, double thr2, int nb_max,
                                    int* __restrict__ band_idx, EigItems it) {
   mu += blockIdx.z * it.vec;
   band_idx += blockIdx.z * it.band;
-  // candidate j >= 1 with |log2(mu_j/theta)| <= 2; rank by (distance, index); the nb_max-1
+  // candidate j >= 1 with |log2(mu_j/theta)| <= 1; rank by (distance, index); the nb_max-1
   // nearest fill band_idx[1..]
   const int j = threadIdx.x;
   const float theta = (float)(thr2 * (double)mu[0]);
@@ -740,7 +743,7 @@ __global__ void select_band_kernel(const float* __restrict__ mu, int m, double t
     return fabsf(log2f(v / theta));
   };
   const float dj = dist(j);
-  if (!(dj <= 2.0f)) return;
+  if (!(dj <= 1.0f)) return;
   int rank = 0;
   for (int t = 1; t < m; ++t) {
     const float dt = dist(t);

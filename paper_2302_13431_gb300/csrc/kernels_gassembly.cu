@@ -97,6 +97,27 @@ __global__ void add_identity_kernel(float2* G, int Q, long long npix, float lam_
   }
 }
 
+__global__ void scatter_box_kernel(const float2* __restrict__ KT, const int* __restrict__ box_lag, int QQ, int nbox,
+                                   float2* __restrict__ K, long long sKT, long long sK) {
+  KT += blockIdx.y * sKT;
+  K += blockIdx.y * sK;
+  const long long total = (long long)QQ * nbox;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int pq = (int)(e / nbox), t = (int)(e % nbox);
+    const int l = box_lag[t];
+    K[e] = l >= 0 ? KT[(long long)l * QQ + pq] : make_float2(0.f, 0.f);
+  }
+}
+
+cudaError_t gassembly_scatter_box(const float2* KT, const int* box_lag, int QQ, int nbox, float2* K, cudaStream_t st,
+                                  int items, long long sKT, long long sK) {
+  long long blocks = ((long long)QQ * nbox + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  scatter_box_kernel<<<dim3((unsigned)blocks, items), 256, 0, st>>>(KT, box_lag, QQ, nbox, K, sKT, sK);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 cudaError_t gassembly_add_identity(float2* G, int Q, long long npix, float lam_size, cudaStream_t st) {
   long long blocks = ((long long)Q * Q * npix + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
@@ -114,39 +135,47 @@ namespace pisco {
 //     KT[l][p*Q + q] = sum_{(b,a): b - a = d_l} P[(q,b)][(p,a)],
 // the entries of each lag summed in the fixed CSR order (bitwise reproducible).  KT is the
 // K x N operand of the second GEMM, G[x][pq] = |Lambda| delta_pq - sum_l E[x][l] KT[l][pq].
-__global__ void collapse_lags_kernel(const float2* __restrict__ P, int n, int Q, int L,
-                                     const int* __restrict__ lagc_ptr, const int* __restrict__ lag_ent,
-                                     int nlag, float2* __restrict__ KT, long long sP, long long sKT) {
+// (3D: |Lambda| = 123, the L x L block is 121 KiB of shared memory.)
+// One CTA per coil pair (p, q) (grid y: item): the L x L block P[(q, b)][(p, a)] is read with
+// coalesced row loads into shared memory, then each lag's entries are summed in the CSR order.
+__global__ void __launch_bounds__(128) collapse_lags_kernel(const float2* __restrict__ P, int n, int Q, int L,
+                                                            const int* __restrict__ lagc_ptr,
+                                                            const int* __restrict__ lag_ent, int nlag,
+                                                            float2* __restrict__ KT, long long sP, long long sKT) {
+  extern __shared__ float2 blk[];  // [L][L]
   P += blockIdx.y * sP;
   KT += blockIdx.y * sKT;
   const int QQ = Q * Q;
-  const long long total = (long long)nlag * QQ;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int l = (int)(idx / QQ), pq = (int)(idx % QQ);
-    const int p = pq / Q, q = pq % Q;
-    const float2* rowq = P + (long long)q * L * n + (long long)p * L;
+  const int pq = blockIdx.x;
+  const int p = pq / Q, q = pq % Q;
+  const float2* src = P + (long long)q * L * n + (long long)p * L;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    const int b = e / L, a = e % L;
+    blk[e] = src[(long long)b * n + a];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nlag; l += blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
     for (int e = lagc_ptr[l]; e < lagc_ptr[l + 1]; ++e) {
-      const int ent = lag_ent[e];
-      const int b = ent / L, a = ent % L;
-      const float2 v = rowq[(long long)b * n + a];
+      const float2 v = blk[lag_ent[e]];
       acc.x += v.x;
       acc.y += v.y;
     }
-    KT[idx] = acc;
+    KT[(long long)l * QQ + pq] = acc;
   }
 }
 
 cudaError_t gassembly_collapse(const float2* P, int n, int Q, int L, const int* lagc_ptr,
                                const int* lag_ent, int nlag, float2* KT, cudaStream_t st, int items, long long sP,
                                long long sKT) {
-  const long long total = (long long)nlag * Q * Q;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  blocks = (blocks + items - 1) / items;
-  collapse_lags_kernel<<<dim3((unsigned)blocks, items), 256, 0, st>>>(P, n, Q, L, lagc_ptr, lag_ent, nlag, KT, sP,
-                                                                      sKT);
+  const size_t smem = (size_t)L * L * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(collapse_lags_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  collapse_lags_kernel<<<dim3(Q * Q, items), 128, smem, st>>>(P, n, Q, L, lagc_ptr, lag_ent, nlag, KT, sP, sKT);
   ++g_launches;
   return cudaGetLastError();
 }

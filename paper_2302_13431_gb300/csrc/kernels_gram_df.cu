@@ -385,33 +385,45 @@ __device__ __forceinline__ void split_entry(const float4& a, float& rh, float& r
 }
 
 // Zb = A * Xb (the band products of the FP64 Rayleigh quotients) in double-float: A's entries as
-// hi + lo float pairs, the band vectors exact in FP32 (they come from the FP32 Ritz block).  Four
-// warps share a row (interleaved 32-wide k slices), each lane accumulates the used band columns
-// (NBU, a compile-time count so the 2 NBU accumulator chains interleave) with the next A entry
-// already in flight; the warp partials are combined in a fixed order.  Zb written in FP64.
+// hi + lo float pairs, the band vectors exact in FP32 (they come from the FP32 Ritz block).  Each
+// product term is accumulated error-free in the manner of Ogita, Rump & Oishi's Dot2 (2005): the
+// exact product hi*x as (p, q) by FMA, the running sum s updated by TwoSum (s, r), and the error
+// terms q + r + lo*x gathered in a second FP32 accumulator c; s + c carries about 48 bits.  One
+// warp per row of A (lanes stride the row: coalesced 16-byte loads), eight rows per CTA sharing the
+// band vectors staged column-major in shared memory (consecutive lanes read consecutive words),
+// only the used band columns (NBU) multiplied, partial sums combined by warp shuffles.
 constexpr int kBandKC = 512;      // k values of Xb staged per pass
-constexpr int kBandSplit = 4;     // warps per row
-constexpr int kBandRows = 2;      // rows per CTA (8 warps)
+constexpr int kBandRows = 8;      // rows per CTA (one warp each)
+
+__device__ __forceinline__ void dot2_term(float& s, float& c, float a_hi, float a_lo, float x) {
+  const float p = a_hi * x;
+  const float q = fmaf(a_hi, x, -p);
+  float t, r;
+  two_sum(s, p, t, r);
+  s = t;
+  c = fmaf(a_lo, x, c + (q + r));
+}
+__device__ __forceinline__ void dot2_merge(float& s, float& c, float s2, float c2) {
+  float t, r;
+  two_sum(s, s2, t, r);
+  s = t;
+  c += c2 + r;
+}
 
 template <int NBV, int NBU, typename TA>
-__device__ __forceinline__ void band_rows_accumulate(const TA* __restrict__ arow, const float2* xs, int kc, int k,
-                                                     float (&arh)[NBV], float (&arl)[NBV], float (&aih)[NBV],
-                                                     float (&ail)[NBV]) {
-  constexpr int STEP = 32 * kBandSplit;
-  if (k >= kc) return;
-  TA nxt = arow[k];
-  for (; k < kc; k += STEP) {
-    const TA cur = nxt;
-    if (k + STEP < kc) nxt = arow[k + STEP];
+__device__ __forceinline__ void band_row_accumulate(const TA* __restrict__ arow, const float2* xs, int kc, int lane,
+                                                    float (&sr)[NBV], float (&cr)[NBV], float (&si)[NBV],
+                                                    float (&ci)[NBV]) {
+  for (int k = lane; k < kc; k += 32) {
     float ahx, alx, ahy, aly;
-    split_entry(cur, ahx, alx, ahy, aly);
+    split_entry(arow[k], ahx, alx, ahy, aly);
 #pragma unroll
     for (int c = 0; c < NBU; ++c) {
-      const float2 x = xs[k * NBV + c];
-      df_fma1(arh[c], arl[c], ahx, alx, x.x);     // Re += Re a Re x
-      df_fma1(aih[c], ail[c], ahx, alx, x.y);     // Im += Re a Im x
-      df_fma1(arh[c], arl[c], -ahy, -aly, x.y);   //      - Im a Im x
-      df_fma1(aih[c], ail[c], ahy, aly, x.x);     //      + Im a Re x
+      const float2 x = xs[c * kBandKC + k];
+      dot2_term(sr[c], cr[c], ahx, alx, x.x);     // Re += Re a Re x
+      dot2_term(sr[c], cr[c], -ahy, -aly, x.y);   //      - Im a Im x
+      dot2_term(si[c], ci[c], ahx, alx, x.y);     // Im += Re a Im x
+      dot2_term(si[c], ci[c], ahy, aly, x.x);     //      + Im a Re x
     }
   }
 }
@@ -421,75 +433,59 @@ __global__ void __launch_bounds__(256) band_matvec_df_kernel(const TA* __restric
                                                              const double2* __restrict__ Xb, int n,
                                                              const int* __restrict__ band_idx,
                                                              double2* __restrict__ Zb, EigItems it) {
-  __shared__ float2 xs[kBandKC * NBV];
+  __shared__ float2 xs[NBV * kBandKC];  // [column][k]
   A += blockIdx.y * it.a;
   Xb += blockIdx.y * it.nb;
   band_idx += blockIdx.y * it.band;
   Zb += blockIdx.y * it.nb;
-  __shared__ float4 part[kBandRows][kBandSplit][NBV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rl = warp / kBandSplit, ks = warp % kBandSplit;
-  const int r = blockIdx.x * kBandRows + rl;
+  const int r = blockIdx.x * kBandRows + warp;
   int nbu = 0;
 #pragma unroll
   for (int c = 0; c < NBV; ++c)
     if (band_idx[c] >= 0) nbu = c + 1;
-  float arh[NBV], arl[NBV], aih[NBV], ail[NBV];
+  float sr[NBV], cr[NBV], si[NBV], ci[NBV];
 #pragma unroll
-  for (int c = 0; c < NBV; ++c) arh[c] = arl[c] = aih[c] = ail[c] = 0.f;
+  for (int c = 0; c < NBV; ++c) sr[c] = cr[c] = si[c] = ci[c] = 0.f;
   for (int k0 = 0; k0 < n; k0 += kBandKC) {
     const int kc = min(kBandKC, n - k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kc * NBV; e += blockDim.x) {
-      const double2 v = Xb[(long long)k0 * NBV + e];
-      xs[e] = make_float2((float)v.x, (float)v.y);  // exact: the band vectors are FP32 values
+    for (int e = threadIdx.x; e < kc * nbu; e += blockDim.x) {
+      const int c = e / kc, k = e % kc;
+      const double2 v = Xb[(long long)(k0 + k) * NBV + c];
+      xs[c * kBandKC + k] = make_float2((float)v.x, (float)v.y);  // exact: the band vectors are FP32 values
     }
     __syncthreads();
     if (r < n) {
       const TA* arow = A + (long long)r * n + k0;
-      const int k = ks * 32 + lane;
       switch (nbu) {
-        case 1: band_rows_accumulate<NBV, 1>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 2: band_rows_accumulate<NBV, 2>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 3: band_rows_accumulate<NBV, 3>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 4: band_rows_accumulate<NBV, 4>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 5: band_rows_accumulate<NBV, 5>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 6: band_rows_accumulate<NBV, 6>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 7: band_rows_accumulate<NBV, 7>(arow, xs, kc, k, arh, arl, aih, ail); break;
-        case 8: band_rows_accumulate<NBV, 8>(arow, xs, kc, k, arh, arl, aih, ail); break;
+        case 1: band_row_accumulate<NBV, 1>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 2: band_row_accumulate<NBV, 2>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 3: band_row_accumulate<NBV, 3>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 4: band_row_accumulate<NBV, 4>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 5: band_row_accumulate<NBV, 5>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 6: band_row_accumulate<NBV, 6>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 7: band_row_accumulate<NBV, 7>(arow, xs, kc, lane, sr, cr, si, ci); break;
+        case 8: band_row_accumulate<NBV, 8>(arow, xs, kc, lane, sr, cr, si, ci); break;
         default: break;
       }
     }
   }
+  if (r >= n) return;
 #pragma unroll
   for (int c = 0; c < NBV; ++c) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const float bh = __shfl_xor_sync(0xffffffffu, arh[c], o), bl = __shfl_xor_sync(0xffffffffu, arl[c], o);
-      const float ch = __shfl_xor_sync(0xffffffffu, aih[c], o), cl = __shfl_xor_sync(0xffffffffu, ail[c], o);
-      df_add(arh[c], arl[c], bh, bl);
-      df_add(aih[c], ail[c], ch, cl);
+      const float a1 = __shfl_xor_sync(0xffffffffu, sr[c], o), a2 = __shfl_xor_sync(0xffffffffu, cr[c], o);
+      const float b1 = __shfl_xor_sync(0xffffffffu, si[c], o), b2 = __shfl_xor_sync(0xffffffffu, ci[c], o);
+      dot2_merge(sr[c], cr[c], a1, a2);
+      dot2_merge(si[c], ci[c], b1, b2);
     }
   }
   if (lane == 0) {
 #pragma unroll
-    for (int c = 0; c < NBV; ++c) part[rl][ks][c] = make_float4(arh[c], arl[c], aih[c], ail[c]);
-  }
-  __syncthreads();
-  // combine the k slices in a fixed order: one thread per (row, band column)
-  if (threadIdx.x < kBandRows * NBV) {
-    const int rr = threadIdx.x / NBV, c = threadIdx.x % NBV;
-    const int row = blockIdx.x * kBandRows + rr;
-    if (row < n) {
-      float4 acc = part[rr][0][c];
-#pragma unroll
-      for (int w = 1; w < kBandSplit; ++w) {
-        const float4 v = part[rr][w][c];
-        df_add(acc.x, acc.y, v.x, v.y);
-        df_add(acc.z, acc.w, v.z, v.w);
-      }
-      Zb[(long long)row * NBV + c] = make_double2((double)acc.x + (double)acc.y, (double)acc.z + (double)acc.w);
-    }
+    for (int c = 0; c < NBV; ++c)
+      Zb[(long long)r * NBV + c] = make_double2((double)sr[c] + (double)cr[c], (double)si[c] + (double)ci[c]);
   }
 }
 

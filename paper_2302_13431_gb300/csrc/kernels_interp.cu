@@ -163,20 +163,32 @@ cudaError_t interp_final_normalize(const float2* T, const float2* M, int Q, long
 namespace pisco {
 
 // maps[q][x] /= ||maps[.][x]|| (sum of squares over the coils; zero pixels stay zero): the
-// normalisation of Sec. VI after a final interpolation pass that wrote unnormalised maps
-__global__ void normalize_maps_kernel(float2* __restrict__ maps, int Q, long long npix, long long sM,
-                                      float2* const* __restrict__ maps_tab) {
+// normalisation of Sec. VI after a final interpolation pass that wrote unnormalised maps.  One
+// thread per pixel keeps its coils in registers (QB per chunk; Q <= QB reads the maps once), so the
+// maps cross HBM once in each direction; grid y is the item (maps_tab[item], or maps + item * sM).
+template <int QB>
+__global__ void __launch_bounds__(256) normalize_maps_kernel(float2* __restrict__ maps, int Q, long long npix,
+                                                             long long sM, float2* const* __restrict__ maps_tab) {
   maps = maps_tab ? maps_tab[blockIdx.y] : maps + blockIdx.y * sM;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < npix; x += (long long)gridDim.x * blockDim.x) {
+    float2 v[QB];
     float n2 = 0.f;
-    for (int q = 0; q < Q; ++q) {
-      const float2 v = maps[(long long)q * npix + x];
-      n2 = fmaf(v.x, v.x, fmaf(v.y, v.y, n2));
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+      v[q] = q < Q ? __ldcs(maps + (long long)q * npix + x) : make_float2(0.f, 0.f);
+      n2 = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, n2));
+    }
+    for (int q = QB; q < Q; ++q) {  // coils beyond the register chunk (read twice)
+      const float2 w = maps[(long long)q * npix + x];
+      n2 = fmaf(w.x, w.x, fmaf(w.y, w.y, n2));
     }
     const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
-    for (int q = 0; q < Q; ++q) {
-      const float2 v = maps[(long long)q * npix + x];
-      maps[(long long)q * npix + x] = make_float2(v.x * s, v.y * s);
+#pragma unroll
+    for (int q = 0; q < QB; ++q)
+      if (q < Q) __stcs(maps + (long long)q * npix + x, make_float2(v[q].x * s, v[q].y * s));
+    for (int q = QB; q < Q; ++q) {
+      const float2 w = maps[(long long)q * npix + x];
+      maps[(long long)q * npix + x] = make_float2(w.x * s, w.y * s);
     }
   }
 }
@@ -186,7 +198,10 @@ cudaError_t normalize_maps(float2* maps, int Q, long long npix, cudaStream_t st,
   long long b = (npix + 255) / 256;
   if (b > 152 * 8) b = 152 * 8;
   b = (b + items - 1) / items;
-  normalize_maps_kernel<<<dim3((unsigned)b, items), 256, 0, st>>>(maps, Q, npix, sM, maps_tab);
+  if (Q <= 16)
+    normalize_maps_kernel<16><<<dim3((unsigned)b, items), 256, 0, st>>>(maps, Q, npix, sM, maps_tab);
+  else
+    normalize_maps_kernel<32><<<dim3((unsigned)b, items), 256, 0, st>>>(maps, Q, npix, sM, maps_tab);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
                                                  unsigned long long seed, float2* __restrict__ V,
                                                  float* __restrict__ eig, PiOpts opt) {
   constexpr int PIX = 256 / QP;
-  __shared__ float2 vs[PIX * QP];
+  __shared__ __align__(16) float2 vs[2][PIX * QP];  // double-buffered iterate: one barrier per step
   __shared__ float red[PIX * 2];
   __shared__ int any_flag;
   {
@@ -85,21 +85,28 @@ __global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
     const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
     v.x *= s; v.y *= s;
   }
-  vs[xi * QP + q] = v;
-  __syncthreads();
+  // a pixel's QP threads lie in one warp for QP <= 32: warp barriers suffice
+  int cur = 0;
+  vs[cur][xi * QP + q] = v;
+  if (QP <= 32) __syncwarp(); else __syncthreads();
   float2 gv = make_float2(0.f, 0.f);
   for (int it = 0; it <= iters; ++it) {
     gv = make_float2(0.f, 0.f);
+    const float4* vp = reinterpret_cast<const float4*>(&vs[cur][xi * QP]);
 #pragma unroll
-    for (int p = 0; p < QP; ++p) cfmac(gv, gcol[p], vs[xi * QP + p]);
+    for (int p = 0; p < QP / 2; ++p) {
+      const float4 t = vp[p];
+      cfmac(gv, gcol[2 * p], make_float2(t.x, t.y));
+      cfmac(gv, gcol[2 * p + 1], make_float2(t.z, t.w));
+    }
     if (it == iters) break;
     const float2 nv = make_float2(v.x - gv.x * inv_lam, v.y - gv.y * inv_lam);
     const float n2 = pixel_sum<QP>(nv.x * nv.x + nv.y * nv.y, red, xi, q);
     const float s = n2 > 0.f ? rsqrtf(n2) : 0.f;
     v = make_float2(nv.x * s, nv.y * s);
-    __syncthreads();
-    vs[xi * QP + q] = v;
-    __syncthreads();
+    cur ^= 1;
+    vs[cur][xi * QP + q] = v;
+    if (QP <= 32) __syncwarp(); else __syncthreads();
   }
   // Rayleigh quotient and phase of the coil-combined low-resolution image
   const float lraw = pixel_sum<QP>(v.x * gv.x + v.y * gv.y, red, xi, q);

@@ -16,6 +16,12 @@
 //
 // Every mbarrier wait is bounded; on expiry the kernel sets bit 16 of *err, stops issuing and
 // still frees its TMEM.
+//
+// A variant (CONV) reads A as plain FP32 complex rows instead of split arrays: TMA brings the
+// FP32 tile into the stage, two converter warps split it in shared memory into the TF32 head and
+// tail tiles (the same arithmetic and the same swizzled positions as the split kernels), make the
+// writes visible to the tensor core's async proxy and release the stage to the MMA thread.  A then
+// crosses HBM at 8 instead of 16 bytes per complex entry, and needs no separate split pass.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
@@ -124,19 +130,30 @@ struct Args {
   int no_loads;   // test hook: the producer issues no loads, so the waits on them expire
 };
 
-template <int NT, int STAGES>
+template <int NT, int STAGES, bool CONV>
+__host__ __device__ constexpr uint32_t stage_bytes() {
+  // split operands: [A head][A tail][B head][B tail]; CONV: [A fp32][A head][A tail][B head][B tail]
+  return CONV ? 3u * A_TILE + 2u * B_TILE : (NT == 3 ? 2u : 1u) * (A_TILE + B_TILE);
+}
+
+template <int NT, int STAGES, bool CONV>
 __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUtensorMap tAh,
                                                      const __grid_constant__ CUtensorMap tAl,
                                                      const __grid_constant__ CUtensorMap tBh,
                                                      const __grid_constant__ CUtensorMap tBl, Args g) {
-  constexpr uint32_t STAGE = (NT == 3 ? 2u : 1u) * (A_TILE + B_TILE);
+  static_assert(!CONV || NT == 3, "the converting variant splits A into head and tail");
+  constexpr uint32_t STAGE = stage_bytes<NT, STAGES, CONV>();
+  constexpr uint32_t A_OFF = CONV ? A_TILE : 0u;            // A head within a stage
+  constexpr uint32_t B_OFF = CONV ? 3u * A_TILE : (NT == 3 ? 2u * A_TILE : A_TILE);
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE);  // full[4], empty[4], accum
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE + 9 * 8);
+  // full[S], empty[S], accum, (CONV) conv[S]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE + (3 * STAGES + 1) * 8);
   const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[STAGES]), accum = su32(&bars[2 * STAGES]);
+  const uint32_t conv0 = su32(&bars[2 * STAGES + 1]);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNC;
   const int total = (g.K2 + BK - 1) / BK;
@@ -158,6 +175,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     for (int s = 0; s < STAGES; ++s) {
       bar_init(full0 + 8 * s, 1);
       bar_init(empty0 + 8 * s, 1);
+      if (CONV) bar_init(conv0 + 8 * s, 64);  // the converter warps
     }
     bar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -176,23 +194,49 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
       if (!ok) break;
       const uint32_t st = base + s * STAGE;
       const uint32_t fb = full0 + 8 * s;
-      bar_expect_tx(fb, STAGE);
       const int kx = (kb0 + i) * BK;
-      tma_2d(st, &tAh, kx, arow0, fb);
-      if (NT == 3) tma_2d(st + A_TILE, &tAl, kx, arow0, fb);
-      const uint32_t sb = st + (NT == 3 ? 2 * A_TILE : A_TILE);
+      if (CONV) {
+        bar_expect_tx(fb, A_TILE + 2 * B_TILE);
+        tma_2d(st, &tAh, kx, arow0, fb);  // the FP32 tile
+      } else {
+        bar_expect_tx(fb, STAGE);
+        tma_2d(st, &tAh, kx, arow0, fb);
+        if (NT == 3) tma_2d(st + A_TILE, &tAl, kx, arow0, fb);
+      }
+      const uint32_t sb = st + B_OFF;
       tma_2d(sb, &tBh, kx, brow0 + 2 * n0, fb);
       if (NT == 3) tma_2d(sb + B_TILE, &tBl, kx, brow0 + 2 * n0, fb);
+    }
+  } else if (CONV && warp >= 2 && nk > 0) {
+    // converters: FP32 tile -> TF32 head and tail tiles of the same stage (same swizzled offsets)
+    const int ct = tid - 64;
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % STAGES, c = i / STAGES;
+      ok = bar_wait(full0 + 8 * s, (uint32_t)(c & 1), g.wait_limit);
+      if (!ok) break;
+      unsigned char* sp = gbase + (size_t)s * STAGE;
+      const float4* src = reinterpret_cast<const float4*>(sp);
+      float4* hd = reinterpret_cast<float4*>(sp + A_TILE);
+      float4* tl = reinterpret_cast<float4*>(sp + 2 * A_TILE);
+#pragma unroll 4
+      for (int e = ct; e < (int)(A_TILE / 16); e += 64) {
+        const float4 v = src[e];
+        const float4 h = make_float4(head(v.x), head(v.y), head(v.z), head(v.w));
+        hd[e] = h;
+        tl[e] = make_float4(head(v.x - h.x), head(v.y - h.y), head(v.z - h.z), head(v.w - h.w));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(conv0 + 8 * s) : "memory");
     }
   } else if (warp == 1 && lane == 0 && nk > 0) {
     // MMA issuer: 4 MMAs of K = 8 per stage (x3 for the head/tail split)
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES, c = i / STAGES;
-      ok = bar_wait(full0 + 8 * s, (uint32_t)(c & 1), g.wait_limit);
+      ok = bar_wait((CONV ? conv0 : full0) + 8 * s, (uint32_t)(c & 1), g.wait_limit);
       if (!ok) break;
       fence_after();
-      const uint32_t st = base + s * STAGE;
-      const uint32_t sb = st + (NT == 3 ? 2 * A_TILE : A_TILE);
+      const uint32_t st = base + s * STAGE + A_OFF;
+      const uint32_t sb = base + s * STAGE + B_OFF;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const uint64_t ah = desc_sw128(st + 32 * j), bh = desc_sw128(sb + 32 * j);
@@ -388,9 +432,9 @@ bool encode_2d(CUtensorMap* map, const float* base, int cols, int rows, int ld_f
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NT, int STAGES>
+template <int NT, int STAGES, bool CONV = false>
 size_t smem_bytes() {
-  return (size_t)STAGES * (NT == 3 ? 2u : 1u) * (A_TILE + B_TILE) + 1024 + 128;
+  return (size_t)STAGES * stage_bytes<NT, STAGES, CONV>() + 1024 + 128;
 }
 
 unsigned grid_for(long long n) {
@@ -402,12 +446,17 @@ unsigned grid_for(long long n) {
 
 void tc2_set_stall(bool on) { g_tc2_stall.store(on ? 1 : 0); }
 
+bool tc2_conv_ok(int K, int lda_fp32, const void* a_fp32) {
+  return a_fp32 != nullptr && (lda_fp32 % 2) == 0 && lda_fp32 >= K && ((uintptr_t)a_fp32 % 16) == 0;
+}
+
 int tc2_k2p(int K) { return ((2 * K + 3) / 4) * 4; }
 int tc2_np(int N) { return ((N + BNC - 1) / BNC) * BNC; }
 
-template <int NT, int S>
+template <int NT, int S, bool CONV = false>
 static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(tc2_kernel<NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<NT, S>());
+  return cudaFuncSetAttribute(tc2_kernel<NT, S, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<NT, S, CONV>());
 }
 
 cudaError_t tc2_prepare() {
@@ -415,6 +464,7 @@ cudaError_t tc2_prepare() {
   if (e == cudaSuccess) e = set_smem<3, 2>();
   if (e == cudaSuccess) e = set_smem<1, 4>();
   if (e == cudaSuccess) e = set_smem<1, 2>();
+  if (e == cudaSuccess) e = set_smem<3, 3, true>();
   return e;
 }
 
@@ -447,7 +497,7 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
                      int nbatch, long long c_stride, int a_per_item, float2* const* c_tab, int c_div,
-                     int b_per_item) {
+                     int b_per_item, const float2* a_fp32, int lda_fp32) {
   if (M <= 0 || N <= 0 || nbatch < 1) return cudaSuccess;
   const int K2 = 2 * K, K2p = tc2_k2p(K), Np = tc2_np(N);
   const int total = (K2 + BK - 1) / BK;
@@ -461,8 +511,16 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   const float* bl = nterms == 3 ? Blo : Bhi;
   const int kcols = K2 > 0 ? K2 : 1;
   const int arows = a_per_item && nbatch > 1 ? M * nbatch : M;
-  if (!encode_2d(&mAh, Ahi, kcols, arows, K2p, BM) || !encode_2d(&mAl, al, kcols, arows, K2p, BM) ||
-      !encode_2d(&mBh, Bhi, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC) ||
+  // A from FP32 complex rows, split in shared memory: three passes, rows 16-byte aligned
+  const bool conv = a_fp32 != nullptr && nterms == 3 && (lda_fp32 % 2) == 0 && lda_fp32 >= K &&
+                    ((uintptr_t)a_fp32 % 16) == 0;
+  if (conv) {
+    if (!encode_2d(&mAh, reinterpret_cast<const float*>(a_fp32), kcols, arows, 2 * lda_fp32, BM)) return cudaErrorInvalidValue;
+    mAl = mAh;
+  } else if (!encode_2d(&mAh, Ahi, kcols, arows, K2p, BM) || !encode_2d(&mAl, al, kcols, arows, K2p, BM)) {
+    return cudaErrorInvalidValue;
+  }
+  if (!encode_2d(&mBh, Bhi, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC) ||
       !encode_2d(&mBl, bl, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC))
     return cudaErrorInvalidValue;
   Args g{M, N, K2, kpb, C, ldc, alpha, beta, diag_val, diag_stride, diag_limit, ws, err,
@@ -476,12 +534,14 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   // short K loops (<= 8 steps per CTA) keep 2 stages: half the shared memory, 2 CTAs per SM, so
   // one CTA's epilogue overlaps another's loads; long loops keep 4 stages in flight
   const bool deep = kpb > 8;
-  if (nterms == 1) {
-    if (deep) tc2_kernel<1, 4><<<grid, 128, smem_bytes<1, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
-    else tc2_kernel<1, 2><<<grid, 128, smem_bytes<1, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
+  if (conv) {
+    tc2_kernel<3, 3, true><<<grid, 128, smem_bytes<3, 3, true>(), st>>>(mAh, mAl, mBh, mBl, g);
+  } else if (nterms == 1) {
+    if (deep) tc2_kernel<1, 4, false><<<grid, 128, smem_bytes<1, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
+    else tc2_kernel<1, 2, false><<<grid, 128, smem_bytes<1, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
   } else {
-    if (deep) tc2_kernel<3, 4><<<grid, 128, smem_bytes<3, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
-    else tc2_kernel<3, 2><<<grid, 128, smem_bytes<3, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
+    if (deep) tc2_kernel<3, 4, false><<<grid, 128, smem_bytes<3, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
+    else tc2_kernel<3, 2, false><<<grid, 128, smem_bytes<3, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
   }
   ++g_launches;
   cudaError_t e = cudaGetLastError();

@@ -72,6 +72,7 @@ struct pisco_plan_s {
   // tensor-core routes (PISCO_FLAG_TC_*): lags of Lambda-Lambda only (compressed CSR), the
   // lag-to-pixel exponentials E [npix_red][nlag] and the folded lag table KT [nlag][Q*Q]
   bool tc_g = false, tc_eig = false;
+  bool a_conv = false;  // A X on the tensor cores reads A32 and splits it in shared memory
   bool masked = false;                 // PISCO_FLAG_MASKED_GRAM
   bool block_pi = false;               // PISCO_FLAG_BLOCK_PI
   bool gram_df = false;                // PISCO_FLAG_GRAM_DF: double-float DFT tables below
@@ -95,6 +96,8 @@ struct pisco_plan_s {
   void* lags_df = nullptr;
   double2* A64 = nullptr;  // FP64 Gram built from the double-float one on request (debug accessor)
   bool g_sep = false;      // 2D G(x) from KT by separable DFT passes instead of the dense lag GEMM
+  bool g_box = false;      // 3D G(x) from KT spread onto the lag box, then separable DFT passes
+  int* d_box_lag = nullptr;  // lag box entry -> compressed lag index (-1: not a lag)
   int *d_sep_rows = nullptr, *d_sep_b2 = nullptr;
   float *IAh = nullptr, *IAl = nullptr, *IBh = nullptr, *IBl = nullptr;
   float2* interpA = nullptr;  // the last axis's interpolation matrix (split into IAh/IAl)
@@ -678,10 +681,11 @@ cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y, long long s
     const int xi = sX != 0 ? items : 1;
     cudaError_t e = tc2_split_b(X, m, 0, n, m, pl->Xh, pl->tc_terms == 3 ? pl->Xl : nullptr, pl->st, xi, sX);
     if (e != cudaSuccess) return e;
-    // sX == 0: every item multiplies the same block (B' of item 0 for all)
+    // sX == 0: every item multiplies the same block (B' of item 0 for all); a_conv: A read as
+    // FP32 and split in shared memory
     return tc2_gemm(pl->tc_terms, n, m, n, pl->Ah, pl->Al, pl->Xh, pl->Xl, one, zero, Y, m, 0.f, 0, 0,
                     pl->tc_splits_ax, pl->tc_ws, &pl->dstatus->flags, pl->st, items, snm, 1, nullptr, 1,
-                    sX != 0 ? 1 : 0);
+                    sX != 0 ? 1 : 0, pl->a_conv ? pl->A32 : nullptr, n);
   }
   return cgemm<float>('N', 'N', n, m, n, one, pl->A32, n, X, m, zero, Y, m, pl->ws32, pl->ws32_elems * pl->items,
                       pl->tiles, pl->st, pl->gemm_splits, pl->gemm_tile, items, IS(pl, pl->A32), sX, snm);
@@ -708,7 +712,7 @@ pisco_status run_eig(pisco_plan_s* pl) {
   const long long snm = IS(pl, pl->X), smm = IS(pl, pl->Gm), svj = IS(pl, pl->Vj);
   pisco_status s;
   OP("eig_misc", eig_random_block(pl->Y, n, m, pl->prm.seed, st));
-  if (pl->tc_eig)  // the Gram's TF32 head/tail split, shared by every block product of the solve
+  if (pl->tc_eig && !pl->a_conv)  // the Gram's TF32 head/tail split, shared by every product of the solve
     OP("eig_gemm_AX", tc2_split_a(pl->A32, n, nullptr, n, n, pl->Ah, pl->tc_terms == 3 ? pl->Al : nullptr, st, items,
                                   IS(pl, pl->A32)));
   // X0 = orth(random block): well conditioned (kappa ~ (1 + sqrt(m/n)) / (1 - sqrt(m/n)))
@@ -768,6 +772,19 @@ pisco_status run_gfield(pisco_plan_s* pl) {
     if (pl->g_sep) {
       OP("g_field_sep", gassembly_field_sep2(pl->KT, Q, pl->nlag, pl->d_sep_rows, pl->d_sep_b2, pl->gdft[1], Nr[1], B[1],
                                              pl->gdft[2], B[2], Nr[2], (float)pl->L, pl->G, st, items, skt, sg));
+      return PISCO_OK;
+    }
+    if (pl->g_box) {
+      // lag box, then x, y, z passes (the last one pixel-major per item), then |Lambda| I - G
+      const long long QI = QQ * items;
+      OP("g_field_sep", gassembly_scatter_box(pl->KT, pl->d_box_lag, (int)QQ, pl->nbox, pl->K, st, items, skt,
+                                              IS(pl, pl->K)));
+      OP("g_field_sep", apply_axis_c(pl->K, pl->gdftT, pl->T1, AxisView{QI, (long long)B[0] * B[1], B[2], Nr[2], 1, 0, 1}, st));
+      OP("g_field_sep", apply_axis_c(pl->T1, pl->gdft[1], pl->T2, AxisView{QI, B[0], B[1], Nr[1], Nr[2]}, st));
+      AxisView vz{QI, 1, B[0], Nr[0], (long long)Nr[1] * Nr[2], 1};
+      vz.pm_group = (int)QQ;
+      OP("g_field_sep", apply_axis_c(pl->T2, pl->gdft[0], pl->G, vz, st));
+      OP("g_field_sep", gassembly_add_identity(pl->G, Q, pl->npix_red * items, (float)pl->L, st));
       return PISCO_OK;
     }
     OP("g_field_tc", tc2_split_b(pl->KT, (int)QQ, 0, pl->nlag, (int)QQ, pl->KTh, tt ? pl->KTl : nullptr, st, items, skt));
@@ -1015,6 +1032,7 @@ static pisco_status plan_create(const pisco_params* p, cudaStream_t cuda_stream,
   pl->tc_g = (p->flags & PISCO_FLAG_TC_GFIELD) != 0;
   pl->tc_eig = (p->flags & PISCO_FLAG_TC_EIG) != 0;
   pl->tc_terms = (p->flags & PISCO_FLAG_TC_1PASS) ? 1 : 3;
+  pl->a_conv = pl->tc_eig && pl->tc_terms == 3 && (pl->n % 2) == 0;
   if ((pl->tc_g || pl->tc_eig) && tc2_prepare() != cudaSuccess) {
     cudaGetLastError();
     delete pl;
@@ -1118,6 +1136,14 @@ static pisco_status plan_create(const pisco_params* p, cudaStream_t cuda_stream,
            dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) && dalloc(pl, &pl->UAh, (size_t)n * k2m2) &&
            dalloc(pl, &pl->UAl, lo_n * n * k2m2) && dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m2) &&
            dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m2);
+    } else if (ok && pl->tc_g && pl->D == 3 && (p->flags & PISCO_FLAG_G_DENSE) == 0) {
+      // 3D: the lag sums as three separable DFT passes over the 13^3 lag box (CUDA cores)
+      pl->g_box = true;
+      std::vector<int> box_lag(pl->nbox, -1);
+      for (int l = 0; l < pl->nlag; ++l) box_lag[pl->lag_ids[l]] = l;
+      ok = upload(pl, &pl->d_box_lag, box_lag) && dalloc(pl, &pl->KT, (size_t)pl->nlag * QQ) &&
+           dalloc(pl, &pl->UAh, (size_t)n * k2m) && dalloc(pl, &pl->UAl, lo_n * n * k2m) &&
+           dalloc(pl, &pl->UBh, (size_t)2 * tc2_np(n) * k2m) && dalloc(pl, &pl->UBl, lo_n * 2 * tc2_np(n) * k2m);
     } else if (ok && pl->tc_g) {
       const size_t k2l = (size_t)tc2_k2p(pl->nlag);
       ok = upload(pl, &pl->E, lag_pixel_matrix(Nr, B, pl->tau, pl->lag_ids)) &&
