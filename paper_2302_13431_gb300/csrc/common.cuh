@@ -146,6 +146,14 @@ struct EigItems {
   long long scale = 0;    // Gram scale
 };
 cudaError_t eig_random_block(float2* X, int n, int m, unsigned long long seed, cudaStream_t st);
+// thin block products for m <= 64 (FP32, CUDA cores): C = Y^H Z (m x m over n rows; ws holds
+// items * eig_thin_chunks(n) * m * m partials, tickets one zeroed int per item) and X = Y W
+int eig_thin_chunks(int n);
+cudaError_t eig_thin_gram(const float2* Y, long long sY, const float2* Z, long long sZ, int n, int m, float2* C,
+                          long long sC, float2* ws, int* tickets, int items, cudaStream_t st);
+cudaError_t eig_thin_apply(const float2* Y, long long sY, const float2* W, long long sW, int n, int m, float2* X,
+                           long long sX, int items, cudaStream_t st);
+
 cudaError_t eig_chol(const float2* Gm, int m, const float* dscale, float shift_rel,
                      const float* acc_in, float2* L, float* dout, float* diagR, DevStatus* status,
                      cudaStream_t st, const EigItems& it = EigItems{});
@@ -155,7 +163,8 @@ cudaError_t eig_chol_inv_blocked(const float2* Gm, int m, const float* dscale, f
                                  const float* acc_in, float2* Rinv, float* diagR, DevStatus* status,
                                  cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
-                       float skip_rel, DevStatus* status, cudaStream_t st, const EigItems& it = EigItems{});
+                       float skip_rel, float stop_rel, DevStatus* status, cudaStream_t st,
+                       const EigItems& it = EigItems{});
 cudaError_t eig_band_matvec(const double2* A, const double2* Xb, int n, int nb, const int* band_idx,
                             double2* Zb, cudaStream_t st, const EigItems& it = EigItems{});
 cudaError_t eig_select_band(const float* mu, int m, double thr2, int nb_max, int* band_idx,
@@ -263,8 +272,9 @@ void tc2_set_stall(bool on);
 // split arrays one after another).
 cudaError_t tc2_split_a(const float2* A, int lda, const float* kscale, int M, int K, float* hi, float* lo,
                         cudaStream_t st, int items = 1, long long a_stride = 0, long long w_stride = 0);
+// cg > 0 (opB 0): column c of B is column c % cg of block c / cg, blocks cgs elements apart
 cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st,
-                        int nbatch = 1, long long b_stride = 0);
+                        int nbatch = 1, long long b_stride = 0, int cg = 0, long long cgs = 0);
 cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, float* lo, cudaStream_t st,
                          int items = 1, long long y_stride = 0);
 // nbatch > 1: gridDim.z runs nbatch products C_b = A_b B_b (B' items of 2 Np rows one after
@@ -274,7 +284,11 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
                      int nbatch = 1, long long c_stride = 0, int a_per_item = 0, float2* const* c_tab = nullptr,
-                     int c_div = 1, int b_per_item = 1, const float2* a_fp32 = nullptr, int lda_fp32 = 0);
+                     int c_div = 1, int b_per_item = 1, const float2* a_fp32 = nullptr, int lda_fp32 = 0,
+                     int rg = 0, int rg_rows = 0, long long rg_plane = 0, int rg_norm = 0);
+// rg > 0 (nbatch 1): the rows of C are (item, y, q) triples, rg_rows = rows per item, rg = Q;
+// row (item, y, q) goes to (c_tab[item] or C + item c_stride) + q rg_plane + y ldc, and with
+// rg_norm (rg dividing 128) each column of a q-group is divided by its 2-norm
 // a_fp32: A given as FP32 complex rows (leading dimension lda_fp32, even; items lda_fp32 * M apart
 // with a_per_item) and split into head and tail in shared memory (three passes only); Ahi/Alo unused
 bool tc2_conv_ok(int K, int lda_fp32, const void* a_fp32);

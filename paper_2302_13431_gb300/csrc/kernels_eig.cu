@@ -552,7 +552,10 @@ cudaError_t eig_trsm(const float2* Y, const float2* L, const float* ds, int n, i
 // A rotation is skipped when |b| <= 3e-7 sqrt(|B_pp B_qq|) + 3e-9 max|B_ii| (relative
 // accuracy for the small Ritz values); the solve stops after a sweep whose rotations all had
 // |b| <= 2e-6 sqrt(|B_pp B_qq|) + 3e-9 max|B_ii| (rotations at that level only stir FP32 rounding
-// noise, which otherwise keeps a converged matrix rotating until the sweep limit).
+// noise, which otherwise keeps a converged matrix rotating until the sweep limit) or joined two
+// Ritz values both below stop_rel max|B_ii| (below every value the threshold split looks at: the
+// unconverged bottom of the block otherwise couples back and forth with its skipped neighbours
+// and converges only linearly).
 // The two-sided update of a round is applied per 2x2 block (pair i rows, pair j columns):
 // B_ij <- J_i^H B_ij J_j, one shared-memory pass; V <- V J likewise.  B and, when it fits
 // (m <= 96), V live in shared memory.  Output: mu (descending) and V with B V = V diag(mu).
@@ -562,7 +565,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
                                                      float* __restrict__ mu,
                                                      float2* __restrict__ Vout,
                                                      float2* __restrict__ Vg, int max_sweeps,
-                                                     float skip_rel, DevStatus* status, EigItems it) {
+                                                     float skip_rel, float stop_rel, DevStatus* status,
+                                                     EigItems it) {
   extern __shared__ float2 sm[];
   Bin += blockIdx.z * it.mm;
   mu += blockIdx.z * it.vec;
@@ -602,6 +606,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
   // pairs whose diagonals both lie below skip_rel * max are left alone: such Ritz vectors are
   // far below the threshold split and mixing among them cannot change the signal subspace
   const float skip_below = skip_rel * s_bnorm;
+  const float stop_below = stop_rel * s_bnorm;
   const int tx = tid & 31, ty = tid >> 5, nty = nt >> 5;  // 32 x (nt/32) map
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -625,7 +630,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
           const float sn = t * c;
           ser = sn * bpq.x / mag; sei = sn * bpq.y / mag;
           on = 1;
-          if (mag > 2e-6f * rel + abs_tol) s_rot = 1;
+          if (mag > 2e-6f * rel + abs_tol && fmaxf(app, aqq) >= stop_below) s_rot = 1;
         }
         rc[4 * i] = c; rc[4 * i + 1] = ser; rc[4 * i + 2] = sei;
         act[i] = on;
@@ -698,8 +703,384 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const float2* __restrict__ 
   }
 }
 
+// The same cyclic Jacobi (ordering, rotation, skip and stop rules) for m <= 64, arranged for
+// latency: the round schedule and the upper-triangle block list are tabulated once; each round
+// updates only the 2x2 blocks (i <= j) and mirrors them (B stays exactly Hermitian); and the
+// rotations of round r+1 are computed by warp 0 while the other warps apply round r to V
+// (rotation parameters double-buffered), so a round costs two barriers and no serial phase.
+constexpr int kJs = 65;  // padded row stride of B in shared memory
+__global__ void __launch_bounds__(544) jacobi_small_kernel(const float2* __restrict__ Bin, int m,
+                                                           float* __restrict__ mu, float2* __restrict__ Vout,
+                                                           int max_sweeps, float skip_rel, float stop_rel,
+                                                           DevStatus* status, EigItems it) {
+  extern __shared__ float2 jsm[];
+  float2* Bs = jsm;               // [64][kJs]
+  float2* Vw = jsm + 64 * kJs;    // [64][64]
+  __shared__ unsigned char sched[63 * 32 * 2];  // (p, q) of every pair of every round
+  __shared__ unsigned char blk[528 * 2];        // (i, j), i <= j, of every block
+  __shared__ float rc[2][32][3];                // c, Re(s e), Im(s e) per pair, two rounds
+  __shared__ int act[2][32];
+  __shared__ int s_rot, s_stop, s_sweeps;
+  __shared__ float s_bnorm;
+  Bin += blockIdx.z * it.mm;
+  mu += blockIdx.z * it.vec;
+  Vout += blockIdx.z * it.vj;
+  if (status) status += blockIdx.z;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int half = m / 2, rounds = m - 1;
+  const int nblk = half * (half + 1) / 2;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e / m, j = e % m;
+    const float2 a = Bin[i * m + j], b = Bin[j * m + i];
+    Bs[i * kJs + j] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+    Vw[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  for (int e = tid; e < rounds * half; e += nt) {
+    const int r = e / half, i = e % half;
+    const int a = (i == 0) ? 0 : 1 + (i - 1 + r) % (m - 1);
+    const int b = 1 + (m - 2 - i + r) % (m - 1);
+    sched[2 * e] = (unsigned char)min(a, b);
+    sched[2 * e + 1] = (unsigned char)max(a, b);
+  }
+  for (int e = tid; e < nblk; e += nt) {
+    int i = 0, base = 0;
+    while (e >= base + (half - i)) { base += half - i; ++i; }
+    blk[2 * e] = (unsigned char)i;
+    blk[2 * e + 1] = (unsigned char)(i + (e - base));
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float bn = 0.f;
+    for (int i = lane; i < m; i += 32) bn = fmaxf(bn, fabsf(Bs[i * kJs + i].x));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+    if (lane == 0) { s_bnorm = bn; s_rot = 0; s_stop = 0; s_sweeps = 0; }
+  }
+  __syncthreads();
+  const float abs_tol = 3e-9f * s_bnorm;
+  const float noise = 1e-4f * s_bnorm;
+  const float skip_below = skip_rel * s_bnorm;
+  const float stop_below = stop_rel * s_bnorm;
+  // warp 0: rotations of global round g (round g % rounds of sweep g / rounds) into buffer g & 1
+  auto rotations = [&](int g) {
+    const int r = g % rounds, buf = g & 1;
+    if (lane < half) {
+      const int p = sched[2 * (r * half + lane)], q = sched[2 * (r * half + lane) + 1];
+      const float2 bpq = Bs[p * kJs + q];
+      // (approximate reciprocals and square roots: the rotation stays orthogonal to rounding,
+      // c = 1/sqrt(1+t^2) and |e| = 1, whatever the accuracy of t; the annihilated entry is
+      // set to zero below, as in the classical method)
+      const float m2 = bpq.x * bpq.x + bpq.y * bpq.y;
+      const float inv = rsqrtf(m2);
+      const float mag = m2 > 0.f ? m2 * inv : 0.f;
+      const float app = Bs[p * kJs + p].x, aqq = Bs[q * kJs + q].x;
+      float c = 1.f, ser = 0.f, sei = 0.f;
+      int on = 0, big = 0;
+      const bool both_low = fabsf(app) < skip_below && fabsf(aqq) < skip_below;
+      const float pr = fmaxf(fabsf(app), noise) * fmaxf(fabsf(aqq), noise);
+      const float rel = pr * rsqrtf(pr);
+      if (!both_low && mag > 3e-7f * rel + abs_tol) {
+        const float z = (app - aqq) * (0.5f * inv);
+        const float h = fmaf(z, z, 1.f);
+        const float t = copysignf(__fdividef(1.f, fabsf(z) + h * rsqrtf(h)), z);
+        c = rsqrtf(fmaf(t, t, 1.f));
+        const float sn = t * c;
+        ser = sn * bpq.x * inv;
+        sei = sn * bpq.y * inv;
+        on = 1;
+        big = mag > 2e-6f * rel + abs_tol && fmaxf(app, aqq) >= stop_below;
+      }
+      rc[buf][lane][0] = c;
+      rc[buf][lane][1] = ser;
+      rc[buf][lane][2] = sei;
+      act[buf][lane] = on;
+      if (__any_sync(__activemask(), big) && lane == 0) s_rot = 1;
+    }
+  };
+  const int gmax = max_sweeps * rounds;
+  if (warp == 0 && gmax > 0) rotations(0);
+  __syncthreads();
+  int g = 0;
+  for (; g < gmax; ++g) {
+    const int buf = g & 1, r = g % rounds;
+    const unsigned char* sp = sched + 2 * r * half;
+    // (1) B <- J^H B J on the blocks i <= j, mirrored
+    for (int e = tid; e < nblk; e += nt) {
+      const int i = blk[2 * e], j = blk[2 * e + 1];
+      const int ai = act[buf][i], aj = act[buf][j];
+      if (!ai && !aj) continue;
+      const int pi = sp[2 * i], qi = sp[2 * i + 1], pj = sp[2 * j], qj = sp[2 * j + 1];
+      float2 x00 = Bs[pi * kJs + pj], x01 = Bs[pi * kJs + qj], x10 = Bs[qi * kJs + pj], x11 = Bs[qi * kJs + qj];
+      if (ai) {  // rows: r0 = c x0 + se x1, r1 = -conj(se) x0 + c x1
+        const float c = rc[buf][i][0];
+        const float2 se = make_float2(rc[buf][i][1], rc[buf][i][2]);
+        const float2 y00 = make_float2(c * x00.x + se.x * x10.x - se.y * x10.y, c * x00.y + se.x * x10.y + se.y * x10.x);
+        const float2 y01 = make_float2(c * x01.x + se.x * x11.x - se.y * x11.y, c * x01.y + se.x * x11.y + se.y * x11.x);
+        const float2 y10 = make_float2(-(se.x * x00.x + se.y * x00.y) + c * x10.x, -(se.x * x00.y - se.y * x00.x) + c * x10.y);
+        const float2 y11 = make_float2(-(se.x * x01.x + se.y * x01.y) + c * x11.x, -(se.x * x01.y - se.y * x01.x) + c * x11.y);
+        x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+      }
+      if (aj) {  // columns: k0 = c x0 + conj(se) x1, k1 = -se x0 + c x1
+        const float c = rc[buf][j][0];
+        const float2 se = make_float2(rc[buf][j][1], rc[buf][j][2]);
+        const float2 y00 = make_float2(c * x00.x + se.x * x01.x + se.y * x01.y, c * x00.y + se.x * x01.y - se.y * x01.x);
+        const float2 y01 = make_float2(-(se.x * x00.x - se.y * x00.y) + c * x01.x, -(se.x * x00.y + se.y * x00.x) + c * x01.y);
+        const float2 y10 = make_float2(c * x10.x + se.x * x11.x + se.y * x11.y, c * x10.y + se.x * x11.y - se.y * x11.x);
+        const float2 y11 = make_float2(-(se.x * x10.x - se.y * x10.y) + c * x11.x, -(se.x * x10.y + se.y * x10.x) + c * x11.y);
+        x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+      }
+      if (i == j) {  // the pair's own block: real diagonal, the rotated entry annihilated
+        x00.y = 0.f;
+        x11.y = 0.f;
+        if (ai) x01 = make_float2(0.f, 0.f);
+        x10 = make_float2(x01.x, -x01.y);
+      }
+      Bs[pi * kJs + pj] = x00; Bs[pi * kJs + qj] = x01; Bs[qi * kJs + pj] = x10; Bs[qi * kJs + qj] = x11;
+      if (i != j) {
+        Bs[pj * kJs + pi] = make_float2(x00.x, -x00.y);
+        Bs[qj * kJs + pi] = make_float2(x01.x, -x01.y);
+        Bs[pj * kJs + qi] = make_float2(x10.x, -x10.y);
+        Bs[qj * kJs + qi] = make_float2(x11.x, -x11.y);
+      }
+    }
+    __syncthreads();
+    // (2) warp 0: the next round's rotations (after a sweep, the stop test); warps 1..: V <- V J
+    if (warp == 0) {
+      const int gn = g + 1;
+      bool stop = gn >= gmax;
+      if (stop && lane == 0) s_sweeps = max_sweeps;
+      if (!stop && gn % rounds == 0) {  // a sweep ended: stop if none of its rotations was large
+        __syncwarp();
+        const int any = s_rot;
+        __syncwarp();
+        if (lane == 0) { s_rot = 0; s_sweeps = gn / rounds; }
+        __syncwarp();
+        stop = !any;
+      }
+      if (stop) {
+        if (lane == 0) s_stop = 1;
+      } else {
+        rotations(gn);
+      }
+    } else {
+      for (int e = tid - 32; e < m * half; e += nt - 32) {
+        const int k = e / half, j = e % half;
+        if (!act[buf][j]) continue;
+        const int pj = sp[2 * j], qj = sp[2 * j + 1];
+        const float c = rc[buf][j][0];
+        const float2 se = make_float2(rc[buf][j][1], rc[buf][j][2]);
+        const float2 xp = Vw[k * m + pj], xq = Vw[k * m + qj];
+        Vw[k * m + pj] = make_float2(c * xp.x + se.x * xq.x + se.y * xq.y, c * xp.y + se.x * xq.y - se.y * xq.x);
+        Vw[k * m + qj] = make_float2(-(se.x * xp.x - se.y * xp.y) + c * xq.x, -(se.x * xp.y + se.y * xp.x) + c * xq.y);
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+  if (tid == 0 && status) status->jacobi_sweeps = (g >= gmax) ? max_sweeps : s_sweeps;
+  __syncthreads();
+  // sort eigenvalues descending (rank by count, ties broken by index) and permute V
+  __shared__ int rk[64];
+  for (int i = tid; i < m; i += nt) {
+    const float v = Bs[i * kJs + i].x;
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const float w = Bs[j * kJs + j].x;
+      rank += (w > v) || (w == v && j < i);
+    }
+    rk[i] = rank;
+    mu[rank] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {
+    const int k = e / m, i = e % m;
+    Vout[k * m + rk[i]] = Vw[k * m + i];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Thin block products of the orthogonal iteration for m <= 64 columns, FP32 on the CUDA cores.
+// thin_gram: C = Y^H Z (m x m) over n rows.  CTA (split, item) runs over its share of the rows in
+// chunks of kThinRows staged in shared memory; thread (ti, tj) of a 16 x 16 grid accumulates the
+// 4 x 4 block of C at rows 4 ti.., columns 4 tj..; the split's partial goes to ws[item][split],
+// and the last CTA of the item to finish (ticket counter, reset by that CTA) sums the partials
+// in split order into C.
+// thin_apply: X = Y W (n x m by m x m), CTA (chunk, item), the same 4 x 4 register blocks.
+// ---------------------------------------------------------------------------------------
+constexpr int kThinRows = 64;
+constexpr int kThinLd = 64 + 1;  // padded row (float2) of the staged operands
+constexpr int kThinMaxSplits = 16;  // row splits of a thin Gram (CTAs per item)
+
+__global__ void __launch_bounds__(256) thin_gram_kernel(const float2* __restrict__ Y, long long sY,
+                                                        const float2* __restrict__ Z, long long sZ, int n, int m,
+                                                        float2* __restrict__ C, long long sC,
+                                                        float2* __restrict__ ws, int* __restrict__ tickets) {
+  extern __shared__ float2 tsm[];
+  float2* Ys = tsm;                       // [kThinRows][kThinLd]
+  float2* Zs = tsm + kThinRows * kThinLd;
+  __shared__ int s_last;
+  const int item = blockIdx.y, split = blockIdx.x, nsp = gridDim.x;
+  Y += item * sY;
+  Z += item * sZ;
+  C += item * sC;
+  // this split's rows: whole chunks of kThinRows, the splits as even as the chunks allow
+  const int nch = (n + kThinRows - 1) / kThinRows;
+  const int c0 = (int)((long long)nch * split / nsp), c1 = (int)((long long)nch * (split + 1) / nsp);
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const bool act = 4 * ti < m && 4 * tj < m;
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+  for (int ch = c0; ch < c1; ++ch) {
+    const int r0 = ch * kThinRows;
+    const int rows = min(kThinRows, n - r0);
+    __syncthreads();
+    for (int e = tid; e < rows * m; e += 256) {
+      const int r = e / m, c = e % m;
+      Ys[r * kThinLd + c] = Y[(long long)(r0 + r) * m + c];
+      Zs[r * kThinLd + c] = Z[(long long)(r0 + r) * m + c];
+    }
+    __syncthreads();
+    if (act) {
+      for (int r = 0; r < rows; ++r) {
+        float2 y[4], z[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          y[a] = Ys[r * kThinLd + min(4 * ti + a, m - 1)];
+          z[a] = Zs[r * kThinLd + min(4 * tj + a, m - 1)];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {  // conj(y) z
+            acc[a][b].x = fmaf(y[a].x, z[b].x, fmaf(y[a].y, z[b].y, acc[a][b].x));
+            acc[a][b].y = fmaf(y[a].x, z[b].y, fmaf(-y[a].y, z[b].x, acc[a][b].y));
+          }
+      }
+    }
+  }
+  const long long mm = (long long)m * m;
+  float2* part = ws + ((long long)item * nsp + split) * mm;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * ti + a, j = 4 * tj + b;
+      if (i < m && j < m) part[i * m + j] = acc[a][b];
+    }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const int t = atomicAdd(&tickets[item], 1);
+    s_last = (t == nsp - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last split of the item: partials summed in split order (all loads of an entry issued
+  // together, up to kThinMaxSplits of them)
+  const float2* base = ws + (long long)item * nsp * mm;
+  for (long long e = tid; e < mm; e += 256) {
+    float2 w[kThinMaxSplits];
+#pragma unroll
+    for (int k = 0; k < kThinMaxSplits; ++k) w[k] = k < nsp ? __ldcg(base + k * mm + e) : make_float2(0.f, 0.f);
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kThinMaxSplits; ++k) {
+      v.x += w[k].x;
+      v.y += w[k].y;
+    }
+    C[e] = v;
+  }
+  if (tid == 0) tickets[item] = 0;
+}
+
+__global__ void __launch_bounds__(256) thin_apply_kernel(const float2* __restrict__ Y, long long sY,
+                                                         const float2* __restrict__ W, long long sW, int n, int m,
+                                                         float2* __restrict__ X, long long sX) {
+  extern __shared__ float2 tsm[];
+  float2* Ys = tsm;                       // [kThinRows][kThinLd]
+  float2* Ws = tsm + kThinRows * kThinLd; // [64][kThinLd]
+  const int item = blockIdx.y;
+  Y += item * sY;
+  W += item * sW;
+  X += item * sX;
+  const int r0 = blockIdx.x * kThinRows;
+  const int rows = min(kThinRows, n - r0);
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  for (int e = tid; e < rows * m; e += 256) {
+    const int r = e / m, c = e % m;
+    Ys[r * kThinLd + c] = Y[(long long)(r0 + r) * m + c];
+  }
+  for (int e = tid; e < m * m; e += 256) Ws[(e / m) * kThinLd + e % m] = W[e];
+  __syncthreads();
+  if (4 * ti >= rows || 4 * tj >= m) return;
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+  for (int k = 0; k < m; ++k) {
+    float2 y[4], w[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      y[a] = Ys[min(4 * ti + a, rows - 1) * kThinLd + k];
+      w[a] = Ws[k * kThinLd + min(4 * tj + a, m - 1)];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {  // y w
+        acc[a][b].x = fmaf(y[a].x, w[b].x, fmaf(-y[a].y, w[b].y, acc[a][b].x));
+        acc[a][b].y = fmaf(y[a].x, w[b].y, fmaf(y[a].y, w[b].x, acc[a][b].y));
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * ti + a, j = 4 * tj + b;
+      if (i < rows && j < m) X[(long long)(r0 + i) * m + j] = acc[a][b];
+    }
+}
+
+int eig_thin_chunks(int n) { return (n + kThinRows - 1) / kThinRows; }
+// row splits of a thin Gram: one chunk of rows each, at most kThinMaxSplits (more CTAs per item:
+// each CTA is latency-bound on its own)
+static int thin_splits(int n) { return std::max(1, std::min(kThinMaxSplits, eig_thin_chunks(n))); }
+
+constexpr size_t kThinSmem = (size_t)2 * 64 * kThinLd * sizeof(float2);
+static bool thin_attrs() {
+  static const bool ok =
+      cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmem) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(thin_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmem) ==
+          cudaSuccess;
+  return ok;
+}
+
+cudaError_t eig_thin_gram(const float2* Y, long long sY, const float2* Z, long long sZ, int n, int m, float2* C,
+                          long long sC, float2* ws, int* tickets, int items, cudaStream_t st) {
+  if (m > 64 || m < 1 || n < 1) return cudaErrorInvalidValue;
+  if (!thin_attrs()) return cudaErrorInvalidValue;
+  thin_gram_kernel<<<dim3(thin_splits(n), items), 256, kThinSmem, st>>>(Y, sY, Z, sZ, n, m, C, sC, ws, tickets);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t eig_thin_apply(const float2* Y, long long sY, const float2* W, long long sW, int n, int m, float2* X,
+                           long long sX, int items, cudaStream_t st) {
+  if (m > 64 || m < 1 || n < 1) return cudaErrorInvalidValue;
+  if (!thin_attrs()) return cudaErrorInvalidValue;
+  thin_apply_kernel<<<dim3(eig_thin_chunks(n), items), 256, kThinSmem, st>>>(Y, sY, W, sW, n, m, X, sX);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_sweeps,
-                       float skip_rel, DevStatus* status, cudaStream_t st, const EigItems& it) {
+                       float skip_rel, float stop_rel, DevStatus* status, cudaStream_t st, const EigItems& it) {
   // V must have room for 2*m*m entries: [0, m*m) output, [m*m, 2*m*m) scratch
   const bool vsmem = m <= 96;
   const size_t smem = (size_t)(vsmem ? 2 : 1) * m * m * sizeof(float2) + 4 * (m / 2) * sizeof(float) +
@@ -710,13 +1091,24 @@ cudaError_t eig_jacobi(const float2* B, int m, float* mu, float2* V, int max_swe
     cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  if (m <= 64 && m % 2 == 0) {
+    constexpr size_t kSmallSmem = (size_t)(64 * kJs + 64 * 64) * sizeof(float2);
+    static bool small_attr = false;
+    if (!small_attr) {
+      cudaFuncSetAttribute(jacobi_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
+      small_attr = true;
+    }
+    jacobi_small_kernel<<<dim3(1, 1, it.n), 544, kSmallSmem, st>>>(B, m, mu, V, max_sweeps, skip_rel, stop_rel, status, it);
+    ++g_launches;
+    return cudaGetLastError();
+  }
   const int threads = 512;
   if (vsmem)
     jacobi_kernel<true><<<dim3(1, 1, it.n), threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps,
-                                                                 skip_rel, status, it);
+                                                                 skip_rel, stop_rel, status, it);
   else
     jacobi_kernel<false><<<dim3(1, 1, it.n), threads, smem, st>>>(B, m, mu, V, V + (size_t)m * m, max_sweeps,
-                                                                  skip_rel, status, it);
+                                                                  skip_rel, stop_rel, status, it);
   ++g_launches;
   return cudaGetLastError();
 }

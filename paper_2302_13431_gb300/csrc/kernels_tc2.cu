@@ -36,14 +36,17 @@ namespace pisco {
 namespace {
 
 constexpr int BM = 128;           // rows of C per CTA (TMEM lanes)
-constexpr int BNC = 32;           // complex columns of C per CTA (64 accumulator columns)
+constexpr int BNC = 32;           // complex columns of one B' tile (64 real rows)
 constexpr int BK = 32;            // real K per stage (128 bytes of FP32: one swizzle row)
 constexpr uint32_t A_TILE = BM * BK * 4;        // 16384
-constexpr uint32_t B_TILE = 2 * BNC * BK * 4;   // 8192
-constexpr uint32_t TMEM_COLS = 64;
+constexpr uint32_t B_TILE = 2 * BNC * BK * 4;   // 8192 per B' tile; a CTA covers WT tiles
 constexpr long long kWait = 4000000000ll;       // ~2 s at 2 GHz
 constexpr long long kWaitStalled = 20000000ll;  // ~10 ms: the wait limit while loads are withheld
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = 64 * WT, M = 128
+template <int WT>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (((64u * WT) >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -83,10 +86,11 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+template <int WT>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc<WT>()), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void commit(uint32_t b) {
@@ -126,25 +130,43 @@ struct Args {
   int c_div;
   int splits;     // K splits (gridDim.z = items * splits); partials of item b, split z at
                   // ws + (b * splits + z) * M * N
+  // row groups (rg > 0, one product over all items' rows): row r is (item, y, q) with
+  // item = r / rg_rows, y = (r % rg_rows) / rg, q = r % rg, written to
+  // (c_tab[item] or C + item * c_stride) + q * rg_plane + y * ldc; rg_norm: every column of a
+  // group of rg rows (one pixel's coils) divided by its 2-norm
+  int rg, rg_rows, rg_norm;
+  long long rg_plane;
   long long wait_limit;  // clock cycles a bounded mbarrier wait may take
   int no_loads;   // test hook: the producer issues no loads, so the waits on them expire
 };
 
-template <int NT, int STAGES, bool CONV>
+template <int NT, bool CONV, int WT>
 __host__ __device__ constexpr uint32_t stage_bytes() {
-  // split operands: [A head][A tail][B head][B tail]; CONV: [A fp32][A head][A tail][B head][B tail]
-  return CONV ? 3u * A_TILE + 2u * B_TILE : (NT == 3 ? 2u : 1u) * (A_TILE + B_TILE);
+  // split operands: [A head][A tail][B head][B tail]; CONV: [A fp32, then its tail][A head][B head][B tail]
+  return (NT == 3 || CONV ? 2u : 1u) * (A_TILE + WT * B_TILE);
 }
 
-template <int NT, int STAGES, bool CONV>
-__global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUtensorMap tAh,
+// One CTA: a 128 x (32 WT) complex tile of C, accumulated in 64 WT TMEM columns (columns
+// 64h .. 64h+31 hold Re, 64h+32 .. 64h+63 Im of the complex columns 32h .. 32h+31).
+template <int NT, int STAGES, bool CONV, int WT>
+__global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_constant__ CUtensorMap tAh,
                                                      const __grid_constant__ CUtensorMap tAl,
                                                      const __grid_constant__ CUtensorMap tBh,
                                                      const __grid_constant__ CUtensorMap tBl, Args g) {
   static_assert(!CONV || NT == 3, "the converting variant splits A into head and tail");
-  constexpr uint32_t STAGE = stage_bytes<NT, STAGES, CONV>();
-  constexpr uint32_t A_OFF = CONV ? A_TILE : 0u;            // A head within a stage
-  constexpr uint32_t B_OFF = CONV ? 3u * A_TILE : (NT == 3 ? 2u * A_TILE : A_TILE);
+  static_assert(STAGES * stage_bytes<NT, CONV, WT>() >= 128u * (BNC * WT + 1) * 8u, "epilogue tile exceeds the ring");
+  static_assert(!CONV || STAGES * stage_bytes<NT, CONV, WT>() >=
+                             128u * (BNC * WT + 1) * 8u + 128u * BNC * WT * 4u + 128u * 8u,
+                "row-group epilogue exceeds the ring");
+  constexpr uint32_t STAGE = stage_bytes<NT, CONV, WT>();
+  constexpr uint32_t A_HEAD = CONV ? A_TILE : 0u;            // A head / tail within a stage
+  constexpr uint32_t A_TAIL = CONV ? 0u : A_TILE;
+  constexpr uint32_t B_OFF = (NT == 3 || CONV) ? 2u * A_TILE : A_TILE;
+  constexpr uint32_t BT = WT * B_TILE;                      // B head (tail) bytes per stage
+  constexpr uint32_t TMEM_COLS = 64 * WT;
+  // warps: 0 producer, 1 MMA issuer, the rest (2-3, or 2-7 converting) converters; warps 0-3
+  // read the accumulator (TMEM lane quarter = warp), all of them share the epilogue
+  constexpr int NTHR = CONV ? 256 : 128, NWARP = NTHR / 32;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -155,7 +177,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[STAGES]), accum = su32(&bars[2 * STAGES]);
   const uint32_t conv0 = su32(&bars[2 * STAGES + 1]);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNC;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNC * WT;
   const int total = (g.K2 + BK - 1) / BK;
   const int zb = (int)blockIdx.z / g.splits;                // batch item
   const int kb0 = ((int)blockIdx.z % g.splits) * g.kpb;    // first K step of this split
@@ -175,7 +197,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     for (int s = 0; s < STAGES; ++s) {
       bar_init(full0 + 8 * s, 1);
       bar_init(empty0 + 8 * s, 1);
-      if (CONV) bar_init(conv0 + 8 * s, 64);  // the converter warps
+      if (CONV) bar_init(conv0 + 8 * s, NTHR - 64);  // the converter warps
     }
     bar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -196,7 +218,7 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
       const uint32_t fb = full0 + 8 * s;
       const int kx = (kb0 + i) * BK;
       if (CONV) {
-        bar_expect_tx(fb, A_TILE + 2 * B_TILE);
+        bar_expect_tx(fb, A_TILE + 2 * BT);
         tma_2d(st, &tAh, kx, arow0, fb);  // the FP32 tile
       } else {
         bar_expect_tx(fb, STAGE);
@@ -205,10 +227,10 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
       }
       const uint32_t sb = st + B_OFF;
       tma_2d(sb, &tBh, kx, brow0 + 2 * n0, fb);
-      if (NT == 3) tma_2d(sb + B_TILE, &tBl, kx, brow0 + 2 * n0, fb);
+      if (NT == 3) tma_2d(sb + BT, &tBl, kx, brow0 + 2 * n0, fb);
     }
   } else if (CONV && warp >= 2 && nk > 0) {
-    // converters: FP32 tile -> TF32 head and tail tiles of the same stage (same swizzled offsets)
+    // converters: FP32 tile -> TF32 head (own slot) and tail (in place), same swizzled offsets
     const int ct = tid - 64;
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES, c = i / STAGES;
@@ -216,10 +238,10 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
       if (!ok) break;
       unsigned char* sp = gbase + (size_t)s * STAGE;
       const float4* src = reinterpret_cast<const float4*>(sp);
-      float4* hd = reinterpret_cast<float4*>(sp + A_TILE);
-      float4* tl = reinterpret_cast<float4*>(sp + 2 * A_TILE);
+      float4* hd = reinterpret_cast<float4*>(sp + A_HEAD);
+      float4* tl = reinterpret_cast<float4*>(sp + A_TAIL);
 #pragma unroll 4
-      for (int e = ct; e < (int)(A_TILE / 16); e += 64) {
+      for (int e = ct; e < (int)(A_TILE / 16); e += NTHR - 64) {
         const float4 v = src[e];
         const float4 h = make_float4(head(v.x), head(v.y), head(v.z), head(v.w));
         hd[e] = h;
@@ -235,15 +257,15 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
       ok = bar_wait((CONV ? conv0 : full0) + 8 * s, (uint32_t)(c & 1), g.wait_limit);
       if (!ok) break;
       fence_after();
-      const uint32_t st = base + s * STAGE + A_OFF;
-      const uint32_t sb = base + s * STAGE + B_OFF;
+      const uint32_t st = base + s * STAGE;
+      const uint32_t sb = st + B_OFF;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const uint64_t ah = desc_sw128(st + 32 * j), bh = desc_sw128(sb + 32 * j);
-        mma(tmem, ah, bh, (i > 0 || j > 0) ? 1u : 0u);
+        const uint64_t ah = desc_sw128(st + A_HEAD + 32 * j), bh = desc_sw128(sb + 32 * j);
+        mma<WT>(tmem, ah, bh, (i > 0 || j > 0) ? 1u : 0u);
         if (NT == 3) {
-          mma(tmem, ah, desc_sw128(sb + B_TILE + 32 * j), 1u);
-          mma(tmem, desc_sw128(st + A_TILE + 32 * j), bh, 1u);
+          mma<WT>(tmem, ah, desc_sw128(sb + BT + 32 * j), 1u);
+          mma<WT>(tmem, desc_sw128(st + A_TAIL + 32 * j), bh, 1u);
         }
       }
       commit(empty0 + 8 * s);
@@ -256,21 +278,25 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
   }
   if (!ok && g.err) atomicOr(g.err, 16);
   fence_after();
-  // accumulator -> registers -> shared tile [128][33] (the stage ring is free: all MMAs done)
+  // accumulator -> registers -> shared tile [128][TS] (the stage ring is free: all MMAs done)
+  constexpr int TS = BNC * WT + 1;
   float2* tile = reinterpret_cast<float2*>(gbase);
-  {
+  if (warp < 4) {
     const int row = warp * 32 + lane;
     uint32_t r[32];
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    if (nk > 0) tmem_ld32(tl, r);
-    else
 #pragma unroll
-      for (int c = 0; c < 32; ++c) r[c] = 0u;
+    for (int h = 0; h < WT; ++h) {
+      if (nk > 0) tmem_ld32(tl + 64 * h, r);
+      else
 #pragma unroll
-    for (int c = 0; c < 32; ++c) tile[row * 33 + c].x = __uint_as_float(r[c]);
-    if (nk > 0) tmem_ld32(tl + 32, r);
+        for (int c = 0; c < 32; ++c) r[c] = 0u;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) tile[row * 33 + c].y = __uint_as_float(r[c]);
+      for (int c = 0; c < 32; ++c) tile[row * TS + 32 * h + c].x = __uint_as_float(r[c]);
+      if (nk > 0) tmem_ld32(tl + 64 * h + 32, r);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) tile[row * TS + 32 * h + c].y = __uint_as_float(r[c]);
+    }
   }
   fence_before();
   __syncthreads();
@@ -278,19 +304,61 @@ __global__ void __launch_bounds__(128, 1) tc2_kernel(const __grid_constant__ CUt
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+  if (g.rg > 0) {
+    float* scl = reinterpret_cast<float*>(gbase + (size_t)BM * TS * sizeof(float2));  // [BM / rg][32 WT]
+    long long* rowoff = reinterpret_cast<long long*>(scl + BM * BNC * WT);                // [BM]
+    if (tid < BM) {  // each thread places one row: (item, y, q) -> offset from the item's output
+      const int gm = m0 + tid;
+      long long off = -1;
+      if (gm < g.M) {
+        const int item = gm / g.rg_rows, rem = gm % g.rg_rows;
+        off = (long long)item * (1ll << 40) + (long long)(rem % g.rg) * g.rg_plane + (long long)(rem / g.rg) * g.ldc;
+      }
+      rowoff[tid] = off;
+    }
+    if (g.rg_norm) {
+      const int ng = BM / g.rg;
+      for (int e = tid; e < ng * BNC * WT; e += NTHR) {
+        const int gi = e / (BNC * WT), c = e % (BNC * WT);
+        float n2 = 0.f;
+        for (int r = 0; r < g.rg; ++r) {
+          const float2 v = tile[(gi * g.rg + r) * TS + c];
+          n2 = fmaf(v.x, v.x, fmaf(v.y, v.y, n2));
+        }
+        scl[e] = n2 > 0.f ? rsqrtf(n2) : 0.f;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    for (int e = warp; e < BM * WT; e += NWARP) {
+      const int rr = e / WT, gn = n0 + 32 * (e % WT) + lane;
+      const long long ro = rowoff[rr];
+      if (ro < 0 || gn >= g.N) continue;
+      const int item = (int)(ro >> 40);
+      float2* base = (g.c_tab ? g.c_tab[item] : g.C + (long long)item * g.c_stride) + (ro & ((1ll << 40) - 1));
+      float2 v = tile[rr * TS + (gn - n0)];
+      if (g.rg_norm) {
+        const float sc = scl[(rr / g.rg) * (BNC * WT) + (gn - n0)];
+        v.x *= sc;
+        v.y *= sc;
+      }
+      __stcs(base + gn, v);
+    }
+    return;
+  }
   if (g.splits > 1) {  // raw partial tile
     float2* out = g.ws + (long long)blockIdx.z * g.M * g.N;
-    for (int rr = warp; rr < BM; rr += 4) {
-      const int gm = m0 + rr, gn = n0 + lane;
-      if (gm < g.M && gn < g.N) out[(long long)gm * g.N + gn] = tile[rr * 33 + lane];
+    for (int e = warp; e < BM * WT; e += NWARP) {
+      const int rr = e / WT, gm = m0 + rr, gn = n0 + 32 * (e % WT) + lane;
+      if (gm < g.M && gn < g.N) out[(long long)gm * g.N + gn] = tile[rr * TS + (gn - n0)];
     }
     return;
   }
   const bool has_beta = (g.beta.x != 0.f || g.beta.y != 0.f);
-  for (int rr = warp; rr < BM; rr += 4) {
-    const int gm = m0 + rr, gn = n0 + lane;
+  for (int e = warp; e < BM * WT; e += NWARP) {
+    const int rr = e / WT, gm = m0 + rr, gn = n0 + 32 * (e % WT) + lane;
     if (gm >= g.M || gn >= g.N) continue;
-    const float2 a = tile[rr * 33 + lane];
+    const float2 a = tile[rr * TS + (gn - n0)];
     float2 o = make_float2(g.alpha.x * a.x - g.alpha.y * a.y, g.alpha.x * a.y + g.alpha.y * a.x);
     float2* cp = Cb + (long long)gm * g.ldc + gn;
     if (has_beta) {
@@ -373,9 +441,10 @@ __global__ void split_at_kernel(const float2* __restrict__ Y, int ldy, int M, in
 }
 
 // B' head/tail rows (see the file comment); columns c >= N of the last tile are zero
+// cg > 0 (opB 0): column c of B is column c % cg of block c / cg, the blocks cgs elements apart
 __global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, int K, int N, int Np,
                                float* __restrict__ hi, float* __restrict__ lo, int K2p, int nbatch,
-                               long long b_stride) {
+                               long long b_stride, int cg, long long cgs) {
   const long long per = (long long)Np * K;
   const long long total = per * nbatch;
   for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < total; e0 += (long long)gridDim.x * blockDim.x) {
@@ -386,7 +455,7 @@ __global__ void split_b_kernel(const float2* __restrict__ B, int ldb, int opB, i
     const int c = (int)(e / K), k = (int)(e % K);
     float2 b = make_float2(0.f, 0.f);
     if (c < N) {
-      if (opB == 0) b = Bb[(long long)k * ldb + c];
+      if (opB == 0) b = cg > 0 ? Bb[(long long)(c / cg) * cgs + (long long)k * ldb + c % cg] : Bb[(long long)k * ldb + c];
       else {
         const float2 s = Bb[(long long)c * ldb + k];
         b = make_float2(s.x, -s.y);
@@ -432,9 +501,9 @@ bool encode_2d(CUtensorMap* map, const float* base, int cols, int rows, int ld_f
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NT, int STAGES, bool CONV = false>
+template <int NT, int STAGES, bool CONV, int WT>
 size_t smem_bytes() {
-  return (size_t)STAGES * stage_bytes<NT, STAGES, CONV>() + 1024 + 128;
+  return (size_t)STAGES * stage_bytes<NT, CONV, WT>() + 1024 + 128;
 }
 
 unsigned grid_for(long long n) {
@@ -453,18 +522,25 @@ bool tc2_conv_ok(int K, int lda_fp32, const void* a_fp32) {
 int tc2_k2p(int K) { return ((2 * K + 3) / 4) * 4; }
 int tc2_np(int N) { return ((N + BNC - 1) / BNC) * BNC; }
 
-template <int NT, int S, bool CONV = false>
+template <int NT, int S, bool CONV, int WT>
 static cudaError_t set_smem() {
-  return cudaFuncSetAttribute(tc2_kernel<NT, S, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes<NT, S, CONV>());
+  return cudaFuncSetAttribute(tc2_kernel<NT, S, CONV, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<NT, S, CONV, WT>());
+}
+
+template <int NT, int S, bool CONV, int WT>
+static void launch(dim3 grid, cudaStream_t st, const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& b,
+                   const CUtensorMap& bl, const Args& g) {
+  tc2_kernel<NT, S, CONV, WT><<<grid, CONV ? 256 : 128, smem_bytes<NT, S, CONV, WT>(), st>>>(a, al, b, bl, g);
 }
 
 cudaError_t tc2_prepare() {
-  cudaError_t e = set_smem<3, 4>();
-  if (e == cudaSuccess) e = set_smem<3, 2>();
-  if (e == cudaSuccess) e = set_smem<1, 4>();
-  if (e == cudaSuccess) e = set_smem<1, 2>();
-  if (e == cudaSuccess) e = set_smem<3, 3, true>();
+  cudaError_t e = set_smem<3, 3, false, 2>();
+  if (e == cudaSuccess) e = set_smem<3, 2, false, 1>();
+  if (e == cudaSuccess) e = set_smem<1, 4, false, 2>();
+  if (e == cudaSuccess) e = set_smem<1, 2, false, 1>();
+  if (e == cudaSuccess) e = set_smem<3, 3, true, 2>();
+  if (e == cudaSuccess) e = set_smem<3, 2, true, 1>();
   return e;
 }
 
@@ -485,10 +561,10 @@ cudaError_t tc2_split_at(const float2* Y, int ldy, int M, int K, float* hi, floa
 }
 
 cudaError_t tc2_split_b(const float2* B, int ldb, int opB, int K, int N, float* hi, float* lo, cudaStream_t st,
-                        int nbatch, long long b_stride) {
+                        int nbatch, long long b_stride, int cg, long long cgs) {
   const int Np = tc2_np(N);
   split_b_kernel<<<grid_for((long long)Np * K * nbatch), 256, 0, st>>>(B, ldb, opB, K, N, Np, hi, lo, tc2_k2p(K),
-                                                                      nbatch, b_stride);
+                                                                      nbatch, b_stride, opB == 0 ? cg : 0, cgs);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -497,12 +573,15 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
                      const float* Blo, float2 alpha, float2 beta, float2* C, int ldc, float diag_val,
                      int diag_stride, int diag_limit, int splits, float2* ws, int* err, cudaStream_t st,
                      int nbatch, long long c_stride, int a_per_item, float2* const* c_tab, int c_div,
-                     int b_per_item, const float2* a_fp32, int lda_fp32) {
+                     int b_per_item, const float2* a_fp32, int lda_fp32, int rg, int rg_rows,
+                     long long rg_plane, int rg_norm) {
   if (M <= 0 || N <= 0 || nbatch < 1) return cudaSuccess;
+  if (rg > 0 && (nbatch != 1 || rg_rows <= 0 || rg_rows % rg != 0 || (rg_norm && BM % rg != 0)))
+    return cudaErrorInvalidValue;
   const int K2 = 2 * K, K2p = tc2_k2p(K), Np = tc2_np(N);
   const int total = (K2 + BK - 1) / BK;
   // split-K: also in batched mode (per item), never with a C table
-  if (splits < 1 || ws == nullptr || c_tab != nullptr) splits = 1;
+  if (splits < 1 || ws == nullptr || c_tab != nullptr || rg > 0) splits = 1;
   if (splits > total) splits = total > 0 ? total : 1;
   const int kpb = total > 0 ? (total + splits - 1) / splits : 0;
   if (kpb > 0) splits = (total + kpb - 1) / kpb;
@@ -514,34 +593,44 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   // A from FP32 complex rows, split in shared memory: three passes, rows 16-byte aligned
   const bool conv = a_fp32 != nullptr && nterms == 3 && (lda_fp32 % 2) == 0 && lda_fp32 >= K &&
                     ((uintptr_t)a_fp32 % 16) == 0;
+  // the row-group epilogue keeps its scales and row offsets beside the tile: converting variants
+  if (rg > 0 && !conv) return cudaErrorInvalidValue;
   if (conv) {
     if (!encode_2d(&mAh, reinterpret_cast<const float*>(a_fp32), kcols, arows, 2 * lda_fp32, BM)) return cudaErrorInvalidValue;
     mAl = mAh;
   } else if (!encode_2d(&mAh, Ahi, kcols, arows, K2p, BM) || !encode_2d(&mAl, al, kcols, arows, K2p, BM)) {
     return cudaErrorInvalidValue;
   }
-  if (!encode_2d(&mBh, Bhi, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC) ||
-      !encode_2d(&mBl, bl, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC))
+  // long K loops (> 8 steps per CTA) take 64 complex columns per CTA (one N = 128 MMA: half the
+  // A loads per output) and 3-4 stages; short ones 32 columns and 2 stages, 2 CTAs per SM, so one
+  // CTA's epilogue overlaps another's loads.
+  const bool wide = kpb > 8;
+  const int wt = wide ? 2 : 1;
+  if (!encode_2d(&mBh, Bhi, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC * wt) ||
+      !encode_2d(&mBl, bl, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC * wt))
     return cudaErrorInvalidValue;
   Args g{M, N, K2, kpb, C, ldc, alpha, beta, diag_val, diag_stride, diag_limit, ws, err,
          nbatch > 1 ? 1 : 0, b_per_item ? 2 * Np : 0, c_stride, a_per_item && nbatch > 1 ? M : 0,
-         nbatch > 1 ? c_tab : nullptr,
+         (nbatch > 1 || rg > 0) ? c_tab : nullptr,
          c_div > 0 ? c_div : 1};
+  g.rg = rg > 0 ? rg : 0;
+  g.rg_rows = rg_rows;
+  g.rg_norm = rg > 0 && rg_norm ? 1 : 0;
+  g.rg_plane = rg_plane;
   g.splits = splits;
   g.no_loads = g_tc2_stall.load() ? 1 : 0;
   g.wait_limit = g.no_loads ? kWaitStalled : kWait;
-  dim3 grid(Np / BNC, (M + BM - 1) / BM, nbatch * splits);
-  // short K loops (<= 8 steps per CTA) keep 2 stages: half the shared memory, 2 CTAs per SM, so
-  // one CTA's epilogue overlaps another's loads; long loops keep 4 stages in flight
-  const bool deep = kpb > 8;
+  dim3 grid((Np + BNC * wt - 1) / (BNC * wt), (M + BM - 1) / BM, nbatch * splits);
   if (conv) {
-    tc2_kernel<3, 3, true><<<grid, 128, smem_bytes<3, 3, true>(), st>>>(mAh, mAl, mBh, mBl, g);
-  } else if (nterms == 1) {
-    if (deep) tc2_kernel<1, 4, false><<<grid, 128, smem_bytes<1, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
-    else tc2_kernel<1, 2, false><<<grid, 128, smem_bytes<1, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
+    if (wide) launch<3, 3, true, 2>(grid, st, mAh, mAl, mBh, mBl, g);
+    else launch<3, 2, true, 1>(grid, st, mAh, mAl, mBh, mBl, g);
+  }
+  else if (nterms == 1) {
+    if (wide) launch<1, 4, false, 2>(grid, st, mAh, mAl, mBh, mBl, g);
+    else launch<1, 2, false, 1>(grid, st, mAh, mAl, mBh, mBl, g);
   } else {
-    if (deep) tc2_kernel<3, 4, false><<<grid, 128, smem_bytes<3, 4>(), st>>>(mAh, mAl, mBh, mBl, g);
-    else tc2_kernel<3, 2, false><<<grid, 128, smem_bytes<3, 2>(), st>>>(mAh, mAl, mBh, mBl, g);
+    if (wide) launch<3, 3, false, 2>(grid, st, mAh, mAl, mBh, mBl, g);
+    else launch<3, 2, false, 1>(grid, st, mAh, mAl, mBh, mBl, g);
   }
   ++g_launches;
   cudaError_t e = cudaGetLastError();

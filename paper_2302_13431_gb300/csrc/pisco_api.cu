@@ -101,11 +101,16 @@ struct pisco_plan_s {
   int *d_sep_rows = nullptr, *d_sep_b2 = nullptr;
   float *IAh = nullptr, *IAl = nullptr, *IBh = nullptr, *IBl = nullptr;
   float2* interpA = nullptr;  // the last axis's interpolation matrix (split into IAh/IAl)
+  // first interpolation axis as one tensor-core GEMM over all rows of V (B' of interpT)
+  float *IXh = nullptr, *IXl = nullptr;
+  bool tc_rows2d = false;  // 2D: both interpolation axes on the tensor cores, normalisation fused
   float *TAh = nullptr, *TAl = nullptr, *TBh = nullptr, *TBl = nullptr;  // their split operands
   float *Ah = nullptr, *Al = nullptr, *Xh = nullptr, *Xl = nullptr;        // A32 and the block
   float *Eh = nullptr, *El = nullptr, *KTh = nullptr, *KTl = nullptr;      // E and the lag table
   float *UAh = nullptr, *UAl = nullptr, *UBh = nullptr, *UBl = nullptr;    // U diag(w), conj(U)^T
   float2* tc_ws = nullptr;
+  float2* thin_ws = nullptr;  // partial Grams of the CUDA-core thin products (m <= 64)
+  int* thin_tk = nullptr;     // their per-item ticket counters
   size_t tc_ws_elems = 0;
   // learned warm start of the power iteration (pisco_set_warm_start)
   bool ws_on = false;
@@ -632,6 +637,10 @@ cudaError_t block_product(pisco_plan_s* pl, bool conj_a, const float2* Y, const 
                           long long sZ, long long sC, int items) {
   if (pl->tc_thin) return thin_product(pl, conj_a, Y, Z, C, sY, sZ, sC, items);
   const int n = pl->n, m = pl->m;
+  if (m <= 64) {
+    if (conj_a) return eig_thin_gram(Y, sY, Z, sZ, n, m, C, sC, pl->thin_ws, pl->thin_tk, items, pl->st);
+    return eig_thin_apply(Y, sY, Z, sZ, n, m, C, sC, items, pl->st);
+  }
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
   if (conj_a)
     return cgemm<float>('C', 'N', m, m, n, one, Y, m, Z, m, zero, C, m, pl->ws32, pl->ws32_elems * pl->items,
@@ -734,7 +743,7 @@ pisco_status run_eig(pisco_plan_s* pl) {
   // Rayleigh-Ritz on the block
   OP("eig_gemm_AX", ax_product(pl, pl->X, pl->Z, snm));
   OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, true, pl->X, pl->Z, pl->Bm, snm, snm, smm, items));
-  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), pl->dstatus, st, it));
+  OP("eig_jacobi", eig_jacobi(pl->Bm, m, pl->mu, pl->Vj, 30, (float)(0.05 * thr2), (float)(0.5 * thr2), pl->dstatus, st, it));
   OP(pl->tc_thin ? "eig_gemm_thin_tc" : "eig_gemm_thin_fp32", block_product(pl, false, pl->X, pl->Vj, pl->U, snm, svj, snm, items));
   // FP64 Rayleigh quotients of the Ritz vectors that decide the split
   OP("eig_misc", eig_select_band(pl->mu, m, thr2, kNbMax, pl->band, st, it));
@@ -834,7 +843,33 @@ pisco_status run_interp(pisco_plan_s* pl, float2* maps) {
                                                    IS(pl, pl->V), 0, tab));
     return PISCO_OK;
   }
-  OP("interp_axis", apply_axis_c(pl->V, pl->interpT, pl->I1, AxisView{QI, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1, 0, 1}, st));
+  if (pl->tc_rows2d) {
+    // 2D on the tensor cores, axis 1 first: W[y][(q, r2)] = M1 V_q for every item (B' of V read
+    // with grouped columns), then one product over the rows (item, y, q) of W: maps rows =
+    // W interpT, each pixel's Q coil rows in one tile and normalised in its epilogue
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    const long long wrows = (long long)N[1] * Q;
+    OP("interp_split", tc2_split_b(pl->V, Nr[2], 0, Nr[1], Q * Nr[2], pl->IBh, pl->IBl, st, items, IS(pl, pl->V), Nr[2],
+                                   (long long)Nr[1] * Nr[2]));
+    OP("interp_axis1_tc", tc2_gemm(3, N[1], Q * Nr[2], Nr[1], pl->IAh, pl->IAl, pl->IBh, pl->IBl, one, zero, pl->I1,
+                             Q * Nr[2], 0.f, 0, 0, 1, nullptr, &pl->dstatus->flags, st, items, wrows * Nr[2], 0,
+                             nullptr, 1, 1));
+    const bool fused = 128 % Q == 0;
+    OP("interp_rows_tc", tc2_gemm(3, (int)(wrows * items), N[2], Nr[2], nullptr, nullptr, pl->IXh, pl->IXl, one, zero, maps,
+                             N[2], 0.f, 0, 0, 1, nullptr, &pl->dstatus->flags, st, 1, (long long)Q * pl->npix, 0, tab,
+                             1, 0, pl->I1, Nr[2], Q, (int)wrows, (long long)N[1] * N[2], fused ? 1 : 0));
+    if (!fused) OP("interp_final_norm", normalize_maps(maps, Q, pl->npix, st, items, 0, tab));
+    return PISCO_OK;
+  }
+  const long long rows1 = QI * Nr[0] * Nr[1];
+  if (pl->IXh && tc2_conv_ok(Nr[2], Nr[2], pl->V) && (rows1 + 127) / 128 <= 65535) {
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    OP("interp_axis_tc", tc2_gemm(3, (int)rows1, N[2], Nr[2], nullptr, nullptr, pl->IXh, pl->IXl, one, zero, pl->I1,
+                                  N[2], 0.f, 0, 0, 1, nullptr, &pl->dstatus->flags, st, 1, 0, 0, nullptr, 1, 0, pl->V,
+                                  Nr[2]));
+  } else {
+    OP("interp_axis", apply_axis_c(pl->V, pl->interpT, pl->I1, AxisView{QI, (long long)Nr[0] * Nr[1], Nr[2], N[2], 1, 0, 1}, st));
+  }
   if (pl->tc_interp) {
     // maps_q = M T_q for every coil q (one batched tensor-core GEMM), then the per-pixel norm
     const bool tt = pl->tc_terms == 3;
@@ -1085,6 +1120,11 @@ static pisco_status plan_create(const pisco_params* p, cudaStream_t cuda_stream,
   ok = ok && dalloc(pl, &pl->X, (size_t)n * M) && dalloc(pl, &pl->Y, (size_t)n * M);
   ok = ok && dalloc(pl, &pl->Z, (size_t)n * M) && dalloc(pl, &pl->U, (size_t)n * M);
   ok = ok && dalloc(pl, &pl->Gm, (size_t)M * M) && dalloc(pl, &pl->Rinv, (size_t)M * M);
+  {
+    const size_t mt = (size_t)std::min(M, 64);
+    ok = ok && dalloc(pl, &pl->thin_ws, (size_t)eig_thin_chunks(pl->n) * mt * mt) && dalloc(pl, &pl->thin_tk, 1);
+    if (ok) ok = cudaMemset(pl->thin_tk, 0, sizeof(int) * (size_t)pl->items) == cudaSuccess;
+  }
   ok = ok && dalloc(pl, &pl->Bm, (size_t)M * M) && dalloc(pl, &pl->Vj, (size_t)2 * M * M);
   ok = ok && dalloc(pl, &pl->mu, (size_t)M) && dalloc(pl, &pl->w, (size_t)M) && dalloc(pl, &pl->ritz, (size_t)M);
   ok = ok && dalloc(pl, &pl->band, (size_t)kNbMax);
@@ -1176,6 +1216,19 @@ static pisco_status plan_create(const pisco_params* p, cudaStream_t cuda_stream,
          dalloc_shared(pl, &pl->IAl, lo_n * N[ax] * k2) && dalloc(pl, &pl->IBh, nb) && dalloc(pl, &pl->IBl, lo_n * nb);
     ok = ok && tc2_split_a(pl->interpA, Nr[ax], nullptr, N[ax], Nr[ax], pl->IAh, lo_n ? pl->IAl : nullptr,
                            nullptr) == cudaSuccess;
+    // the first (contiguous) axis: I1 = V interpT with V's rows read as FP32 and split in shared
+    // memory (three passes only; rows of 16-byte multiples, item blocks 16-byte aligned)
+    if (ok && pl->tc_terms == 3 && Nr[2] % 2 == 0 && ((long long)Q * pl->npix_red) % 2 == 0) {
+      const size_t nx = (size_t)2 * tc2_np(N[2]) * tc2_k2p(Nr[2]);
+      ok = dalloc_shared(pl, &pl->IXh, nx) && dalloc_shared(pl, &pl->IXl, nx) &&
+           tc2_split_b(pl->interpT, N[2], 0, Nr[2], N[2], pl->IXh, pl->IXl, nullptr, 1, 0) == cudaSuccess;
+      // 2D: W (N1 x Q Nr2 per item, in I1) must fit I1 and keep its item blocks 16-byte aligned;
+      // the row-grouped product needs its rows (items N1 Q) within the grid's y limit
+      const long long wsz = (long long)N[1] * Q * Nr[2];
+      pl->tc_rows2d = ok && pl->D == 2 && wsz <= IS(pl, pl->I1) && wsz % 2 == 0 && IS(pl, pl->I1) % 2 == 0 &&
+                      ((long long)N[1] * Q * items + 127) / 128 <= 65535 &&
+                      (size_t)2 * tc2_np(Q * Nr[2]) * k2 <= nb;
+    }
   }
   ok = ok && dalloc(pl, &pl->dstatus, 1);
   ok = ok && dalloc(pl, &pl->calib_stage, (size_t)Q * Nc[0] * Nc[1] * Nc[2]);
