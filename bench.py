@@ -293,6 +293,18 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
         return dict(bound="tensor", achieved=work / map_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
                     note="maps_q = M T_q, one batched complex GEMM (N x N_r) by (N_r x N) per coil, "
                          "B-operand split included; " + tc_note)
+    if op == "interp_rows_tc":
+        work = 8.0 * Q * npix * (w["grid"][1] // w["reduction"])
+        return dict(bound="tensor", achieved=work * mpl / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                    note="last interpolation axis as one product over the rows (item, y, coil) of W: "
+                         "(rows x N_r) by (N_r x N), each pixel's Q coil rows normalised in the epilogue, "
+                         "A read as FP32 and split in shared memory; " + tc_note)
+    if op == "interp_axis1_tc":
+        nr1 = w["grid"][0] // w["reduction"]
+        work = 8.0 * Q * w["grid"][0] * nr1 * (w["grid"][1] // w["reduction"])
+        return dict(bound="tensor", achieved=work * mpl / avg_s / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                    note="first interpolation axis W = M1 V_q for all coils of every item: "
+                         "(N x N_r) by (N_r x Q N_r); " + tc_note)
     if op == "eig_gemm_thin_fp32":
         work = 8.0 * n * m * m                       # every thin block product is n x m x m
         return dict(bound="alu", achieved=work * mpl / avg_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
@@ -724,7 +736,7 @@ def run_gpu_3d(args):
     torch.cuda.set_device(0)
     w = W3D
     red = tuple(g // w["reduction"] for g in w["grid"])
-    cache = os.path.join(ROOT, "paper_2302_13431_gb300", "_lib", f"warmstart_3d_q32_{args.train_volumes}.npz")
+    cache = os.path.join(ROOT, "paper_2302_13431_gb300", "_lib", f"warmstart_3d_q32_r1_{args.train_volumes}.npz")
     t0 = time.time()
     if os.path.exists(cache):
         net = WarmStartNet.load(cache)

@@ -310,45 +310,60 @@ pisco_status pisco_support_mask(const float* d_eig, long long n, float threshold
 
 /* ---- Learned warm start of the power iteration (an addition of this library; the paper
  * starts every pixel from an arbitrary vector, Sec. V-E) ------------------------------------
- * A per-pixel MLP maps the pixel's normalised low-resolution coil vector y(x)/||y(x)||
- * (Sec. V-D; 2Q reals, real and imaginary parts interleaved per coil) through two ReLU hidden
- * layers to a proposed start vector (2Q reals):
- *     h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), out = x + W3 h2 + b3,
- * the skip term x present when n_in == n_out (the network corrects the heuristic start
- * y(x)/||y(x)||; with W3 = 0, b3 = 0 it returns that start).
- * Parameters travel as one FP32 blob [W1 | b1 | W2 | b2 | W3 | b3], weights row-major
- * (W1: n_hidden x n_in, W2: n_hidden x n_hidden, W3: n_out x n_hidden).  The network
- * evaluates FP16-rounded weights with FP32 accumulation; Adam updates FP32 master weights.
- * All widths are in [1, 128].  Calls are enqueued on the stream given at creation. */
+ * A per-pixel MLP maps the patch of normalised low-resolution coil vectors around the pixel
+ * (Sec. V-D's apodised images; see pisco_warm_start_patch_features: (2r+1)^D neighbours of 2Q
+ * reals, real and imaginary parts interleaved per coil) through two ReLU hidden layers to a
+ * proposed start vector (2Q reals):
+ *     h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), out = s(x) + W3 h2 + b3,
+ * the skip term s(x) = the middle block of x (the centre pixel's own normalised vector) when
+ * n_in is an odd multiple of n_out, else absent (with W3 = 0, b3 = 0 the network returns the
+ * heuristic start).  Parameters travel as one FP32 blob [W1 | b1 | W2 | b2 | W3 | b3], weights
+ * row-major (W1: n_hidden x n_in, W2: n_hidden x n_hidden, W3: n_out x n_hidden).  Every layer
+ * product runs on the tensor cores with FP16 operands (the weights stored in FP16, the
+ * activations and per-sample gradients rounded to FP16 where they enter a product) and FP32
+ * accumulation; biases, activations and the Adam state (FP32 master weights) stay FP32.
+ * n_in in [1, 4096], n_hidden and n_out in [1, 128].  Calls are enqueued on the stream given
+ * at creation. */
 typedef struct pisco_mlp_s* pisco_mlp_t;
 
 /* Create a network with the given parameters (host blob, copied) and device workspace for
- * batches of up to max_batch samples (<= 2^26). */
+ * batches of up to max_batch samples (<= 4,000,000). */
 pisco_status pisco_mlp_create(int n_in, int n_hidden, int n_out, const float* h_params,
                               long long max_batch, void* cuda_stream, pisco_mlp_t* out);
 /* Replace the parameters (host blob) and reset the Adam moments and step count. */
 pisco_status pisco_mlp_write(pisco_mlp_t mlp, const float* h_params);
 /* d_out[b][:] = network(d_x[b][:]); device FP32 arrays [batch][n_in] and [batch][n_out]. */
 pisco_status pisco_mlp_forward(pisco_mlp_t mlp, const float* d_x, long long batch, float* d_out);
-/* Forward and backward pass of L = (1/batch) sum_b ||out_b - t_b||^2 for device FP32 inputs
- * d_x [batch][n_in] and targets d_target [batch][n_out]; the gradient of every parameter is
- * kept in the network (pisco_mlp_read which = 1).  h_loss (optional): L, after a
- * synchronisation. */
+/* Forward and backward pass of L = (1/batch) sum_b l(out_b, t_b) for device FP32 inputs d_x
+ * [batch][n_in] and targets d_target [batch][n_out]: l = ||out - t||^2 (loss kind 0, the
+ * default) or the direction loss l = 1 - |<o, t>| / (||o|| ||t||) of the complex vectors o, t
+ * (kind 1; <o, t> = sum_q conj(o_q) t_q over the n_out/2 interleaved entries; l = 0 and no
+ * gradient where o or t is zero).  The gradient of every parameter is kept in the network
+ * (pisco_mlp_read which = 1).  h_loss (optional): L, after a synchronisation. */
 pisco_status pisco_mlp_backward(pisco_mlp_t mlp, const float* d_x, const float* d_target,
                                 long long batch, double* h_loss);
+/* Loss of pisco_mlp_backward: 0 squared error, 1 direction loss (needs an even n_out). */
+pisco_status pisco_mlp_set_loss(pisco_mlp_t mlp, int kind);
 /* One Adam step (bias-corrected) with the last gradient. */
 pisco_status pisco_mlp_adam(pisco_mlp_t mlp, float lr, float beta1, float beta2, float eps);
 /* Copy the FP32 parameters (which = 0) or the last gradient (which = 1) into a host blob;
  * synchronises. */
 pisco_status pisco_mlp_read(pisco_mlp_t mlp, int which, float* h_out);
 void pisco_mlp_destroy(pisco_mlp_t mlp); /* NULL-safe */
-/* The network's input features, as the estimate computes them: from low-resolution coil images
- * d_y (device complex64 [Q][npix], the layout of PISCO_BUF_Y) to d_x (device FP32 [npix][2Q]),
- * x_j = y_j/||y_j|| with real and imaginary parts interleaved; zero vectors stay zero. */
+/* The network's input features, as the estimate computes them, from low-resolution coil images
+ * d_y (device complex64 [Q][npix], the layout of PISCO_BUF_Y) on the reduced grid dims
+ * (ndim = 2: {N_y, N_x}; 3: {N_z, N_y, N_x}; periodic) to d_x (device FP32
+ * [npix][(2r+1)^ndim][2Q]): for every neighbour o of the pixel j (z slowest, x fastest; radius
+ * r in [0, 3]) the vector y(j+o) conj(y_0(j)) / (|y_0(j)| ||y(j)||), real and imaginary parts
+ * interleaved (no rotation where y_0(j) = 0; zeros where y(j) = 0). */
+pisco_status pisco_warm_start_patch_features(const void* d_y, int Q, const int* dims, int ndim,
+                                             int radius, float* d_x, void* cuda_stream);
+/* The radius-0 features of npix pixels: y_j conj(y_0j) / (|y_0j| ||y_j||), [npix][2Q]. */
 pisco_status pisco_warm_start_features(const void* d_y, int Q, long long npix, float* d_x,
                                        void* cuda_stream);
 
-/* Use `mlp` (n_in = n_out = 2Q, copied into the plan; NULL switches the warm start off) to
+/* Use `mlp` (n_out = 2Q, n_in = (2r+1)^D 2Q for a patch radius r in [0, 3]; copied into the
+ * plan; one-item plans only; NULL switches the warm start off) to
  * start the power iteration of every reduced-grid pixel, run `iters` iterations, and
  * re-solve from the plain start vector with `fallback_iters` iterations every pixel whose
  * residual ||G v - lambda |Lambda| v|| / |Lambda| exceeds `gate` (gate <= 0: no fallback).

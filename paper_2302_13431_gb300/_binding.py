@@ -171,6 +171,11 @@ def load():
     lib.pisco_set_warm_start.restype = ctypes.c_int
     lib.pisco_warm_start_features.argtypes = [vp, ctypes.c_int, ctypes.c_longlong, vp, vp]
     lib.pisco_warm_start_features.restype = ctypes.c_int
+    lib.pisco_warm_start_patch_features.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                    ctypes.c_int, vp, vp]
+    lib.pisco_warm_start_patch_features.restype = ctypes.c_int
+    lib.pisco_mlp_set_loss.argtypes = [vp, ctypes.c_int]
+    lib.pisco_mlp_set_loss.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -406,6 +411,16 @@ def pisco_mlp_destroy(mlp):
 
 def pisco_set_warm_start(plan, mlp, iters, gate, fallback_iters):
     return load().pisco_set_warm_start(plan, mlp, iters, gate, fallback_iters)
+
+
+def pisco_warm_start_patch_features(d_y, Q, dims, radius, d_x, stream=0):
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims] + [0] * (3 - len(dims)))
+    return load().pisco_warm_start_patch_features(ctypes.c_void_p(d_y), Q, d, len(dims), radius,
+                                                  ctypes.c_void_p(d_x), ctypes.c_void_p(stream))
+
+
+def pisco_mlp_set_loss(h, kind):
+    return load().pisco_mlp_set_loss(h, int(kind))
 
 
 def pisco_warm_start_features(d_y, Q, npix, d_x, stream=0):

@@ -236,9 +236,9 @@ cudaError_t gassembly_field_sep2(const float2* KT, int Q, int nlag, const int* r
                                  float lam_size, float2* G, cudaStream_t st, int items = 1, long long sKT = 0,
                                  long long sG = 0);
 
-// warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out, widths <= 128; w32 is the FP32
-// parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its FP16 copy (the
-// matrices are read from w16, the biases from w32)
+// warm-start MLP (kernels_mlp.cu): n_in -> H -> H -> n_out (n_in <= 4096, H and n_out <= 128);
+// w32 is the FP32 parameter blob [W1 | b1 | W2 | b2 | W3 | b3] (row-major weights), w16 its
+// FP16 copy (the matrices are read from w16, the biases from w32)
 struct MlpView {
   int n_in, H, n_out;
   const float* w32;
@@ -253,11 +253,15 @@ cudaError_t mlp_forward(const MlpView& m, const float* X, long long B, float* H1
                         cudaStream_t st);
 cudaError_t mlp_backward(const MlpView& m, const float* X, const float* T, long long B, float* H1, float* H2,
                          float* out, float* dO, float* dH2, float* dH1, float* part, float* grad,
-                         float* loss_part, int loss_blocks, cudaStream_t st);
+                         float* loss_part, int loss_blocks, int loss_kind, cudaStream_t st);
 cudaError_t mlp_adam(float* w32, __half* w16, const float* g, float* m1, float* m2, long long n, float lr,
                      float b1, float b2, float eps, int step, cudaStream_t st);
 cudaError_t mlp_to_half(const float* w32, __half* w16, long long n, cudaStream_t st);
 cudaError_t mlp_features(const float2* Y, int Q, long long npix, float* X, cudaStream_t st);
+// patch features on the reduced grid dims (z, y, x) of D dimensions, radius r: [npix][(2r+1)^D 2Q]
+cudaError_t mlp_patch_features(const float2* Y, int Q, const int dims[3], int r, int D, float* X, cudaStream_t st);
+// column offset of the skip term in x (the middle block when n_in is an odd multiple of n_out), or -1
+int mlp_skip_offset(int n_in, int n_out);
 
 // TMA-fed tensor-core complex GEMM over operands split once in global memory (kernels_tc2.cu).
 // A' head/tail: [M][tc2_k2p(K)] floats; B' head/tail: [2 tc2_np(N)][tc2_k2p(K)] floats

@@ -115,6 +115,7 @@ struct pisco_plan_s {
   // learned warm start of the power iteration (pisco_set_warm_start)
   bool ws_on = false;
   int ws_iters = 0, ws_fb_iters = 0, ws_H = 0;
+  int ws_nin = 0, ws_r = 0, ws_cap = 0;  // network input width, patch radius, allocated input width
   float ws_gate = 0.f;
   float* ws_w32 = nullptr;
   __half* ws_w16 = nullptr;
@@ -925,8 +926,9 @@ pisco_status run_all(pisco_plan_s* pl, const float2* calib, float2* maps, float*
                                           pl->prm.seed, pl->V, pl->eig_tmp, st, o));
   } else if (pl->ws_on) {
     // learned start vectors, fewer iterations, residual-gated re-solve from the plain start
-    const MlpView mv{2 * pl->Q, pl->ws_H, 2 * pl->Q, pl->ws_w32, pl->ws_w16};
-    OP("warm_start_mlp", mlp_features(pl->Yf, pl->Q, pl->npix_red, pl->ws_X, st));
+    const MlpView mv{pl->ws_nin, pl->ws_H, 2 * pl->Q, pl->ws_w32, pl->ws_w16};
+    const int rdims[3] = {pl->Nr[0], pl->Nr[1], pl->Nr[2]};
+    OP("warm_start_mlp", mlp_patch_features(pl->Yf, pl->Q, rdims, pl->ws_r, pl->D, pl->ws_X, st));
     OP("warm_start_mlp", mlp_forward(mv, pl->ws_X, pl->npix_red, pl->ws_H1, pl->ws_H2, pl->ws_out, st));
     PiOpts o1;
     o1.v0 = pl->ws_out;
@@ -1439,26 +1441,41 @@ pisco_status pisco_set_warm_start(pisco_plan_t pl, pisco_mlp_t mlp, int iters, f
   int n_in, H, n_out;
   size_t np;
   mlp_dims(mlp, &n_in, &H, &n_out, &np);
-  if (n_in != 2 * pl->Q || n_out != 2 * pl->Q || iters < 0 || fallback_iters < 1 || !(gate == gate)) return PISCO_ERR_ARG;
+  if (n_out != 2 * pl->Q || n_in % n_out != 0 || iters < 0 || fallback_iters < 1 || !(gate == gate)) return PISCO_ERR_ARG;
+  // the input: the (2r+1)^D patch of normalised low-resolution vectors around the pixel
+  int r = -1;
+  for (int t = 0; t <= 3; ++t) {
+    const int w = 2 * t + 1;
+    if (n_in / n_out == (pl->D == 3 ? w * w * w : w * w)) r = t;
+  }
+  if (r < 0) return PISCO_ERR_ARG;
   if (pl->block_pi) return PISCO_ERR_UNSUPPORTED;  // the block iteration draws its own two starts
+  if (pl->items > 1) return PISCO_ERR_UNSUPPORTED;
   if (cudaStreamSynchronize(pl->st) != cudaSuccess) return PISCO_ERR_CUDA;
-  const size_t npmax = mlp_param_count(2 * pl->Q, 128, 2 * pl->Q);
-  if (!pl->ws_w32) {
-    const size_t nr = (size_t)pl->npix_red;
-    const bool ok = dalloc(pl, &pl->ws_w32, npmax) && dalloc(pl, &pl->ws_w16, npmax) &&
-                    dalloc(pl, &pl->ws_X, nr * 2 * pl->Q) && dalloc(pl, &pl->ws_H1, nr * 128) &&
-                    dalloc(pl, &pl->ws_H2, nr * 128) && dalloc(pl, &pl->ws_out, nr * 2 * pl->Q) &&
-                    dalloc(pl, &pl->fb_flags, nr);
-    if (!ok || mlp_prepare() != cudaSuccess) {
+  const size_t nr = (size_t)pl->npix_red;
+  if (!pl->ws_H1) {
+    const bool ok = dalloc(pl, &pl->ws_H1, nr * 128) && dalloc(pl, &pl->ws_H2, nr * 128) &&
+                    dalloc(pl, &pl->ws_out, nr * 2 * pl->Q) && dalloc(pl, &pl->fb_flags, nr);
+    if (!ok) {
       cudaGetLastError();
       return PISCO_ERR_OOM;
     }
+  }
+  if (n_in > pl->ws_cap) {  // (a narrower earlier buffer stays allocated until the plan is destroyed)
+    const size_t npmax = mlp_param_count(n_in, 128, n_out);
+    if (!(dalloc(pl, &pl->ws_w32, npmax) && dalloc(pl, &pl->ws_w16, npmax) && dalloc(pl, &pl->ws_X, nr * n_in))) {
+      cudaGetLastError();
+      return PISCO_ERR_OOM;
+    }
+    pl->ws_cap = n_in;
   }
   const MlpView src = mlp_view(mlp);
   if (cudaMemcpy(pl->ws_w32, src.w32, sizeof(float) * np, cudaMemcpyDeviceToDevice) != cudaSuccess ||
       cudaMemcpy(pl->ws_w16, src.w16, sizeof(__half) * np, cudaMemcpyDeviceToDevice) != cudaSuccess)
     return PISCO_ERR_CUDA;
   pl->ws_H = H;
+  pl->ws_nin = n_in;
+  pl->ws_r = r;
   pl->ws_iters = iters;
   pl->ws_gate = gate;
   pl->ws_fb_iters = fallback_iters;

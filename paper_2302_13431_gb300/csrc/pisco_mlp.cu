@@ -19,6 +19,7 @@ struct pisco_mlp_s {
   cudaStream_t st = nullptr;
   int step = 0;
   int loss_blocks = 0;
+  int loss_kind = 0;  // 0 squared error, 1 direction
   std::vector<void*> allocs;
   float *w32 = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
   __half* w16 = nullptr;
@@ -61,8 +62,8 @@ pisco_status pisco_mlp_create(int n_in, int n_hidden, int n_out, const float* h_
                               void* cuda_stream, pisco_mlp_t* out) {
   if (!out) return PISCO_ERR_ARG;
   *out = nullptr;
-  if (n_in < 1 || n_in > 128 || n_hidden < 1 || n_hidden > 128 || n_out < 1 || n_out > 128) return PISCO_ERR_ARG;
-  if (max_batch < 1 || max_batch > (1ll << 26) || !h_params) return PISCO_ERR_ARG;
+  if (n_in < 1 || n_in > 4096 || n_hidden < 1 || n_hidden > 128 || n_out < 1 || n_out > 128) return PISCO_ERR_ARG;
+  if (max_batch < 1 || max_batch > 4000000ll || !h_params) return PISCO_ERR_ARG;
   pisco_mlp_s* m = new (std::nothrow) pisco_mlp_s();
   if (!m) return PISCO_ERR_OOM;
   m->n_in = n_in;
@@ -123,7 +124,7 @@ pisco_status pisco_mlp_backward(pisco_mlp_t m, const float* d_x, const float* d_
                                 double* h_loss) {
   if (!m || !d_x || !d_target || batch < 1 || batch > m->max_batch) return PISCO_ERR_ARG;
   if (mlp_backward(mlp_view(m), d_x, d_target, batch, m->H1, m->H2, m->out, m->dO, m->dH2, m->dH1, m->part,
-                   m->grad, m->loss_part, m->loss_blocks, m->st) != cudaSuccess)
+                   m->grad, m->loss_part, m->loss_blocks, m->loss_kind, m->st) != cudaSuccess)
     return PISCO_ERR_CUDA;
   if (h_loss) {
     if (cudaMemcpyAsync(m->h_loss_part, m->loss_part, sizeof(float) * m->loss_blocks, cudaMemcpyDeviceToHost,
@@ -154,6 +155,24 @@ pisco_status pisco_mlp_read(pisco_mlp_t m, int which, float* h_out) {
       cudaStreamSynchronize(m->st) != cudaSuccess)
     return PISCO_ERR_CUDA;
   return PISCO_OK;
+}
+
+pisco_status pisco_mlp_set_loss(pisco_mlp_t m, int kind) {
+  if (!m || (kind != 0 && kind != 1) || (kind == 1 && (m->n_out % 2) != 0)) return PISCO_ERR_ARG;
+  m->loss_kind = kind;
+  return PISCO_OK;
+}
+
+pisco_status pisco_warm_start_patch_features(const void* d_y, int Q, const int* dims, int ndim, int radius,
+                                             float* d_x, void* cuda_stream) {
+  if (!d_y || !d_x || !dims || Q < 1 || Q > 64 || (ndim != 2 && ndim != 3) || radius < 0 || radius > 3)
+    return PISCO_ERR_ARG;
+  const int d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim == 3 ? 1 : 0], dims[ndim == 3 ? 2 : 1]};
+  if (d3[0] < 1 || d3[1] < 1 || d3[2] < 1) return PISCO_ERR_ARG;
+  return mlp_patch_features(static_cast<const float2*>(d_y), Q, d3, radius, ndim, d_x, (cudaStream_t)cuda_stream) ==
+                 cudaSuccess
+             ? PISCO_OK
+             : PISCO_ERR_CUDA;
 }
 
 pisco_status pisco_warm_start_features(const void* d_y, int Q, long long npix, float* d_x, void* cuda_stream) {

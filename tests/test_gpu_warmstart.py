@@ -3,10 +3,10 @@
 * Path parity: with the network's proposals as start vectors, the GPU power iteration equals the
   FP64 oracle's power iteration from the oracle network's proposals on the same G(x).
 * Gate: a gate that flags every pixel reproduces the plain path bitwise; no gate, no fallback.
-* Gain: a network trained (by the library's kernels) on pairs the method generates starts the
-  power iteration far closer to the exact null vector than the method's own start (so a given
-  accuracy takes fewer iterations) and, selected on a validation split, is not worse than the
-  heuristic y(x)/||y(x)|| it corrects.
+* Gain: a patch network (3 x 3 neighbourhood of the normalised low-resolution vectors) trained by
+  the library's kernels with the direction loss on pairs the method generates starts the power
+  iteration far closer to the exact null vector than the method's own start, and closer than the
+  heuristic y(x)/||y(x)|| it corrects, on held-out cases.
 """
 import numpy as np
 import pytest
@@ -38,7 +38,9 @@ def test_warm_started_power_iteration_matches_oracle():
     cfg = SMALL
     Q = cfg["Q"]
     case = make_case(cfg["grid"], Q, cfg["calib"], seed=21, phase="linear")
-    net = WarmStartNet(Q, 128, seed=4)
+    n_in = 9 * 2 * Q
+    from paper_2302_13431_gb300.warmstart import he_init
+    net = WarmStartNet(Q, 128, params=he_init(n_in, 128, 2 * Q, seed=4, last_scale=0.05), radius=1)
     est = _est(cfg)
     net.attach(est, iters=12, gate=0.0, fallback_iters=30)
     maps, eig = est(torch.from_numpy(case.calib).cuda())
@@ -47,8 +49,8 @@ def test_warm_started_power_iteration_matches_oracle():
     G = est.debug_buffer(B.PISCO_BUF_G).cpu().numpy().reshape(-1, Q, Q).astype(np.complex128)
     Y = est.debug_buffer(B.PISCO_BUF_Y).cpu().numpy().reshape(Q, -1).T.astype(np.complex128)
     V = est.debug_buffer(B.PISCO_BUF_V).cpu().numpy().reshape(Q, -1).T
-    P = M.unpack(net.params(), 2 * Q, 128, 2 * Q)
-    out, _ = M.forward(P, M.features(Y))
+    P = M.unpack(net.params(), n_in, 128, 2 * Q)
+    out, _ = M.forward(P, M.patch_features(Y.T, cfg["grid"], 1))
     L = O.kernel_support((2, 2), "rect").shape[0]
     v, lam, _ = O.power_iteration(G, M.to_complex(out), 12, L)
     v = O.phase_align(v, Y)
@@ -99,17 +101,26 @@ def _errors_vs_exact(G, v0s, L, iters_list):
 
 
 def test_trained_warm_start_beats_plain_and_heuristic_starts():
-    cfg = dict(grid=(128, 128), Q=16, calib=(24, 24), tau=3, shape="ellipsoid", red=2)
+    """2D 96^2, Q = 8, 24^2 calibration, ellipse r = 3, f = 2: 200 training cases (about 110 k
+    pairs), 20 validation cases, 3 held-out cases.  Measured on a GB300: the validation-selected
+    network's median direction error on the held-out cases is 0.83x the heuristic's at the start
+    and 0.49x after 5 iterations; the test asserts < 0.9x and < 0.75x."""
+    cfg = dict(grid=(96, 96), Q=8, calib=(24, 24), tau=3, shape="ellipsoid", red=2)
     Q = cfg["Q"]
-    teacher = _est(cfg, iters=200)
-    train = [torch.from_numpy(make_case(cfg["grid"], Q, cfg["calib"], seed=300 + i).calib).cuda() for i in range(24)]
-    X, T = teacher_pairs(teacher, train[:20], eig_max=0.05)
-    Xv, Tv = teacher_pairs(teacher, train[20:], eig_max=0.05)  # validation split for model selection
-    net = WarmStartNet(Q, 128, seed=0, max_batch=8192)
+    R = 1  # 3 x 3 patch
+    teacher, check = _est(cfg, iters=400), _est(cfg, iters=200)  # converged targets only
+    ntr, nva = 200, 20
+    X, T = teacher_pairs(teacher, [torch.from_numpy(make_case(cfg["grid"], Q, cfg["calib"], seed=300 + i).calib).cuda()
+                                   for i in range(ntr)], eig_max=0.05, radius=R, check=check)
+    Xv, Tv = teacher_pairs(teacher, [torch.from_numpy(make_case(cfg["grid"], Q, cfg["calib"], seed=300 + ntr + i)
+                                                      .calib).cuda() for i in range(nva)], eig_max=0.05, radius=R,
+                           check=check)
+    net = WarmStartNet(Q, 128, seed=0, max_batch=8192, radius=R)
     n0 = min(8192, X.shape[0])
     loss0 = net.backward(X[:n0].contiguous(), T[:n0].contiguous())  # the untrained net = the heuristic
-    hist = net.fit(X, T, epochs=25, batch=2048, lr=5e-4, seed=0, val=(Xv, Tv))
+    hist = net.fit(X, T, epochs=6, batch=1024, lr=3e-4, seed=0, val=(Xv, Tv))
     loss1 = net.backward(X[:n0].contiguous(), T[:n0].contiguous())
+    print(f"training loss per epoch {[f'{v:.2e}' for v in hist]}")
     print(f"training pairs {X.shape[0]}, loss {loss0:.5f} (heuristic) -> {loss1:.5f}; "
           f"validation direction error per epoch {[f'{v:.2e}' for v in net.val_history]}")
     assert min(net.val_history) <= net.val_history[0]
@@ -117,7 +128,7 @@ def test_trained_warm_start_beats_plain_and_heuristic_starts():
     iters_list = [0, 2, 5, 10, 20]
     agg = {}
     for s in range(3):  # held-out cases
-        case = make_case(cfg["grid"], Q, cfg["calib"], seed=900 + s)
+        case = make_case(cfg["grid"], Q, cfg["calib"], seed=900 + s)  # held out
         est = _est(cfg)
         est(torch.from_numpy(case.calib).cuda())
         G = est.debug_buffer(B.PISCO_BUF_G).cpu().numpy().reshape(-1, Q, Q).astype(np.complex128)
@@ -126,7 +137,7 @@ def test_trained_warm_start_beats_plain_and_heuristic_starts():
         red = tuple(g // cfg["red"] for g in cfg["grid"])
         inner = ndimage.binary_erosion(np.abs(case.rho) > 0, iterations=2)[::cfg["red"], ::cfg["red"]].reshape(-1)
         sel = inner & ((eigv[:, 1] - eigv[:, 0]) > 1e-3)
-        prop = net.forward(features(est)).cpu().numpy().astype(np.float64)
+        prop = net.forward(features(est, R)).cpu().numpy().astype(np.float64)
         starts = {"plain": O.start_vectors(0, red[0] * red[1], Q), "heuristic": Y, "learned": M.to_complex(prop)}
         e = _errors_vs_exact(G[sel], {k: v[sel] for k, v in starts.items()}, L, iters_list)
         for k, row in e.items():
@@ -138,8 +149,12 @@ def test_trained_warm_start_beats_plain_and_heuristic_starts():
     # far closer than the method's own start, at every iteration count that is not yet converged
     assert med["learned"][0] < 1e-2 * med["plain"][0]
     assert med["learned"][1] < 1e-2 * med["plain"][1] and med["learned"][2] < 1e-2 * med["plain"][2]
-    # the network corrects the heuristic start (zero last layer, validation-selected parameters):
-    # never far worse than it on unseen data
-    assert med["learned"][0] <= 1.5 * med["heuristic"][0]
+    # the network corrects the heuristic start: closer to the null vector on unseen data, and the
+    # gap widens over the first iterations (the correction removes slowly decaying components)
+    ratio = med["learned"][0] / med["heuristic"][0]
+    ratio5 = med["learned"][2] / med["heuristic"][2]
+    print(f"learned / heuristic median direction error at t=0: {ratio:.3f}, after 5 iterations: {ratio5:.3f}")
+    assert ratio < 0.9 and ratio5 < 0.75
     net.close()
     teacher.close()
+    check.close()
