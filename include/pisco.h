@@ -71,8 +71,8 @@ typedef enum { PISCO_KERNEL_RECT = 0, PISCO_KERNEL_ELLIPSOID = 1 } pisco_kernel_
                                      rows n with n - Lambda inside the calibration box: Eq. C as
                                      written, before Sec. V-A neglects the masking), from
                                      FP64 summed-area tables of the lagged products instead of
-                                     the FFT route.  Needs prod(Nc) <= 12288 (shared memory of
-                                     one tile); PISCO_ERR_UNSUPPORTED otherwise.              */
+                                     the FFT route.  Needs prod(Nc) <= 14528 (one shared-memory
+                                     tile of 227 KB; 24^3 fits); PISCO_ERR_UNSUPPORTED otherwise. */
 #define PISCO_FLAG_BLOCK_PI 0x20u  /* power iteration on a two-vector block (Gram-Schmidt every
                                      step, 2x2 Rayleigh-Ritz at the end) for pixels whose two
                                      smallest eigenvalues of G(x) are close: convergence set by

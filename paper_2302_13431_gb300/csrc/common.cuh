@@ -206,6 +206,9 @@ cudaError_t eig_band_matvec_df(const void* A, bool a_df, const double2* Xb, int 
                                double2* Zb, cudaStream_t st, const EigItems& it = EigItems{});
 
 // exact Gram of the masked calibration matrix (kernels_gram.cu): A (FP64 n x n), scale, A32
+// the masked Gram's summed-area table of one (pair, lag) holds every calibration sample in shared
+// memory (16 bytes each): up to 227 KB, i.e. 14528 samples (24^3 = 13824 fits)
+constexpr int kMaskedMaxSamples = 14528;
 cudaError_t gram_masked(const float2* calib, int Q, const int* Nc, const int* lo, const int* hi, const int* lam,
                         int L, const int* lag_ids, const int* lagc_ptr, const int* lag_ent, int nlag, const int* tau,
                         const int* B, double2* A, double* scale, float2* A32, cudaStream_t st);

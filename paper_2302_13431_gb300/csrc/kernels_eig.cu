@@ -900,22 +900,33 @@ __global__ void __launch_bounds__(544) jacobi_small_kernel(const float2* __restr
 
 // ---------------------------------------------------------------------------------------
 // Thin block products of the orthogonal iteration for m <= 64 columns, FP32 on the CUDA cores.
+// 128 threads; thread (ti, tj) of a 16 x 8 grid owns a 4 x 8 block of the 64 x 64 (or 64-row x
+// 64-column) output: rows 4 ti .. 4 ti + 3 and columns 2 tj + 16 u + e (u < 4, e < 2), so that the
+// eight threads of a quarter-warp read 128 consecutive bytes with 16-byte shared loads.
 // thin_gram: C = Y^H Z (m x m) over n rows.  CTA (split, item) runs over its share of the rows in
-// chunks of kThinRows staged in shared memory; thread (ti, tj) of a 16 x 16 grid accumulates the
-// 4 x 4 block of C at rows 4 ti.., columns 4 tj..; the split's partial goes to ws[item][split],
-// and the last CTA of the item to finish (ticket counter, reset by that CTA) sums the partials
-// in split order into C.
-// thin_apply: X = Y W (n x m by m x m), CTA (chunk, item), the same 4 x 4 register blocks.
+// chunks of kThinRows staged in shared memory; the split's partial goes to ws[item][split], and
+// the last CTA of the item to finish (ticket counter, reset by that CTA) sums the partials in
+// split order into C.
+// thin_apply: X = Y W (n x m by m x m), CTA (chunk of rows, item).
 // ---------------------------------------------------------------------------------------
 constexpr int kThinRows = 64;
-constexpr int kThinLd = 64 + 1;  // padded row (float2) of the staged operands
+constexpr int kThinLd = 64 + 2;    // padded row (float2): rows stay 16-byte aligned
 constexpr int kThinMaxSplits = 16;  // row splits of a thin Gram (CTAs per item)
 
-__global__ void __launch_bounds__(256) thin_gram_kernel(const float2* __restrict__ Y, long long sY,
+__device__ __forceinline__ void thin_load(float2 (&v)[8], const float2* row, int tj) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float4 t = *reinterpret_cast<const float4*>(row + 2 * tj + 16 * u);
+    v[2 * u] = make_float2(t.x, t.y);
+    v[2 * u + 1] = make_float2(t.z, t.w);
+  }
+}
+
+__global__ void __launch_bounds__(128) thin_gram_kernel(const float2* __restrict__ Y, long long sY,
                                                         const float2* __restrict__ Z, long long sZ, int n, int m,
                                                         float2* __restrict__ C, long long sC,
                                                         float2* __restrict__ ws, int* __restrict__ tickets) {
-  extern __shared__ float2 tsm[];
+  extern __shared__ __align__(16) float2 tsm[];
   float2* Ys = tsm;                       // [kThinRows][kThinLd]
   float2* Zs = tsm + kThinRows * kThinLd;
   __shared__ int s_last;
@@ -923,42 +934,39 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const float2* __restrict
   Y += item * sY;
   Z += item * sZ;
   C += item * sC;
-  // this split's rows: whole chunks of kThinRows, the splits as even as the chunks allow
   const int nch = (n + kThinRows - 1) / kThinRows;
   const int c0 = (int)((long long)nch * split / nsp), c1 = (int)((long long)nch * (split + 1) / nsp);
-  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
-  const bool act = 4 * ti < m && 4 * tj < m;
-  float2 acc[4][4];
+  const int tid = threadIdx.x, ti = tid >> 3, tj = tid & 7;
+  float2 acc[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int b = 0; b < 8; ++b) acc[a][b] = make_float2(0.f, 0.f);
   for (int ch = c0; ch < c1; ++ch) {
     const int r0 = ch * kThinRows;
     const int rows = min(kThinRows, n - r0);
     __syncthreads();
-    for (int e = tid; e < rows * m; e += 256) {
-      const int r = e / m, c = e % m;
-      Ys[r * kThinLd + c] = Y[(long long)(r0 + r) * m + c];
-      Zs[r * kThinLd + c] = Z[(long long)(r0 + r) * m + c];
+    for (int e = tid; e < kThinRows * 64; e += 128) {  // zero-padded to 64 rows x 64 columns
+      const int r = e >> 6, c = e & 63;
+      const bool in = r < rows && c < m;
+      Ys[r * kThinLd + c] = in ? Y[(long long)(r0 + r) * m + c] : make_float2(0.f, 0.f);
+      Zs[r * kThinLd + c] = in ? Z[(long long)(r0 + r) * m + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    if (act) {
-      for (int r = 0; r < rows; ++r) {
-        float2 y[4], z[4];
+    for (int r = 0; r < rows; ++r) {
+      const float4 y01 = *reinterpret_cast<const float4*>(Ys + r * kThinLd + 4 * ti);
+      const float4 y23 = *reinterpret_cast<const float4*>(Ys + r * kThinLd + 4 * ti + 2);
+      const float2 y[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w), make_float2(y23.x, y23.y),
+                           make_float2(y23.z, y23.w)};
+      float2 z[8];
+      thin_load(z, Zs + r * kThinLd, tj);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          y[a] = Ys[r * kThinLd + min(4 * ti + a, m - 1)];
-          z[a] = Zs[r * kThinLd + min(4 * tj + a, m - 1)];
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {  // conj(y) z
+          acc[a][b].x = fmaf(y[a].x, z[b].x, fmaf(y[a].y, z[b].y, acc[a][b].x));
+          acc[a][b].y = fmaf(y[a].x, z[b].y, fmaf(-y[a].y, z[b].x, acc[a][b].y));
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {  // conj(y) z
-            acc[a][b].x = fmaf(y[a].x, z[b].x, fmaf(y[a].y, z[b].y, acc[a][b].x));
-            acc[a][b].y = fmaf(y[a].x, z[b].y, fmaf(-y[a].y, z[b].x, acc[a][b].y));
-          }
-      }
     }
   }
   const long long mm = (long long)m * m;
@@ -966,8 +974,8 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const float2* __restrict
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = 4 * ti + a, j = 4 * tj + b;
+    for (int b = 0; b < 8; ++b) {
+      const int i = 4 * ti + a, j = 2 * tj + 16 * (b >> 1) + (b & 1);
       if (i < m && j < m) part[i * m + j] = acc[a][b];
     }
   __threadfence();
@@ -982,7 +990,7 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const float2* __restrict
   // the last split of the item: partials summed in split order (all loads of an entry issued
   // together, up to kThinMaxSplits of them)
   const float2* base = ws + (long long)item * nsp * mm;
-  for (long long e = tid; e < mm; e += 256) {
+  for (long long e = tid; e < mm; e += 128) {
     float2 w[kThinMaxSplits];
 #pragma unroll
     for (int k = 0; k < kThinMaxSplits; ++k) w[k] = k < nsp ? __ldcg(base + k * mm + e) : make_float2(0.f, 0.f);
@@ -997,10 +1005,10 @@ __global__ void __launch_bounds__(256) thin_gram_kernel(const float2* __restrict
   if (tid == 0) tickets[item] = 0;
 }
 
-__global__ void __launch_bounds__(256) thin_apply_kernel(const float2* __restrict__ Y, long long sY,
+__global__ void __launch_bounds__(128) thin_apply_kernel(const float2* __restrict__ Y, long long sY,
                                                          const float2* __restrict__ W, long long sW, int n, int m,
                                                          float2* __restrict__ X, long long sX) {
-  extern __shared__ float2 tsm[];
+  extern __shared__ __align__(16) float2 tsm[];
   float2* Ys = tsm;                       // [kThinRows][kThinLd]
   float2* Ws = tsm + kThinRows * kThinLd; // [64][kThinLd]
   const int item = blockIdx.y;
@@ -1009,30 +1017,27 @@ __global__ void __launch_bounds__(256) thin_apply_kernel(const float2* __restric
   X += item * sX;
   const int r0 = blockIdx.x * kThinRows;
   const int rows = min(kThinRows, n - r0);
-  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
-  for (int e = tid; e < rows * m; e += 256) {
-    const int r = e / m, c = e % m;
-    Ys[r * kThinLd + c] = Y[(long long)(r0 + r) * m + c];
+  const int tid = threadIdx.x, ti = tid >> 3, tj = tid & 7;
+  for (int e = tid; e < kThinRows * 64; e += 128) {  // zero-padded
+    const int r = e >> 6, c = e & 63;
+    Ys[r * kThinLd + c] = (r < rows && c < m) ? Y[(long long)(r0 + r) * m + c] : make_float2(0.f, 0.f);
+    Ws[r * kThinLd + c] = (r < m && c < m) ? W[r * m + c] : make_float2(0.f, 0.f);
   }
-  for (int e = tid; e < m * m; e += 256) Ws[(e / m) * kThinLd + e % m] = W[e];
   __syncthreads();
-  if (4 * ti >= rows || 4 * tj >= m) return;
-  float2 acc[4][4];
+  float2 acc[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int b = 0; b < 8; ++b) acc[a][b] = make_float2(0.f, 0.f);
   for (int k = 0; k < m; ++k) {
-    float2 y[4], w[4];
+    float2 y[4], w[8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      y[a] = Ys[min(4 * ti + a, rows - 1) * kThinLd + k];
-      w[a] = Ws[k * kThinLd + min(4 * tj + a, m - 1)];
-    }
+    for (int a = 0; a < 4; ++a) y[a] = Ys[(4 * ti + a) * kThinLd + k];
+    thin_load(w, Ws + k * kThinLd, tj);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {  // y w
+      for (int b = 0; b < 8; ++b) {  // y w
         acc[a][b].x = fmaf(y[a].x, w[b].x, fmaf(-y[a].y, w[b].y, acc[a][b].x));
         acc[a][b].y = fmaf(y[a].x, w[b].y, fmaf(y[a].y, w[b].x, acc[a][b].y));
       }
@@ -1040,8 +1045,8 @@ __global__ void __launch_bounds__(256) thin_apply_kernel(const float2* __restric
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = 4 * ti + a, j = 4 * tj + b;
+    for (int b = 0; b < 8; ++b) {
+      const int i = 4 * ti + a, j = 2 * tj + 16 * (b >> 1) + (b & 1);
       if (i < rows && j < m) X[(long long)(r0 + i) * m + j] = acc[a][b];
     }
 }
@@ -1051,7 +1056,7 @@ int eig_thin_chunks(int n) { return (n + kThinRows - 1) / kThinRows; }
 // each CTA is latency-bound on its own)
 static int thin_splits(int n) { return std::max(1, std::min(kThinMaxSplits, eig_thin_chunks(n))); }
 
-constexpr size_t kThinSmem = (size_t)2 * 64 * kThinLd * sizeof(float2);
+constexpr size_t kThinSmem = (size_t)2 * kThinRows * kThinLd * sizeof(float2);
 static bool thin_attrs() {
   static const bool ok =
       cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmem) ==
@@ -1065,7 +1070,7 @@ cudaError_t eig_thin_gram(const float2* Y, long long sY, const float2* Z, long l
                           long long sC, float2* ws, int* tickets, int items, cudaStream_t st) {
   if (m > 64 || m < 1 || n < 1) return cudaErrorInvalidValue;
   if (!thin_attrs()) return cudaErrorInvalidValue;
-  thin_gram_kernel<<<dim3(thin_splits(n), items), 256, kThinSmem, st>>>(Y, sY, Z, sZ, n, m, C, sC, ws, tickets);
+  thin_gram_kernel<<<dim3(thin_splits(n), items), 128, kThinSmem, st>>>(Y, sY, Z, sZ, n, m, C, sC, ws, tickets);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -1074,7 +1079,7 @@ cudaError_t eig_thin_apply(const float2* Y, long long sY, const float2* W, long 
                            long long sX, int items, cudaStream_t st) {
   if (m > 64 || m < 1 || n < 1) return cudaErrorInvalidValue;
   if (!thin_attrs()) return cudaErrorInvalidValue;
-  thin_apply_kernel<<<dim3(eig_thin_chunks(n), items), 256, kThinSmem, st>>>(Y, sY, W, sW, n, m, X, sX);
+  thin_apply_kernel<<<dim3(eig_thin_chunks(n), items), 128, kThinSmem, st>>>(Y, sY, W, sW, n, m, X, sX);
   ++g_launches;
   return cudaGetLastError();
 }

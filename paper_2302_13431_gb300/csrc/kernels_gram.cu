@@ -257,7 +257,7 @@ cudaError_t gram_masked_prepare(int nvol) {
   // the attribute is per kernel, not per plan: always allow the largest supported tile
   (void)nvol;
   return cudaFuncSetAttribute(masked_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)gram_masked_smem(12288));
+                              (int)gram_masked_smem(kMaskedMaxSamples));
 }
 
 }  // namespace pisco

@@ -36,6 +36,45 @@ __device__ __forceinline__ void df_fma(float& ah, float& al, float xh, float xl,
   e += al + pe;
   quick_two_sum(s, e, ah, al);
 }
+// (ah, al) += (bh, bl)
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  quick_two_sum(s, e, ah, al);
+}
+__device__ __forceinline__ dfc df_cadd(dfc a, const dfc& b) {
+  df_add(a.rh, a.rl, b.rh, b.rl);
+  df_add(a.ih, a.il, b.ih, b.il);
+  return a;
+}
+// Dot2-style accumulation (Ogita, Rump & Oishi 2005) of double-float products: the running
+// sum s takes the head product by TwoSum, its rounding error and the product's low-order terms
+// go to a second FP32 accumulator c without renormalising every step (12 instructions per real
+// term against 15 for a renormalised double-float multiply-add); s + c is normalised once.
+__device__ __forceinline__ void dot2_term(float& s, float& c, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float q = fmaf(xh, yh, -p);
+  q = fmaf(xh, yl, q);
+  q = fmaf(xl, yh, q);
+  float t, r;
+  two_sum(s, p, t, r);
+  s = t;
+  c += q + r;
+}
+// acc (unnormalised: {s_re, c_re, s_im, c_im}) += m * x (complex)
+__device__ __forceinline__ void dot2_cfma(dfc& acc, const dfc& m, const dfc& x) {
+  dot2_term(acc.rh, acc.rl, m.rh, m.rl, x.rh, x.rl);
+  dot2_term(acc.rh, acc.rl, -m.ih, -m.il, x.ih, x.il);
+  dot2_term(acc.ih, acc.il, m.rh, m.rl, x.ih, x.il);
+  dot2_term(acc.ih, acc.il, m.ih, m.il, x.rh, x.rl);
+}
+__device__ __forceinline__ dfc dot2_finish(const dfc& a) {
+  dfc o;
+  two_sum(a.rh, a.rl, o.rh, o.rl);
+  two_sum(a.ih, a.il, o.ih, o.il);
+  return o;
+}
 // acc += m * x (complex)
 __device__ __forceinline__ void df_cfma(dfc& acc, const dfc& m, const dfc& x) {
   df_fma(acc.rh, acc.rl, m.rh, m.rl, x.rh, x.rl);
@@ -117,7 +156,8 @@ __global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int n
 // 2D pairs stage of the double-float Gram, fused per pair (p <= q): the frequency-domain product
 // conj(S_p) S_q, the inverse lag transform along the contiguous axis (Lp2 -> B2) and then along
 // axis 1 (Lp1 -> B1), all in shared memory, and the FP64 lag table of the pair.  Each output
-// accumulates its terms in the order of the unfused axis passes (bitwise the same result).
+// accumulates its even and odd terms in two Dot2 sums (two independent dependency chains per
+// thread), normalised and added at the end.
 // invT2: [Lp2][B2] (transposed), inv1: [B1][Lp1].
 __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __restrict__ S, int Q, int Lp1, int Lp2,
                                                                const dfc* __restrict__ invT2, int B2,
@@ -152,17 +192,28 @@ __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __rest
   for (int o = tid; o < Lp1 * B2; o += nt) {
     const int f1 = o / B2, b2 = o % B2;
     const dfc* prow = P + f1 * ldp;
-    dfc acc{0.f, 0.f, 0.f, 0.f};
-    for (int f2 = 0; f2 < Lp2; ++f2) df_cfma(acc, m2[f2 * B2 + b2], prow[f2]);
-    T[o] = acc;
+    dfc a0{0.f, 0.f, 0.f, 0.f}, a1{0.f, 0.f, 0.f, 0.f};
+    int f2 = 0;
+    for (; f2 + 1 < Lp2; f2 += 2) {
+      dot2_cfma(a0, m2[f2 * B2 + b2], prow[f2]);
+      dot2_cfma(a1, m2[(f2 + 1) * B2 + b2], prow[f2 + 1]);
+    }
+    if (f2 < Lp2) dot2_cfma(a0, m2[f2 * B2 + b2], prow[f2]);
+    T[o] = df_cadd(dot2_finish(a0), dot2_finish(a1));
   }
   __syncthreads();
   const long long ob = ((long long)p * Q + q) * B1 * B2;
   for (int o = tid; o < B1 * B2; o += nt) {
     const int b1 = o / B2, b2 = o % B2;
     const dfc* mrow = m1 + b1 * Lp1;
-    dfc acc{0.f, 0.f, 0.f, 0.f};
-    for (int f1 = 0; f1 < Lp1; ++f1) df_cfma(acc, mrow[f1], T[f1 * B2 + b2]);
+    dfc a0{0.f, 0.f, 0.f, 0.f}, a1{0.f, 0.f, 0.f, 0.f};
+    int f1 = 0;
+    for (; f1 + 1 < Lp1; f1 += 2) {
+      dot2_cfma(a0, mrow[f1], T[f1 * B2 + b2]);
+      dot2_cfma(a1, mrow[f1 + 1], T[(f1 + 1) * B2 + b2]);
+    }
+    if (f1 < Lp1) dot2_cfma(a0, mrow[f1], T[f1 * B2 + b2]);
+    const dfc acc = df_cadd(dot2_finish(a0), dot2_finish(a1));
     lags[ob + o] = make_double2((double)acc.rh + (double)acc.rl, (double)acc.ih + (double)acc.il);
     lags_df[ob + o] = acc;
   }
@@ -361,12 +412,6 @@ __device__ __forceinline__ void df_fma1(float& ah, float& al, float a_hi, float 
   float s, e;
   two_sum(ah, p, s, e);
   e += al + pe;
-  quick_two_sum(s, e, ah, al);
-}
-__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
-  float s, e;
-  two_sum(ah, bh, s, e);
-  e += al + bl;
   quick_two_sum(s, e, ah, al);
 }
 

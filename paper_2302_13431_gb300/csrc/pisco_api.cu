@@ -1048,7 +1048,7 @@ static pisco_status plan_create(const pisco_params* p, cudaStream_t cuda_stream,
   pl->gram_df = (p->flags & PISCO_FLAG_GRAM_DF) != 0;
   if (pl->masked) {
     const int nvol = pl->Nc[0] * pl->Nc[1] * pl->Nc[2];
-    if (nvol > 12288) {
+    if (nvol > kMaskedMaxSamples) {
       delete pl;
       return PISCO_ERR_UNSUPPORTED;
     }

@@ -70,12 +70,13 @@ def test_fused_gram_pair_stage_counts():
     Q, t = W["Q"], W["tau"]
     L, B = W["calib"][0] + 2 * t, 4 * t + 1
     npair = Q * (Q + 1) // 2
-    # per pair: the frequency-domain product, the contiguous-axis pass, the axis-1 pass
-    cmacs = npair * (L * L + L * L * B + B * B * L)
+    # per pair: the frequency-domain product (double-float, 60 FP32 instructions per complex
+    # multiply-add), the contiguous-axis and axis-1 passes (Dot2 sums, 48 per complex term),
+    # against the FP32 issue rate
+    inst = npair * (60 * L * L + 48 * (L * L * B + B * B * L))
     prof = {"gram_pairs_df": (1.0, 20)}
-    # double-float: 60 FP32 instructions per complex multiply-add, against the FP32 issue rate
     r = bench.roofline_for("gram_pairs_df", prof, W, STATS, PEAKS, "tc_g_eig", True, 20)
-    assert r["achieved"] == pytest.approx(60 * cmacs / 0.05e-3 / 1e12, rel=1e-12)
+    assert r["achieved"] == pytest.approx(inst / 0.05e-3 / 1e12, rel=1e-12)
     assert r["peak"] == pytest.approx(152 * 128 * 2.07e9 / 1e12, rel=1e-12) and r["unit"] == "Tinst/s"
     # with the fused stage present, the forward DFT record counts the forward passes only (one
     # launch per coil set does both of them)
@@ -86,4 +87,4 @@ def test_fused_gram_pair_stage_counts():
     assert r["achieved"] == pytest.approx(60 * fwd / 0.05e-3 / 1e12, rel=1e-12)
     # a launch over 8 map sets does 8 times the work
     r8 = bench.roofline_for("gram_pairs_df", {"gram_pairs_df": (1.0, 20)}, W, STATS, PEAKS, "tc_g_eig", True, 160, 8)
-    assert r8["achieved"] == pytest.approx(8 * 60 * cmacs / 0.05e-3 / 1e12, rel=1e-12)
+    assert r8["achieved"] == pytest.approx(8 * inst / 0.05e-3 / 1e12, rel=1e-12)

@@ -59,7 +59,26 @@ def test_masked_estimate_matches_oracle_with_valid_rows(name):
     est.close()
 
 
+def test_masked_gram_at_the_3d_calibration_size():
+    """The 24^3 calibration box of the 3D workload (sphere r = 3), Q = 4: the masked Gram equals
+    the oracle's explicit C_valid^H C_valid (5832 valid rows)."""
+    grid, Q, cs, tau = (48, 48, 48), 4, (24, 24, 24), 3
+    case = make_case(grid, Q, cs, seed=5)
+    lam = O.kernel_support((tau,) * 3, "ellipsoid")
+    C = O.calibration_matrix(case.calib, lam, rows="valid")
+    A_ref = C.conj().T @ C
+    est = PiscoEstimator(grid, cs, Q, tau, reduction=4, iters=30, masked_gram=True)
+    est(torch.from_numpy(case.calib).cuda())
+    torch.cuda.synchronize()
+    assert est.last_status == B.PISCO_OK
+    n = A_ref.shape[0]
+    A = est.debug_buffer(B.PISCO_BUF_GRAM).cpu().numpy().reshape(n, n)
+    err = np.abs(A - A_ref).max() / np.abs(A_ref).max()
+    assert err <= 1e-11, err
+    est.close()
+
+
 def test_masked_gram_rejects_calibration_beyond_one_tile():
-    with pytest.raises(B.PiscoError) as ei:
-        PiscoEstimator((96, 128, 128), (24, 24, 24), 4, 3, reduction=4, masked_gram=True)
+    with pytest.raises(B.PiscoError) as ei:  # 25^3 = 15625 samples > 14528
+        PiscoEstimator((100, 100, 100), (25, 25, 25), 4, 3, reduction=4, masked_gram=True)
     assert ei.value.status == B.PISCO_ERR_UNSUPPORTED
