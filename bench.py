@@ -213,10 +213,16 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
-# DRAM bytes (read + write) per launch of each op's main kernel on the 2D 256x256 Q=32
-# workload, from one ncu --set full capture (cold caches); an op whose kernel changed since
-# its capture has no entry
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per map set of one launch of each op's main kernel on the 2D 256x256
+# Q=32 workload, from one ncu --set full capture of a 16-map-set group (cold caches; the traffic
+# of these kernels grows in proportion to the map sets a launch covers, so a launch of g map sets
+# is reported as g times this); an op whose kernel changed since its capture has no entry
+NCU_TRAFFIC = {
+    "power_iteration": ((553.688832e6 + 17.805056e6) / 16, "profiles/power_iteration_2d_256x256_q32_batch16.md"),
+    "gram_pairs_df": ((11.86304e6 + 1.903104e6) / 16, "profiles/gram_pairs_df_2d_256x256_q32_batch16.md"),
+    "eig_gemm_AX": ((112.17536e6 + 3.384064e6) / 16, "profiles/tc2_ax_2d_256x256_q32_batch16.md"),
+    "interp_rows_tc": ((67.679488e6 + 207.202048e6) / 16, "profiles/tc2_interp_rows_2d_256x256_q32_batch16.md"),
+}
 
 
 def n_lags(w):
@@ -419,8 +425,10 @@ def run_gpu(args):
     if args.launch_config:
         tuned = dict(tuned, **json.loads(args.launch_config))
     elif args.tune:
+        # the batched form as one group: every stage one launch over the step's map sets (the
+        # autotuner tunes the other knobs; chains of one plan per map set are not tried here)
         from paper_2302_13431_gb300.autotune import tune
-        tuned, tune_table = tune([spec] * nb, calibs=bcal)
+        tuned, tune_table = tune([spec] * nb, calibs=bcal, refine=(("tc_interp", True),))
     # ---- plain FP32 PISCO, one plan, one map per call (per-slice launches): comparison point ----
     maps1 = torch.empty((w["Q"],) + w["grid"], dtype=torch.complex64, device="cuda")
     eig1 = torch.empty(red, dtype=torch.float32, device="cuda")
@@ -536,9 +544,9 @@ def run_gpu(args):
     roof.pop("ms_per_step", None)
     roof["kernel"] = dom
     tr = NCU_TRAFFIC.get(dom) if w is WORKLOAD else None
-    roof["traffic"] = tr[0] if tr else None
+    roof["traffic"] = tr[0] * groups["largest"] if tr else None
     if tr:
-        roof["traffic_source"] = tr[1]
+        roof["traffic_source"] = f"{tr[1]} (per map set x {groups['largest']} map sets per launch)"
     roof["measured"] = (f"CUDA events around each launch of the op in eager runs of the timed batch configuration "
                         f"({groups['groups']} group(s), largest {groups['largest']} map sets per launch)")
 
@@ -793,9 +801,9 @@ def run_gpu_3d(args):
         for k, ((c, inner), r) in enumerate(zip(evals, ref)):
             est.estimate_into(c, maps, eig)
             if k == 0:  # against the oracle's exact null vectors at the sampled pixels
-                V = est.debug_buffer(B.PISCO_BUF_V).cpu().numpy().reshape(w["Q"], -1).T[idx][osel]
+                V = est.debug_buffer(B.PISCO_BUF_V).cpu().numpy().reshape(w["Q"], -1).T[idx][osel].astype(np.complex128)
                 cs = np.abs(np.sum(np.conj(V) * v_exact, axis=1)) / np.linalg.norm(V, axis=1)
-                dir_err = 1.0 - cs
+                dir_err = np.maximum(1.0 - cs, 0.0)
                 lam_err = float(np.abs(eig.cpu().numpy().reshape(-1)[idx][osel] - lam_exact).max())
             a = maps.cpu().numpy().reshape(w["Q"], -1).T
             b = r.reshape(w["Q"], -1).T

@@ -100,12 +100,15 @@ def _time_batch(specs, calibs, steps, warmup, ref=None):
         batch.close()
 
 
-def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None, refresh=False, verbose=False):
+def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None, refresh=False, verbose=False,
+         refine=None):
     """Best configuration (dict of KNOB_KEYS) for the batch `specs` (PiscoBatch spec dicts).
 
-    calibs: device calibration tensors (synthetic ones are generated when None).  Returns
+    calibs: device calibration tensors (synthetic ones are generated when None).  refine: the
+    (knob, value) toggles tried on the best candidate of the sweep (default REFINE).  Returns
     (config, table) where table lists every candidate with its milliseconds per batch step."""
-    key = _shape_key(specs)
+    refine = REFINE if refine is None else tuple(refine)
+    key = _shape_key(specs) + ("" if refine == REFINE else "|refine=" + json.dumps(refine))
     db = {}
     if cache and os.path.exists(cache):
         try:
@@ -134,7 +137,7 @@ def tune(specs, calibs=None, steps=3, warmup=2, cache=DEFAULT_CACHE, cands=None,
         raise RuntimeError("autotune: no candidate passed the correctness gate: " + repr(table))
     best = min(ok, key=lambda r: r["ms"])
     if cands is None:
-        for knob, val in REFINE:
+        for knob, val in refine:
             c = {k: best[k] for k in KNOB_KEYS}
             if c[knob] == val:
                 continue

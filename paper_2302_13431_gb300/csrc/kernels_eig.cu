@@ -798,17 +798,21 @@ __global__ void __launch_bounds__(544) jacobi_small_kernel(const float2* __restr
     }
   };
   const int gmax = max_sweeps * rounds;
+  const int nwv = nt / 32 - 1;  // warps updating V
   if (warp == 0 && gmax > 0) rotations(0);
+  // this thread's block (i <= j) of the two-sided update, fixed for the whole solve
+  const bool has_blk = tid < nblk;
+  const int bi = has_blk ? blk[2 * tid] : 0, bj = has_blk ? blk[2 * tid + 1] : 0;
   __syncthreads();
   int g = 0;
   for (; g < gmax; ++g) {
     const int buf = g & 1, r = g % rounds;
     const unsigned char* sp = sched + 2 * r * half;
     // (1) B <- J^H B J on the blocks i <= j, mirrored
-    for (int e = tid; e < nblk; e += nt) {
-      const int i = blk[2 * e], j = blk[2 * e + 1];
+    if (has_blk) {
+      const int i = bi, j = bj;
       const int ai = act[buf][i], aj = act[buf][j];
-      if (!ai && !aj) continue;
+      if (ai || aj) {
       const int pi = sp[2 * i], qi = sp[2 * i + 1], pj = sp[2 * j], qj = sp[2 * j + 1];
       float2 x00 = Bs[pi * kJs + pj], x01 = Bs[pi * kJs + qj], x10 = Bs[qi * kJs + pj], x11 = Bs[qi * kJs + qj];
       if (ai) {  // rows: r0 = c x0 + se x1, r1 = -conj(se) x0 + c x1
@@ -842,6 +846,7 @@ __global__ void __launch_bounds__(544) jacobi_small_kernel(const float2* __restr
         Bs[pj * kJs + qi] = make_float2(x10.x, -x10.y);
         Bs[qj * kJs + qi] = make_float2(x11.x, -x11.y);
       }
+      }
     }
     __syncthreads();
     // (2) warp 0: the next round's rotations (after a sweep, the stop test); warps 1..: V <- V J
@@ -863,15 +868,17 @@ __global__ void __launch_bounds__(544) jacobi_small_kernel(const float2* __restr
         rotations(gn);
       }
     } else {
-      for (int e = tid - 32; e < m * half; e += nt - 32) {
-        const int k = e / half, j = e % half;
-        if (!act[buf][j]) continue;
+      // lane = pair (its rotation read once per round), warps 1.. step through the rows
+      const int j = lane;
+      if (j < half && act[buf][j]) {
         const int pj = sp[2 * j], qj = sp[2 * j + 1];
         const float c = rc[buf][j][0];
         const float2 se = make_float2(rc[buf][j][1], rc[buf][j][2]);
-        const float2 xp = Vw[k * m + pj], xq = Vw[k * m + qj];
-        Vw[k * m + pj] = make_float2(c * xp.x + se.x * xq.x + se.y * xq.y, c * xp.y + se.x * xq.y - se.y * xq.x);
-        Vw[k * m + qj] = make_float2(-(se.x * xp.x - se.y * xp.y) + c * xq.x, -(se.x * xp.y + se.y * xp.x) + c * xq.y);
+        for (int k = warp - 1; k < m; k += nwv) {
+          const float2 xp = Vw[k * m + pj], xq = Vw[k * m + qj];
+          Vw[k * m + pj] = make_float2(c * xp.x + se.x * xq.x + se.y * xq.y, c * xp.y + se.x * xq.y - se.y * xq.x);
+          Vw[k * m + qj] = make_float2(-(se.x * xp.x - se.y * xp.y) + c * xq.x, -(se.x * xp.y + se.y * xp.x) + c * xq.y);
+        }
       }
     }
     __syncthreads();
