@@ -800,6 +800,7 @@ def run_gpu_3d(args):
         errs, fb = [], []
         for k, ((c, inner), r) in enumerate(zip(evals, ref)):
             est.estimate_into(c, maps, eig)
+            torch.cuda.synchronize()
             if k == 0:  # against the oracle's exact null vectors at the sampled pixels
                 V = est.debug_buffer(B.PISCO_BUF_V).cpu().numpy().reshape(w["Q"], -1).T[idx][osel].astype(np.complex128)
                 cs = np.abs(np.sum(np.conj(V) * v_exact, axis=1)) / np.linalg.norm(V, axis=1)
