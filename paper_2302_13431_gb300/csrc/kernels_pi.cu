@@ -33,8 +33,10 @@ __device__ __forceinline__ float pixel_sum(float v, float* red, int xi, int q) {
 // the counter-based start; a residual gate that flags pixels whose final residual
 // ||G v - lambda |Lambda| v|| / |Lambda| exceeds `gate`; and a fallback pass that re-solves
 // only the flagged pixels (CTAs without one exit at once; the others write flagged pixels only).
+// (up to 32 coils: at most 85 registers a thread, so that three CTAs share an SM; the G column
+// takes 64 of them)
 template <int QP>
-__global__ void __launch_bounds__(256) pi_kernel(const float2* __restrict__ G,
+__global__ void __launch_bounds__(256, QP <= 32 ? 3 : 1) pi_kernel(const float2* __restrict__ G,
                                                  const float2* __restrict__ Y, int Q,
                                                  long long npix, int iters, float lam_size,
                                                  unsigned long long seed, float2* __restrict__ V,
