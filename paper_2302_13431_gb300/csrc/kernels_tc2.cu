@@ -371,6 +371,255 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
   }
 }
 
+// Row-tile persistent form of the converting, row-grouped product, for K2 <= 128 (one 128-row
+// tile of A fits shared memory whole): a CTA loads its A tile once by TMA and splits it in place
+// (head) and beside it (tail), then runs over every 64-column tile of C, B' streamed through a
+// two-stage ring, the accumulator double-buffered in TMEM (2 x 128 columns) so that the epilogue
+// of one column tile overlaps the MMAs of the next.  CTAs loop over row tiles (grid <= SM count).
+// Warps: 0 producer, 1 MMA issuer, 2-3 converters, 4-7 epilogue (TMEM lane quarter = warp - 4).
+// Epilogue: each warp's 32 rows; the per-pixel norm over groups of rg rows (8 <= rg <= 32, so a
+// group never leaves its warp) through a per-warp shared tile; the stores go through the same
+// tile transposed, so a store instruction writes two 128-byte runs of one output row each.
+namespace rows {
+constexpr int KSMAX = 4;                               // K steps of 32 real columns: K2 <= 128
+constexpr int S = 2;                                   // B' ring stages
+constexpr uint32_t BT = 2 * B_TILE;                    // one 64-column B' tile (head or tail)
+constexpr uint32_t RSTAGE = 2 * BT;                    // head + tail
+constexpr uint32_t AT_OFF = KSMAX * A_TILE;            // A tails (heads in place of the FP32 tile)
+constexpr uint32_t R_OFF = 2 * KSMAX * A_TILE;
+constexpr uint32_t STG_OFF = R_OFF + S * RSTAGE;       // per warp: [32][17] float2, or [32][33] float
+constexpr uint32_t STG_WARP = 32 * 17 * 8;
+constexpr uint32_t SCL_OFF = STG_OFF + 4 * STG_WARP;   // per warp: [32 / rg][32] scales
+constexpr uint32_t BAR_OFF = SCL_OFF + 4 * 128 * 4;
+// afull, aconv, aempty, done, bfull[S], bempty[S], accf[2], acce[2]
+constexpr int NBAR = 4 + 2 * S + 4;
+constexpr uint32_t TOTAL = BAR_OFF + NBAR * 8 + 16;
+constexpr uint32_t TMEM_COLS = 256;
+static_assert(4 * STG_WARP >= 4 * 32 * 33 * 4, "norm tile exceeds the staging tile");
+}  // namespace rows
+
+__global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant__ CUtensorMap tA,
+                                                          const __grid_constant__ CUtensorMap tBh,
+                                                          const __grid_constant__ CUtensorMap tBl, Args g) {
+  using namespace rows;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = su32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gb = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gb + BAR_OFF);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + BAR_OFF + NBAR * 8);
+  const uint32_t afull = su32(&bars[0]), aconv = su32(&bars[1]), aempty = su32(&bars[2]), done = su32(&bars[3]);
+  const uint32_t bfull0 = su32(&bars[4]), bempty0 = su32(&bars[4 + S]);
+  const uint32_t accf0 = su32(&bars[4 + 2 * S]), acce0 = su32(&bars[6 + 2 * S]);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ks = (g.K2 + BK - 1) / BK;
+  const int nct = (g.N + 63) / 64;
+  const int ntiles = (g.M + BM - 1) / BM;
+  const long long lim = g.wait_limit;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    bar_init(afull, 1);
+    bar_init(aconv, 64);
+    bar_init(aempty, 1);
+    bar_init(done, 1);
+    for (int s = 0; s < S; ++s) {
+      bar_init(bfull0 + 8 * s, 1);
+      bar_init(bempty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      bar_init(accf0 + 8 * b, 1);
+      bar_init(acce0 + 8 * b, 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0 && !g.no_loads) {
+      // producer: per row tile, the whole A tile (after the previous tile's MMAs have retired),
+      // then B' head and tail of every (column tile, K step) into the ring
+      int it = 0, na = 0;
+      for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
+        if (na > 0 && !(ok = bar_wait(aempty, (uint32_t)((na - 1) & 1), lim))) break;
+        bar_expect_tx(afull, (uint32_t)ks * A_TILE);
+        for (int kk = 0; kk < ks; ++kk) tma_2d(base + kk * A_TILE, &tA, kk * BK, rt * BM, afull);
+        ++na;
+        for (int ct = 0; ct < nct && ok; ++ct) {
+          for (int kk = 0; kk < ks; ++kk) {
+            const int s = it % S, c = it / S;
+            if (it >= S && !(ok = bar_wait(bempty0 + 8 * s, (uint32_t)((c - 1) & 1), lim))) break;
+            const uint32_t fb = bfull0 + 8 * s, sb = base + R_OFF + s * RSTAGE;
+            bar_expect_tx(fb, RSTAGE);
+            tma_2d(sb, &tBh, kk * BK, 128 * ct, fb);
+            tma_2d(sb + BT, &tBl, kk * BK, 128 * ct, fb);
+            ++it;
+          }
+        }
+      }
+      // every load this thread issued has landed before the CTA may exit (bounded)
+      for (int j = it - S > 0 ? it - S : 0; j < it; ++j) bar_wait(bfull0 + 8 * (j % S), (uint32_t)((j / S) & 1), lim);
+      if (na > 0) bar_wait(afull, (uint32_t)((na - 1) & 1), lim);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: 4 x 3 MMAs (N = 128, K = 8) per (column tile, K step) into TMEM buffer tc & 1
+      int it = 0, tc = 0, na = 0;
+      bool issued = false;
+      for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
+        if (!(ok = bar_wait(aconv, (uint32_t)(na & 1), lim))) break;
+        ++na;
+        fence_after();
+        for (int ct = 0; ct < nct && ok; ++ct) {
+          const int b = tc & 1, u = tc >> 1;
+          if (tc >= 2 && !(ok = bar_wait(acce0 + 8 * b, (uint32_t)((u - 1) & 1), lim))) break;
+          fence_after();
+          const uint32_t d = tmem + 128u * b;
+          for (int kk = 0; kk < ks; ++kk) {
+            const int s = it % S, c = it / S;
+            if (!(ok = bar_wait(bfull0 + 8 * s, (uint32_t)(c & 1), lim))) break;
+            fence_after();
+            const uint32_t sa = base + kk * A_TILE, sb = base + R_OFF + s * RSTAGE;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint64_t ah = desc_sw128(sa + 32 * j), bh = desc_sw128(sb + 32 * j);
+              mma<2>(d, ah, bh, (kk > 0 || j > 0) ? 1u : 0u);
+              mma<2>(d, ah, desc_sw128(sb + BT + 32 * j), 1u);
+              mma<2>(d, desc_sw128(sa + AT_OFF + 32 * j), bh, 1u);
+            }
+            issued = true;
+            commit(bempty0 + 8 * s);
+            ++it;
+          }
+          if (!ok) break;
+          commit(accf0 + 8 * b);
+          ++tc;
+        }
+        if (!ok) break;
+        commit(aempty);
+      }
+      if (issued) {  // every MMA retired before TMEM is freed (bounded)
+        commit(done);
+        bar_wait(done, 0, lim);
+      }
+    }
+  } else if (warp < 4) {
+    // converters: FP32 A tile -> TF32 head (in place) and tail (beside it), same swizzled offsets
+    const int ct = tid - 64;
+    int na = 0;
+    for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
+      if (!(ok = bar_wait(afull, (uint32_t)(na & 1), lim))) break;
+      ++na;
+      float4* a = reinterpret_cast<float4*>(gb);
+      float4* t = reinterpret_cast<float4*>(gb + AT_OFF);
+      const int n4 = ks * (int)(A_TILE / 16);
+#pragma unroll 4
+      for (int e = ct; e < n4; e += 64) {
+        const float4 v = a[e];
+        const float4 h = make_float4(head(v.x), head(v.y), head(v.z), head(v.w));
+        a[e] = h;
+        t[e] = make_float4(head(v.x - h.x), head(v.y - h.y), head(v.z - h.z), head(v.w - h.w));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aconv) : "memory");
+    }
+  } else {
+    // epilogue: rows 32 (warp - 4) + lane of the tile; waits are made warp-uniform, so the
+    // warp-collective TMEM loads run in every lane or in none
+    const int qw = warp - 4;
+    float* sq = reinterpret_cast<float*>(gb + STG_OFF + qw * STG_WARP);     // [32][33] |v|^2
+    float2* stg = reinterpret_cast<float2*>(gb + STG_OFF + qw * STG_WARP);  // [32][17] values
+    float* scl = reinterpret_cast<float*>(gb + SCL_OFF) + qw * 128;         // [32 / rg][32]
+    const int rg = g.rg;
+    const bool norm = g.rg_norm != 0;
+    int tc = 0;
+    for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
+      const int gm = rt * BM + 32 * qw + lane;
+      float2* rowp = nullptr;
+      if (gm < g.M) {
+        const int item = gm / g.rg_rows, rem = gm % g.rg_rows;
+        rowp = (g.c_tab ? g.c_tab[item] : g.C + (long long)item * g.c_stride) + (long long)(rem % rg) * g.rg_plane +
+               (long long)(rem / rg) * g.ldc;
+      }
+      for (int ct = 0; ct < nct && ok; ++ct) {
+        const int b = tc & 1, u = tc >> 1;
+        ok = __all_sync(0xffffffffu, bar_wait(accf0 + 8 * b, (uint32_t)(u & 1), lim));
+        if (!ok) break;
+        fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(32 * qw) << 16) + 128u * b;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          uint32_t re[32], im[32];
+          tmem_ld32(ta + 64 * h, re);
+          tmem_ld32(ta + 64 * h + 32, im);
+          if (h == 1) {  // both halves read: the buffer is free for the column tile after next
+            fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
+          }
+          const int x0 = 64 * ct + 32 * h;
+          if (x0 >= g.N) continue;
+          if (norm) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              const float x = __uint_as_float(re[c]), y = __uint_as_float(im[c]);
+              sq[lane * 33 + c] = fmaf(x, x, y * y);
+            }
+            __syncwarp();
+            for (int gi = 0; gi < 32 / rg; ++gi) {
+              float n2 = 0.f;
+              for (int r = 0; r < rg; ++r) n2 += sq[(gi * rg + r) * 33 + lane];
+              scl[gi * 32 + lane] = n2 > 0.f ? rsqrtf(n2) : 0.f;
+            }
+            __syncwarp();
+            const float* sc = scl + (lane / rg) * 32;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              const float f = sc[c];
+              re[c] = __float_as_uint(__uint_as_float(re[c]) * f);
+              im[c] = __float_as_uint(__uint_as_float(im[c]) * f);
+            }
+          }
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              stg[lane * 17 + j] = make_float2(__uint_as_float(re[16 * hh + j]), __uint_as_float(im[16 * hh + j]));
+            __syncwarp();
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+              const int rr = 2 * i + (lane >> 4), col = lane & 15;
+              float2* p = reinterpret_cast<float2*>(
+                  __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rowp), rr));
+              const int x = x0 + 16 * hh + col;
+              if (p != nullptr && x < g.N) __stcs(p + x, stg[rr * 17 + col]);
+            }
+            __syncwarp();
+          }
+        }
+        ++tc;
+      }
+    }
+  }
+  __syncwarp();
+  if (!ok && g.err) atomicOr(g.err, 16);
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 // C = alpha * sum_z ws[z] + beta * C (+ diag), partials summed in z order; grid y = batch item
 // (its partials at ws + item * splits * M * N, its C at C + item * c_stride)
 __global__ void splitk_reduce_kernel(const float2* __restrict__ ws, int splits, int M, int N, float2 alpha,
@@ -534,8 +783,23 @@ static void launch(dim3 grid, cudaStream_t st, const CUtensorMap& a, const CUten
   tc2_kernel<NT, S, CONV, WT><<<grid, CONV ? 256 : 128, smem_bytes<NT, S, CONV, WT>(), st>>>(a, al, b, bl, g);
 }
 
+int sm_count() {
+  static std::atomic<int> n{0};
+  int v = n.load();
+  if (v <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v <= 0)
+      v = 1;
+    n.store(v);
+  }
+  return v;
+}
+
 cudaError_t tc2_prepare() {
-  cudaError_t e = set_smem<3, 3, false, 2>();
+  cudaError_t e = cudaFuncSetAttribute(tc2_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(rows::TOTAL + 1024));
+  if (e == cudaSuccess) e = set_smem<3, 3, false, 2>();
   if (e == cudaSuccess) e = set_smem<3, 2, false, 1>();
   if (e == cudaSuccess) e = set_smem<1, 4, false, 2>();
   if (e == cudaSuccess) e = set_smem<1, 2, false, 1>();
@@ -605,7 +869,10 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   // A loads per output) and 3-4 stages; short ones 32 columns and 2 stages, 2 CTAs per SM, so one
   // CTA's epilogue overlaps another's loads.
   const bool wide = kpb > 8;
-  const int wt = wide ? 2 : 1;
+  // row-grouped products whose A tile fits shared memory whole (K2 <= 128) and whose pixel groups
+  // stay within a warp (8 <= rg <= 32 when normalised): the row-tile persistent kernel
+  const bool rows_res = conv && rg > 0 && K2 > 0 && K2 <= rows::KSMAX * BK && (!rg_norm || (rg >= 8 && rg <= 32));
+  const int wt = (wide || rows_res) ? 2 : 1;
   if (!encode_2d(&mBh, Bhi, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC * wt) ||
       !encode_2d(&mBl, bl, kcols, 2 * Np * (b_per_item ? nbatch : 1), K2p, 2 * BNC * wt))
     return cudaErrorInvalidValue;
@@ -620,6 +887,12 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   g.splits = splits;
   g.no_loads = g_tc2_stall.load() ? 1 : 0;
   g.wait_limit = g.no_loads ? kWaitStalled : kWait;
+  if (rows_res) {
+    const int ntiles = (M + BM - 1) / BM, nsm = sm_count();
+    tc2_rows_kernel<<<ntiles < nsm ? ntiles : nsm, 256, rows::TOTAL + 1024, st>>>(mAh, mBh, mBl, g);
+    ++g_launches;
+    return cudaGetLastError();
+  }
   dim3 grid((Np + BNC * wt - 1) / (BNC * wt), (M + BM - 1) / BM, nbatch * splits);
   if (conv) {
     if (wide) launch<3, 3, true, 2>(grid, st, mAh, mAl, mBh, mBl, g);

@@ -33,6 +33,9 @@ CASES = {
     "2d_q33": ((48, 48), 33, (20, 20), 2, "ellipsoid", 2, 20, "poly4"),
     "3d_small": ((16, 24, 20), 4, (10, 12, 10), 2, "ellipsoid", 2, 30, "poly4"),
     "2d_256_q32": ((256, 256), 32, (32, 32), 3, "ellipsoid", 4, 30, "poly4"),
+    # fused per-pixel normalisation over 16 / 8 coil rows; ragged row and column tiles
+    "2d_q16": ((64, 80), 16, (20, 20), 2, "ellipsoid", 2, 30, "poly4"),
+    "2d_q8": ((72, 96), 8, (24, 24), 2, "ellipsoid", 4, 30, "poly4"),
 }
 _cache = {}
 
@@ -324,7 +327,7 @@ def test_double_float_gram_matches_explicit_CtC_and_maps(name):
 
 
 # ---- the last interpolation pass on the tensor cores (PISCO_FLAG_TC_INTERP) --------------------
-@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32"])
+@pytest.mark.parametrize("name", ["2d_small_rect", "2d_ragged", "3d_small", "2d_q33", "2d_256_q32", "2d_q16", "2d_q8"])
 def test_tensor_core_interpolation_matches_oracle_and_fp32_route(name):
     """maps_q = M T_q as one batched split-TF32 GEMM, then the per-pixel normalisation: the same
     map gate as the FP32 route, and within 1e-5 of the FP32 route's maps on the gated pixels.
