@@ -18,10 +18,13 @@
 // still frees its TMEM.
 //
 // A variant (CONV) reads A as plain FP32 complex rows instead of split arrays: TMA brings the
-// FP32 tile into the stage, two converter warps split it in shared memory into the TF32 head and
-// tail tiles (the same arithmetic and the same swizzled positions as the split kernels), make the
-// writes visible to the tensor core's async proxy and release the stage to the MMA thread.  A then
-// crosses HBM at 8 instead of 16 bytes per complex entry, and needs no separate split pass.
+// FP32 tile into the stage, four converter warps (one per TMEM lane quarter) read one row each,
+// split it into TF32 head and tail (the arithmetic of the split kernels) and store both into
+// tensor memory, from where the MMAs read A (lane = row, K along the columns).  A then crosses HBM
+// at 8 instead of 16 bytes per complex entry and needs no separate split pass, and the split A
+// takes no shared memory: the tensor core reads only B from shared memory, the converters read
+// the FP32 tile once and write nothing there (the stage ring is bound by shared-memory bandwidth
+// otherwise).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
@@ -93,6 +96,14 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
       "l"(a), "l"(b), "r"(idesc<WT>()), "r"(acc)
       : "memory");
 }
+// A from tensor memory (lane = row of A, K in consecutive 32-bit columns), B from shared memory
+template <int WT>
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc<WT>()), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void commit(uint32_t b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
 }
@@ -108,6 +119,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ float4 ld_shared_f4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
 }
 
 __device__ __forceinline__ float head(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
@@ -142,9 +170,12 @@ struct Args {
 
 template <int NT, bool CONV, int WT>
 __host__ __device__ constexpr uint32_t stage_bytes() {
-  // split operands: [A head][A tail][B head][B tail]; CONV: [A fp32, then its tail][A head][B head][B tail]
-  return (NT == 3 || CONV ? 2u : 1u) * (A_TILE + WT * B_TILE);
+  // split operands: [A head][A tail][B head][B tail]; CONV: [A fp32][B head][B tail] (the split A
+  // goes to tensor memory)
+  return CONV ? A_TILE + 2u * WT * B_TILE : (NT == 3 ? 2u : 1u) * (A_TILE + WT * B_TILE);
 }
+
+__host__ __device__ constexpr uint32_t pow2_cols(uint32_t n) { return n <= 32 ? 32 : 2 * pow2_cols((n + 1) / 2); }
 
 // One CTA: a 128 x (32 WT) complex tile of C, accumulated in 64 WT TMEM columns (columns
 // 64h .. 64h+31 hold Re, 64h+32 .. 64h+63 Im of the complex columns 32h .. 32h+31).
@@ -159,13 +190,15 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
                              128u * (BNC * WT + 1) * 8u + 128u * BNC * WT * 4u + 128u * 8u,
                 "row-group epilogue exceeds the ring");
   constexpr uint32_t STAGE = stage_bytes<NT, CONV, WT>();
-  constexpr uint32_t A_HEAD = CONV ? A_TILE : 0u;            // A head / tail within a stage
-  constexpr uint32_t A_TAIL = CONV ? 0u : A_TILE;
-  constexpr uint32_t B_OFF = (NT == 3 || CONV) ? 2u * A_TILE : A_TILE;
+  constexpr uint32_t A_TAIL = A_TILE;                        // split A: head at 0, tail here
+  constexpr uint32_t B_OFF = CONV ? A_TILE : (NT == 3 ? 2u : 1u) * A_TILE;
   constexpr uint32_t BT = WT * B_TILE;                      // B head (tail) bytes per stage
-  constexpr uint32_t TMEM_COLS = 64 * WT;
-  // warps: 0 producer, 1 MMA issuer, the rest (2-3, or 2-7 converting) converters; warps 0-3
-  // read the accumulator (TMEM lane quarter = warp), all of them share the epilogue
+  constexpr uint32_t ACC_COLS = 64 * WT;
+  // CONV: the split A of stage s in TMEM columns ACC_COLS + 64 s (head) and + 32 (tail)
+  constexpr uint32_t TMEM_COLS = CONV ? pow2_cols(ACC_COLS + 64 * STAGES) : ACC_COLS;
+  static_assert(TMEM_COLS <= 512, "tensor memory holds 512 columns");
+  // warps: 0 producer, 1 MMA issuer, (CONV) 4-7 converters (TMEM lane quarter = warp - 4);
+  // warps 0-3 read the accumulator (TMEM lane quarter = warp), all of them share the epilogue
   constexpr int NTHR = CONV ? 256 : 128, NWARP = NTHR / 32;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
@@ -197,7 +230,7 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
     for (int s = 0; s < STAGES; ++s) {
       bar_init(full0 + 8 * s, 1);
       bar_init(empty0 + 8 * s, 1);
-      if (CONV) bar_init(conv0 + 8 * s, NTHR - 64);  // the converter warps
+      if (CONV) bar_init(conv0 + 8 * s, 128);  // the converter warps
     }
     bar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -229,25 +262,33 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
       tma_2d(sb, &tBh, kx, brow0 + 2 * n0, fb);
       if (NT == 3) tma_2d(sb + BT, &tBl, kx, brow0 + 2 * n0, fb);
     }
-  } else if (CONV && warp >= 2 && nk > 0) {
-    // converters: FP32 tile -> TF32 head (own slot) and tail (in place), same swizzled offsets
-    const int ct = tid - 64;
+  } else if (CONV && warp >= 4 && nk > 0) {
+    // converters: row r of the FP32 tile (128-byte swizzled: 16-byte chunk ch of row r at chunk
+    // ch ^ (r & 7)) -> TF32 head and tail in TMEM lane r, K in consecutive columns; the waits are
+    // warp-uniform, so the warp-collective TMEM stores run in every lane or in none
+    const int q = warp - 4, r = 32 * q + lane;
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + ACC_COLS;
     for (int i = 0; i < nk && ok; ++i) {
       const int s = i % STAGES, c = i / STAGES;
-      ok = bar_wait(full0 + 8 * s, (uint32_t)(c & 1), g.wait_limit);
+      ok = __all_sync(0xffffffffu, bar_wait(full0 + 8 * s, (uint32_t)(c & 1), g.wait_limit));
       if (!ok) break;
-      unsigned char* sp = gbase + (size_t)s * STAGE;
-      const float4* src = reinterpret_cast<const float4*>(sp);
-      float4* hd = reinterpret_cast<float4*>(sp + A_HEAD);
-      float4* tl = reinterpret_cast<float4*>(sp + A_TAIL);
-#pragma unroll 4
-      for (int e = ct; e < (int)(A_TILE / 16); e += NTHR - 64) {
-        const float4 v = src[e];
-        const float4 h = make_float4(head(v.x), head(v.y), head(v.z), head(v.w));
-        hd[e] = h;
-        tl[e] = make_float4(head(v.x - h.x), head(v.y - h.y), head(v.z - h.z), head(v.w - h.w));
+      const uint32_t row = base + s * STAGE + r * 128;
+      uint32_t hd[32], tl[32];
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        const float4 v = ld_shared_f4(row + ((uint32_t)(ch ^ (r & 7)) << 4));
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float h = head(e[u]);
+          hd[4 * ch + u] = __float_as_uint(h);
+          tl[4 * ch + u] = __float_as_uint(head(e[u] - h));
+        }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tmem_st32(tq + 64 * s, hd);
+      tmem_st32(tq + 64 * s + 32, tl);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      fence_before();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(conv0 + 8 * s) : "memory");
     }
   } else if (warp == 1 && lane == 0 && nk > 0) {
@@ -261,11 +302,19 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
       const uint32_t sb = st + B_OFF;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const uint64_t ah = desc_sw128(st + A_HEAD + 32 * j), bh = desc_sw128(sb + 32 * j);
-        mma<WT>(tmem, ah, bh, (i > 0 || j > 0) ? 1u : 0u);
-        if (NT == 3) {
-          mma<WT>(tmem, ah, desc_sw128(sb + BT + 32 * j), 1u);
-          mma<WT>(tmem, desc_sw128(st + A_TAIL + 32 * j), bh, 1u);
+        const uint64_t bh = desc_sw128(sb + 32 * j);
+        if (CONV) {
+          const uint32_t ah = tmem + ACC_COLS + 64 * s + 8 * j;
+          mma_ts<WT>(tmem, ah, bh, (i > 0 || j > 0) ? 1u : 0u);
+          mma_ts<WT>(tmem, ah, desc_sw128(sb + BT + 32 * j), 1u);
+          mma_ts<WT>(tmem, ah + 32, bh, 1u);
+        } else {
+          const uint64_t ah = desc_sw128(st + 32 * j);
+          mma<WT>(tmem, ah, bh, (i > 0 || j > 0) ? 1u : 0u);
+          if (NT == 3) {
+            mma<WT>(tmem, ah, desc_sw128(sb + BT + 32 * j), 1u);
+            mma<WT>(tmem, desc_sw128(st + A_TAIL + 32 * j), bh, 1u);
+          }
         }
       }
       commit(empty0 + 8 * s);
@@ -803,8 +852,8 @@ cudaError_t tc2_prepare() {
   if (e == cudaSuccess) e = set_smem<3, 2, false, 1>();
   if (e == cudaSuccess) e = set_smem<1, 4, false, 2>();
   if (e == cudaSuccess) e = set_smem<1, 2, false, 1>();
-  if (e == cudaSuccess) e = set_smem<3, 3, true, 2>();
-  if (e == cudaSuccess) e = set_smem<3, 2, true, 1>();
+  if (e == cudaSuccess) e = set_smem<3, 4, true, 2>();
+  if (e == cudaSuccess) e = set_smem<3, 3, true, 1>();
   return e;
 }
 
@@ -866,8 +915,8 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
     return cudaErrorInvalidValue;
   }
   // long K loops (> 8 steps per CTA) take 64 complex columns per CTA (one N = 128 MMA: half the
-  // A loads per output) and 3-4 stages; short ones 32 columns and 2 stages, 2 CTAs per SM, so one
-  // CTA's epilogue overlaps another's loads.
+  // A loads per output) and 3-4 stages; short ones 32 columns and 2-3 stages, 2 CTAs per SM, so
+  // one CTA's epilogue overlaps another's loads.
   const bool wide = kpb > 8;
   // row-grouped products whose A tile fits shared memory whole (K2 <= 128) and whose pixel groups
   // stay within a warp (8 <= rg <= 32 when normalised): the row-tile persistent kernel
@@ -895,8 +944,8 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   }
   dim3 grid((Np + BNC * wt - 1) / (BNC * wt), (M + BM - 1) / BM, nbatch * splits);
   if (conv) {
-    if (wide) launch<3, 3, true, 2>(grid, st, mAh, mAl, mBh, mBl, g);
-    else launch<3, 2, true, 1>(grid, st, mAh, mAl, mBh, mBl, g);
+    if (wide) launch<3, 4, true, 2>(grid, st, mAh, mAl, mBh, mBl, g);
+    else launch<3, 3, true, 1>(grid, st, mAh, mAl, mBh, mBl, g);
   }
   else if (nterms == 1) {
     if (wide) launch<1, 4, false, 2>(grid, st, mAh, mAl, mBh, mBl, g);
