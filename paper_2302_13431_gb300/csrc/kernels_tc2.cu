@@ -186,10 +186,10 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
                                                      const __grid_constant__ CUtensorMap tBl, Args g) {
   static_assert(!CONV || NT == 3, "the converting variant splits A into head and tail");
   static_assert(STAGES * stage_bytes<NT, CONV, WT>() >= 128u * (BNC * WT + 1) * 8u, "epilogue tile exceeds the ring");
-  static_assert(!CONV || STAGES * stage_bytes<NT, CONV, WT>() >=
-                             128u * (BNC * WT + 1) * 8u + 128u * BNC * WT * 4u + 128u * 8u,
-                "row-group epilogue exceeds the ring");
   constexpr uint32_t STAGE = stage_bytes<NT, CONV, WT>();
+  // the row-group epilogue keeps scales and row offsets beside the tile: converting variants whose
+  // ring holds all three (the host launches row-grouped products on those only)
+  constexpr bool RG_OK = CONV && STAGES * STAGE >= 128u * (BNC * WT + 1) * 8u + 128u * BNC * WT * 4u + 128u * 8u;
   constexpr uint32_t A_TAIL = A_TILE;                        // split A: head at 0, tail here
   constexpr uint32_t B_OFF = CONV ? A_TILE : (NT == 3 ? 2u : 1u) * A_TILE;
   constexpr uint32_t BT = WT * B_TILE;                      // B head (tail) bytes per stage
@@ -353,7 +353,11 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  if (g.rg > 0) {
+  if (g.rg > 0 && !RG_OK) {
+    if (tid == 0 && g.err) atomicOr(g.err, 16);
+    return;
+  }
+  if (RG_OK && g.rg > 0) {
     float* scl = reinterpret_cast<float*>(gbase + (size_t)BM * TS * sizeof(float2));  // [BM / rg][32 WT]
     long long* rowoff = reinterpret_cast<long long*>(scl + BM * BNC * WT);                // [BM]
     if (tid < BM) {  // each thread places one row: (item, y, q) -> offset from the item's output
@@ -852,7 +856,7 @@ cudaError_t tc2_prepare() {
   if (e == cudaSuccess) e = set_smem<3, 2, false, 1>();
   if (e == cudaSuccess) e = set_smem<1, 4, false, 2>();
   if (e == cudaSuccess) e = set_smem<1, 2, false, 1>();
-  if (e == cudaSuccess) e = set_smem<3, 4, true, 2>();
+  if (e == cudaSuccess) e = set_smem<3, 2, true, 2>();
   if (e == cudaSuccess) e = set_smem<3, 3, true, 1>();
   return e;
 }
@@ -915,9 +919,11 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
     return cudaErrorInvalidValue;
   }
   // long K loops (> 8 steps per CTA) take 64 complex columns per CTA (one N = 128 MMA: half the
-  // A loads per output) and 3-4 stages; short ones 32 columns and 2-3 stages, 2 CTAs per SM, so
-  // one CTA's epilogue overlaps another's loads.
-  const bool wide = kpb > 8;
+  // A loads per output): split operands 3-4 stages, converting 2 stages at 2 CTAs per SM (one
+  // CTA's conversions and loads fill the other's gaps on the tensor pipe); short ones 32 columns
+  // and 2-3 stages, 2 CTAs per SM, so one CTA's epilogue overlaps another's loads.  Row-grouped
+  // products take the 32-column form.
+  const bool wide = kpb > 8 && rg == 0;
   // row-grouped products whose A tile fits shared memory whole (K2 <= 128) and whose pixel groups
   // stay within a warp (8 <= rg <= 32 when normalised): the row-tile persistent kernel
   const bool rows_res = conv && rg > 0 && K2 > 0 && K2 <= rows::KSMAX * BK && (!rg_norm || (rg >= 8 && rg <= 32));
@@ -944,7 +950,7 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   }
   dim3 grid((Np + BNC * wt - 1) / (BNC * wt), (M + BM - 1) / BM, nbatch * splits);
   if (conv) {
-    if (wide) launch<3, 4, true, 2>(grid, st, mAh, mAl, mBh, mBl, g);
+    if (wide) launch<3, 2, true, 2>(grid, st, mAh, mAl, mBh, mBl, g);
     else launch<3, 3, true, 1>(grid, st, mAh, mAl, mBh, mBl, g);
   }
   else if (nterms == 1) {
