@@ -425,35 +425,40 @@ __global__ void __launch_bounds__(CONV ? 256 : 128, 1) tc2_kernel(const __grid_c
 }
 
 // Row-tile persistent form of the converting, row-grouped product, for K2 <= 128 (one 128-row
-// tile of A fits shared memory whole): a CTA loads its A tile once by TMA and splits it in place
-// (head) and beside it (tail), then runs over every 64-column tile of C, B' streamed through a
-// two-stage ring, the accumulator double-buffered in TMEM (2 x 128 columns) so that the epilogue
-// of one column tile overlaps the MMAs of the next.  CTAs loop over row tiles (grid <= SM count).
-// Warps: 0 producer, 1 MMA issuer, 2-3 converters, 4-7 epilogue (TMEM lane quarter = warp - 4).
-// Epilogue: each warp's 32 rows; the per-pixel norm over groups of rg rows (8 <= rg <= 32, so a
-// group never leaves its warp) through a per-warp shared tile; the stores go through the same
-// tile transposed, so a store instruction writes two 128-byte runs of one output row each.
+// tile of A covers the whole K): a CTA loads its A tile by TMA, four converter warps split it into
+// TF32 head and tail in tensor memory (lane = row, K along the columns, one barrier per K step so
+// the MMAs start on the first), and the CTA runs over every 64-column tile of C with B' streamed
+// through a four-stage ring and the accumulator double-buffered in TMEM (2 x 128 columns), so the
+// epilogue of one column tile overlaps the MMAs of the next.  The FP32 A buffer is refilled with
+// the next row tile as soon as it is converted; CTAs loop over row tiles (grid <= SM count).
+// Warps: 0 producer, 1 MMA issuer, 4-7 epilogue (TMEM lane quarter = warp - 4), 8-11 converters
+// (lane quarter = warp - 8).  Epilogue: each warp's 32 rows; the per-pixel norm over groups of rg
+// rows (8 <= rg <= 32, so a group never leaves its warp) through a per-warp shared tile; the
+// stores go through the same tile transposed, so a store instruction writes two 128-byte runs of
+// one output row each.
 namespace rows {
 constexpr int KSMAX = 4;                               // K steps of 32 real columns: K2 <= 128
-constexpr int S = 2;                                   // B' ring stages
+constexpr int S = 4;                                   // B' ring stages
+constexpr int NTHR = 384;
 constexpr uint32_t BT = 2 * B_TILE;                    // one 64-column B' tile (head or tail)
 constexpr uint32_t RSTAGE = 2 * BT;                    // head + tail
-constexpr uint32_t AT_OFF = KSMAX * A_TILE;            // A tails (heads in place of the FP32 tile)
-constexpr uint32_t R_OFF = 2 * KSMAX * A_TILE;
+constexpr uint32_t R_OFF = KSMAX * A_TILE;             // after the FP32 A tile
 constexpr uint32_t STG_OFF = R_OFF + S * RSTAGE;       // per warp: [32][17] float2, or [32][33] float
 constexpr uint32_t STG_WARP = 32 * 17 * 8;
 constexpr uint32_t SCL_OFF = STG_OFF + 4 * STG_WARP;   // per warp: [32 / rg][32] scales
 constexpr uint32_t BAR_OFF = SCL_OFF + 4 * 128 * 4;
-// afull, aconv, aempty, done, bfull[S], bempty[S], accf[2], acce[2]
-constexpr int NBAR = 4 + 2 * S + 4;
+// afull, araw, aempty, done, aconv[KSMAX], bfull[S], bempty[S], accf[2], acce[2]
+constexpr int NBAR = 4 + KSMAX + 2 * S + 4;
 constexpr uint32_t TOTAL = BAR_OFF + NBAR * 8 + 16;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 512;                    // accumulators 0 / 128, split A from 256
+constexpr uint32_t A_COL = 256;
 static_assert(4 * STG_WARP >= 4 * 32 * 33 * 4, "norm tile exceeds the staging tile");
+static_assert(A_COL + 64 * KSMAX <= TMEM_COLS, "split A exceeds tensor memory");
 }  // namespace rows
 
-__global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant__ CUtensorMap tA,
-                                                          const __grid_constant__ CUtensorMap tBh,
-                                                          const __grid_constant__ CUtensorMap tBl, Args g) {
+__global__ void __launch_bounds__(rows::NTHR, 1) tc2_rows_kernel(const __grid_constant__ CUtensorMap tA,
+                                                                 const __grid_constant__ CUtensorMap tBh,
+                                                                 const __grid_constant__ CUtensorMap tBl, Args g) {
   using namespace rows;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
@@ -461,9 +466,9 @@ __global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant_
   unsigned char* gb = smem_raw + (base - raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(gb + BAR_OFF);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gb + BAR_OFF + NBAR * 8);
-  const uint32_t afull = su32(&bars[0]), aconv = su32(&bars[1]), aempty = su32(&bars[2]), done = su32(&bars[3]);
-  const uint32_t bfull0 = su32(&bars[4]), bempty0 = su32(&bars[4 + S]);
-  const uint32_t accf0 = su32(&bars[4 + 2 * S]), acce0 = su32(&bars[6 + 2 * S]);
+  const uint32_t afull = su32(&bars[0]), araw = su32(&bars[1]), aempty = su32(&bars[2]), done = su32(&bars[3]);
+  const uint32_t aconv0 = su32(&bars[4]), bfull0 = su32(&bars[4 + KSMAX]), bempty0 = su32(&bars[4 + KSMAX + S]);
+  const uint32_t accf0 = su32(&bars[4 + KSMAX + 2 * S]), acce0 = su32(&bars[6 + KSMAX + 2 * S]);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ks = (g.K2 + BK - 1) / BK;
   const int nct = (g.N + 63) / 64;
@@ -478,9 +483,10 @@ __global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant_
   }
   if (tid == 0) {
     bar_init(afull, 1);
-    bar_init(aconv, 64);
+    bar_init(araw, 128);
     bar_init(aempty, 1);
     bar_init(done, 1);
+    for (int k = 0; k < KSMAX; ++k) bar_init(aconv0 + 8 * k, 128);
     for (int s = 0; s < S; ++s) {
       bar_init(bfull0 + 8 * s, 1);
       bar_init(bempty0 + 8 * s, 1);
@@ -499,11 +505,11 @@ __global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant_
 
   if (warp == 0) {
     if (lane == 0 && !g.no_loads) {
-      // producer: per row tile, the whole A tile (after the previous tile's MMAs have retired),
-      // then B' head and tail of every (column tile, K step) into the ring
+      // producer: per row tile, the FP32 A tile (once the previous one is converted), then B'
+      // head and tail of every (column tile, K step) into the ring
       int it = 0, na = 0;
       for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
-        if (na > 0 && !(ok = bar_wait(aempty, (uint32_t)((na - 1) & 1), lim))) break;
+        if (na > 0 && !(ok = bar_wait(araw, (uint32_t)((na - 1) & 1), lim))) break;
         bar_expect_tx(afull, (uint32_t)ks * A_TILE);
         for (int kk = 0; kk < ks; ++kk) tma_2d(base + kk * A_TILE, &tA, kk * BK, rt * BM, afull);
         ++na;
@@ -525,13 +531,11 @@ __global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant_
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer: 4 x 3 MMAs (N = 128, K = 8) per (column tile, K step) into TMEM buffer tc & 1
+      // MMA issuer: 4 x 3 MMAs (N = 128, K = 8, A from TMEM) per (column tile, K step) into
+      // accumulator buffer tc & 1
       int it = 0, tc = 0, na = 0;
       bool issued = false;
-      for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
-        if (!(ok = bar_wait(aconv, (uint32_t)(na & 1), lim))) break;
-        ++na;
-        fence_after();
+      for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x, ++na) {
         for (int ct = 0; ct < nct && ok; ++ct) {
           const int b = tc & 1, u = tc >> 1;
           if (tc >= 2 && !(ok = bar_wait(acce0 + 8 * b, (uint32_t)((u - 1) & 1), lim))) break;
@@ -539,15 +543,16 @@ __global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant_
           const uint32_t d = tmem + 128u * b;
           for (int kk = 0; kk < ks; ++kk) {
             const int s = it % S, c = it / S;
+            if (ct == 0 && !(ok = bar_wait(aconv0 + 8 * kk, (uint32_t)(na & 1), lim))) break;
             if (!(ok = bar_wait(bfull0 + 8 * s, (uint32_t)(c & 1), lim))) break;
             fence_after();
-            const uint32_t sa = base + kk * A_TILE, sb = base + R_OFF + s * RSTAGE;
+            const uint32_t sb = base + R_OFF + s * RSTAGE, ta = tmem + A_COL + 64 * kk;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              const uint64_t ah = desc_sw128(sa + 32 * j), bh = desc_sw128(sb + 32 * j);
-              mma<2>(d, ah, bh, (kk > 0 || j > 0) ? 1u : 0u);
-              mma<2>(d, ah, desc_sw128(sb + BT + 32 * j), 1u);
-              mma<2>(d, desc_sw128(sa + AT_OFF + 32 * j), bh, 1u);
+              const uint64_t bh = desc_sw128(sb + 32 * j);
+              mma_ts<2>(d, ta + 8 * j, bh, (kk > 0 || j > 0) ? 1u : 0u);
+              mma_ts<2>(d, ta + 8 * j, desc_sw128(sb + BT + 32 * j), 1u);
+              mma_ts<2>(d, ta + 32 + 8 * j, bh, 1u);
             }
             issued = true;
             commit(bempty0 + 8 * s);
@@ -558,34 +563,48 @@ __global__ void __launch_bounds__(256, 1) tc2_rows_kernel(const __grid_constant_
           ++tc;
         }
         if (!ok) break;
-        commit(aempty);
+        commit(aempty);  // the split A of this row tile may be overwritten once these retire
       }
       if (issued) {  // every MMA retired before TMEM is freed (bounded)
         commit(done);
         bar_wait(done, 0, lim);
       }
     }
-  } else if (warp < 4) {
-    // converters: FP32 A tile -> TF32 head (in place) and tail (beside it), same swizzled offsets
-    const int ct = tid - 64;
+  } else if (warp >= 8) {
+    // converters: row r of the FP32 tile (128-byte swizzled: 16-byte chunk ch of row r at chunk
+    // ch ^ (r & 7)) -> TF32 head and tail in TMEM lane r; waits warp-uniform, so the
+    // warp-collective TMEM stores run in every lane or in none
+    const int q = warp - 8, r = 32 * q + lane;
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + A_COL;
     int na = 0;
-    for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x) {
-      if (!(ok = bar_wait(afull, (uint32_t)(na & 1), lim))) break;
-      ++na;
-      float4* a = reinterpret_cast<float4*>(gb);
-      float4* t = reinterpret_cast<float4*>(gb + AT_OFF);
-      const int n4 = ks * (int)(A_TILE / 16);
-#pragma unroll 4
-      for (int e = ct; e < n4; e += 64) {
-        const float4 v = a[e];
-        const float4 h = make_float4(head(v.x), head(v.y), head(v.z), head(v.w));
-        a[e] = h;
-        t[e] = make_float4(head(v.x - h.x), head(v.y - h.y), head(v.z - h.z), head(v.w - h.w));
+    for (int rt = blockIdx.x; rt < ntiles && ok; rt += gridDim.x, ++na) {
+      ok = __all_sync(0xffffffffu, bar_wait(afull, (uint32_t)(na & 1), lim));
+      if (ok && na > 0) ok = __all_sync(0xffffffffu, bar_wait(aempty, (uint32_t)((na - 1) & 1), lim));
+      if (!ok) break;
+      fence_after();
+      for (int kk = 0; kk < ks; ++kk) {
+        const uint32_t row = base + kk * A_TILE + r * 128;
+        uint32_t hd[32], tl[32];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          const float4 v = ld_shared_f4(row + ((uint32_t)(ch ^ (r & 7)) << 4));
+          const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float h = head(e[u]);
+            hd[4 * ch + u] = __float_as_uint(h);
+            tl[4 * ch + u] = __float_as_uint(head(e[u] - h));
+          }
+        }
+        tmem_st32(tq + 64 * kk, hd);
+        tmem_st32(tq + 64 * kk + 32, tl);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aconv0 + 8 * kk) : "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aconv) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(araw) : "memory");  // FP32 tile read
     }
-  } else {
+  } else if (warp >= 4) {
     // epilogue: rows 32 (warp - 4) + lane of the tile; waits are made warp-uniform, so the
     // warp-collective TMEM loads run in every lane or in none
     const int qw = warp - 4;
@@ -944,7 +963,7 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   g.wait_limit = g.no_loads ? kWaitStalled : kWait;
   if (rows_res) {
     const int ntiles = (M + BM - 1) / BM, nsm = sm_count();
-    tc2_rows_kernel<<<ntiles < nsm ? ntiles : nsm, 256, rows::TOTAL + 1024, st>>>(mAh, mBh, mBl, g);
+    tc2_rows_kernel<<<ntiles < nsm ? ntiles : nsm, rows::NTHR, rows::TOTAL + 1024, st>>>(mAh, mBh, mBl, g);
     ++g_launches;
     return cudaGetLastError();
   }
