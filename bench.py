@@ -220,8 +220,8 @@ def run_reference(args):
 NCU_TRAFFIC = {
     "power_iteration": ((553.688832e6 + 17.805056e6) / 16, "profiles/power_iteration_2d_256x256_q32_batch16.md"),
     "gram_pairs_df": ((11.86304e6 + 1.903104e6) / 16, "profiles/gram_pairs_df_2d_256x256_q32_batch16.md"),
-    "eig_gemm_AX": ((112.17536e6 + 3.384064e6) / 16, "profiles/tc2_ax_2d_256x256_q32_batch16.md"),
-    "interp_rows_tc": ((67.679488e6 + 207.202048e6) / 16, "profiles/tc2_interp_rows_2d_256x256_q32_batch16.md"),
+    "eig_gemm_AX": ((112.174848e6 + 3.561728e6) / 16, "profiles/tc2_ax_2d_256x256_q32_batch16.md"),
+    "interp_rows_tc": ((67.691264e6 + 207.474176e6) / 16, "profiles/tc2_interp_rows_2d_256x256_q32_batch16.md"),
 }
 
 
