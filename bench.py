@@ -219,7 +219,6 @@ def run_reference(args):
 # is reported as g times this); an op whose kernel changed since its capture has no entry
 NCU_TRAFFIC = {
     "power_iteration": ((553.688832e6 + 17.805056e6) / 16, "profiles/power_iteration_2d_256x256_q32_batch16.md"),
-    "gram_pairs_df": ((11.86304e6 + 1.903104e6) / 16, "profiles/gram_pairs_df_2d_256x256_q32_batch16.md"),
     "eig_gemm_AX": ((112.174848e6 + 3.561728e6) / 16, "profiles/tc2_ax_2d_256x256_q32_batch16.md"),
     "interp_rows_tc": ((67.691264e6 + 207.474176e6) / 16, "profiles/tc2_interp_rows_2d_256x256_q32_batch16.md"),
 }
@@ -324,11 +323,12 @@ def roofline_for(op, prof, w, stats, peaks, precision, tc_interp=False, nmaps=No
         Lp = w["calib"][0] + 2 * w["tau"]
         B = 4 * w["tau"] + 1
         npair = Q * (Q + 1) // 2
-        inst = npair * (60.0 * Lp * Lp + 48.0 * (Lp * B * Lp + B * B * Lp))
+        inst = npair * (60.0 * Lp * Lp + 24.0 * (Lp * B * Lp + B * B * Lp))
         return dict(bound="alu", achieved=inst * mpl / avg_s / 1e12, peak=inst_peak, unit="Tinst/s",
                     note="Gram pair stage fused per coil pair: the pair product (60 FP32 instructions per "
-                         "double-float complex multiply-add) and both inverse lag passes (Dot2 accumulation, "
-                         "48 per complex term); peak = 152 SMs x 128 FP32 lanes x 2070 MHz instructions/s")
+                         "double-float complex multiply-add) and both inverse lag passes (Dot2 accumulation; "
+                         "lags +d and -d share their cosine and sine sums: 24 per complex term and lag); "
+                         "peak = 152 SMs x 128 FP32 lanes x 2070 MHz instructions/s")
     if op == "g_field_sep":
         nr1, nr2 = w["grid"][0] // w["reduction"], w["grid"][1] // w["reduction"]
         B = 4 * w["tau"] + 1

@@ -155,10 +155,29 @@ __global__ void scatter_pairs_df_kernel(const dfc* __restrict__ Rp, int Q, int n
 
 // 2D pairs stage of the double-float Gram, fused per pair (p <= q): the frequency-domain product
 // conj(S_p) S_q, the inverse lag transform along the contiguous axis (Lp2 -> B2) and then along
-// axis 1 (Lp1 -> B1), all in shared memory, and the FP64 lag table of the pair.  Each output
-// accumulates its even and odd terms in two Dot2 sums (two independent dependency chains per
-// thread), normalised and added at the end.
-// invT2: [Lp2][B2] (transposed), inv1: [B1][Lp1].
+// axis 1 (Lp1 -> B1), all in shared memory, and the FP64 lag table of the pair.
+// Both inverse passes pair the lags +d and -d: with the table entry of lag d >= 0 at frequency f
+// equal to (c + i s) / Lp, c = cos(2 pi f d / Lp), s = sin(2 pi f d / Lp), and that of lag -d
+// equal to (c - i s) / Lp, the two outputs are C + i S and C - i S for C = sum_f c x_f and
+// S = sum_f s x_f (x_f complex).  A thread computes the four real Dot2 sums (Re and Im of C and
+// of S: four independent dependency chains) of one (row, d >= 0) and writes both lags: half the
+// products of evaluating every lag on its own.  (For d = 0 the sine column is exactly zero.)
+// invT2: [Lp2][B2] (transposed), inv1: [B1][Lp1]; B1, B2 odd (lags -2 tau .. 2 tau).
+__device__ __forceinline__ void dot2_lag_pair(dfc& cs, dfc& sn, const dfc& w, const dfc& x) {
+  dot2_term(cs.rh, cs.rl, w.rh, w.rl, x.rh, x.rl);
+  dot2_term(cs.ih, cs.il, w.rh, w.rl, x.ih, x.il);
+  dot2_term(sn.rh, sn.rl, w.ih, w.il, x.rh, x.rl);
+  dot2_term(sn.ih, sn.il, w.ih, w.il, x.ih, x.il);
+}
+// (C + i S, C - i S) from the finished sums
+__device__ __forceinline__ void lag_pair_outputs(const dfc& C, const dfc& Sx, dfc& plus, dfc& minus) {
+  plus = C;
+  minus = C;
+  df_add(plus.rh, plus.rl, -Sx.ih, -Sx.il);
+  df_add(plus.ih, plus.il, Sx.rh, Sx.rl);
+  df_add(minus.rh, minus.rl, Sx.ih, Sx.il);
+  df_add(minus.ih, minus.il, -Sx.rh, -Sx.rl);
+}
 __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __restrict__ S, int Q, int Lp1, int Lp2,
                                                                const dfc* __restrict__ invT2, int B2,
                                                                const dfc* __restrict__ inv1, int B1,
@@ -181,6 +200,7 @@ __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __rest
   const dfc* Sp = S + p * nfreq;
   const dfc* Sq = S + q * nfreq;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int c2 = B2 / 2, c1 = B1 / 2;  // table columns / rows of lag 0
   for (int i = tid; i < Lp2 * B2; i += nt) m2[i] = invT2[i];
   for (int i = tid; i < B1 * Lp1; i += nt) m1[i] = inv1[i];
   for (int f = tid; f < Lp1 * Lp2; f += nt) {
@@ -189,33 +209,33 @@ __global__ void __launch_bounds__(256) pairs_inverse_df_kernel(const dfc* __rest
     P[(f / Lp2) * ldp + f % Lp2] = acc;
   }
   __syncthreads();
-  for (int o = tid; o < Lp1 * B2; o += nt) {
-    const int f1 = o / B2, b2 = o % B2;
+  for (int o = tid; o < Lp1 * (c2 + 1); o += nt) {
+    const int f1 = o / (c2 + 1), d = o % (c2 + 1);
     const dfc* prow = P + f1 * ldp;
-    dfc a0{0.f, 0.f, 0.f, 0.f}, a1{0.f, 0.f, 0.f, 0.f};
-    int f2 = 0;
-    for (; f2 + 1 < Lp2; f2 += 2) {
-      dot2_cfma(a0, m2[f2 * B2 + b2], prow[f2]);
-      dot2_cfma(a1, m2[(f2 + 1) * B2 + b2], prow[f2 + 1]);
-    }
-    if (f2 < Lp2) dot2_cfma(a0, m2[f2 * B2 + b2], prow[f2]);
-    T[o] = df_cadd(dot2_finish(a0), dot2_finish(a1));
+    const dfc* wcol = m2 + c2 + d;
+    dfc cs{0.f, 0.f, 0.f, 0.f}, sn{0.f, 0.f, 0.f, 0.f};
+    for (int f2 = 0; f2 < Lp2; ++f2) dot2_lag_pair(cs, sn, wcol[f2 * B2], prow[f2]);
+    dfc plus, minus;
+    lag_pair_outputs(dot2_finish(cs), dot2_finish(sn), plus, minus);
+    T[f1 * B2 + c2 + d] = plus;
+    if (d > 0) T[f1 * B2 + c2 - d] = minus;
   }
   __syncthreads();
   const long long ob = ((long long)p * Q + q) * B1 * B2;
-  for (int o = tid; o < B1 * B2; o += nt) {
-    const int b1 = o / B2, b2 = o % B2;
-    const dfc* mrow = m1 + b1 * Lp1;
-    dfc a0{0.f, 0.f, 0.f, 0.f}, a1{0.f, 0.f, 0.f, 0.f};
-    int f1 = 0;
-    for (; f1 + 1 < Lp1; f1 += 2) {
-      dot2_cfma(a0, mrow[f1], T[f1 * B2 + b2]);
-      dot2_cfma(a1, mrow[f1 + 1], T[(f1 + 1) * B2 + b2]);
+  for (int o = tid; o < (c1 + 1) * B2; o += nt) {
+    const int d = o / B2, b2 = o % B2;
+    const dfc* mrow = m1 + (c1 + d) * Lp1;
+    dfc cs{0.f, 0.f, 0.f, 0.f}, sn{0.f, 0.f, 0.f, 0.f};
+    for (int f1 = 0; f1 < Lp1; ++f1) dot2_lag_pair(cs, sn, mrow[f1], T[f1 * B2 + b2]);
+    dfc plus, minus;
+    lag_pair_outputs(dot2_finish(cs), dot2_finish(sn), plus, minus);
+    const long long op = ob + (long long)(c1 + d) * B2 + b2, om = ob + (long long)(c1 - d) * B2 + b2;
+    lags[op] = make_double2((double)plus.rh + (double)plus.rl, (double)plus.ih + (double)plus.il);
+    lags_df[op] = plus;
+    if (d > 0) {
+      lags[om] = make_double2((double)minus.rh + (double)minus.rl, (double)minus.ih + (double)minus.il);
+      lags_df[om] = minus;
     }
-    if (f1 < Lp1) dot2_cfma(a0, mrow[f1], T[f1 * B2 + b2]);
-    const dfc acc = df_cadd(dot2_finish(a0), dot2_finish(a1));
-    lags[ob + o] = make_double2((double)acc.rh + (double)acc.rl, (double)acc.ih + (double)acc.il);
-    lags_df[ob + o] = acc;
   }
 }
 

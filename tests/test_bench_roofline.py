@@ -71,9 +71,9 @@ def test_fused_gram_pair_stage_counts():
     L, B = W["calib"][0] + 2 * t, 4 * t + 1
     npair = Q * (Q + 1) // 2
     # per pair: the frequency-domain product (double-float, 60 FP32 instructions per complex
-    # multiply-add), the contiguous-axis and axis-1 passes (Dot2 sums, 48 per complex term),
-    # against the FP32 issue rate
-    inst = npair * (60 * L * L + 48 * (L * L * B + B * B * L))
+    # multiply-add), the contiguous-axis and axis-1 passes (Dot2 sums; the lags +d and -d share
+    # their cosine and sine sums, 24 per complex term and lag), against the FP32 issue rate
+    inst = npair * (60 * L * L + 24 * (L * L * B + B * B * L))
     prof = {"gram_pairs_df": (1.0, 20)}
     r = bench.roofline_for("gram_pairs_df", prof, W, STATS, PEAKS, "tc_g_eig", True, 20)
     assert r["achieved"] == pytest.approx(inst / 0.05e-3 / 1e12, rel=1e-12)
