@@ -1,5 +1,5 @@
-// Dense complex GEMM on the tensor cores, fed by TMA: the pipelined form of the split-precision
-// contraction of kernels_tc.cu.
+// Dense complex GEMM on the tensor cores (tcgen05, TF32 with an FP32 accumulator in TMEM), fed by
+// TMA, in split precision.
 //
 //   C = alpha * A * op(B) + beta * C  (+ diag_val on columns c % diag_stride == 0, c < diag_limit)
 //
@@ -926,7 +926,7 @@ cudaError_t tc2_gemm(int nterms, int M, int N, int K, const float* Ahi, const fl
   const float* bl = nterms == 3 ? Blo : Bhi;
   const int kcols = K2 > 0 ? K2 : 1;
   const int arows = a_per_item && nbatch > 1 ? M * nbatch : M;
-  // A from FP32 complex rows, split in shared memory: three passes, rows 16-byte aligned
+  // A from FP32 complex rows, split on the way into tensor memory: three passes, rows 16-byte aligned
   const bool conv = a_fp32 != nullptr && nterms == 3 && (lda_fp32 % 2) == 0 && lda_fp32 >= K &&
                     ((uintptr_t)a_fp32 % 16) == 0;
   // the row-group epilogue keeps its scales and row offsets beside the tile: converting variants

@@ -72,7 +72,7 @@ struct pisco_plan_s {
   // tensor-core routes (PISCO_FLAG_TC_*): lags of Lambda-Lambda only (compressed CSR), the
   // lag-to-pixel exponentials E [npix_red][nlag] and the folded lag table KT [nlag][Q*Q]
   bool tc_g = false, tc_eig = false;
-  bool a_conv = false;  // A X on the tensor cores reads A32 and splits it in shared memory
+  bool a_conv = false;  // A X on the tensor cores reads A32 and splits it into tensor memory
   bool masked = false;                 // PISCO_FLAG_MASKED_GRAM
   bool block_pi = false;               // PISCO_FLAG_BLOCK_PI
   bool gram_df = false;                // PISCO_FLAG_GRAM_DF: double-float DFT tables below
@@ -692,7 +692,7 @@ cudaError_t ax_product(pisco_plan_s* pl, const float2* X, float2* Y, long long s
     cudaError_t e = tc2_split_b(X, m, 0, n, m, pl->Xh, pl->tc_terms == 3 ? pl->Xl : nullptr, pl->st, xi, sX);
     if (e != cudaSuccess) return e;
     // sX == 0: every item multiplies the same block (B' of item 0 for all); a_conv: A read as
-    // FP32 and split in shared memory
+    // FP32 and split into tensor memory
     return tc2_gemm(pl->tc_terms, n, m, n, pl->Ah, pl->Al, pl->Xh, pl->Xl, one, zero, Y, m, 0.f, 0, 0,
                     pl->tc_splits_ax, pl->tc_ws, &pl->dstatus->flags, pl->st, items, snm, 1, nullptr, 1,
                     sX != 0 ? 1 : 0, pl->a_conv ? pl->A32 : nullptr, n);
